@@ -1,0 +1,154 @@
+/*
+ * psolve -- spectral-multigrid Poisson solver for one GPU (C ABI).
+ *
+ * Computes the gravitational potential Phi of a density rho on a spherical
+ * (r, theta, phi) or cylindrical (R, z, phi) grid with vacuum boundary
+ * conditions, following Mandal, Gressel, Ziegler & Mignone, "A fast
+ * spectral-multigrid Poisson solver in non-Cartesian geometries":
+ *   Sec. 2.1   finite-volume Laplacian (Eq. poisson_discrete),
+ *   Sec. 2.2   azimuthal Fourier decomposition into 2-D Helmholtz problems
+ *              (Eqs. helmholz_sph, helmholz_cyl, eigenv_sph, eigenv_cyl),
+ *   Sec. 3     multigrid with the alternating approximate line smoother,
+ *   Sec. 4     James' screening-mass vacuum boundary conditions with
+ *              discrete Green's functions,
+ *   Sec. 5.1   the seven-step workflow (density in, potential out).
+ *
+ * Data layout of every 3-D field passed to the library: FP64, row-major
+ * [n_r][n_tz][n_phi] (azimuth fastest), values at cell centres.
+ * Mode planes (stage entry points): FP64 complex (re, im interleaved),
+ * [M][n_tz][n_r] with M = n_phi/2 + 1 and the radial index fastest.
+ *
+ * Pointers are DEVICE pointers unless a name ends in _host.  All work is
+ * enqueued on the handle's stream; functions that report a status read it
+ * back with a synchronisation of that stream.  Handles are not thread-safe.
+ * Errors are return codes (never an abort); psolve_last_error() gives the
+ * message of the last failing call on the calling thread.
+ */
+#ifndef PSOLVE_H
+#define PSOLVE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psolve_ctx* psolve_t;
+
+enum { PSOLVE_SPHERICAL = 0, PSOLVE_CYLINDRICAL = 1 };
+enum { PSOLVE_UNIFORM = 0, PSOLVE_LOG = 1 };
+enum { PSOLVE_FP64 = 0, PSOLVE_MIXED = 1 };
+enum {
+  PSOLVE_OK = 0,
+  PSOLVE_ERR_ARG = -1,           /* invalid argument or unsupported grid        */
+  PSOLVE_ERR_CUDA = -2,          /* a CUDA call failed                          */
+  PSOLVE_ERR_NOMEM = -3,         /* device allocation failed                    */
+  PSOLVE_ERR_NOT_CONVERGED = -4, /* max_cycles reached or stagnation above tol  */
+  PSOLVE_ERR_NONFINITE = -5      /* NaN / Inf in a residual norm                */
+};
+
+/* Allocation hooks: when set, every device workspace of a handle is obtained
+ * from alloc(bytes, user) and returned with free(ptr, user); otherwise
+ * cudaMalloc / cudaFree are used.  alloc returns NULL on failure. */
+typedef void* (*psolve_alloc_fn)(size_t bytes, void* user);
+typedef void (*psolve_free_fn)(void* ptr, void* user);
+
+typedef struct {
+  int geometry;        /* PSOLVE_SPHERICAL or PSOLVE_CYLINDRICAL                  */
+  int n_r;             /* radial cells, power of two >= 8                         */
+  int n_tz;            /* theta (spherical) or z (cylindrical) cells, power of 2 >= 8 */
+  int n_phi;           /* azimuthal cells, power of two, 4 <= n_phi <= 1024       */
+  int spacing;         /* radial spacing PSOLVE_UNIFORM or PSOLVE_LOG             */
+  double r_in, r_out;  /* radial extent, 0 <= r_in < r_out (log: r_in > 0)        */
+  double t_min, t_max; /* theta range (spherical, default 0, pi) or z range
+                          (cylindrical, default -(r_out-r_in)/2 .. +...);
+                          used only when t_max > t_min                            */
+  double G;            /* gravitational constant; 0 selects 1                     */
+  int precision;       /* PSOLVE_FP64 or PSOLVE_MIXED                             */
+  int max_cycles;      /* V-cycle cap per mode and solve; 0 selects 100           */
+  int nu_pre, nu_post; /* smoothing cycles before / after coarse correction; 0 -> 2 */
+  int n_sor;           /* SOR sweeps per line relaxation; 0 -> 2                  */
+  int use_graph;       /* 1: replay the solve as a captured CUDA graph            */
+  psolve_alloc_fn alloc_fn; /* optional allocation hooks (see above)            */
+  psolve_free_fn free_fn;
+  void* alloc_user;
+} psolve_desc;
+
+/* Per-solve statistics (psolve_get_stats).  Arrays sized by the caller:
+ * cycles_psi / cycles_phi / status hold M entries when non-NULL. */
+typedef struct {
+  int n_modes;              /* M = n_phi/2 + 1                                   */
+  int iterations_psi;       /* outer iterations of the Psi solve (max over modes) */
+  int iterations_phi;       /* same for the Phi solve                            */
+  double rel_residual_psi;  /* sqrt(sum_m |r^m|^2 / sum_m |f^m|^2), volume-weighted */
+  double rel_residual_phi;
+  double setup_ms;          /* psolve_create wall time (incl. DGF tables)        */
+  int* cycles_psi;          /* per-mode V-cycles, Psi solve (may be NULL)        */
+  int* cycles_phi;          /* per-mode V-cycles, Phi solve (may be NULL)        */
+  int* status;              /* per-mode PSOLVE_OK / NOT_CONVERGED / NONFINITE    */
+} psolve_stats;
+
+/* Plan a solver (Sec. 5.1 step 1): geometry and operator tables per
+ * multigrid level, per-line relaxation parameters (App. A), coarsest-level
+ * factors, discrete Green's function tables (Sec. 4.2) and workspaces.
+ * Uses the current device and the legacy default stream until
+ * psolve_set_stream.  Returns PSOLVE_OK and *out, or an error (*out NULL). */
+int psolve_create(psolve_t* out, int geometry, int n_r, int n_theta_or_z, int n_phi,
+                  int radial_spacing, double r_in, double r_out);
+/* Same with every option; fields left zero take their defaults. */
+int psolve_create_ex(psolve_t* out, const psolve_desc* d);
+
+/* Solve (Sec. 5.1 steps 2-7): rho [n_r][n_tz][n_phi] -> phi (same layout),
+ * device pointers, phi must not alias rho.  tol is the relative residual of
+ * each mode's Helmholtz problem in the volume-weighted L2 norm (App. B),
+ * tol <= 0 selects 1e-8.  Returns PSOLVE_OK, PSOLVE_ERR_NOT_CONVERGED (phi
+ * holds the last iterate) or another error. */
+int psolve_solve(psolve_t h, const double* rho, double* phi, double tol);
+
+/* n independent solves (handles may differ in size and kind), enqueued on
+ * each handle's own stream; the same return convention, first error wins. */
+int psolve_solve_batched(psolve_t* hs, const double* const* rhos, double* const* phis, int n,
+                         double tol);
+
+int psolve_set_stream(psolve_t h, void* cuda_stream);
+int psolve_get_stats(psolve_t h, psolve_stats* st);
+/* Number of boundary points nb (the side of the DGF table) and modes M. */
+int psolve_get_sizes(psolve_t h, int* n_modes, int* n_boundary, int* n_levels);
+const char* psolve_last_error(void);
+void psolve_destroy(psolve_t h);
+
+/* ---- stage entry points (each runs one step of the solve on all modes) ---- */
+
+/* Sec. 2.2: rho_hat[m][j][i] = (4 pi G / n_phi) sum_k rho[i][j][k] e^{-2 pi i m k / n_phi},
+ * i.e. the right-hand side 4 pi G rho^m of the mode equations. */
+int psolve_stage_forward(psolve_t h, const double* rho, double* f_hat);
+/* Sec. 2.2, Eq. Hermitian_symmetry: phi[i][j][k] = Re sum over all n_phi modes
+ * with the upper half rebuilt as conjugates; imaginary parts of m = 0 and
+ * m = n_phi/2 ignored. */
+int psolve_stage_inverse(psolve_t h, const double* phi_hat, double* phi);
+/* Sec. 3: solve L_m u = f for every mode with zero ghost values, by the
+ * handle's precision mode; f_hat, u_hat as mode planes; u_hat is the initial
+ * guess on entry when warm != 0.  cycles_host (M ints, may be NULL) receives
+ * the V-cycles per mode. */
+int psolve_stage_mg_solve(psolve_t h, const double* f_hat, double* u_hat, double tol, int warm,
+                          int* cycles_host);
+/* Sec. 3.2 / 3.1 single steps at multigrid level `level` (0 = finest), in
+ * FP64 (precision 0) or FP32 (1) planes [M][n_tz_l][n_r_l] complex:
+ *   smooth:   `cycles` alternating line-smoothing cycles on e with rhs f;
+ *   restrict: coarse = R (f - L e), the area-weighted restriction of the defect;
+ *   prolong:  e += P coarse, bilinear prolongation from level+1. */
+int psolve_stage_smooth(psolve_t h, int level, int precision, void* e, const void* f, int cycles);
+int psolve_stage_restrict(psolve_t h, int level, int precision, const void* e, const void* f,
+                          void* coarse);
+int psolve_stage_prolong(psolve_t h, int level, int precision, void* e, const void* coarse);
+/* Eqs. charge_sph / charge_cyl: sigma[m][b] (complex) from psi_hat. */
+int psolve_stage_screening(psolve_t h, const double* psi_hat, double* sigma);
+/* Eqs. theta_left..theta_top: theta[m][t] = sum_s Gt[m][t][s] sigma[m][s]. */
+int psolve_stage_boundary(psolve_t h, const double* sigma, double* theta);
+/* Copy the DGF table Gt[m][t][s] (FP64, M * nb * nb) to device memory dst. */
+int psolve_get_dgf(psolve_t h, double* dst);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,261 @@
+"""psolve: spectral-multigrid self-gravity solver for one GPU.
+
+Thin ctypes binding of the C ABI in ``include/psolve.h`` (same function
+names).  Argument marshalling only: every step of a solve runs in the CUDA
+kernels of ``_build/libpsolve.so``.  PyTorch provides device memory (the
+library's workspaces come from the torch caching allocator through the
+allocation hooks of ``psolve_desc``) and the CUDA stream.  There is no CPU
+path: without the built library every call raises.
+"""
+import ctypes
+import os
+
+SPHERICAL, CYLINDRICAL = 0, 1
+UNIFORM, LOG = 0, 1
+FP64, MIXED = 0, 1
+OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NOT_CONVERGED, ERR_NONFINITE = 0, -1, -2, -3, -4, -5
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpsolve.so")
+_lib = None
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_int), ("n_r", ctypes.c_int), ("n_tz", ctypes.c_int),
+                ("n_phi", ctypes.c_int), ("spacing", ctypes.c_int), ("r_in", ctypes.c_double),
+                ("r_out", ctypes.c_double), ("t_min", ctypes.c_double), ("t_max", ctypes.c_double),
+                ("G", ctypes.c_double), ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
+                ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("n_sor", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("alloc_fn", ALLOC_FN), ("free_fn", FREE_FN),
+                ("alloc_user", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_modes", ctypes.c_int), ("iterations_psi", ctypes.c_int),
+                ("iterations_phi", ctypes.c_int), ("rel_residual_psi", ctypes.c_double),
+                ("rel_residual_phi", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("cycles_psi", ctypes.POINTER(ctypes.c_int)),
+                ("cycles_phi", ctypes.POINTER(ctypes.c_int)),
+                ("status", ctypes.POINTER(ctypes.c_int))]
+
+
+def lib():
+    """The loaded library; raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpsolve.so is not built (run __graft_entry__.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+        sig = {
+            "psolve_create": (I, [ctypes.POINTER(P), I, I, I, I, I, D, D]),
+            "psolve_create_ex": (I, [ctypes.POINTER(P), ctypes.POINTER(Desc)]),
+            "psolve_solve": (I, [P, P, P, D]),
+            "psolve_solve_batched": (I, [P, P, P, I, D]),
+            "psolve_set_stream": (I, [P, P]),
+            "psolve_get_stats": (I, [P, ctypes.POINTER(Stats)]),
+            "psolve_get_sizes": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "psolve_last_error": (ctypes.c_char_p, []),
+            "psolve_destroy": (V, [P]),
+            "psolve_stage_forward": (I, [P, P, P]),
+            "psolve_stage_inverse": (I, [P, P, P]),
+            "psolve_stage_mg_solve": (I, [P, P, P, D, I, ctypes.POINTER(I)]),
+            "psolve_stage_smooth": (I, [P, I, I, P, P, I]),
+            "psolve_stage_restrict": (I, [P, I, I, P, P, P]),
+            "psolve_stage_prolong": (I, [P, I, I, P, P]),
+            "psolve_stage_screening": (I, [P, P, P]),
+            "psolve_stage_boundary": (I, [P, P, P]),
+            "psolve_get_dgf": (I, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error():
+    return lib().psolve_last_error().decode()
+
+
+def check(rc, what):
+    if rc != OK:
+        raise PSolveError(rc, "%s failed (%d): %s" % (what, rc, last_error()))
+    return rc
+
+
+class PSolveError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(msg)
+        self.code = code
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _TorchAllocator:
+    """Allocation hooks that take the library's workspaces from torch."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.live = {}
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, user):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device="cuda")
+        except Exception:
+            return None
+        self.live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(self, ptr, user):
+        self.live.pop(ptr, None)
+
+
+class Solver:
+    """One planned solver (psolve_create_ex) bound to torch's current stream."""
+
+    def __init__(self, geometry, n_r, n_tz, n_phi, spacing, r_in, r_out, t_min=None, t_max=None,
+                 G=1.0, precision=MIXED, max_cycles=0, nu_pre=0, nu_post=0, n_sor=0,
+                 use_graph=True, torch_alloc=True):
+        import torch
+        self.torch = torch
+        L = lib()
+        d = Desc()
+        d.geometry, d.n_r, d.n_tz, d.n_phi, d.spacing = geometry, n_r, n_tz, n_phi, spacing
+        d.r_in, d.r_out = r_in, r_out
+        d.t_min = 0.0 if t_min is None else t_min
+        d.t_max = 0.0 if t_max is None else t_max
+        d.G, d.precision, d.max_cycles = G, precision, max_cycles
+        d.nu_pre, d.nu_post, d.n_sor, d.use_graph = nu_pre, nu_post, n_sor, int(bool(use_graph))
+        self._alloc = _TorchAllocator() if torch_alloc else None
+        if self._alloc is not None:
+            d.alloc_fn, d.free_fn = self._alloc.alloc, self._alloc.free
+        self.desc = d
+        self.shape = (n_r, n_tz, n_phi)
+        h = ctypes.c_void_p()
+        check(L.psolve_create_ex(ctypes.byref(h), ctypes.byref(d)), "psolve_create_ex")
+        self.h = h
+        check(L.psolve_set_stream(h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+              "psolve_set_stream")
+        M, nb, nl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(L.psolve_get_sizes(h, ctypes.byref(M), ctypes.byref(nb), ctypes.byref(nl)),
+              "psolve_get_sizes")
+        self.n_modes, self.n_boundary, self.n_levels = M.value, nb.value, nl.value
+
+    @classmethod
+    def from_spec(cls, spec, **kw):
+        return cls(spec["geometry"], spec["n_r"], spec["n_tz"], spec["n_phi"], spec["spacing"],
+                   spec["r_in"], spec["r_out"], spec.get("t_min"), spec.get("t_max"), **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().psolve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- solve ---------------------------------------------------------------
+    def _need(self, t, shape, dtype):
+        torch = self.torch
+        if not (t.is_cuda and t.dtype == dtype and tuple(t.shape) == tuple(shape) and t.is_contiguous()):
+            raise ValueError("expected a contiguous CUDA %s tensor of shape %s" % (dtype, shape))
+
+    def solve(self, rho, phi=None, tol=1e-8, raise_on_error=True):
+        torch = self.torch
+        self._need(rho, self.shape, torch.float64)
+        if phi is None:
+            phi = torch.empty_like(rho)
+        rc = lib().psolve_solve(self.h, _ptr(rho), _ptr(phi), float(tol))
+        if raise_on_error:
+            check(rc, "psolve_solve")
+        return phi, rc
+
+    def stats(self):
+        M = self.n_modes
+        cp = (ctypes.c_int * M)()
+        cf = (ctypes.c_int * M)()
+        stv = (ctypes.c_int * M)()
+        s = Stats()
+        s.cycles_psi = ctypes.cast(cp, ctypes.POINTER(ctypes.c_int))
+        s.cycles_phi = ctypes.cast(cf, ctypes.POINTER(ctypes.c_int))
+        s.status = ctypes.cast(stv, ctypes.POINTER(ctypes.c_int))
+        check(lib().psolve_get_stats(self.h, ctypes.byref(s)), "psolve_get_stats")
+        return dict(n_modes=s.n_modes, iterations_psi=s.iterations_psi,
+                    iterations_phi=s.iterations_phi, rel_residual_psi=s.rel_residual_psi,
+                    rel_residual_phi=s.rel_residual_phi, setup_ms=s.setup_ms,
+                    cycles_psi=list(cp), cycles_phi=list(cf), status=list(stv))
+
+    # -- stages ----------------------------------------------------------------
+    def planes(self, level=0, dtype=None):
+        """Empty complex planes [M, n_tz_l, n_r_l] of a multigrid level."""
+        torch = self.torch
+        n_r, n_tz = self.shape[0] >> level, self.shape[1] >> level
+        dtype = dtype or torch.complex128
+        return torch.zeros((self.n_modes, n_tz, n_r), dtype=dtype, device="cuda")
+
+    def stage_forward(self, rho):
+        f = self.planes()
+        check(lib().psolve_stage_forward(self.h, _ptr(rho), _ptr(f)), "psolve_stage_forward")
+        return f
+
+    def stage_inverse(self, phi_hat):
+        phi = self.torch.empty(self.shape, dtype=self.torch.float64, device="cuda")
+        check(lib().psolve_stage_inverse(self.h, _ptr(phi_hat), _ptr(phi)), "psolve_stage_inverse")
+        return phi
+
+    def stage_mg_solve(self, f_hat, tol=1e-8, u0=None):
+        u = self.planes() if u0 is None else u0.clone()
+        cyc = (ctypes.c_int * self.n_modes)()
+        rc = lib().psolve_stage_mg_solve(self.h, _ptr(f_hat), _ptr(u), float(tol),
+                                         int(u0 is not None), cyc)
+        return u, list(cyc), rc
+
+    def stage_smooth(self, level, e, f, cycles=1):
+        prec = 1 if self.desc.precision == MIXED else 0
+        check(lib().psolve_stage_smooth(self.h, level, prec, _ptr(e), _ptr(f), cycles),
+              "psolve_stage_smooth")
+        return e
+
+    def stage_restrict(self, level, e, f):
+        prec = 1 if self.desc.precision == MIXED else 0
+        c = self.planes(level + 1, e.dtype)
+        check(lib().psolve_stage_restrict(self.h, level, prec, _ptr(e), _ptr(f), _ptr(c)),
+              "psolve_stage_restrict")
+        return c
+
+    def stage_prolong(self, level, e, coarse):
+        prec = 1 if self.desc.precision == MIXED else 0
+        check(lib().psolve_stage_prolong(self.h, level, prec, _ptr(e), _ptr(coarse)),
+              "psolve_stage_prolong")
+        return e
+
+    def stage_screening(self, psi_hat):
+        s = self.torch.zeros((self.n_modes, self.n_boundary), dtype=self.torch.complex128,
+                             device="cuda")
+        check(lib().psolve_stage_screening(self.h, _ptr(psi_hat), _ptr(s)), "psolve_stage_screening")
+        return s
+
+    def stage_boundary(self, sigma):
+        t = self.torch.zeros_like(sigma)
+        check(lib().psolve_stage_boundary(self.h, _ptr(sigma), _ptr(t)), "psolve_stage_boundary")
+        return t
+
+    def dgf(self):
+        g = self.torch.zeros((self.n_modes, self.n_boundary, self.n_boundary),
+                             dtype=self.torch.float64, device="cuda")
+        check(lib().psolve_get_dgf(self.h, _ptr(g)), "psolve_get_dgf")
+        return g

@@ -1,0 +1,588 @@
+// C ABI of the solver (include/psolve.h): plan creation, the seven-step
+// solve (Sec. 5.1) as eager launches or one captured CUDA graph with a
+// WHILE node per multigrid solve, stage entry points and statistics.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/psolve.h"
+#include "dgf.h"
+#include "solver.h"
+
+using namespace ps;
+
+static thread_local std::string g_err;
+static const double kPi = 3.14159265358979323846;
+
+struct SolveStats {
+  int* cycles = nullptr;
+  int* status = nullptr;
+  double2* nf2 = nullptr;
+  double2* nr2 = nullptr;
+  int* iter = nullptr;
+};
+
+struct psolve_ctx {
+  Arena A;
+  psolve_desc d{};
+  PlaneGeo g;
+  Law rlaw, tlaw;
+  int M = 0, nb = 0, construction = -1;
+  MGSolver mg;
+  std::vector<BPoint> bp;
+  BDev bdev{};
+  double* gt = nullptr;
+  double2* tw = nullptr;
+  double2 *u = nullptr, *f = nullptr, *sigma = nullptr, *theta = nullptr;
+  SolveStats sp, sf;
+  int* d_worst = nullptr;
+  int* h_worst = nullptr;
+  cudaStream_t st = 0;
+  double setup_ms = 0;
+  // captured solve
+  cudaGraphExec_t gexec = nullptr;
+  const double* g_rho = nullptr;
+  double* g_phi = nullptr;
+  double g_tol = -1;
+};
+
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+static bool cuda_ok(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return false;
+  }
+  return true;
+}
+
+static bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// worst status over both solves -> d_worst
+__global__ void k_worst(const int* a, const int* b, int n, int* out) {
+  int w = 0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    int s1 = a[k], s2 = b[k];
+    if (s1 == -5 || s2 == -5) w = min(w, -5);
+    else if (s1 == -4 || s2 == -4 || s1 == 2 || s2 == 2 || s1 == 1 || s2 == 1) w = min(w, -4);
+  }
+  for (int o = 16; o > 0; o >>= 1) w = min(w, __shfl_down_sync(0xffffffffu, w, o));
+  __shared__ int sw[32];
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int r = 0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) r = min(r, sw[i]);
+    *out = r;
+  }
+}
+
+static void snapshot(psolve_ctx* h, SolveStats& s) {
+  const int M = h->M;
+  cudaMemcpyAsync(s.cycles, h->mg.d_cycles, sizeof(int) * M, cudaMemcpyDeviceToDevice, h->st);
+  cudaMemcpyAsync(s.status, h->mg.d_status, sizeof(int) * M, cudaMemcpyDeviceToDevice, h->st);
+  cudaMemcpyAsync(s.nf2, h->mg.d_nf2, sizeof(double2) * M, cudaMemcpyDeviceToDevice, h->st);
+  cudaMemcpyAsync(s.nr2, h->mg.d_nr2, sizeof(double2) * M, cudaMemcpyDeviceToDevice, h->st);
+  cudaMemcpyAsync(s.iter, h->mg.d_iter, sizeof(int), cudaMemcpyDeviceToDevice, h->st);
+}
+
+static int create_impl(psolve_t* out, const psolve_desc* din) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!out || !din) return fail(PSOLVE_ERR_ARG, "null argument");
+  *out = nullptr;
+  psolve_desc d = *din;
+  if (d.geometry != PSOLVE_SPHERICAL && d.geometry != PSOLVE_CYLINDRICAL)
+    return fail(PSOLVE_ERR_ARG, "geometry must be PSOLVE_SPHERICAL or PSOLVE_CYLINDRICAL");
+  if (!pow2(d.n_r) || !pow2(d.n_tz) || d.n_r < 8 || d.n_tz < 8 || d.n_r > 1024 || d.n_tz > 1024)
+    return fail(PSOLVE_ERR_ARG, "n_r and n_tz must be powers of two in [8, 1024]");
+  if (d.n_r / d.n_tz > 16 || d.n_tz / d.n_r > 16)
+    return fail(PSOLVE_ERR_ARG, "n_r / n_tz must lie within [1/16, 16]");
+  if (!pow2(d.n_phi) || d.n_phi < 4 || d.n_phi > 1024)
+    return fail(PSOLVE_ERR_ARG, "n_phi must be a power of two in [4, 1024]");
+  if (d.spacing != PSOLVE_UNIFORM && d.spacing != PSOLVE_LOG)
+    return fail(PSOLVE_ERR_ARG, "radial spacing must be PSOLVE_UNIFORM or PSOLVE_LOG");
+  if (!(d.r_in >= 0.0) || !(d.r_out > d.r_in) || (d.spacing == PSOLVE_LOG && !(d.r_in > 0.0)))
+    return fail(PSOLVE_ERR_ARG, "need 0 <= r_in < r_out (r_in > 0 for logarithmic spacing)");
+  if (!(d.t_max > d.t_min)) {
+    if (d.geometry == PSOLVE_SPHERICAL) { d.t_min = 0.0; d.t_max = kPi; }
+    else { d.t_min = -0.5 * (d.r_out - d.r_in); d.t_max = 0.5 * (d.r_out - d.r_in); }
+  }
+  if (d.geometry == PSOLVE_SPHERICAL && (d.t_min < -1e-12 || d.t_max > kPi + 1e-12))
+    return fail(PSOLVE_ERR_ARG, "theta range must lie within [0, pi]");
+  if (d.G == 0.0) d.G = 1.0;
+  if (d.max_cycles <= 0) d.max_cycles = 100;
+  if (d.nu_pre <= 0) d.nu_pre = 2;
+  if (d.nu_post < 0) d.nu_post = 2;
+  if (d.nu_post == 0) d.nu_post = 2;
+  if (d.n_sor <= 0) d.n_sor = 2;
+  if (d.precision != PSOLVE_FP64 && d.precision != PSOLVE_MIXED)
+    return fail(PSOLVE_ERR_ARG, "precision must be PSOLVE_FP64 or PSOLVE_MIXED");
+
+  std::unique_ptr<psolve_ctx> h(new psolve_ctx());
+  h->d = d;
+  h->A.alloc_fn = d.alloc_fn;
+  h->A.free_fn = d.free_fn;
+  h->A.user = d.alloc_user;
+  const int geo = d.geometry == PSOLVE_SPHERICAL ? SPH : CYL;
+  h->rlaw = Law{d.r_in, d.r_out, d.n_r, d.spacing == PSOLVE_LOG ? LOGS : UNI};
+  h->tlaw = Law{d.t_min, d.t_max, d.n_tz, UNI};
+  h->g.geometry = geo;
+  h->g.n_phi = d.n_phi;
+  h->g.G = d.G;
+  h->g.r = axis_from_law(geo == SPH ? 0 : 1, h->rlaw, 1, d.n_r);
+  h->g.t = axis_from_law(geo == SPH ? 2 : 3, h->tlaw, 1, d.n_tz);
+  h->g.build();
+  h->M = d.n_phi / 2 + 1;
+  const int M = h->M;
+  const size_t plane = size_t(d.n_r) * d.n_tz;
+  std::string err;
+  std::vector<int> modes(M);
+  for (int m = 0; m < M; ++m) modes[m] = m;
+  MGOptions o;
+  o.precision = d.precision;
+  o.nu1 = d.nu_pre;
+  o.nu2 = d.nu_post;
+  o.n_sor = d.n_sor;
+  o.max_cycles = d.max_cycles;
+  if (!h->mg.init(h->A, h->g, false, modes, {}, M, o, err)) {
+    h->A.release_all();
+    return fail(PSOLVE_ERR_NOMEM, "multigrid setup: " + err);
+  }
+  h->u = static_cast<double2*>(h->A.get(sizeof(double2) * plane * M));
+  h->f = static_cast<double2*>(h->A.get(sizeof(double2) * plane * M));
+  // twiddles e^{-2 pi i k / N}
+  std::vector<double2> tw(d.n_phi / 2);
+  for (int k = 0; k < d.n_phi / 2; ++k)
+    tw[k] = make_double2(std::cos(2.0 * kPi * k / d.n_phi), -std::sin(2.0 * kPi * k / d.n_phi));
+  h->tw = static_cast<double2*>(h->A.get(sizeof(double2) * tw.size()));
+  // boundary points, screening and coupling coefficients
+  h->bp = boundary_points(h->g);
+  h->nb = int(h->bp.size());
+  const int nb = h->nb;
+  std::vector<int> adj(nb);
+  std::vector<double> sig(nb), cpl(nb);
+  std::vector<int> cells, cbp;
+  std::vector<int> slot_of_cell(plane, -1);
+  for (int b = 0; b < nb; ++b) {
+    adj[b] = (h->bp[b].aj - 1) * d.n_r + (h->bp[b].ai - 1);
+    sig[b] = h->bp[b].sigma_coef;
+    cpl[b] = h->bp[b].couple;
+    int& sc = slot_of_cell[adj[b]];
+    if (sc < 0) {
+      sc = int(cells.size());
+      cells.push_back(adj[b]);
+      cbp.push_back(b);
+      cbp.push_back(-1);
+    } else {
+      cbp[2 * sc + 1] = b;
+    }
+  }
+  auto up_i = [&](const std::vector<int>& v) {
+    int* p = static_cast<int*>(h->A.get(sizeof(int) * std::max<size_t>(1, v.size())));
+    if (p) cudaMemcpy(p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice);
+    return p;
+  };
+  auto up_d = [&](const std::vector<double>& v) {
+    double* p = static_cast<double*>(h->A.get(sizeof(double) * std::max<size_t>(1, v.size())));
+    if (p) cudaMemcpy(p, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice);
+    return p;
+  };
+  h->bdev.nb = nb;
+  h->bdev.ncell = int(cells.size());
+  h->bdev.adj = up_i(adj);
+  h->bdev.sig = up_d(sig);
+  h->bdev.cpl = up_d(cpl);
+  h->bdev.cell = up_i(cells);
+  h->bdev.cbp = up_i(cbp);
+  h->bdev.plane_cells = int(plane);
+  h->sigma = static_cast<double2*>(h->A.get(sizeof(double2) * size_t(M) * std::max(nb, 1)));
+  h->theta = static_cast<double2*>(h->A.get(sizeof(double2) * size_t(M) * std::max(nb, 1)));
+  h->gt = static_cast<double*>(h->A.get(sizeof(double) * size_t(M) * nb * nb));
+  for (SolveStats* s : {&h->sp, &h->sf}) {
+    s->cycles = static_cast<int*>(h->A.get(sizeof(int) * M));
+    s->status = static_cast<int*>(h->A.get(sizeof(int) * M));
+    s->nf2 = static_cast<double2*>(h->A.get(sizeof(double2) * M));
+    s->nr2 = static_cast<double2*>(h->A.get(sizeof(double2) * M));
+    s->iter = static_cast<int*>(h->A.get(sizeof(int)));
+  }
+  h->d_worst = static_cast<int*>(h->A.get(sizeof(int)));
+  if (!h->u || !h->f || !h->tw || !h->gt || !h->theta || !h->d_worst || !h->sf.iter) {
+    h->A.release_all();
+    return fail(PSOLVE_ERR_NOMEM, "out of device memory");
+  }
+  cudaMemcpy(h->tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice);
+  cudaMallocHost(&h->h_worst, sizeof(int));
+  // discrete Green's function tables (Sec. 5.1 step 1), scratch released after
+  {
+    Arena scratch;
+    scratch.alloc_fn = d.alloc_fn;
+    scratch.free_fn = d.free_fn;
+    scratch.user = d.alloc_user;
+    bool ok = build_dgf(h->g, h->rlaw, h->tlaw, h->bp, h->gt, scratch, h->st, h->construction, err);
+    cudaDeviceSynchronize();
+    scratch.release_all();
+    if (!ok) {
+      h->A.release_all();
+      return fail(err.find("memory") != std::string::npos ? PSOLVE_ERR_NOMEM : PSOLVE_ERR_ARG,
+                  "DGF: " + err);
+    }
+  }
+  if (!cuda_ok("create")) {
+    h->A.release_all();
+    return PSOLVE_ERR_CUDA;
+  }
+  h->setup_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = h.release();
+  return PSOLVE_OK;
+}
+
+extern "C" int psolve_create_ex(psolve_t* out, const psolve_desc* d) {
+  try {
+    return create_impl(out, d);
+  } catch (const std::exception& e) {
+    return fail(PSOLVE_ERR_NOMEM, std::string("create: ") + e.what());
+  }
+}
+
+extern "C" int psolve_create(psolve_t* out, int geometry, int n_r, int n_tz, int n_phi,
+                             int spacing, double r_in, double r_out) {
+  psolve_desc d{};
+  d.geometry = geometry; d.n_r = n_r; d.n_tz = n_tz; d.n_phi = n_phi; d.spacing = spacing;
+  d.r_in = r_in; d.r_out = r_out; d.precision = PSOLVE_MIXED; d.use_graph = 1;
+  return psolve_create_ex(out, &d);
+}
+
+extern "C" void psolve_destroy(psolve_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->mg.h_cont) cudaFreeHost(h->mg.h_cont);
+  if (h->h_worst) cudaFreeHost(h->h_worst);
+  h->A.release_all();
+  delete h;
+}
+
+extern "C" int psolve_set_stream(psolve_t h, void* s) {
+  if (!h) return fail(PSOLVE_ERR_ARG, "null handle");
+  h->st = static_cast<cudaStream_t>(s);
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  return PSOLVE_OK;
+}
+
+extern "C" const char* psolve_last_error(void) { return g_err.c_str(); }
+
+extern "C" int psolve_get_sizes(psolve_t h, int* n_modes, int* n_boundary, int* n_levels) {
+  if (!h) return fail(PSOLVE_ERR_ARG, "null handle");
+  if (n_modes) *n_modes = h->M;
+  if (n_boundary) *n_boundary = h->nb;
+  if (n_levels) *n_levels = int(h->mg.lv.size());
+  return PSOLVE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the solve (Sec. 5.1 steps 2-7)
+// ---------------------------------------------------------------------------
+static void enqueue_front(psolve_t h, const double* rho) {
+  launch_fft_forward(rho, h->f, h->d.n_r, h->d.n_tz, h->d.n_phi, 4.0 * kPi * h->d.G / h->d.n_phi,
+                     h->tw, h->st);
+  cudaMemsetAsync(h->u, 0, sizeof(double2) * size_t(h->M) * h->d.n_r * h->d.n_tz, h->st);
+  h->mg.init_loop(h->st);
+}
+
+static void enqueue_middle(psolve_t h) {
+  snapshot(h, h->sp);
+  launch_screening(h->bdev, h->u, h->sigma, h->M, h->st);
+  launch_boundary_potential(h->gt, h->sigma, h->theta, h->M, h->nb, h->st);
+  launch_rhs_ghosts(h->bdev, h->f, h->theta, h->M, h->st);
+  h->mg.init_loop(h->st);
+}
+
+static void enqueue_back(psolve_t h, double* phi) {
+  snapshot(h, h->sf);
+  launch_fft_inverse(h->u, phi, h->d.n_r, h->d.n_tz, h->d.n_phi, h->tw, h->st);
+  k_worst<<<1, 256, 0, h->st>>>(h->sp.status, h->sf.status, h->M, h->d_worst);
+  cudaMemcpyAsync(h->h_worst, h->d_worst, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+}
+
+static int add_while(psolve_t h, cudaGraph_t graph, double tol, cudaStream_t body_st) {
+  cudaGraphConditionalHandle cond;
+  if (cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+    return -1;
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraph_t cg;
+  if (cudaStreamGetCaptureInfo(h->st, &cs, nullptr, &cg, &deps, nullptr, &ndeps) != cudaSuccess)
+    return -1;
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = cond;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &p) != cudaSuccess) return -1;
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  if (cudaStreamUpdateCaptureDependencies(h->st, &node, nullptr, 1,
+                                          cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return -1;
+  if (cudaStreamBeginCaptureToGraph(body_st, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return -1;
+  h->mg.loop_body(h->f, h->u, tol, body_st, 1, cond);
+  cudaGraph_t out;
+  if (cudaStreamEndCapture(body_st, &out) != cudaSuccess) return -1;
+  return 0;
+}
+
+static int capture(psolve_t h, const double* rho, double* phi, double tol) {
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  cudaStream_t cap = h->st, body_st;
+  bool own = false;
+  if (cap == 0) {   // the legacy stream cannot be captured
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return -1;
+    own = true;
+  }
+  cudaStream_t saved = h->st;
+  h->st = cap;
+  cudaStreamCreateWithFlags(&body_st, cudaStreamNonBlocking);
+  cudaGraph_t graph;
+  cudaGraphCreate(&graph, 0);
+  int rc = 0;
+  if (cudaStreamBeginCaptureToGraph(cap, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+      cudaSuccess)
+    rc = -1;
+  if (!rc) {
+    enqueue_front(h, rho);
+    rc = add_while(h, graph, tol, body_st);
+    if (!rc) {
+      enqueue_middle(h);
+      rc = add_while(h, graph, tol, body_st);
+    }
+    if (!rc) enqueue_back(h, phi);
+    cudaGraph_t g2;
+    if (cudaStreamEndCapture(cap, &g2) != cudaSuccess) rc = -1;
+  }
+  if (!rc && cudaGraphInstantiate(&h->gexec, graph, 0) != cudaSuccess) rc = -1;
+  cudaGraphDestroy(graph);
+  cudaStreamDestroy(body_st);
+  h->st = saved;
+  if (own) cudaStreamDestroy(cap);
+  cudaGetLastError();
+  if (rc) { h->gexec = nullptr; return -1; }
+  h->g_rho = rho;
+  h->g_phi = phi;
+  h->g_tol = tol;
+  return 0;
+}
+
+static int finish(psolve_t h) {
+  if (cudaStreamSynchronize(h->st) != cudaSuccess || !cuda_ok("solve"))
+    return fail(PSOLVE_ERR_CUDA, g_err.empty() ? "solve failed" : g_err);
+  const int w = *h->h_worst;
+  if (w == -5) return fail(PSOLVE_ERR_NONFINITE, "non-finite residual norm");
+  if (w == -4) return fail(PSOLVE_ERR_NOT_CONVERGED, "a mode did not reach the tolerance");
+  return PSOLVE_OK;
+}
+
+static int enqueue_solve(psolve_t h, const double* rho, double* phi, double tol) {
+  if (h->d.use_graph) {
+    if (!h->gexec || h->g_rho != rho || h->g_phi != phi || h->g_tol != tol) {
+      if (capture(h, rho, phi, tol) != 0)
+        return fail(PSOLVE_ERR_CUDA, "graph capture failed: " + g_err);
+    }
+    if (cudaGraphLaunch(h->gexec, h->st) != cudaSuccess) return fail(PSOLVE_ERR_CUDA, "graph launch");
+    return PSOLVE_OK;
+  }
+  std::string err;
+  enqueue_front(h, rho);
+  if (h->mg.eager_solve(h->f, h->u, tol, h->st, err) != 0) return fail(PSOLVE_ERR_CUDA, err);
+  enqueue_middle(h);
+  if (h->mg.eager_solve(h->f, h->u, tol, h->st, err) != 0) return fail(PSOLVE_ERR_CUDA, err);
+  enqueue_back(h, phi);
+  return PSOLVE_OK;
+}
+
+extern "C" int psolve_solve(psolve_t h, const double* rho, double* phi, double tol) {
+  if (!h || !rho || !phi) return fail(PSOLVE_ERR_ARG, "null argument");
+  if (rho == phi) return fail(PSOLVE_ERR_ARG, "phi must not alias rho");
+  if (tol <= 0) tol = 1e-8;
+  int rc = enqueue_solve(h, rho, phi, tol);
+  if (rc != PSOLVE_OK) return rc;
+  return finish(h);
+}
+
+extern "C" int psolve_solve_batched(psolve_t* hs, const double* const* rhos, double* const* phis,
+                                    int n, double tol) {
+  if (!hs || !rhos || !phis || n < 0) return fail(PSOLVE_ERR_ARG, "null argument");
+  if (tol <= 0) tol = 1e-8;
+  for (int k = 0; k < n; ++k) {
+    if (!hs[k] || !rhos[k] || !phis[k] || rhos[k] == phis[k])
+      return fail(PSOLVE_ERR_ARG, "invalid batch entry");
+    if (!hs[k]->d.use_graph) return fail(PSOLVE_ERR_ARG, "batched solves need use_graph handles");
+  }
+  for (int k = 0; k < n; ++k) {
+    int rc = enqueue_solve(hs[k], rhos[k], phis[k], tol);
+    if (rc != PSOLVE_OK) return rc;
+  }
+  int first = PSOLVE_OK;
+  for (int k = 0; k < n; ++k) {
+    int rc = finish(hs[k]);
+    if (rc != PSOLVE_OK && first == PSOLVE_OK) first = rc;
+  }
+  return first;
+}
+
+extern "C" int psolve_get_stats(psolve_t h, psolve_stats* s) {
+  if (!h || !s) return fail(PSOLVE_ERR_ARG, "null argument");
+  cudaStreamSynchronize(h->st);
+  const int M = h->M;
+  s->n_modes = M;
+  s->setup_ms = h->setup_ms;
+  std::vector<double2> nf(M), nr(M);
+  for (int pass = 0; pass < 2; ++pass) {
+    SolveStats& q = pass ? h->sf : h->sp;
+    int it = 0;
+    cudaMemcpy(&it, q.iter, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpy(nf.data(), q.nf2, sizeof(double2) * M, cudaMemcpyDeviceToHost);
+    cudaMemcpy(nr.data(), q.nr2, sizeof(double2) * M, cudaMemcpyDeviceToHost);
+    double a = 0, b = 0;
+    for (int m = 0; m < M; ++m) { a += nr[m].x + nr[m].y; b += nf[m].x + nf[m].y; }
+    const double rel = b > 0 ? std::sqrt(a / b) : 0.0;
+    int* cyc = pass ? s->cycles_phi : s->cycles_psi;
+    if (cyc) cudaMemcpy(cyc, q.cycles, sizeof(int) * M, cudaMemcpyDeviceToHost);
+    if (pass) { s->iterations_phi = it - 1; s->rel_residual_phi = rel; }
+    else { s->iterations_psi = it - 1; s->rel_residual_psi = rel; }
+  }
+  if (s->status) {
+    std::vector<int> a(M), b(M);
+    cudaMemcpy(a.data(), h->sp.status, sizeof(int) * M, cudaMemcpyDeviceToHost);
+    cudaMemcpy(b.data(), h->sf.status, sizeof(int) * M, cudaMemcpyDeviceToHost);
+    for (int m = 0; m < M; ++m) {
+      int w = PSOLVE_OK;
+      if (a[m] == -5 || b[m] == -5) w = PSOLVE_ERR_NONFINITE;
+      else if (a[m] != 0 || b[m] != 0) w = PSOLVE_ERR_NOT_CONVERGED;
+      s->status[m] = w;
+    }
+  }
+  return cuda_ok("stats") ? PSOLVE_OK : PSOLVE_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// stage entry points
+// ---------------------------------------------------------------------------
+extern "C" int psolve_stage_forward(psolve_t h, const double* rho, double* f_hat) {
+  if (!h || !rho || !f_hat) return fail(PSOLVE_ERR_ARG, "null argument");
+  launch_fft_forward(rho, reinterpret_cast<double2*>(f_hat), h->d.n_r, h->d.n_tz, h->d.n_phi,
+                     4.0 * kPi * h->d.G / h->d.n_phi, h->tw, h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("forward") ? PSOLVE_OK
+                                                                             : PSOLVE_ERR_CUDA;
+}
+
+extern "C" int psolve_stage_inverse(psolve_t h, const double* phi_hat, double* phi) {
+  if (!h || !phi_hat || !phi) return fail(PSOLVE_ERR_ARG, "null argument");
+  launch_fft_inverse(reinterpret_cast<const double2*>(phi_hat), phi, h->d.n_r, h->d.n_tz,
+                     h->d.n_phi, h->tw, h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("inverse") ? PSOLVE_OK
+                                                                             : PSOLVE_ERR_CUDA;
+}
+
+extern "C" int psolve_stage_mg_solve(psolve_t h, const double* f_hat, double* u_hat, double tol,
+                                     int warm, int* cycles_host) {
+  if (!h || !f_hat || !u_hat) return fail(PSOLVE_ERR_ARG, "null argument");
+  if (tol <= 0) tol = 1e-8;
+  const size_t bytes = sizeof(double2) * size_t(h->M) * h->d.n_r * h->d.n_tz;
+  if (!warm) cudaMemsetAsync(u_hat, 0, bytes, h->st);
+  std::string err;
+  if (h->mg.eager_solve(reinterpret_cast<const double2*>(f_hat), reinterpret_cast<double2*>(u_hat),
+                        tol, h->st, err) != 0)
+    return fail(PSOLVE_ERR_CUDA, err);
+  if (cycles_host)
+    cudaMemcpyAsync(cycles_host, h->mg.d_cycles, sizeof(int) * h->M, cudaMemcpyDeviceToHost, h->st);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess || !cuda_ok("mg_solve")) return PSOLVE_ERR_CUDA;
+  std::vector<int> st(h->M);
+  cudaMemcpy(st.data(), h->mg.d_status, sizeof(int) * h->M, cudaMemcpyDeviceToHost);
+  for (int v : st)
+    if (v == -5) return fail(PSOLVE_ERR_NONFINITE, "non-finite residual");
+  for (int v : st)
+    if (v != 0) return fail(PSOLVE_ERR_NOT_CONVERGED, "a mode did not converge");
+  return PSOLVE_OK;
+}
+
+// Stage helpers operate on all M planes: a full active list.
+static void full_batch(psolve_t h) {
+  launch_init_active(h->mg.d_act, h->mg.d_nact, h->M, h->mg.S, h->st);
+}
+
+static int check_level(psolve_t h, int level, int precision, bool need_next) {
+  if (level < 0 || level >= int(h->mg.lv.size()) || (need_next && level + 1 >= int(h->mg.lv.size())))
+    return fail(PSOLVE_ERR_ARG, "level out of range");
+  if (precision != (h->d.precision == PSOLVE_MIXED ? 1 : 0))
+    return fail(PSOLVE_ERR_ARG, "stage precision must match the handle (0 FP64, 1 mixed/FP32)");
+  return PSOLVE_OK;
+}
+
+extern "C" int psolve_stage_smooth(psolve_t h, int level, int precision, void* e, const void* f,
+                                   int cycles) {
+  if (!h || !e || !f) return fail(PSOLVE_ERR_ARG, "null argument");
+  int rc = check_level(h, level, precision, false);
+  if (rc) return rc;
+  full_batch(h);
+  h->mg.smooth(level, e, f, cycles, false, h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("smooth") ? PSOLVE_OK
+                                                                            : PSOLVE_ERR_CUDA;
+}
+
+extern "C" int psolve_stage_restrict(psolve_t h, int level, int precision, const void* e,
+                                     const void* f, void* coarse) {
+  if (!h || !e || !f || !coarse) return fail(PSOLVE_ERR_ARG, "null argument");
+  int rc = check_level(h, level, precision, true);
+  if (rc) return rc;
+  full_batch(h);
+  h->mg.restrict_(level, e, f, coarse, h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("restrict") ? PSOLVE_OK
+                                                                              : PSOLVE_ERR_CUDA;
+}
+
+extern "C" int psolve_stage_prolong(psolve_t h, int level, int precision, void* e,
+                                    const void* coarse) {
+  if (!h || !e || !coarse) return fail(PSOLVE_ERR_ARG, "null argument");
+  int rc = check_level(h, level, precision, true);
+  if (rc) return rc;
+  full_batch(h);
+  h->mg.prolong(level, e, coarse, h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("prolong") ? PSOLVE_OK
+                                                                             : PSOLVE_ERR_CUDA;
+}
+
+extern "C" int psolve_stage_screening(psolve_t h, const double* psi_hat, double* sigma) {
+  if (!h || !psi_hat || !sigma) return fail(PSOLVE_ERR_ARG, "null argument");
+  launch_screening(h->bdev, reinterpret_cast<const double2*>(psi_hat),
+                   reinterpret_cast<double2*>(sigma), h->M, h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("screening") ? PSOLVE_OK
+                                                                               : PSOLVE_ERR_CUDA;
+}
+
+extern "C" int psolve_stage_boundary(psolve_t h, const double* sigma, double* theta) {
+  if (!h || !sigma || !theta) return fail(PSOLVE_ERR_ARG, "null argument");
+  launch_boundary_potential(h->gt, reinterpret_cast<const double2*>(sigma),
+                            reinterpret_cast<double2*>(theta), h->M, h->nb, h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("boundary") ? PSOLVE_OK
+                                                                              : PSOLVE_ERR_CUDA;
+}
+
+extern "C" int psolve_get_dgf(psolve_t h, double* dst) {
+  if (!h || !dst) return fail(PSOLVE_ERR_ARG, "null argument");
+  cudaMemcpyAsync(dst, h->gt, sizeof(double) * size_t(h->M) * h->nb * h->nb,
+                  cudaMemcpyDeviceToDevice, h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("dgf") ? PSOLVE_OK
+                                                                         : PSOLVE_ERR_CUDA;
+}

@@ -1,0 +1,665 @@
+// Multigrid kernels for the per-mode Helmholtz problems (Sec. 3).
+//
+// Planes hold the real and imaginary part of one mode as the two components
+// of a float2 / double2: the operator L_m is real, so both are relaxed by the
+// same line operations.  Dirichlet ghosts of the error equation are zero; a
+// face of zero area has a zero coefficient, so pole / axis ghosts never enter
+// the stencil.
+#include <cstdio>
+
+#include "kernels.h"
+
+namespace ps {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ const T* rtab(const LevelDev& L);
+template <> __device__ __forceinline__ const double* rtab<double>(const LevelDev& L) { return L.rd; }
+template <> __device__ __forceinline__ const float* rtab<float>(const LevelDev& L) { return L.rf; }
+template <typename T> __device__ __forceinline__ const T* ttab(const LevelDev& L);
+template <> __device__ __forceinline__ const double* ttab<double>(const LevelDev& L) { return L.td; }
+template <> __device__ __forceinline__ const float* ttab<float>(const LevelDev& L) { return L.tf; }
+template <typename T> __device__ __forceinline__ const T* omr(const LevelDev& L);
+template <> __device__ __forceinline__ const double* omr<double>(const LevelDev& L) { return L.omr_d; }
+template <> __device__ __forceinline__ const float* omr<float>(const LevelDev& L) { return L.omr_f; }
+template <typename T> __device__ __forceinline__ const T* omt(const LevelDev& L);
+template <> __device__ __forceinline__ const double* omt<double>(const LevelDev& L) { return L.omt_d; }
+template <> __device__ __forceinline__ const float* omt<float>(const LevelDev& L) { return L.omt_f; }
+template <typename T> __device__ __forceinline__ T s2of(const Batch& B, int slot);
+template <> __device__ __forceinline__ double s2of<double>(const Batch& B, int slot) { return B.s2d[slot]; }
+template <> __device__ __forceinline__ float s2of<float>(const Batch& B, int slot) { return B.s2f[slot]; }
+
+#define RTAB(tab, id, i) (tab)[(id) * (L.nr + 2) + (i)]
+#define TTAB(tab, id, j) (tab)[(id) * (L.nt + 2) + (j)]
+
+template <typename V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+
+template <typename V, typename T> __device__ __forceinline__ V vmk(T a, T b);
+template <> __device__ __forceinline__ float2 vmk<float2, float>(float a, float b) { return make_float2(a, b); }
+template <> __device__ __forceinline__ double2 vmk<double2, double>(double a, double b) { return make_double2(a, b); }
+
+template <typename V> __device__ __forceinline__ V shfl_up1(V v) {
+  v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
+  v.y = __shfl_up_sync(0xffffffffu, v.y, 1);
+  return v;
+}
+template <typename V> __device__ __forceinline__ V shfl_dn1(V v) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, 1);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, 1);
+  return v;
+}
+
+__device__ __forceinline__ bool plane_of(const Batch& B, int k, int& p, int& slot) {
+  if (k >= *B.nact) return false;
+  p = B.act[k];
+  slot = B.slot ? B.slot[p] : p;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Radial-line relaxation (Sec. 3.2): all lines j of one zebra colour; each
+// warp owns one line, each lane CPL consecutive cells.  The line right-hand
+// side f - P (aN e_{j+1} + aS e_{j-1}) is frozen, then n_sor even-odd SOR
+// sweeps with the line's omega_j.  zero_init: e is taken as 0 on entry (the
+// first pass of a level in a V-cycle).
+// ---------------------------------------------------------------------------
+template <typename T, int CPL>
+__global__ void __launch_bounds__(256) k_rpass(LevelDev L, Batch B, vec2_t<T>* __restrict__ e,
+                                               const vec2_t<T>* __restrict__ f, int color,
+                                               int zero_init, int n_sor) {
+  typedef vec2_t<T> V;
+  int p, slot;
+  if (!plane_of(B, blockIdx.y, p, slot)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = 2 * (blockIdx.x * (blockDim.x >> 5) + warp) + color;
+  const int nr = L.nr, nt = L.nt;
+  if (j >= nt) return;
+  const size_t base = size_t(p) * nr * nt;
+  const T* rt = rtab<T>(L);
+  const T* tt = ttab<T>(L);
+  const T s2 = s2of<T>(B, slot);
+  const T aN = TTAB(tt, TT_AN, j + 1), aS = TTAB(tt, TT_AS, j + 1);
+  const T Tj = TTAB(tt, TT_T, j + 1), dtj = TTAB(tt, TT_DT, j + 1);
+  const T w = omr<T>(L)[size_t(slot) * nt + j];
+  const T w1 = T(1) - w;
+  const bool nb_zero = zero_init && color == 0;
+  const int i0 = lane * CPL;
+  const bool on = i0 < nr;
+  V ev[CPL], fl[CPL];
+  T ae[CPL], aw[CPL], id[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    const int i = i0 + c;
+    ev[c] = vzero<V>();
+    fl[c] = vzero<V>();
+    ae[c] = aw[c] = id[c] = T(0);
+    if (on) {
+      const V fv = f[base + size_t(j) * nr + i];
+      V un = vzero<V>(), us = vzero<V>();
+      if (!nb_zero) {
+        if (j + 1 < nt) un = e[base + size_t(j + 1) * nr + i];
+        if (j > 0) us = e[base + size_t(j - 1) * nr + i];
+      }
+      const T P = RTAB(rt, RT_P, i + 1);
+      fl[c] = vmk<V, T>(fv.x - P * (aN * un.x + aS * us.x), fv.y - P * (aN * un.y + aS * us.y));
+      if (!zero_init) ev[c] = e[base + size_t(j) * nr + i];
+      ae[c] = RTAB(rt, RT_AE, i + 1);
+      aw[c] = RTAB(rt, RT_AW, i + 1);
+      id[c] = T(1) / (RTAB(rt, RT_DR, i + 1) + P * dtj - s2 * RTAB(rt, RT_Q, i + 1) * Tj);
+    }
+  }
+  const bool last = (i0 + CPL >= nr);
+  for (int it = 0; it < n_sor; ++it) {
+#pragma unroll
+    for (int par = 0; par < 2; ++par) {
+      V left = shfl_up1(ev[CPL - 1]);
+      V right = shfl_dn1(ev[0]);
+      if (lane == 0) left = vzero<V>();
+      if (last) right = vzero<V>();
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        if (on && ((i0 + c) & 1) == par) {
+          const V em = (c > 0) ? ev[c - 1] : left;
+          const V ep = (c < CPL - 1) ? ev[c + 1] : right;
+          const T tx = (fl[c].x - ae[c] * ep.x - aw[c] * em.x) * id[c];
+          const T ty = (fl[c].y - ae[c] * ep.y - aw[c] * em.y) * id[c];
+          ev[c].x = w1 * ev[c].x + w * tx;
+          ev[c].y = w1 * ev[c].y + w * ty;
+        }
+      }
+    }
+  }
+  if (on) {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) e[base + size_t(j) * nr + i0 + c] = ev[c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Polar / vertical-line relaxation: lines i of one zebra colour.  A block
+// stages a tile of TW columns (plus one neighbour column each side) of e and
+// the colour's columns of f in shared memory; each warp relaxes one column
+// with CPL consecutive cells per lane.
+// ---------------------------------------------------------------------------
+template <typename T, int CPL>
+__global__ void __launch_bounds__(256) k_tpass(LevelDev L, Batch B, vec2_t<T>* __restrict__ e,
+                                               const vec2_t<T>* __restrict__ f, int color,
+                                               int n_sor, int TW) {
+  typedef vec2_t<T> V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int p, slot;
+  if (!plane_of(B, blockIdx.y, p, slot)) return;
+  const int nr = L.nr, nt = L.nt;
+  const int SW = TW + 2, HW = TW / 2;
+  V* se = reinterpret_cast<V*>(smem_raw);   // [nt][SW]
+  V* sf = se + size_t(nt) * SW;              // [nt][HW]
+  const size_t base = size_t(p) * nr * nt;
+  const int i0 = blockIdx.x * TW;
+  for (int idx = threadIdx.x; idx < nt * SW; idx += blockDim.x) {
+    const int j = idx / SW, cc = idx - j * SW, i = i0 - 1 + cc;
+    se[idx] = (i >= 0 && i < nr) ? e[base + size_t(j) * nr + i] : vzero<V>();
+  }
+  for (int idx = threadIdx.x; idx < nt * HW; idx += blockDim.x) {
+    const int j = idx / HW, k = idx - j * HW;
+    sf[idx] = f[base + size_t(j) * nr + i0 + color + 2 * k];
+  }
+  __syncthreads();
+  const T* rt = rtab<T>(L);
+  const T* tt = ttab<T>(L);
+  const T s2 = s2of<T>(B, slot);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int j0 = lane * CPL;
+  const bool on = j0 < nt;
+  const bool last = (j0 + CPL >= nt);
+  for (int k = warp; k < HW; k += nw) {
+    const int cc = 1 + color + 2 * k, i = i0 + color + 2 * k;
+    const T P = RTAB(rt, RT_P, i + 1), aE = RTAB(rt, RT_AE, i + 1), aW = RTAB(rt, RT_AW, i + 1);
+    const T dr = RTAB(rt, RT_DR, i + 1), Qi = RTAB(rt, RT_Q, i + 1);
+    const T w = omt<T>(L)[size_t(slot) * nr + i], w1 = T(1) - w;
+    V ev[CPL], g[CPL];
+    T an[CPL], as[CPL], id[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int j = j0 + c;
+      ev[c] = vzero<V>();
+      g[c] = vzero<V>();
+      an[c] = as[c] = id[c] = T(0);
+      if (on) {
+        const V fv = sf[j * HW + k], ue = se[j * SW + cc + 1], uw = se[j * SW + cc - 1];
+        g[c] = vmk<V, T>(fv.x - aE * ue.x - aW * uw.x, fv.y - aE * ue.y - aW * uw.y);
+        ev[c] = se[j * SW + cc];
+        an[c] = P * TTAB(tt, TT_AN, j + 1);
+        as[c] = P * TTAB(tt, TT_AS, j + 1);
+        id[c] = T(1) / (dr + P * TTAB(tt, TT_DT, j + 1) - s2 * Qi * TTAB(tt, TT_T, j + 1));
+      }
+    }
+    for (int it = 0; it < n_sor; ++it) {
+#pragma unroll
+      for (int par = 0; par < 2; ++par) {
+        V left = shfl_up1(ev[CPL - 1]);
+        V right = shfl_dn1(ev[0]);
+        if (lane == 0) left = vzero<V>();
+        if (last) right = vzero<V>();
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          if (on && ((j0 + c) & 1) == par) {
+            const V em = (c > 0) ? ev[c - 1] : left;
+            const V ep = (c < CPL - 1) ? ev[c + 1] : right;
+            const T tx = (g[c].x - an[c] * ep.x - as[c] * em.x) * id[c];
+            const T ty = (g[c].y - an[c] * ep.y - as[c] * em.y) * id[c];
+            ev[c].x = w1 * ev[c].x + w * tx;
+            ev[c].y = w1 * ev[c].y + w * ty;
+          }
+        }
+      }
+    }
+    if (on) {
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) se[(j0 + c) * SW + cc] = ev[c];
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nt * HW; idx += blockDim.x) {
+    const int j = idx / HW, k = idx - j * HW;
+    e[base + size_t(j) * nr + i0 + color + 2 * k] = se[j * SW + 1 + color + 2 * k];
+  }
+}
+
+template <typename T, int CPL>
+static void rpass(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f, int color,
+                  bool zi, int n_sor, cudaStream_t st) {
+  const int lines = (L.nt - color + 1) / 2;
+  dim3 grid((lines + 7) / 8, B.max_planes);
+  k_rpass<T, CPL><<<grid, 256, 0, st>>>(L, B, e, f, color, zi ? 1 : 0, n_sor);
+}
+
+template <typename T>
+static void rpass_any(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
+                      int color, bool zi, int n_sor, cudaStream_t st) {
+  switch (L.nr <= 32 ? 1 : L.nr / 32) {
+    case 1: rpass<T, 1>(L, B, e, f, color, zi, n_sor, st); break;
+    case 2: rpass<T, 2>(L, B, e, f, color, zi, n_sor, st); break;
+    case 4: rpass<T, 4>(L, B, e, f, color, zi, n_sor, st); break;
+    case 8: rpass<T, 8>(L, B, e, f, color, zi, n_sor, st); break;
+    case 16: rpass<T, 16>(L, B, e, f, color, zi, n_sor, st); break;
+    case 32: rpass<T, 32>(L, B, e, f, color, zi, n_sor, st); break;
+    default: std::fprintf(stderr, "psolve: radial size %d unsupported\n", L.nr);
+  }
+}
+
+static int tile_width(int nr, int nt, size_t vbytes) {
+  int tw = nr < 32 ? nr : 32;
+  while (tw > 2 && size_t(nt) * (tw + 2 + tw / 2) * vbytes > 160 * 1024) tw /= 2;
+  return tw;
+}
+
+template <typename T, int CPL>
+static void tpass(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f, int color,
+                  int n_sor, cudaStream_t st) {
+  const int TW = tile_width(L.nr, L.nt, sizeof(vec2_t<T>));
+  const size_t sm = size_t(L.nt) * (TW + 2 + TW / 2) * sizeof(vec2_t<T>);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tpass<T, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  dim3 grid(L.nr / TW, B.max_planes);
+  k_tpass<T, CPL><<<grid, 256, sm, st>>>(L, B, e, f, color, n_sor, TW);
+}
+
+template <typename T>
+static void tpass_any(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
+                      int color, int n_sor, cudaStream_t st) {
+  switch (L.nt <= 32 ? 1 : L.nt / 32) {
+    case 1: tpass<T, 1>(L, B, e, f, color, n_sor, st); break;
+    case 2: tpass<T, 2>(L, B, e, f, color, n_sor, st); break;
+    case 4: tpass<T, 4>(L, B, e, f, color, n_sor, st); break;
+    case 8: tpass<T, 8>(L, B, e, f, color, n_sor, st); break;
+    case 16: tpass<T, 16>(L, B, e, f, color, n_sor, st); break;
+    case 32: tpass<T, 32>(L, B, e, f, color, n_sor, st); break;
+    default: std::fprintf(stderr, "psolve: polar size %d unsupported\n", L.nt);
+  }
+}
+
+template <typename T>
+void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
+                   int cycles, int n_sor, bool zero_init, cudaStream_t st) {
+  for (int c = 0; c < cycles; ++c) {
+    const bool zi = zero_init && c == 0;
+    rpass_any<T>(L, B, e, f, 0, zi, n_sor, st);
+    rpass_any<T>(L, B, e, f, 1, zi, n_sor, st);
+    tpass_any<T>(L, B, e, f, 0, n_sor, st);
+    tpass_any<T>(L, B, e, f, 1, n_sor, st);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Defect and area-weighted restriction (Sec. 3.1): one thread per coarse cell
+// computes the defect f - L e of its four children and their weighted mean.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ vec2_t<T> defect(const LevelDev& L, const T* rt, const T* tt, T s2,
+                                           const vec2_t<T>* __restrict__ e,
+                                           const vec2_t<T>* __restrict__ f, int i, int j) {
+  typedef vec2_t<T> V;
+  const int nr = L.nr, nt = L.nt;
+  const V c = e[size_t(j) * nr + i];
+  const V E = (i + 1 < nr) ? e[size_t(j) * nr + i + 1] : vzero<V>();
+  const V W = (i > 0) ? e[size_t(j) * nr + i - 1] : vzero<V>();
+  const V N = (j + 1 < nt) ? e[size_t(j + 1) * nr + i] : vzero<V>();
+  const V S = (j > 0) ? e[size_t(j - 1) * nr + i] : vzero<V>();
+  const T aE = RTAB(rt, RT_AE, i + 1), aW = RTAB(rt, RT_AW, i + 1), P = RTAB(rt, RT_P, i + 1);
+  const T aN = P * TTAB(tt, TT_AN, j + 1), aS = P * TTAB(tt, TT_AS, j + 1);
+  const T d = RTAB(rt, RT_DR, i + 1) + P * TTAB(tt, TT_DT, j + 1) -
+              s2 * RTAB(rt, RT_Q, i + 1) * TTAB(tt, TT_T, j + 1);
+  const V fv = f[size_t(j) * nr + i];
+  return vmk<V, T>(fv.x - (aE * E.x + aW * W.x + aN * N.x + aS * S.x + d * c.x),
+                   fv.y - (aE * E.y + aW * W.y + aN * N.y + aS * S.y + d * c.y));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict(LevelDev L, LevelDev C, Batch B,
+                                                  const vec2_t<T>* __restrict__ e,
+                                                  const vec2_t<T>* __restrict__ f,
+                                                  vec2_t<T>* __restrict__ fc) {
+  typedef vec2_t<T> V;
+  int p, slot;
+  if (!plane_of(B, blockIdx.y, p, slot)) return;
+  const int cidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cidx >= C.nr * C.nt) return;
+  const int J = cidx / C.nr, I = cidx - J * C.nr;
+  const T* rt = rtab<T>(L);
+  const T* tt = ttab<T>(L);
+  const T s2 = s2of<T>(B, slot);
+  const size_t base = size_t(p) * L.nr * L.nt;
+  T ax = 0, ay = 0;
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int i = 2 * I + a, j = 2 * J + b;
+      const V r = defect<T>(L, rt, tt, s2, e + base, f + base, i, j);
+      const T wgt = RTAB(rt, RT_RW, i + 1) * TTAB(tt, TT_RW, j + 1);
+      ax += wgt * r.x;
+      ay += wgt * r.y;
+    }
+  fc[size_t(p) * C.nr * C.nt + cidx] = vmk<V, T>(ax, ay);
+}
+
+template <typename T>
+void launch_restrict(const LevelDev& F, const LevelDev& C, const Batch& B, const vec2_t<T>* e,
+                     const vec2_t<T>* f, vec2_t<T>* fc, cudaStream_t st) {
+  const int n = C.nr * C.nt;
+  dim3 grid((n + 255) / 256, B.max_planes);
+  k_restrict<T><<<grid, 256, 0, st>>>(F, C, B, e, f, fc);
+}
+
+// ---------------------------------------------------------------------------
+// Bilinear prolongation in (r^2, theta) / (R, z) and correction (Sec. 3.1).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ vec2_t<T> coarse_val(const LevelDev& C, const vec2_t<T>* __restrict__ ec,
+                                               int I, int J, int m) {
+  typedef vec2_t<T> V;
+  T fac = T(1);
+  const T sgn = (m & 1) ? T(-1) : T(1);
+  int Ic = I, Jc = J;
+  if (I == 0) { if (C.gL == GH_ZERO) return vzero<V>(); Ic = 1; if (C.gL == GH_PARITY) fac *= sgn; }
+  if (I == C.nr + 1) { if (C.gR == GH_ZERO) return vzero<V>(); Ic = C.nr; if (C.gR == GH_PARITY) fac *= sgn; }
+  if (J == 0) { if (C.gB == GH_ZERO) return vzero<V>(); Jc = 1; if (C.gB == GH_PARITY) fac *= sgn; }
+  if (J == C.nt + 1) { if (C.gT == GH_ZERO) return vzero<V>(); Jc = C.nt; if (C.gT == GH_PARITY) fac *= sgn; }
+  const V v = ec[size_t(Jc - 1) * C.nr + (Ic - 1)];
+  return vmk<V, T>(fac * v.x, fac * v.y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong(LevelDev L, LevelDev C, Batch B,
+                                                 vec2_t<T>* __restrict__ e,
+                                                 const vec2_t<T>* __restrict__ ec) {
+  typedef vec2_t<T> V;
+  int p, slot;
+  if (!plane_of(B, blockIdx.y, p, slot)) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L.nr * L.nt) return;
+  const int j = idx / L.nr, i = idx - j * L.nr;
+  const int i1 = i + 1, j1 = j + 1;
+  const int I1 = (i1 & 1) ? (i1 + 1) / 2 - 1 : i1 / 2, J1 = (j1 & 1) ? (j1 + 1) / 2 - 1 : j1 / 2;
+  const T* rt = rtab<T>(L);
+  const T* tt = ttab<T>(L);
+  const T p1 = RTAB(rt, RT_P1, i1), p2 = RTAB(rt, RT_P2, i1);
+  const T q1 = TTAB(tt, TT_P1, j1), q2 = TTAB(tt, TT_P2, j1);
+  const int m = B.mode[slot];
+  const V* ecp = ec + size_t(p) * C.nr * C.nt;
+  const V a = coarse_val<T>(C, ecp, I1, J1, m), b = coarse_val<T>(C, ecp, I1 + 1, J1, m);
+  const V c = coarse_val<T>(C, ecp, I1, J1 + 1, m), d = coarse_val<T>(C, ecp, I1 + 1, J1 + 1, m);
+  V& u = e[size_t(p) * L.nr * L.nt + idx];
+  u.x += p1 * q1 * a.x + p2 * q1 * b.x + p1 * q2 * c.x + p2 * q2 * d.x;
+  u.y += p1 * q1 * a.y + p2 * q1 * b.y + p1 * q2 * c.y + p2 * q2 * d.y;
+}
+
+template <typename T>
+void launch_prolong(const LevelDev& F, const LevelDev& C, const Batch& B, vec2_t<T>* e,
+                    const vec2_t<T>* ec, cudaStream_t st) {
+  const int n = F.nr * F.nt;
+  dim3 grid((n + 255) / 256, B.max_planes);
+  k_prolong<T><<<grid, 256, 0, st>>>(F, C, B, e, ec);
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: e = L_m^{-1} f with the precomputed FP64 inverse.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_coarse(LevelDev C, Batch B, const double* __restrict__ inv, int nc,
+                         const vec2_t<T>* __restrict__ fc, vec2_t<T>* __restrict__ ec) {
+  typedef vec2_t<T> V;
+  extern __shared__ double2 sfc[];
+  int p, slot;
+  if (!plane_of(B, blockIdx.x, p, slot)) return;
+  const V* fp = fc + size_t(p) * nc;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) sfc[k] = make_double2(double(fp[k].x), double(fp[k].y));
+  __syncthreads();
+  const double* A = inv + size_t(slot) * nc * nc;
+  for (int row = threadIdx.x; row < nc; row += blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    for (int k = 0; k < nc; ++k) {
+      const double a = A[size_t(row) * nc + k];
+      sx += a * sfc[k].x;
+      sy += a * sfc[k].y;
+    }
+    ec[size_t(p) * nc + row] = vmk<V, T>(T(sx), T(sy));
+  }
+}
+
+template <typename T>
+void launch_coarse(const LevelDev& C, const Batch& B, const double* inv, int nc,
+                   const vec2_t<T>* fc, vec2_t<T>* ec, cudaStream_t st) {
+  const int th = nc < 256 ? ((nc + 31) / 32) * 32 : 256;
+  k_coarse<T><<<B.max_planes, th, nc * sizeof(double2), st>>>(C, B, inv, nc, fc, ec);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 solution update and residual with per-plane norms (the outer loop of
+// the mixed-precision iterative refinement, and of the FP64 path).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_update(int n, Batch B, double2* __restrict__ u, const vec2_t<T>* __restrict__ e) {
+  int p, slot;
+  if (!plane_of(B, blockIdx.y, p, slot)) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const size_t o = size_t(p) * n + idx;
+  const vec2_t<T> v = e[o];
+  double2 w = u[o];
+  w.x += double(v.x);
+  w.y += double(v.y);
+  u[o] = w;
+}
+
+template <typename T>
+void launch_update(const LevelDev& L, const Batch& B, double2* u, const vec2_t<T>* e,
+                   cudaStream_t st) {
+  const int n = L.nr * L.nt;
+  dim3 grid((n + 255) / 256, B.max_planes);
+  k_update<T><<<grid, 256, 0, st>>>(n, B, u, e);
+}
+
+int residual_blocks(int nr, int nt) { return (nr * nt + 255) / 256; }
+
+__device__ __forceinline__ double4 add4(double4 a, double4 b) {
+  return make_double4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+__device__ double4 block_sum4(double4 v, double4* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    v.z += __shfl_down_sync(0xffffffffu, v.z, o);
+    v.w += __shfl_down_sync(0xffffffffu, v.w, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double4 s = make_double4(0, 0, 0, 0);
+  if (threadIdx.x == 0)
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) s = add4(s, sh[w]);
+  return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const double2* __restrict__ f,
+                                                  const double2* __restrict__ u,
+                                                  vec2_t<T>* __restrict__ r, double4* part,
+                                                  double4* psum, int* cnt) {
+  __shared__ double4 sh[8];
+  __shared__ int last;
+  int p, slot;
+  if (!plane_of(B, blockIdx.y, p, slot)) return;
+  const int nr = L.nr, nt = L.nt, n = nr * nt;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  double4 acc = make_double4(0, 0, 0, 0);
+  if (idx < n) {
+    const int j = idx / nr, i = idx - j * nr;
+    const size_t base = size_t(p) * n;
+    const double s2 = B.s2d[slot];
+    const double2 rv = defect<double>(L, L.rd, L.td, s2, u + base, f + base, i, j);
+    const double2 fv = f[base + idx];
+    r[base + idx] = vmk<vec2_t<T>, T>(T(rv.x), T(rv.y));
+    const double dv = L.rd[RT_V * (nr + 2) + i + 1] * L.td[TT_V * (nt + 2) + j + 1];
+    acc = make_double4(dv * rv.x * rv.x, dv * rv.y * rv.y, dv * fv.x * fv.x, dv * fv.y * fv.y);
+  }
+  const double4 s = block_sum4(acc, sh);
+  const int nblk = gridDim.x;
+  if (threadIdx.x == 0) {
+    part[size_t(p) * nblk + blockIdx.x] = s;
+    __threadfence();
+    last = (atomicAdd(&cnt[p], 1) == nblk - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double4 t = make_double4(0, 0, 0, 0);
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+      const double2* q2 = reinterpret_cast<const double2*>(&part[size_t(p) * nblk + b]);
+      const double2 qa = __ldcg(q2), qb = __ldcg(q2 + 1);
+      const double4 q = make_double4(qa.x, qa.y, qb.x, qb.y);
+      t = add4(t, q);
+    }
+    const double4 tot = block_sum4(t, sh);
+    if (threadIdx.x == 0) {
+      psum[p] = tot;
+      cnt[p] = 0;
+    }
+  }
+}
+
+template <typename T>
+void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
+                     vec2_t<T>* r, double4* part, double4* psum, int* cnt, cudaStream_t st) {
+  dim3 grid(residual_blocks(L.nr, L.nt), B.max_planes);
+  k_residual<T><<<grid, 256, 0, st>>>(L, B, f, u, r, part, psum, cnt);
+}
+
+// ---------------------------------------------------------------------------
+// Retirement (App. B criterion, per mode and component) and compaction.
+// ---------------------------------------------------------------------------
+enum { ST_ACTIVE = 1, ST_OK = 0, ST_STAGNATED = 2, ST_NOTCONV = -4, ST_NONFINITE = -5 };
+
+__global__ void __launch_bounds__(1024) k_retire(int* act, int* nact, const double4* __restrict__ psum,
+                                                  RetireState S, double tol, int max_cycles,
+                                                  int stagnation, int use_cond,
+                                                  unsigned long long handle) {
+  __shared__ double smax[32];
+  __shared__ int scan[1024];
+  __shared__ int base_out;
+  const int n = *nact;
+  const int iter = *S.iter;
+  const int tid = threadIdx.x;
+  if (iter == 0) {
+    double mx = 0.0;
+    for (int k = tid; k < n; k += blockDim.x) {
+      const int p = act[k];
+      const double4 s = psum[p];
+      S.nf2[p] = make_double2(s.z, s.w);
+      mx = fmax(mx, fmax(s.z, s.w));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) smax[tid >> 5] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      double m2 = 0.0;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) m2 = fmax(m2, smax[w]);
+      *S.fmax2 = m2;
+    }
+    __syncthreads();
+  }
+  const double floor2 = 1e-28 * (*S.fmax2);
+  const double tol2 = tol * tol;
+  if (tid == 0) base_out = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+    const int k = c0 + tid;
+    int keep = 0, p = -1;
+    if (k < n) {
+      p = act[k];
+      const double4 s = psum[p];
+      const double2 nf = S.nf2[p];
+      const double2 prev = S.nr2[p];
+      const double tre = tol2 * fmax(nf.x, floor2), tim = tol2 * fmax(nf.y, floor2);
+      int st = ST_ACTIVE;
+      if (!isfinite(s.x) || !isfinite(s.y)) st = ST_NONFINITE;
+      else if (s.x <= tre && s.y <= tim) st = ST_OK;
+      else if (iter >= max_cycles) st = ST_NOTCONV;
+      else if (stagnation && iter >= 3 && s.x + s.y > 0.81 * (prev.x + prev.y)) st = ST_STAGNATED;
+      S.nr2[p] = make_double2(s.x, s.y);
+      S.cycles[p] = iter;
+      S.status[p] = st;
+      keep = (st == ST_ACTIVE);
+    }
+    __syncthreads();
+    scan[tid] = keep;
+    __syncthreads();
+    for (int o = 1; o < int(blockDim.x); o <<= 1) {
+      const int v = (tid >= o) ? scan[tid - o] : 0;
+      __syncthreads();
+      scan[tid] += v;
+      __syncthreads();
+    }
+    if (keep) act[base_out + scan[tid] - 1] = p;
+    __syncthreads();
+    if (tid == 0) base_out += scan[blockDim.x - 1];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    *nact = base_out;
+    *S.iter = iter + 1;
+    *S.cont = base_out > 0 ? 1 : 0;
+    if (use_cond) cudaGraphSetConditional(handle, base_out > 0 ? 1u : 0u);
+  }
+}
+
+void launch_retire(int* act, int* nact, const double4* psum, RetireState S, double tol,
+                   int max_cycles, int stagnation, int use_cond, unsigned long long handle,
+                   cudaStream_t st) {
+  k_retire<<<1, 1024, 0, st>>>(act, nact, psum, S, tol, max_cycles, stagnation, use_cond, handle);
+}
+
+__global__ void k_init_active(int* act, int* nact, int n, RetireState S) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    act[k] = k;
+    S.cycles[k] = 0;
+    S.status[k] = ST_ACTIVE;
+    S.nr2[k] = make_double2(0.0, 0.0);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *nact = n;
+    *S.iter = 0;
+    *S.cont = 1;
+  }
+}
+
+void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t st) {
+  k_init_active<<<(n + 255) / 256, 256, 0, st>>>(act, nact, n, S);
+}
+
+#define INST(T)                                                                                  \
+  template void launch_smooth<T>(const LevelDev&, const Batch&, vec2_t<T>*, const vec2_t<T>*,   \
+                                 int, int, bool, cudaStream_t);                                  \
+  template void launch_restrict<T>(const LevelDev&, const LevelDev&, const Batch&,               \
+                                   const vec2_t<T>*, const vec2_t<T>*, vec2_t<T>*, cudaStream_t); \
+  template void launch_prolong<T>(const LevelDev&, const LevelDev&, const Batch&, vec2_t<T>*,   \
+                                  const vec2_t<T>*, cudaStream_t);                               \
+  template void launch_coarse<T>(const LevelDev&, const Batch&, const double*, int,             \
+                                 const vec2_t<T>*, vec2_t<T>*, cudaStream_t);                    \
+  template void launch_update<T>(const LevelDev&, const Batch&, double2*, const vec2_t<T>*,     \
+                                 cudaStream_t);                                                  \
+  template void launch_residual<T>(const LevelDev&, const Batch&, const double2*,               \
+                                   const double2*, vec2_t<T>*, double4*, double4*, int*,        \
+                                   cudaStream_t);
+INST(float)
+INST(double)
+
+}  // namespace ps

@@ -1,0 +1,119 @@
+// Launch interface of the device kernels (all asynchronous on `st`).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace ps {
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { typedef float2 type; };
+template <> struct Vec2<double> { typedef double2 type; };
+template <typename T> using vec2_t = typename Vec2<T>::type;
+
+// Device view of one multigrid level.
+struct LevelDev {
+  int nr, nt;
+  const double* rd;   // RT_N x (nr+2) radial tables
+  const double* td;   // TT_N x (nt+2) polar tables
+  const float* rf;    // float copies
+  const float* tf;
+  const double* omr_d;  // [slots][nt]  r-line relaxation parameters
+  const double* omt_d;  // [slots][nr]  polar-line relaxation parameters
+  const float* omr_f;
+  const float* omt_f;
+  int gL, gR, gB, gT;   // coarse-ghost rules when this level is prolongated from
+};
+
+// A batch of planes: plane p of a level buffer starts at p * nr * nt; its
+// mode slot is slot[p] (identity when slot == nullptr); the mode's
+// [sin(m pi/N)/(pi/N)]^2 is s2[slot].  Only the planes act[0..*nact) are
+// touched; grids are sized for max_planes and surplus blocks return.
+struct Batch {
+  const int* act;
+  const int* nact;
+  const int* slot;     // plane -> mode slot (nullptr: identity)
+  const int* mode;     // slot -> azimuthal mode number m (pole / axis parity)
+  const double* s2d;   // slot -> s_m^2
+  const float* s2f;
+  int max_planes;
+};
+
+// ---- FFT (k_fft.cu) --------------------------------------------------------
+// f[m][j][i] (double2) = scale * sum_k rho[i][j][k] e^{-2 pi i m k / N}
+void launch_fft_forward(const double* rho, double2* f, int nr, int nt, int N, double scale,
+                        const double2* tw, cudaStream_t st);
+void launch_fft_inverse(const double2* fh, double* phi, int nr, int nt, int N,
+                        const double2* tw, cudaStream_t st);
+
+// ---- multigrid (k_mg.cu), T = float or double ---------------------------------
+template <typename T>
+void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e,
+                   const vec2_t<T>* f,
+                   int cycles, int n_sor, bool zero_init, cudaStream_t st);
+template <typename T>
+void launch_restrict(const LevelDev& F, const LevelDev& C, const Batch& B,
+                     const vec2_t<T>* e,
+                     const vec2_t<T>* f,
+                     vec2_t<T>* fc,
+                     cudaStream_t st);
+template <typename T>
+void launch_prolong(const LevelDev& F, const LevelDev& C, const Batch& B,
+                    vec2_t<T>* e,
+                    const vec2_t<T>* ec,
+                    cudaStream_t st);
+template <typename T>
+void launch_coarse(const LevelDev& C, const Batch& B, const double* inv, int nc,
+                   const vec2_t<T>* fc,
+                   vec2_t<T>* ec,
+                   cudaStream_t st);
+// u += e over the planes of the batch (level-0 sizes)
+template <typename T>
+void launch_update(const LevelDev& L, const Batch& B, double2* u,
+                   const vec2_t<T>* e,
+                   cudaStream_t st);
+// r = f - L u (FP64), stored as T2; per-block partial sums of dV r^2 (and
+// dV f^2 when want_f) into part[p * nblk + b] as (rr_re, rr_im, ff_re, ff_im).
+// Deterministic per-plane sums: each block writes its partial to
+// part[p * nblk + b]; the last block of a plane (counter cnt[p]) adds the
+// partials in block order into psum[p] and resets the counter.
+template <typename T>
+void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
+                     vec2_t<T>* r, double4* part, double4* psum, int* cnt, cudaStream_t st);
+int residual_blocks(int nr, int nt);
+
+// Convergence bookkeeping: sums partials, retires converged planes, compacts
+// the active list, counts cycles and sets status; writes *cont (and the
+// graph conditional when handle != 0).
+struct RetireState {
+  double2* nf2;      // [planes] |f|^2 per component (set on iteration 0)
+  double2* nr2;      // [planes] latest |r|^2
+  int* cycles;       // [planes]
+  int* status;       // [planes]
+  int* iter;         // scalar
+  int* cont;         // scalar: 1 while planes remain
+  double* fmax2;     // scalar: max over planes of |f|^2 (iteration 0)
+};
+void launch_retire(int* act, int* nact, const double4* psum, RetireState S, double tol,
+                   int max_cycles, int stagnation, int use_cond, unsigned long long cond_handle,
+                   cudaStream_t st);
+void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t st);
+
+// ---- boundary treatment (k_bc.cu) ---------------------------------------------
+struct BDev {
+  int nb;
+  int ncell;            // domain cells next to at least one boundary ghost
+  const int* adj;       // [nb] adjacent cell index (j-1)*nr + (i-1)
+  const double* sig;    // [nb] screening coefficient (incl. 1/(4 pi G))
+  const double* cpl;    // [nb] coefficient of the ghost value in L at adj
+  const int* cell;      // [ncell] cell index
+  const int* cbp;       // [2*ncell] boundary points touching the cell (-1 = none)
+  int plane_cells;      // nr * nt
+};
+void launch_screening(const BDev& b, const double2* psi, double2* sigma, int M, cudaStream_t st);
+void launch_boundary_potential(const double* gt, const double2* sigma, double2* theta, int M,
+                               int nb, cudaStream_t st);
+// f2 = f - sum over the adjacent ghosts of cpl * (-theta), in place on f
+void launch_rhs_ghosts(const BDev& b, double2* f, const double2* theta, int M, cudaStream_t st);
+
+}  // namespace ps

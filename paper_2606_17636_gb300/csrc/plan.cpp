@@ -1,0 +1,315 @@
+// Host-side plan: grid geometry (Sec. 2.1.1, 2.1.2), multigrid level tables
+// (Sec. 3.1), per-line relaxation parameters (App. A) and coarsest-level
+// inverses (Sec. 3.3, solved exactly).
+#include "plan.h"
+
+#include <algorithm>
+#include <cstdio>
+
+namespace ps {
+
+static const double kPoleTol = 1e-12;
+static const double kPi = 3.14159265358979323846;
+
+void Axis::centres() {
+  x.assign(n + 2, 0.0);
+  for (int c = 0; c < n + 2; ++c) {
+    double a = F[c], b = F[c + 1];
+    switch (kind) {
+      case 0:  // r, spherical: volume-weighted centroid, Eq. cell_centers_sph
+        x[c] = 0.75 * (b * b * b * b - a * a * a * a) / (b * b * b - a * a * a);
+        break;
+      case 1:  // R, cylindrical
+        x[c] = (2.0 / 3.0) * (b * b * b - a * a * a) / (b * b - a * a);
+        break;
+      case 2:  // theta
+        x[c] = (std::sin(b) - std::sin(a) + a * std::cos(a) - b * std::cos(b)) /
+               (std::cos(a) - std::cos(b));
+        break;
+      default:
+        x[c] = 0.5 * (a + b);
+    }
+  }
+}
+
+Axis axis_from_law(int kind, const Law& L, long c_first, long c_last) {
+  Axis a;
+  a.kind = kind;
+  a.spacing = L.spacing;
+  a.n = int(c_last - c_first + 1);
+  a.F.resize(a.n + 3);
+  for (int q = 0; q < a.n + 3; ++q) a.F[q] = L.face(c_first - 2 + q);
+  a.centres();
+  return a;
+}
+
+Axis coarse_axis(const Axis& f) {
+  Axis c;
+  c.kind = f.kind;
+  c.spacing = f.spacing;
+  c.n = f.n / 2;
+  c.F.resize(c.n + 3);
+  for (int q = 0; q <= c.n; ++q) c.F[q + 1] = f.F[1 + 2 * q];
+  if (f.spacing == LOGS && (f.kind == 0 || f.kind == 1)) {
+    double qr = c.F[2] / c.F[1];
+    c.F[0] = c.F[1] / qr;
+    c.F[c.n + 2] = c.F[c.n + 1] * qr;
+  } else {
+    double d = c.F[2] - c.F[1];
+    c.F[0] = c.F[1] - d;
+    c.F[c.n + 2] = c.F[c.n + 1] + d;
+  }
+  c.centres();
+  return c;
+}
+
+static double sin_face(double th) {
+  if (std::fabs(th) < kPoleTol || std::fabs(th - kPi) < kPoleTol) return 0.0;
+  return std::sin(th);
+}
+
+bool PlaneGeo::has_inner() const { return r.F[1] > 0.0; }
+bool PlaneGeo::has_lower() const { return geometry == CYL || sin_face(t.F[1]) != 0.0; }
+bool PlaneGeo::has_upper() const { return geometry == CYL || sin_face(t.F[t.n + 1]) != 0.0; }
+
+double PlaneGeo::s2(int m) const {
+  double s = std::sin(double(m) * kPi / double(n_phi)) / (kPi / double(n_phi));
+  return s * s;
+}
+
+void PlaneGeo::build() {
+  const int nr = r.n, nt = t.n;
+  aE.assign(nr + 2, 0.0); aW.assign(nr + 2, 0.0);
+  P.assign(nr + 2, 1.0); Q.assign(nr + 2, 0.0); vr.assign(nr + 2, 0.0);
+  aN.assign(nt + 2, 0.0); aS.assign(nt + 2, 0.0);
+  T.assign(nt + 2, 1.0); vt.assign(nt + 2, 0.0);
+  for (int c = 0; c < nr + 2; ++c) {
+    double lo = r.F[c], hi = r.F[c + 1];
+    if (geometry == SPH) {  // nabla^2_r and R_i (Sec. 2.1.1)
+      double v3 = hi * hi * hi - lo * lo * lo;
+      if (c + 1 < nr + 2) aE[c] = 3.0 * hi * hi / v3 / (r.x[c + 1] - r.x[c]);
+      if (c > 0) aW[c] = 3.0 * lo * lo / v3 / (r.x[c] - r.x[c - 1]);
+      P[c] = Q[c] = 1.5 / r.x[c] * (hi * hi - lo * lo) / v3;
+      vr[c] = v3 / 3.0;
+    } else {  // nabla^2_R and W_i (Sec. 2.1.2)
+      double v2 = hi * hi - lo * lo;
+      if (c + 1 < nr + 2) aE[c] = 2.0 * hi / v2 / (r.x[c + 1] - r.x[c]);
+      if (c > 0) aW[c] = 2.0 * lo / v2 / (r.x[c] - r.x[c - 1]);
+      P[c] = 1.0;
+      Q[c] = 2.0 / (r.x[c] * (hi + lo));
+      vr[c] = v2 / 2.0;
+    }
+  }
+  for (int c = 0; c < nt + 2; ++c) {
+    double lo = t.F[c], hi = t.F[c + 1];
+    if (geometry == SPH) {  // nabla^2_theta / R_i and T_j
+      double vc = std::cos(lo) - std::cos(hi);
+      if (c + 1 < nt + 2) aN[c] = sin_face(hi) / vc / (t.x[c + 1] - t.x[c]);
+      if (c > 0) aS[c] = sin_face(lo) / vc / (t.x[c] - t.x[c - 1]);
+      T[c] = (hi - lo) / (std::sin(t.x[c]) * vc);
+      vt[c] = vc;
+    } else {  // nabla^2_z
+      double dz = hi - lo;
+      if (c + 1 < nt + 2) aN[c] = 1.0 / dz / (t.x[c + 1] - t.x[c]);
+      if (c > 0) aS[c] = 1.0 / dz / (t.x[c] - t.x[c - 1]);
+      T[c] = 1.0;
+      vt[c] = dz;
+    }
+  }
+}
+
+// App. A: mu_1 = sum (a_j + c_j) cos(pi delta_j / L) w_j / sum b_j w_j,
+// omega = 2 / (1 + sqrt(1 - mu_1^2)), x_0 and x_{N+1} the boundary points.
+double wkb_omega(const double* a, const double* c, const double* b, const double* x, int N) {
+  double L = x[N + 1] - x[0], num = 0.0, den = 0.0;
+  for (int j = 1; j <= N; ++j) {
+    double s = std::sin(kPi * (x[j] - x[0]) / L);
+    double w = s * s;
+    num += (a[j - 1] + c[j - 1]) * std::cos(kPi * (x[j] - x[j - 1]) / L) * w;
+    den += b[j - 1] * w;
+  }
+  double rho = std::min(std::fabs(num / den), 1.0);
+  return 2.0 / (1.0 + std::sqrt(1.0 - rho * rho));
+}
+
+static bool invert(std::vector<double>& A, int n) {  // Gauss-Jordan, partial pivoting
+  std::vector<double> I(size_t(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) I[size_t(i) * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int rr = col + 1; rr < n; ++rr)
+      if (std::fabs(A[size_t(rr) * n + col]) > std::fabs(A[size_t(piv) * n + col])) piv = rr;
+    if (A[size_t(piv) * n + col] == 0.0) return false;
+    if (piv != col)
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[size_t(piv) * n + k], A[size_t(col) * n + k]);
+        std::swap(I[size_t(piv) * n + k], I[size_t(col) * n + k]);
+      }
+    double d = 1.0 / A[size_t(col) * n + col];
+    for (int k = 0; k < n; ++k) { A[size_t(col) * n + k] *= d; I[size_t(col) * n + k] *= d; }
+    for (int rr = 0; rr < n; ++rr) {
+      if (rr == col) continue;
+      double fct = A[size_t(rr) * n + col];
+      if (fct == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        A[size_t(rr) * n + k] -= fct * A[size_t(col) * n + k];
+        I[size_t(rr) * n + k] -= fct * I[size_t(col) * n + k];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,
+                     Hierarchy& H, std::string& err) {
+  H.lv.clear();
+  PlaneGeo g = fine;
+  g.build();
+  while (true) {
+    LevelHost L;
+    L.g = g;
+    if (neumann) L.g.aW[1] = 0.0;
+    H.lv.push_back(L);
+    if (std::min(g.r.n, g.t.n) <= 4) break;
+    if (g.r.n % 2 || g.t.n % 2) { err = "grid sizes must be powers of two"; return false; }
+    PlaneGeo c;
+    c.geometry = g.geometry; c.n_phi = g.n_phi; c.G = g.G;
+    c.r = coarse_axis(g.r);
+    c.t = coarse_axis(g.t);
+    c.build();
+    g = c;
+  }
+  const int nlev = int(H.lv.size());
+  const int M = int(modes.size());
+  for (int l = 0; l < nlev; ++l) {
+    LevelHost& L = H.lv[l];
+    const PlaneGeo& p = L.g;
+    const int nr = p.r.n, nt = p.t.n, NR = nr + 2, NT = nt + 2;
+    L.rtab.assign(size_t(RT_N) * NR, 0.0);
+    L.ttab.assign(size_t(TT_N) * NT, 0.0);
+    for (int i = 0; i < NR; ++i) {
+      L.rtab[RT_AE * NR + i] = p.aE[i];
+      L.rtab[RT_AW * NR + i] = p.aW[i];
+      L.rtab[RT_P * NR + i] = p.P[i];
+      L.rtab[RT_Q * NR + i] = p.Q[i];
+      L.rtab[RT_DR * NR + i] = -(p.aE[i] + p.aW[i]);
+      L.rtab[RT_V * NR + i] = p.vr[i];
+    }
+    for (int j = 0; j < NT; ++j) {
+      L.ttab[TT_AN * NT + j] = p.aN[j];
+      L.ttab[TT_AS * NT + j] = p.aS[j];
+      L.ttab[TT_T * NT + j] = p.T[j];
+      L.ttab[TT_DT * NT + j] = -(p.aN[j] + p.aS[j]);
+      L.ttab[TT_V * NT + j] = p.vt[j];
+    }
+    // restriction (Sec. 3.1): weight = overlap area of the fine cell in the
+    // (r^2, theta) or (R, z) plane, normalised over the four children
+    if (l + 1 < nlev) {
+      auto ra = [&](int i) {
+        double a = p.r.F[i], b = p.r.F[i + 1];
+        return p.geometry == SPH ? std::fabs(b * b - a * a) : std::fabs(b - a);
+      };
+      auto tb = [&](int j) { return std::fabs(p.t.F[j + 1] - p.t.F[j]); };
+      for (int i = 1; i <= nr; ++i) {
+        int s = (i % 2) ? i + 1 : i - 1;
+        L.rtab[RT_RW * NR + i] = ra(i) / (ra(i) + ra(s));
+      }
+      for (int j = 1; j <= nt; ++j) {
+        int s = (j % 2) ? j + 1 : j - 1;
+        L.ttab[TT_RW * NT + j] = tb(j) / (tb(j) + tb(s));
+      }
+      // prolongation weights: bilinear in (r^2, theta) or (R, z) between the
+      // two coarse centres that bracket each fine centre
+      const PlaneGeo& c = H.lv[l + 1].g;
+      auto xi = [&](const Axis& a, int k) { return p.geometry == SPH ? a.x[k] * a.x[k] : a.x[k]; };
+      for (int i = 1; i <= nr; ++i) {
+        int I1 = (i % 2) ? (i + 1) / 2 - 1 : i / 2, I2 = I1 + 1;
+        double den = std::fabs(xi(c.r, I2) - xi(c.r, I1));
+        L.rtab[RT_P1 * NR + i] = std::fabs(xi(c.r, I2) - xi(p.r, i)) / den;
+        L.rtab[RT_P2 * NR + i] = std::fabs(xi(c.r, I1) - xi(p.r, i)) / den;
+      }
+      for (int j = 1; j <= nt; ++j) {
+        int J1 = (j % 2) ? (j + 1) / 2 - 1 : j / 2, J2 = J1 + 1;
+        double den = std::fabs(c.t.x[J2] - c.t.x[J1]);
+        L.ttab[TT_P1 * NT + j] = std::fabs(c.t.x[J2] - p.t.x[j]) / den;
+        L.ttab[TT_P2 * NT + j] = std::fabs(c.t.x[J1] - p.t.x[j]) / den;
+      }
+    }
+    // coarse-ghost rules used when this level is prolongated from
+    if (neumann) L.gL = GH_EVEN;
+    else if (!p.has_inner()) L.gL = (p.geometry == CYL) ? GH_PARITY : GH_EVEN;
+    else L.gL = GH_ZERO;
+    L.gR = GH_ZERO;
+    L.gB = p.has_lower() ? GH_ZERO : GH_PARITY;
+    L.gT = p.has_upper() ? GH_ZERO : GH_PARITY;
+    // App. A relaxation parameters per line and mode
+    L.om_r.assign(size_t(M) * nt, 1.0);
+    L.om_t.assign(size_t(M) * nr, 1.0);
+    std::vector<double> a(std::max(nr, nt)), cc(std::max(nr, nt)), b(std::max(nr, nt));
+    for (int k = 0; k < M; ++k) {
+      int m = modes[k];
+      for (int j = 1; j <= nt; ++j) {
+        for (int i = 1; i <= nr; ++i) {
+          a[i - 1] = L.g.aW[i];
+          cc[i - 1] = L.g.aE[i];
+          b[i - 1] = L.g.diag(m, i, j);
+        }
+        L.om_r[size_t(k) * nt + j - 1] = wkb_omega(a.data(), cc.data(), b.data(), p.r.x.data(), nr);
+      }
+      for (int i = 1; i <= nr; ++i) {
+        for (int j = 1; j <= nt; ++j) {
+          a[j - 1] = p.P[i] * p.aS[j];
+          cc[j - 1] = p.P[i] * p.aN[j];
+          b[j - 1] = L.g.diag(m, i, j);
+        }
+        L.om_t[size_t(k) * nr + i - 1] = wkb_omega(a.data(), cc.data(), b.data(), p.t.x.data(), nt);
+      }
+    }
+  }
+  // coarsest level: dense inverse of L_m (zero ghosts) per mode
+  const LevelHost& C = H.lv.back();
+  const int nr = C.g.r.n, nt = C.g.t.n, nc = nr * nt;
+  H.nc = nc;
+  H.coarse_inv.assign(size_t(M) * nc * nc, 0.0);
+  std::vector<double> A(size_t(nc) * nc);
+  for (int k = 0; k < M; ++k) {
+    std::fill(A.begin(), A.end(), 0.0);
+    int m = modes[k];
+    for (int j = 1; j <= nt; ++j)
+      for (int i = 1; i <= nr; ++i) {
+        int row = (j - 1) * nr + (i - 1);
+        A[size_t(row) * nc + row] = C.g.diag(m, i, j);
+        if (i < nr) A[size_t(row) * nc + row + 1] = C.g.aE[i];
+        if (i > 1) A[size_t(row) * nc + row - 1] = C.g.aW[i];
+        if (j < nt) A[size_t(row) * nc + row + nr] = C.g.P[i] * C.g.aN[j];
+        if (j > 1) A[size_t(row) * nc + row - nr] = C.g.P[i] * C.g.aS[j];
+      }
+    if (!invert(A, nc)) { err = "singular coarsest-level operator"; return false; }
+    std::copy(A.begin(), A.end(), H.coarse_inv.begin() + size_t(k) * nc * nc);
+  }
+  return true;
+}
+
+std::vector<BPoint> boundary_points(const PlaneGeo& g) {
+  std::vector<BPoint> out;
+  const int nr = g.r.n, nt = g.t.n;
+  const double dphi = 2.0 * kPi / g.n_phi;
+  const double inv4piG = 1.0 / (4.0 * kPi * g.G);
+  auto dv = [&](int i, int j) { return g.vr[i] * g.vt[j] * dphi; };
+  if (g.has_inner())
+    for (int j = 1; j <= nt; ++j)
+      out.push_back({'L', 0, j, 1, j, g.aE[0] * inv4piG, g.aW[1], dv(0, j)});
+  for (int j = 1; j <= nt; ++j)
+    out.push_back({'R', nr + 1, j, nr, j, g.aW[nr + 1] * inv4piG, g.aE[nr], dv(nr + 1, j)});
+  if (g.has_lower())
+    for (int i = 1; i <= nr; ++i)
+      out.push_back({'B', i, 0, i, 1, g.P[i] * g.aN[0] * inv4piG, g.P[i] * g.aS[1], dv(i, 0)});
+  if (g.has_upper())
+    for (int i = 1; i <= nr; ++i)
+      out.push_back({'T', i, nt + 1, i, nt, g.P[i] * g.aS[nt + 1] * inv4piG, g.P[i] * g.aN[nt],
+                     dv(i, nt + 1)});
+  return out;
+}
+
+}  // namespace ps

@@ -1,0 +1,90 @@
+// Host-side plan of a solver: grid geometry, multigrid level tables, per-line
+// relaxation parameters, coarsest-level inverses and the boundary-point list.
+// Everything here runs once in psolve_create; nothing here is on the solve path.
+#pragma once
+#include <cmath>
+#include <string>
+#include <vector>
+
+namespace ps {
+
+enum { SPH = 0, CYL = 1 };
+enum { UNI = 0, LOGS = 1 };
+enum { GH_ZERO = 0, GH_PARITY = 1, GH_EVEN = 2 };
+
+// radial / polar table ids inside a level's packed table block
+enum { RT_AE = 0, RT_AW, RT_P, RT_Q, RT_DR, RT_V, RT_RW, RT_P1, RT_P2, RT_N };
+enum { TT_AN = 0, TT_AS, TT_T, TT_DT, TT_V, TT_RW, TT_P1, TT_P2, TT_N };
+
+// Grid law of one axis: face k sits at lo + k (hi-lo)/n (uniform) or
+// lo (hi/lo)^(k/n) (log).  Cell c spans faces c-1 .. c (cells 1..n inside).
+struct Law {
+  double lo = 0, hi = 1;
+  int n = 1;
+  int spacing = UNI;
+  double face(long k) const {
+    if (spacing == LOGS) return lo * std::pow(hi / lo, double(k) / double(n));
+    return lo + double(k) * ((hi - lo) / double(n));
+  }
+};
+
+// One axis: n cells plus one ghost each side; F[c] c = 0..n+2, x[c] c = 0..n+1.
+struct Axis {
+  int kind = 0;  // 0 r_sph, 1 r_cyl, 2 theta, 3 z
+  int n = 0;
+  int spacing = UNI;
+  std::vector<double> F, x;
+  void centres();
+};
+Axis axis_from_law(int kind, const Law& L, long c_first, long c_last);  // cells c_first..c_last
+Axis coarse_axis(const Axis& a);
+
+// 2-D plane tables (double), indices as in the paper: cell 1..n, ghosts 0, n+1.
+struct PlaneGeo {
+  int geometry = SPH;
+  Axis r, t;
+  int n_phi = 4;
+  double G = 1.0;
+  std::vector<double> aE, aW, P, Q, aN, aS, T, vr, vt;
+  bool has_inner() const;
+  bool has_lower() const;
+  bool has_upper() const;
+  void build();
+  double s2(int m) const;
+  double diag(int m, int i, int j) const {
+    return -(aE[i] + aW[i]) - P[i] * (aN[j] + aS[j]) - s2(m) * Q[i] * T[j];
+  }
+};
+
+struct LevelHost {
+  PlaneGeo g;
+  std::vector<double> rtab, ttab;   // packed RT_N x (nr+2), TT_N x (nt+2)
+  std::vector<double> om_r, om_t;   // [M][nt], [M][nr]
+  int gL = 0, gR = 0, gB = 0, gT = 0;
+};
+
+struct Hierarchy {
+  std::vector<LevelHost> lv;
+  std::vector<double> coarse_inv;   // [M][nc][nc] inverse of L_m on the coarsest level
+  int nc = 0;
+};
+
+// Build levels down to min(n_r, n_t) == 4; neumann zeroes the inner radial
+// face coefficient on every level.  modes: list of azimuthal mode numbers
+// whose omega tables / coarse inverses are needed (index = plane-mode slot).
+bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,
+                     Hierarchy& H, std::string& err);
+
+double wkb_omega(const double* a, const double* c, const double* b, const double* x, int N);
+
+struct BPoint {
+  char side;       // 'L','R','B','T'
+  int i, j;        // ghost cell indices
+  int ai, aj;      // adjacent domain cell
+  double sigma_coef;   // screening-mass coefficient incl. 1/(4 pi G)
+  double couple;       // coefficient of the ghost value in L at the adjacent cell
+  double dV;           // 3-D volume of the ghost cell
+};
+std::vector<BPoint> boundary_points(const PlaneGeo& g);
+
+}  // namespace ps

@@ -1,0 +1,203 @@
+// Batched multigrid solver: level upload, V-cycle schedule and the outer
+// refinement loop with per-mode retirement (Sec. 3, App. B; Sec. 5.2's
+// mode-by-mode iteration replaced by a batch that drops converged modes).
+#include "solver.h"
+
+#include <cstring>
+
+namespace ps {
+
+void* Arena::get(size_t n) {
+  if (n == 0) n = 16;
+  n = (n + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (alloc_fn) {
+    p = alloc_fn(n, user);
+  } else if (cudaMalloc(&p, n) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) {
+    blocks.push_back(p);
+    bytes += n;
+  }
+  return p;
+}
+
+void Arena::release_all() {
+  for (void* p : blocks) {
+    if (free_fn) free_fn(p, user);
+    else cudaFree(p);
+  }
+  blocks.clear();
+  bytes = 0;
+}
+
+template <typename X>
+static X* upload(Arena& A, const std::vector<X>& v) {
+  X* d = static_cast<X*>(A.get(v.size() * sizeof(X)));
+  if (d && !v.empty()) cudaMemcpy(d, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice);
+  return d;
+}
+
+static std::vector<float> to_f(const std::vector<double>& v) {
+  return std::vector<float>(v.begin(), v.end());
+}
+
+bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,
+                    const std::vector<int>& plane_slot, int mp, const MGOptions& o,
+                    std::string& err) {
+  opt = o;
+  max_planes = mp;
+  if (!build_hierarchy(fine, neumann, modes, H, err)) return false;
+  const int nl = int(H.lv.size());
+  lv.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    const LevelHost& h = H.lv[l];
+    LevelDev& d = lv[l];
+    d.nr = h.g.r.n;
+    d.nt = h.g.t.n;
+    d.rd = upload(A, h.rtab);
+    d.td = upload(A, h.ttab);
+    d.rf = upload(A, to_f(h.rtab));
+    d.tf = upload(A, to_f(h.ttab));
+    d.omr_d = upload(A, h.om_r);
+    d.omt_d = upload(A, h.om_t);
+    d.omr_f = upload(A, to_f(h.om_r));
+    d.omt_f = upload(A, to_f(h.om_t));
+    d.gL = h.gL; d.gR = h.gR; d.gB = h.gB; d.gT = h.gT;
+    if (!d.rd || !d.omt_f) { err = "out of device memory"; return false; }
+  }
+  std::vector<double> s2(modes.size());
+  for (size_t k = 0; k < modes.size(); ++k) s2[k] = fine.s2(modes[k]);
+  d_s2 = upload(A, s2);
+  d_s2f = upload(A, to_f(s2));
+  d_mode = upload(A, modes);
+  d_slot = plane_slot.empty() ? nullptr : upload(A, plane_slot);
+  d_inv = upload(A, H.coarse_inv);
+  const size_t vb = vbytes();
+  e.assign(nl, nullptr);
+  f.assign(nl, nullptr);
+  for (int l = 0; l < nl; ++l) {
+    const size_t n = size_t(mp) * lv[l].nr * lv[l].nt * vb;
+    e[l] = A.get(n);
+    f[l] = A.get(n);
+    if (!e[l] || !f[l]) { err = "out of device memory"; return false; }
+  }
+  const int nblk = residual_blocks(lv[0].nr, lv[0].nt);
+  d_act = static_cast<int*>(A.get(sizeof(int) * mp));
+  d_nact = static_cast<int*>(A.get(sizeof(int)));
+  d_part = static_cast<double4*>(A.get(sizeof(double4) * size_t(mp) * nblk));
+  d_psum = static_cast<double4*>(A.get(sizeof(double4) * mp));
+  d_cnt = static_cast<int*>(A.get(sizeof(int) * mp));
+  d_cycles = static_cast<int*>(A.get(sizeof(int) * mp));
+  d_status = static_cast<int*>(A.get(sizeof(int) * mp));
+  d_nf2 = static_cast<double2*>(A.get(sizeof(double2) * mp));
+  d_nr2 = static_cast<double2*>(A.get(sizeof(double2) * mp));
+  d_iter = static_cast<int*>(A.get(sizeof(int)));
+  d_cont = static_cast<int*>(A.get(sizeof(int)));
+  d_fmax2 = static_cast<double*>(A.get(sizeof(double)));
+  if (!d_fmax2 || !d_cnt) { err = "out of device memory"; return false; }
+  cudaMemset(d_cnt, 0, sizeof(int) * mp);
+  if (cudaMallocHost(&h_cont, sizeof(int)) != cudaSuccess) { err = "pinned allocation failed"; return false; }
+  batch.act = d_act;
+  batch.nact = d_nact;
+  batch.slot = d_slot;
+  batch.mode = d_mode;
+  batch.s2d = d_s2;
+  batch.s2f = d_s2f;
+  batch.max_planes = mp;
+  S.nf2 = d_nf2;
+  S.nr2 = d_nr2;
+  S.cycles = d_cycles;
+  S.status = d_status;
+  S.iter = d_iter;
+  S.cont = d_cont;
+  S.fmax2 = d_fmax2;
+  return cudaGetLastError() == cudaSuccess;
+}
+
+// ---- typed dispatch -----------------------------------------------------------
+void MGSolver::smooth(int l, void* ee, const void* ff, int cycles, bool zi, cudaStream_t st) {
+  if (opt.precision)
+    launch_smooth<float>(lv[l], batch, (float2*)ee, (const float2*)ff, cycles, opt.n_sor, zi, st);
+  else
+    launch_smooth<double>(lv[l], batch, (double2*)ee, (const double2*)ff, cycles, opt.n_sor, zi, st);
+}
+void MGSolver::restrict_(int l, const void* ee, const void* ff, void* fc, cudaStream_t st) {
+  if (opt.precision)
+    launch_restrict<float>(lv[l], lv[l + 1], batch, (const float2*)ee, (const float2*)ff, (float2*)fc, st);
+  else
+    launch_restrict<double>(lv[l], lv[l + 1], batch, (const double2*)ee, (const double2*)ff, (double2*)fc, st);
+}
+void MGSolver::prolong(int l, void* ee, const void* ec, cudaStream_t st) {
+  if (opt.precision)
+    launch_prolong<float>(lv[l], lv[l + 1], batch, (float2*)ee, (const float2*)ec, st);
+  else
+    launch_prolong<double>(lv[l], lv[l + 1], batch, (double2*)ee, (const double2*)ec, st);
+}
+void MGSolver::coarse(const void* fc, void* ec, cudaStream_t st) {
+  const LevelDev& C = lv.back();
+  if (opt.precision)
+    launch_coarse<float>(C, batch, d_inv, H.nc, (const float2*)fc, (float2*)ec, st);
+  else
+    launch_coarse<double>(C, batch, d_inv, H.nc, (const double2*)fc, (double2*)ec, st);
+}
+void MGSolver::residual(const double2* ff, const double2* u, cudaStream_t st) {
+  if (opt.precision)
+    launch_residual<float>(lv[0], batch, ff, u, (float2*)f[0], d_part, d_psum, d_cnt, st);
+  else
+    launch_residual<double>(lv[0], batch, ff, u, (double2*)f[0], d_part, d_psum, d_cnt, st);
+}
+
+// One V-cycle on the error equation L e_0 = f_0 (f_0 = FP64 residual in the
+// buffer precision), e_0 starting from zero (Sec. 3: pre-smoothing,
+// defect restriction, coarse correction, prolongation, post-smoothing).
+void MGSolver::vcycle(cudaStream_t st) {
+  const int nl = int(lv.size());
+  for (int l = 0; l < nl - 1; ++l) {
+    if (opt.nu1 > 0) smooth(l, e[l], f[l], opt.nu1, true, st);
+    else cudaMemsetAsync(e[l], 0, size_t(max_planes) * lv[l].nr * lv[l].nt * vbytes(), st);
+    restrict_(l, e[l], f[l], f[l + 1], st);
+  }
+  coarse(f[nl - 1], e[nl - 1], st);
+  for (int l = nl - 2; l >= 0; --l) {
+    prolong(l, e[l], e[l + 1], st);
+    if (opt.nu2 > 0) smooth(l, e[l], f[l], opt.nu2, false, st);
+  }
+}
+
+void MGSolver::init_loop(cudaStream_t st) { launch_init_active(d_act, d_nact, max_planes, S, st); }
+
+void MGSolver::loop_body(const double2* ff, double2* u, double tol, cudaStream_t st, int use_cond,
+                         unsigned long long cond) {
+  residual(ff, u, st);
+  launch_retire(d_act, d_nact, d_psum, S, tol, opt.max_cycles, opt.stagnation, use_cond, cond, st);
+  vcycle(st);
+  if (opt.precision)
+    launch_update<float>(lv[0], batch, u, (const float2*)e[0], st);
+  else
+    launch_update<double>(lv[0], batch, u, (const double2*)e[0], st);
+}
+
+int MGSolver::eager_solve(const double2* ff, double2* u, double tol, cudaStream_t st,
+                          std::string& err) {
+  init_loop(st);
+  for (int it = 0; it <= opt.max_cycles + 1; ++it) {
+    residual(ff, u, st);
+    launch_retire(d_act, d_nact, d_psum, S, tol, opt.max_cycles, opt.stagnation, 0, 0, st);
+    cudaMemcpyAsync(h_cont, d_cont, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      err = cudaGetErrorString(cudaGetLastError());
+      return -2;
+    }
+    if (!*h_cont) return 0;
+    vcycle(st);
+    if (opt.precision)
+      launch_update<float>(lv[0], batch, u, (const float2*)e[0], st);
+    else
+      launch_update<double>(lv[0], batch, u, (const double2*)e[0], st);
+  }
+  return 0;
+}
+
+}  // namespace ps

@@ -1,0 +1,81 @@
+// Batched per-mode multigrid solver on the device (host-side orchestration).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+namespace ps {
+
+// Device memory owner with optional user allocation hooks.
+struct Arena {
+  void* (*alloc_fn)(size_t, void*) = nullptr;
+  void (*free_fn)(void*, void*) = nullptr;
+  void* user = nullptr;
+  std::vector<void*> blocks;
+  size_t bytes = 0;
+  void* get(size_t n);
+  void release_all();
+};
+
+struct MGOptions {
+  int precision = 1;   // 0 FP64, 1 mixed (FP32 V-cycles inside FP64 refinement)
+  int nu1 = 2, nu2 = 2, n_sor = 2;
+  int max_cycles = 100;
+  int stagnation = 0;  // retire planes whose residual stops falling
+};
+
+class MGSolver {
+ public:
+  // fine: plane geometry; modes[s]: azimuthal mode number of slot s;
+  // plane_slot (size max_planes, may be empty = identity); neumann: inner
+  // radial face carries a prescribed flux (zero coefficient on all levels).
+  bool init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,
+            const std::vector<int>& plane_slot, int max_planes, const MGOptions& o,
+            std::string& err);
+  // Solve L u = f for all planes (u holds the initial guess).  Enqueued on
+  // st; with cond_handle (use_cond) the loop is a graph WHILE body; in eager
+  // mode the host reads the continue flag each iteration.
+  void init_loop(cudaStream_t st);
+  void loop_body(const double2* f, double2* u, double tol, cudaStream_t st, int use_cond,
+                 unsigned long long cond);
+  int eager_solve(const double2* f, double2* u, double tol, cudaStream_t st, std::string& err);
+  void vcycle(cudaStream_t st);
+  // results (device arrays, per plane)
+  int* d_cycles = nullptr;
+  int* d_status = nullptr;
+  double2* d_nf2 = nullptr;
+  double2* d_nr2 = nullptr;
+  int* d_iter = nullptr;
+  int* d_cont = nullptr;
+  int* h_cont = nullptr;   // pinned
+  Hierarchy H;
+  std::vector<LevelDev> lv;
+  Batch batch{};
+  MGOptions opt;
+  int max_planes = 0;
+  // level buffers (T2 of the precision): e[l], f[l]
+  std::vector<void*> e, f;
+  // stage helpers on explicit buffers
+  void smooth(int level, void* e, const void* f, int cycles, bool zero_init, cudaStream_t st);
+  void restrict_(int level, const void* e, const void* f, void* fc, cudaStream_t st);
+  void prolong(int level, void* e, const void* ec, cudaStream_t st);
+  void coarse(const void* fc, void* ec, cudaStream_t st);
+  void residual(const double2* f, const double2* u, cudaStream_t st);
+  int* d_act = nullptr;
+  int* d_nact = nullptr;
+  int* d_slot = nullptr;
+  int* d_mode = nullptr;
+  double* d_s2 = nullptr;
+  float* d_s2f = nullptr;
+  double* d_inv = nullptr;
+  double4* d_part = nullptr;
+  double4* d_psum = nullptr;
+  int* d_cnt = nullptr;
+  double* d_fmax2 = nullptr;
+  RetireState S{};
+  int precision_of_buffers = 1;
+  size_t vbytes() const { return opt.precision ? sizeof(float2) : sizeof(double2); }
+};
+
+}  // namespace ps

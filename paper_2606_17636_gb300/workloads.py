@@ -74,6 +74,9 @@ def _clumps(sp, rng, n=4):
     for _ in range(n):
         if sp["geometry"] == SPHERICAL:
             lo, hi = max(0.3, sp["r_in"] * 3), min(5.0, sp["r_out"] / 2)
+            if hi <= lo:       # narrow shells: clumps in the middle half of the shell
+                d = sp["r_out"] - sp["r_in"]
+                lo, hi = sp["r_in"] + 0.25 * d, sp["r_in"] + 0.75 * d
             rc = np.exp(rng.uniform(np.log(lo), np.log(hi)))
             ct = rng.uniform(-0.7, 0.7)
             pc = rng.uniform(0.0, 2 * np.pi)

@@ -1,0 +1,128 @@
+"""Stage-by-stage parity of the CUDA path with the FP64 oracle (through the
+C ABI stage entry points)."""
+import numpy as np
+import pytest
+
+from gpu_helpers import SMALL, clumps, oracle_plane, to_gpu, to_oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ps():
+    import paper_2606_17636_gb300 as m
+    m.lib()
+    return m
+
+
+def _solver(ps, key, precision):
+    return ps.Solver.from_spec(SMALL[key], precision=precision, use_graph=False)
+
+
+@pytest.mark.parametrize("key", list(SMALL))
+def test_forward_and_inverse_transforms(ps, key):
+    from oracle import dft
+    sp = SMALL[key]
+    s = _solver(ps, key, ps.FP64)
+    rho = np.random.default_rng(1).standard_normal((sp["n_r"], sp["n_tz"], sp["n_phi"]))
+    f = s.stage_forward(torch.from_numpy(rho).cuda()).cpu().numpy()
+    ref = 4 * np.pi * dft.forward(rho)
+    assert np.abs(to_oracle(f) - ref).max() <= 1e-13 * np.abs(ref).max()
+    spec = np.random.default_rng(2).standard_normal(ref.shape) + 1j * np.random.default_rng(3).standard_normal(ref.shape)
+    back = s.stage_inverse(torch.from_numpy(to_gpu(spec)).cuda()).cpu().numpy()
+    ref2 = dft.inverse(spec, sp["n_phi"])
+    assert np.abs(back - ref2).max() <= 1e-13 * np.abs(ref2).max()
+    s.close()
+
+
+def _rand_planes(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+@pytest.mark.parametrize("key", list(SMALL))
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-5)])
+@pytest.mark.parametrize("level", [0, 1])
+def test_smooth_restrict_prolong(ps, key, precision, tol, level):
+    from oracle import mg
+    sp = SMALL[key]
+    s = _solver(ps, key, precision)
+    p = oracle_plane(sp)
+    H = mg.Hierarchy(p)
+    nr, nt, M = sp["n_r"] >> level, sp["n_tz"] >> level, s.n_modes
+    cdt = torch.complex128 if precision == 0 else torch.complex64
+    e0 = _rand_planes((M, nt, nr), 10 + level)
+    f0 = _rand_planes((M, nt, nr), 20 + level)
+    # smoothing: one cycle of Algorithm 1
+    e = torch.from_numpy(e0).to(cdt).cuda()
+    f = torch.from_numpy(f0).to(cdt).cuda()
+    got = s.stage_smooth(level, e.clone(), f, 1).cpu().numpy().astype(np.complex128)
+    ref = np.zeros_like(got)
+    for m in range(M):
+        u = np.zeros((nr + 2, nt + 2), complex)
+        u[1:-1, 1:-1] = e.cpu().numpy()[m].T
+        H.smooth(level, m, u, f.cpu().numpy()[m].T.astype(complex), 1)
+        ref[m] = u[1:-1, 1:-1].T
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    # defect restriction
+    gotc = s.stage_restrict(level, e, f).cpu().numpy().astype(np.complex128)
+    for m in range(M):
+        u = np.zeros((nr + 2, nt + 2), complex)
+        u[1:-1, 1:-1] = e.cpu().numpy()[m].T
+        r = H.residual(level, m, u, f.cpu().numpy()[m].T.astype(complex))
+        refc = H.restrict(level, r).T
+        assert np.abs(gotc[m] - refc).max() <= tol * np.abs(refc).max()
+    # prolongation + correction
+    ec = torch.from_numpy(_rand_planes(gotc.shape, 30)).to(cdt).cuda()
+    gotp = s.stage_prolong(level, e.clone(), ec).cpu().numpy().astype(np.complex128)
+    for m in range(M):
+        refp = e.cpu().numpy()[m].astype(complex) + H.prolong(level, m, ec.cpu().numpy()[m].T.astype(complex)).T
+        assert np.abs(gotp[m] - refp).max() <= tol * np.abs(refp).max()
+    s.close()
+
+
+@pytest.mark.parametrize("key", list(SMALL))
+def test_mg_solve_reaches_direct_solution_and_counts_cycles(ps, key):
+    import scipy.sparse.linalg as spla
+
+    from oracle import mg, operator
+    sp = SMALL[key]
+    s = _solver(ps, key, ps.FP64)
+    p = oracle_plane(sp)
+    M = s.n_modes
+    f = _rand_planes((M, sp["n_tz"], sp["n_r"]), 7)
+    u, cyc, rc = s.stage_mg_solve(torch.from_numpy(f).cuda(), tol=1e-12)
+    assert rc == 0
+    u = u.cpu().numpy()
+    H = mg.Hierarchy(p)
+    for m in range(M):
+        A = operator.matrix(p, m).tocsc()
+        b = f[m].T
+        x = spla.spsolve(A, operator.to_vec(b.real)) + 1j * spla.spsolve(A, operator.to_vec(b.imag))
+        ref = operator.from_vec(x, sp["n_r"], sp["n_tz"]).T
+        assert np.abs(u[m] - ref).max() <= 1e-10 * np.abs(ref).max()
+        if m in (0, 1, M - 1):
+            _, c_or, _ = H.solve(m, b, 1e-12)
+            assert abs(cyc[m] - c_or) <= 1, (m, cyc[m], c_or)
+    s.close()
+
+
+@pytest.mark.parametrize("key", list(SMALL))
+def test_screening_boundary_and_dgf(ps, key):
+    from oracle import dgf, james
+    sp = SMALL[key]
+    s = _solver(ps, key, ps.FP64)
+    p = oracle_plane(sp)
+    gt = dgf.dgf(p)
+    got_gt = s.dgf().cpu().numpy()
+    assert got_gt.shape == gt.shape
+    assert np.abs(got_gt - gt).max() <= 1e-9 * np.abs(gt).max()
+    psi = _rand_planes((s.n_modes, sp["n_tz"], sp["n_r"]), 5)
+    sig = s.stage_screening(torch.from_numpy(psi).cuda()).cpu().numpy()
+    ref_sig = np.stack([james.screening_mass(p, psi[m].T) for m in range(s.n_modes)])
+    assert np.abs(sig - ref_sig).max() <= 1e-13 * np.abs(ref_sig).max()
+    th = s.stage_boundary(torch.from_numpy(ref_sig).cuda()).cpu().numpy()
+    ref_th = np.einsum("mts,ms->mt", got_gt, ref_sig)
+    assert np.abs(th - ref_th).max() <= 1e-13 * np.abs(ref_th).max()
+    s.close()
