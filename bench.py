@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Throughput of the spectral-multigrid Poisson solve.
+
+Workload: 256 x 128 x 256 log-spherical grid, r in [0.05, 20], seeded
+lognormal density (see paper_2606_17636_gb300/workloads.py, workload 3),
+tolerance 1e-8 relative residual per mode, mixed precision (FP32 V-cycles in
+FP64 iterative refinement); the plain FP64 GPU path is timed on the same
+input for comparison.  One step = one full solve (density in, potential out).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own replica of the problem on its own
+GPU (independent problems: weak scaling, no collective on the data path);
+rank 0 prints one JSON line with the whole-job throughput.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = 3
+TOL = 1e-8
+METRIC = "solves/s at 256x128x256 log-spherical: mixed vs FP64 GPU at 1e-8 rel residual"
+CONFIG = {"workload": "log-spherical 256x128x256, r in [0.05, 20], lognormal density (k^-3), "
+                      "tol 1e-8 per mode", "n_r": 256, "n_theta": 128, "n_phi": 256,
+          "geometry": "spherical", "spacing": "log", "precision": "mixed (FP32 V-cycles, FP64 residual/update)"}
+
+
+def args_():
+    a = argparse.ArgumentParser()
+    a.add_argument("--gpus", type=int, default=1)
+    a.add_argument("--steps", type=int, default=40)
+    a.add_argument("--warmup", type=int, default=3)
+    a.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    a.add_argument("--no-baseline", action="store_true")
+    a.add_argument("--eager", action="store_true",
+                   help="host-driven loop instead of the captured graph (for per-kernel profiling)")
+    return a.parse_args()
+
+
+def dist():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as td
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        td.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as td
+        td.barrier()
+
+
+def allmax(ws, v, dev):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-i", str(index), "-lms", "200"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle baseline (the reference arm of this build)
+# --------------------------------------------------------------------------
+ORACLE_SAMPLE_MODES = (0, 1, 64, 128)
+
+
+def oracle_sample(rho, spec):
+    """Time the oracle's solve (Sec. 5.1 steps 2-7) on a bounded sample: the
+    full forward and inverse DFT plus the per-mode work (sparse factorisation,
+    both solves, screening mass, boundary convolution) of four modes, scaled
+    to all modes.  The DGF table is setup (excluded, as the paper excludes
+    it); random values stand in since they do not change the work."""
+    import numpy as np
+    import scipy.sparse.linalg as spla
+
+    from oracle import dft, james, operator
+    from oracle.geometry import Plane
+    p = Plane.make(spec["geometry"], spec["n_r"], spec["n_tz"], spec["n_phi"], spec["spacing"],
+                   spec["r_in"], spec["r_out"], t_min=spec["t_min"], t_max=spec["t_max"])
+    nb = len(james.boundary_points(p))
+    gt = np.random.default_rng(0).standard_normal((nb, nb))
+    t0 = time.perf_counter()
+    f = 4 * np.pi * p.G * dft.forward(rho)
+    t1 = time.perf_counter()
+    for m in ORACLE_SAMPLE_MODES:
+        lu = spla.splu(operator.matrix(p, m).tocsc())
+        b = operator.to_vec(f[:, :, m])
+        x = lu.solve(np.ascontiguousarray(b.real)) + 1j * lu.solve(np.ascontiguousarray(b.imag))
+        psi = operator.from_vec(x, p.n_r, p.n_t)
+        sig = james.screening_mass(p, psi)
+        th = gt @ sig
+        g = james.ghost_values(p, -th)
+        b2 = operator.to_vec(f[:, :, m] - operator.ghost_rhs(p, g))
+        lu.solve(np.ascontiguousarray(b2.real))
+        lu.solve(np.ascontiguousarray(b2.imag))
+    t2 = time.perf_counter()
+    dft.inverse(f, spec["n_phi"])
+    t3 = time.perf_counter()
+    M = spec["n_phi"] // 2 + 1
+    est = (t1 - t0) + (t3 - t2) + (t2 - t1) * M / len(ORACLE_SAMPLE_MODES)
+    return est, t3 - t0
+
+
+def _oracle_child(q, rho, spec):
+    q.put(oracle_sample(rho, spec))
+
+
+def run_oracle_sample(rho, spec):
+    """Run the sample in a spawned single-threaded process; returns
+    (estimated seconds per full solve, seconds spent)."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    pr = ctx.Process(target=_oracle_child, args=(q, rho, spec))
+    pr.start()
+    res = q.get(timeout=600)
+    pr.join(timeout=60)
+    return res
+
+
+def cpu_info():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def reference_arm(a, ws, rank):
+    if rank != 0:
+        return
+    from paper_2606_17636_gb300 import workloads
+    w = workloads.workload(WORKLOAD)
+    for _ in range(a.warmup):
+        run_oracle_sample(w["rho"], w["spec"])
+    times = []
+    spent = 0.0
+    for _ in range(a.steps):
+        est, sp = run_oracle_sample(w["rho"], w["spec"])
+        times.append(est)
+        spent += sp
+    per = statistics.mean(times)
+    v = 1.0 / per
+    sample = ("full forward/inverse DFT + per-mode work of modes %s of %d, scaled to all modes; "
+              "DGF setup excluded" % (list(ORACLE_SAMPLE_MODES), w["spec"]["n_phi"] // 2 + 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(CONFIG, precision="f64 (CPU oracle, sparse direct per mode)"),
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_info()},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def time_solves(torch, s, rho, phi, steps, stream, tag):
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push(tag)
+    ev0.record(stream)
+    for _ in range(steps):
+        s.solve(rho, phi, tol=TOL)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def ours(a, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2606_17636_gb300 as ps
+    from paper_2606_17636_gb300 import workloads
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0 and not a.no_baseline:      # CPU baseline first: spawned before heavy GPU work
+        w0 = workloads.workload(WORKLOAD)
+        base_s, base_spent = run_oracle_sample(w0["rho"], w0["spec"])
+    w = workloads.workload(WORKLOAD)
+    spec = w["spec"]
+    stream = torch.cuda.current_stream()
+    rho_host = torch.from_numpy(w["rho"]).pin_memory()
+    rho = rho_host.to(dev)
+    phi = torch.empty_like(rho)
+    sm = ps.Solver.from_spec(spec, precision=ps.MIXED, use_graph=not a.eager)
+    sd = ps.Solver.from_spec(spec, precision=ps.FP64, use_graph=not a.eager)
+    for _ in range(max(3, a.warmup)):
+        sm.solve(rho, phi, tol=TOL)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    time.sleep(0.5)                         # let the sampler start before the timed region
+    t = time_solves(torch, sm, rho, phi, a.steps, stream, "bench_mixed")
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    t = allmax(ws, t, dev)
+    st = sm.stats()
+    value = ws * a.steps / t
+    # FP64 GPU path on the same input and tolerance
+    phi64 = torch.empty_like(rho)
+    for _ in range(2):
+        sd.solve(rho, phi64, tol=TOL)
+    k64 = max(2, a.steps // 2)
+    t64 = allmax(ws, time_solves(torch, sd, rho, phi64, k64, stream, "bench_fp64"), dev)
+    st64 = sd.stats()
+    fp64_value = ws * k64 / t64
+    diff = float(torch.linalg.vector_norm(phi - phi64) / torch.linalg.vector_norm(phi64))
+    # end to end through the public call with host buffers
+    phi_host = torch.empty_like(rho_host).pin_memory()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        rho.copy_(rho_host, non_blocking=True)
+        sm.solve(rho, phi, tol=TOL)
+        phi_host.copy_(phi, non_blocking=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    te2e = allmax(ws, ev0.elapsed_time(ev1) / 1e3, dev)
+    e2e = ws * a.steps / te2e
+    # dominant kernel, timed alone on the same stream: one alternating-line
+    # smoothing cycle of the finest level over all modes, FP32 planes
+    roof = smoother_roofline(torch, ps, sm, stream)
+    launches = launches_per_solve(sm, st)
+    if rank != 0:
+        return
+    cells = spec["n_r"] * spec["n_tz"] * spec["n_phi"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": dict(CONFIG, l2="working set ~0.45 GB per solve > 129 MB L2; no flush needed",
+                       parallelism="replicas" if ws > 1 else "single GPU"),
+        "cell_updates_per_s": value * cells,
+        "fp64_gpu": {"value": fp64_value, "unit": "solves/s", "ms_per_step": 1e3 * t64 / k64,
+                     "speedup_mixed_vs_fp64": value / fp64_value},
+        "mixed_vs_fp64_rel_l2": diff,
+        "solver": {"iterations_psi": st["iterations_psi"], "iterations_phi": st["iterations_phi"],
+                   "rel_residual_psi": st["rel_residual_psi"], "rel_residual_phi": st["rel_residual_phi"],
+                   "sum_mode_cycles_psi": sum(st["cycles_psi"]), "sum_mode_cycles_phi": sum(st["cycles_phi"]),
+                   "cycles_m0": [st["cycles_psi"][0], st["cycles_phi"][0]],
+                   "fp64_iterations": [st64["iterations_psi"], st64["iterations_phi"]],
+                   "setup_ms": st["setup_ms"]},
+        "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": rho.numel() * 8,
+                "d2h_bytes_per_step": phi.numel() * 8},
+        "gpu_launches": launches * a.steps,
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    if not a.no_baseline:
+        line["cpu_baseline"] = {"value": 1.0 / base_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                "sample": "full DFT + modes %s of %d scaled to all modes (%.1f s of CPU); "
+                                          "DGF setup excluded" % (list(ORACLE_SAMPLE_MODES),
+                                                                  spec["n_phi"] // 2 + 1, base_spent),
+                                "cpu": cpu_info()}
+    print(json.dumps(line), flush=True)
+
+
+def launches_per_solve(s, st):
+    """Kernel launches of one solve: fixed ones plus the per-iteration body
+    of each multigrid loop (residual, retirement, V-cycle, update)."""
+    d = s.desc
+    nl = s.n_levels
+    nu1, nu2 = d.nu_pre or 2, d.nu_post or 2
+    body = 2 + (nl - 1) * (4 * nu1 + 1 + 1 + 4 * nu2) + 1 + 1
+    fixed = 1 + 1 + 3 + 1 + 1 + 1           # fft, init x2, screening/boundary/ghosts, ifft, status
+    return fixed + body * (st["iterations_psi"] + 1 + st["iterations_phi"] + 1)
+
+
+def smoother_roofline(torch, ps, s, stream):
+    """One alternating-line smoothing cycle (radial zebra pass + polar zebra
+    pass, 4 launches) on the finest level over all modes in FP32, timed with
+    CUDA events.  Algorithmic bytes per cell per cycle: each zebra pass reads
+    e once and f once and writes e once over the plane (8 B float2 each),
+    twice (radial, polar): 2 x 24 B = 48 B per complex cell."""
+    M = s.n_modes
+    n_r, n_tz = s.shape[0], s.shape[1]
+    e = torch.zeros((M, n_tz, n_r), dtype=torch.complex64, device="cuda")
+    f = torch.randn((M, n_tz, n_r), dtype=torch.complex64, device="cuda")
+    for _ in range(3):
+        s.stage_smooth(0, e, f, 1)
+    reps = 20
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("bench_smoother")
+    ev0.record(stream)
+    s.stage_smooth(0, e, f, reps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    dt = ev0.elapsed_time(ev1) / 1e3 / reps
+    bytes_ = 48.0 * M * n_tz * n_r
+    pk = peaks().get("hbm_gbs")
+    ach = bytes_ / dt / 1e9
+    return {"kernel": "finest-level smoothing cycle (k_rpass x2 + k_tpass x2, FP32, all modes)",
+            "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
+            "frac": (ach / pk) if pk else None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": None, "algorithmic_bytes_per_launch_set": bytes_, "avg_ms": dt * 1e3}
+
+
+def main():
+    a = args_()
+    ws, rank, local = dist()
+    if a.impl == "reference":
+        reference_arm(a, ws, rank)
+    else:
+        ours(a, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

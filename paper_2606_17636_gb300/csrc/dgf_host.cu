@@ -230,8 +230,6 @@ static bool build_aux(const PlaneGeo& g, const Law& rlaw, const Law& tlaw,
   std::vector<double> xt, yt, xs, ys;
   xt.reserve(size_t(nb) * ring_max);
   int max_cells = 0;
-  const double* sF = nullptr;
-  (void)sF;
   auto sin_face = [&](double th) {
     return (std::fabs(th) < kTol || std::fabs(th - kPi) < kTol) ? 0.0 : std::sin(th);
   };

@@ -41,259 +41,11 @@ template <typename V, typename T> __device__ __forceinline__ V vmk(T a, T b);
 template <> __device__ __forceinline__ float2 vmk<float2, float>(float a, float b) { return make_float2(a, b); }
 template <> __device__ __forceinline__ double2 vmk<double2, double>(double a, double b) { return make_double2(a, b); }
 
-template <typename V> __device__ __forceinline__ V shfl_up1(V v) {
-  v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
-  v.y = __shfl_up_sync(0xffffffffu, v.y, 1);
-  return v;
-}
-template <typename V> __device__ __forceinline__ V shfl_dn1(V v) {
-  v.x = __shfl_down_sync(0xffffffffu, v.x, 1);
-  v.y = __shfl_down_sync(0xffffffffu, v.y, 1);
-  return v;
-}
-
 __device__ __forceinline__ bool plane_of(const Batch& B, int k, int& p, int& slot) {
   if (k >= *B.nact) return false;
   p = B.act[k];
   slot = B.slot ? B.slot[p] : p;
   return true;
-}
-
-// ---------------------------------------------------------------------------
-// Radial-line relaxation (Sec. 3.2): all lines j of one zebra colour; each
-// warp owns one line, each lane CPL consecutive cells.  The line right-hand
-// side f - P (aN e_{j+1} + aS e_{j-1}) is frozen, then n_sor even-odd SOR
-// sweeps with the line's omega_j.  zero_init: e is taken as 0 on entry (the
-// first pass of a level in a V-cycle).
-// ---------------------------------------------------------------------------
-template <typename T, int CPL>
-__global__ void __launch_bounds__(256) k_rpass(LevelDev L, Batch B, vec2_t<T>* __restrict__ e,
-                                               const vec2_t<T>* __restrict__ f, int color,
-                                               int zero_init, int n_sor) {
-  typedef vec2_t<T> V;
-  int p, slot;
-  if (!plane_of(B, blockIdx.y, p, slot)) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = 2 * (blockIdx.x * (blockDim.x >> 5) + warp) + color;
-  const int nr = L.nr, nt = L.nt;
-  if (j >= nt) return;
-  const size_t base = size_t(p) * nr * nt;
-  const T* rt = rtab<T>(L);
-  const T* tt = ttab<T>(L);
-  const T s2 = s2of<T>(B, slot);
-  const T aN = TTAB(tt, TT_AN, j + 1), aS = TTAB(tt, TT_AS, j + 1);
-  const T Tj = TTAB(tt, TT_T, j + 1), dtj = TTAB(tt, TT_DT, j + 1);
-  const T w = omr<T>(L)[size_t(slot) * nt + j];
-  const T w1 = T(1) - w;
-  const bool nb_zero = zero_init && color == 0;
-  const int i0 = lane * CPL;
-  const bool on = i0 < nr;
-  V ev[CPL], fl[CPL];
-  T ae[CPL], aw[CPL], id[CPL];
-#pragma unroll
-  for (int c = 0; c < CPL; ++c) {
-    const int i = i0 + c;
-    ev[c] = vzero<V>();
-    fl[c] = vzero<V>();
-    ae[c] = aw[c] = id[c] = T(0);
-    if (on) {
-      const V fv = f[base + size_t(j) * nr + i];
-      V un = vzero<V>(), us = vzero<V>();
-      if (!nb_zero) {
-        if (j + 1 < nt) un = e[base + size_t(j + 1) * nr + i];
-        if (j > 0) us = e[base + size_t(j - 1) * nr + i];
-      }
-      const T P = RTAB(rt, RT_P, i + 1);
-      fl[c] = vmk<V, T>(fv.x - P * (aN * un.x + aS * us.x), fv.y - P * (aN * un.y + aS * us.y));
-      if (!zero_init) ev[c] = e[base + size_t(j) * nr + i];
-      ae[c] = RTAB(rt, RT_AE, i + 1);
-      aw[c] = RTAB(rt, RT_AW, i + 1);
-      id[c] = T(1) / (RTAB(rt, RT_DR, i + 1) + P * dtj - s2 * RTAB(rt, RT_Q, i + 1) * Tj);
-    }
-  }
-  const bool last = (i0 + CPL >= nr);
-  for (int it = 0; it < n_sor; ++it) {
-#pragma unroll
-    for (int par = 0; par < 2; ++par) {
-      V left = shfl_up1(ev[CPL - 1]);
-      V right = shfl_dn1(ev[0]);
-      if (lane == 0) left = vzero<V>();
-      if (last) right = vzero<V>();
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        if (on && ((i0 + c) & 1) == par) {
-          const V em = (c > 0) ? ev[c - 1] : left;
-          const V ep = (c < CPL - 1) ? ev[c + 1] : right;
-          const T tx = (fl[c].x - ae[c] * ep.x - aw[c] * em.x) * id[c];
-          const T ty = (fl[c].y - ae[c] * ep.y - aw[c] * em.y) * id[c];
-          ev[c].x = w1 * ev[c].x + w * tx;
-          ev[c].y = w1 * ev[c].y + w * ty;
-        }
-      }
-    }
-  }
-  if (on) {
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) e[base + size_t(j) * nr + i0 + c] = ev[c];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Polar / vertical-line relaxation: lines i of one zebra colour.  A block
-// stages a tile of TW columns (plus one neighbour column each side) of e and
-// the colour's columns of f in shared memory; each warp relaxes one column
-// with CPL consecutive cells per lane.
-// ---------------------------------------------------------------------------
-template <typename T, int CPL>
-__global__ void __launch_bounds__(256) k_tpass(LevelDev L, Batch B, vec2_t<T>* __restrict__ e,
-                                               const vec2_t<T>* __restrict__ f, int color,
-                                               int n_sor, int TW) {
-  typedef vec2_t<T> V;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  int p, slot;
-  if (!plane_of(B, blockIdx.y, p, slot)) return;
-  const int nr = L.nr, nt = L.nt;
-  const int SW = TW + 2, HW = TW / 2;
-  V* se = reinterpret_cast<V*>(smem_raw);   // [nt][SW]
-  V* sf = se + size_t(nt) * SW;              // [nt][HW]
-  const size_t base = size_t(p) * nr * nt;
-  const int i0 = blockIdx.x * TW;
-  for (int idx = threadIdx.x; idx < nt * SW; idx += blockDim.x) {
-    const int j = idx / SW, cc = idx - j * SW, i = i0 - 1 + cc;
-    se[idx] = (i >= 0 && i < nr) ? e[base + size_t(j) * nr + i] : vzero<V>();
-  }
-  for (int idx = threadIdx.x; idx < nt * HW; idx += blockDim.x) {
-    const int j = idx / HW, k = idx - j * HW;
-    sf[idx] = f[base + size_t(j) * nr + i0 + color + 2 * k];
-  }
-  __syncthreads();
-  const T* rt = rtab<T>(L);
-  const T* tt = ttab<T>(L);
-  const T s2 = s2of<T>(B, slot);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int j0 = lane * CPL;
-  const bool on = j0 < nt;
-  const bool last = (j0 + CPL >= nt);
-  for (int k = warp; k < HW; k += nw) {
-    const int cc = 1 + color + 2 * k, i = i0 + color + 2 * k;
-    const T P = RTAB(rt, RT_P, i + 1), aE = RTAB(rt, RT_AE, i + 1), aW = RTAB(rt, RT_AW, i + 1);
-    const T dr = RTAB(rt, RT_DR, i + 1), Qi = RTAB(rt, RT_Q, i + 1);
-    const T w = omt<T>(L)[size_t(slot) * nr + i], w1 = T(1) - w;
-    V ev[CPL], g[CPL];
-    T an[CPL], as[CPL], id[CPL];
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-      const int j = j0 + c;
-      ev[c] = vzero<V>();
-      g[c] = vzero<V>();
-      an[c] = as[c] = id[c] = T(0);
-      if (on) {
-        const V fv = sf[j * HW + k], ue = se[j * SW + cc + 1], uw = se[j * SW + cc - 1];
-        g[c] = vmk<V, T>(fv.x - aE * ue.x - aW * uw.x, fv.y - aE * ue.y - aW * uw.y);
-        ev[c] = se[j * SW + cc];
-        an[c] = P * TTAB(tt, TT_AN, j + 1);
-        as[c] = P * TTAB(tt, TT_AS, j + 1);
-        id[c] = T(1) / (dr + P * TTAB(tt, TT_DT, j + 1) - s2 * Qi * TTAB(tt, TT_T, j + 1));
-      }
-    }
-    for (int it = 0; it < n_sor; ++it) {
-#pragma unroll
-      for (int par = 0; par < 2; ++par) {
-        V left = shfl_up1(ev[CPL - 1]);
-        V right = shfl_dn1(ev[0]);
-        if (lane == 0) left = vzero<V>();
-        if (last) right = vzero<V>();
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          if (on && ((j0 + c) & 1) == par) {
-            const V em = (c > 0) ? ev[c - 1] : left;
-            const V ep = (c < CPL - 1) ? ev[c + 1] : right;
-            const T tx = (g[c].x - an[c] * ep.x - as[c] * em.x) * id[c];
-            const T ty = (g[c].y - an[c] * ep.y - as[c] * em.y) * id[c];
-            ev[c].x = w1 * ev[c].x + w * tx;
-            ev[c].y = w1 * ev[c].y + w * ty;
-          }
-        }
-      }
-    }
-    if (on) {
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) se[(j0 + c) * SW + cc] = ev[c];
-    }
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < nt * HW; idx += blockDim.x) {
-    const int j = idx / HW, k = idx - j * HW;
-    e[base + size_t(j) * nr + i0 + color + 2 * k] = se[j * SW + 1 + color + 2 * k];
-  }
-}
-
-template <typename T, int CPL>
-static void rpass(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f, int color,
-                  bool zi, int n_sor, cudaStream_t st) {
-  const int lines = (L.nt - color + 1) / 2;
-  dim3 grid((lines + 7) / 8, B.max_planes);
-  k_rpass<T, CPL><<<grid, 256, 0, st>>>(L, B, e, f, color, zi ? 1 : 0, n_sor);
-}
-
-template <typename T>
-static void rpass_any(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
-                      int color, bool zi, int n_sor, cudaStream_t st) {
-  switch (L.nr <= 32 ? 1 : L.nr / 32) {
-    case 1: rpass<T, 1>(L, B, e, f, color, zi, n_sor, st); break;
-    case 2: rpass<T, 2>(L, B, e, f, color, zi, n_sor, st); break;
-    case 4: rpass<T, 4>(L, B, e, f, color, zi, n_sor, st); break;
-    case 8: rpass<T, 8>(L, B, e, f, color, zi, n_sor, st); break;
-    case 16: rpass<T, 16>(L, B, e, f, color, zi, n_sor, st); break;
-    case 32: rpass<T, 32>(L, B, e, f, color, zi, n_sor, st); break;
-    default: std::fprintf(stderr, "psolve: radial size %d unsupported\n", L.nr);
-  }
-}
-
-static int tile_width(int nr, int nt, size_t vbytes) {
-  int tw = nr < 32 ? nr : 32;
-  while (tw > 2 && size_t(nt) * (tw + 2 + tw / 2) * vbytes > 160 * 1024) tw /= 2;
-  return tw;
-}
-
-template <typename T, int CPL>
-static void tpass(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f, int color,
-                  int n_sor, cudaStream_t st) {
-  const int TW = tile_width(L.nr, L.nt, sizeof(vec2_t<T>));
-  const size_t sm = size_t(L.nt) * (TW + 2 + TW / 2) * sizeof(vec2_t<T>);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_tpass<T, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
-  dim3 grid(L.nr / TW, B.max_planes);
-  k_tpass<T, CPL><<<grid, 256, sm, st>>>(L, B, e, f, color, n_sor, TW);
-}
-
-template <typename T>
-static void tpass_any(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
-                      int color, int n_sor, cudaStream_t st) {
-  switch (L.nt <= 32 ? 1 : L.nt / 32) {
-    case 1: tpass<T, 1>(L, B, e, f, color, n_sor, st); break;
-    case 2: tpass<T, 2>(L, B, e, f, color, n_sor, st); break;
-    case 4: tpass<T, 4>(L, B, e, f, color, n_sor, st); break;
-    case 8: tpass<T, 8>(L, B, e, f, color, n_sor, st); break;
-    case 16: tpass<T, 16>(L, B, e, f, color, n_sor, st); break;
-    case 32: tpass<T, 32>(L, B, e, f, color, n_sor, st); break;
-    default: std::fprintf(stderr, "psolve: polar size %d unsupported\n", L.nt);
-  }
-}
-
-template <typename T>
-void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
-                   int cycles, int n_sor, bool zero_init, cudaStream_t st) {
-  for (int c = 0; c < cycles; ++c) {
-    const bool zi = zero_init && c == 0;
-    rpass_any<T>(L, B, e, f, 0, zi, n_sor, st);
-    rpass_any<T>(L, B, e, f, 1, zi, n_sor, st);
-    tpass_any<T>(L, B, e, f, 0, n_sor, st);
-    tpass_any<T>(L, B, e, f, 1, n_sor, st);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -406,38 +158,6 @@ void launch_prolong(const LevelDev& F, const LevelDev& C, const Batch& B, vec2_t
   const int n = F.nr * F.nt;
   dim3 grid((n + 255) / 256, B.max_planes);
   k_prolong<T><<<grid, 256, 0, st>>>(F, C, B, e, ec);
-}
-
-// ---------------------------------------------------------------------------
-// Coarsest level: e = L_m^{-1} f with the precomputed FP64 inverse.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_coarse(LevelDev C, Batch B, const double* __restrict__ inv, int nc,
-                         const vec2_t<T>* __restrict__ fc, vec2_t<T>* __restrict__ ec) {
-  typedef vec2_t<T> V;
-  extern __shared__ double2 sfc[];
-  int p, slot;
-  if (!plane_of(B, blockIdx.x, p, slot)) return;
-  const V* fp = fc + size_t(p) * nc;
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) sfc[k] = make_double2(double(fp[k].x), double(fp[k].y));
-  __syncthreads();
-  const double* A = inv + size_t(slot) * nc * nc;
-  for (int row = threadIdx.x; row < nc; row += blockDim.x) {
-    double sx = 0.0, sy = 0.0;
-    for (int k = 0; k < nc; ++k) {
-      const double a = A[size_t(row) * nc + k];
-      sx += a * sfc[k].x;
-      sy += a * sfc[k].y;
-    }
-    ec[size_t(p) * nc + row] = vmk<V, T>(T(sx), T(sy));
-  }
-}
-
-template <typename T>
-void launch_coarse(const LevelDev& C, const Batch& B, const double* inv, int nc,
-                   const vec2_t<T>* fc, vec2_t<T>* ec, cudaStream_t st) {
-  const int th = nc < 256 ? ((nc + 31) / 32) * 32 : 256;
-  k_coarse<T><<<B.max_planes, th, nc * sizeof(double2), st>>>(C, B, inv, nc, fc, ec);
 }
 
 // ---------------------------------------------------------------------------
@@ -646,14 +366,10 @@ void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t 
 }
 
 #define INST(T)                                                                                  \
-  template void launch_smooth<T>(const LevelDev&, const Batch&, vec2_t<T>*, const vec2_t<T>*,   \
-                                 int, int, bool, cudaStream_t);                                  \
   template void launch_restrict<T>(const LevelDev&, const LevelDev&, const Batch&,               \
                                    const vec2_t<T>*, const vec2_t<T>*, vec2_t<T>*, cudaStream_t); \
   template void launch_prolong<T>(const LevelDev&, const LevelDev&, const Batch&, vec2_t<T>*,   \
                                   const vec2_t<T>*, cudaStream_t);                               \
-  template void launch_coarse<T>(const LevelDev&, const Batch&, const double*, int,             \
-                                 const vec2_t<T>*, vec2_t<T>*, cudaStream_t);                    \
   template void launch_update<T>(const LevelDev&, const Batch&, double2*, const vec2_t<T>*,     \
                                  cudaStream_t);                                                  \
   template void launch_residual<T>(const LevelDev&, const Batch&, const double2*,               \

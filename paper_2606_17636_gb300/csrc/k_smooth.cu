@@ -1,0 +1,190 @@
+// Fused-colour line smoothing for levels held in global memory (Sec. 3.2).
+//
+// One launch relaxes both zebra colours of one direction: it reads e_in and
+// writes e_out (ping-pong), so the colour-0 lines a block needs are never
+// overwritten by another block.  The first colour-1 neighbour that belongs to
+// the next block is recomputed from e_in (one extra line or column per block),
+// giving exactly the values the two-launch ordering produces.  A smoothing
+// cycle is a radial pass e -> tmp followed by a polar pass tmp -> e.
+#include <cstdio>
+
+#include "lines.cuh"
+
+namespace ps {
+
+// Radial pass, both colours: a block owns 8 lines [j0, j0+8) (8 warps).
+template <typename T, int CPL>
+__global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_t<T>* __restrict__ ein,
+                                                vec2_t<T>* __restrict__ eout,
+                                                const vec2_t<T>* __restrict__ f, int zero_init,
+                                                int n_sor) {
+  typedef vec2_t<T> V;
+  extern __shared__ __align__(16) unsigned char sraw[];
+  V* s0 = reinterpret_cast<V*>(sraw);   // 5 colour-0 lines (4 own + 1 recomputed)
+  if (blockIdx.y >= *B.nact) return;
+  const int p = B.act[blockIdx.y];
+  const int slot = B.slot ? B.slot[p] : p;
+  const int nr = L.nr, nt = L.nt;
+  const int warp = threadIdx.x >> 5;
+  const int j0 = blockIdx.x * 8;
+  const size_t base = size_t(p) * nr * nt;
+  const T* rt = rt_<T>(L);
+  const T* tt = tt_<T>(L);
+  const T s2 = s2_<T>(B, slot);
+  const T* om = omr_<T>(L) + size_t(slot) * nt;
+  const V* ei = ein + base;
+  const V* fi = f + base;
+  if (warp < 5) {                 // colour 0: lines j0, j0+2, .., j0+8
+    const int j = j0 + 2 * warp;
+    if (j < nt) {
+      V ev[CPL];
+      const V* nn = (!zero_init && j + 1 < nt) ? ei + size_t(j + 1) * nr : nullptr;
+      const V* ss = (!zero_init && j > 0) ? ei + size_t(j - 1) * nr : nullptr;
+      relax_rline<T, CPL>(L, rt, tt, s2, om[j], j, zero_init ? nullptr : ei + size_t(j) * nr, nn, ss,
+                          fi + size_t(j) * nr, n_sor, ev);
+      const int lane = threadIdx.x & 31;
+      if (lane * CPL < nr) st_run<V, CPL>(s0 + warp * nr + lane * CPL, ev);
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  if (warp < 4) {                 // colour 1: lines j0+1, .., j0+7
+    const int j = j0 + 1 + 2 * warp;
+    if (j < nt) {
+      V ev[CPL];
+      const V* nn = (j + 1 < nt) ? s0 + (warp + 1) * nr : nullptr;
+      const V* ss = s0 + warp * nr;
+      relax_rline<T, CPL>(L, rt, tt, s2, om[j], j, zero_init ? nullptr : ei + size_t(j) * nr, nn, ss,
+                          fi + size_t(j) * nr, n_sor, ev);
+      if (lane * CPL < nr) st_run<V, CPL>(eout + base + size_t(j) * nr + lane * CPL, ev);
+    }
+  } else {                        // store the block's colour-0 lines
+    const int k = warp - 4, j = j0 + 2 * k;
+    if (j < nt && lane * CPL < nr) {
+      V ev[CPL];
+      ld_run<V, CPL>(ev, s0 + k * nr + lane * CPL);
+      st_run<V, CPL>(eout + base + size_t(j) * nr + lane * CPL, ev);
+    }
+  }
+}
+
+// Polar pass, both colours: a block owns TW columns [i0, i0+TW); shared
+// memory holds columns i0-1 .. i0+TW+1 of e_in and of f (row stride TW+3).
+template <typename T, int CPL>
+__global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_t<T>* __restrict__ ein,
+                                                vec2_t<T>* __restrict__ eout,
+                                                const vec2_t<T>* __restrict__ f, int n_sor, int TW) {
+  typedef vec2_t<T> V;
+  extern __shared__ __align__(16) unsigned char sraw[];
+  if (blockIdx.y >= *B.nact) return;
+  const int p = B.act[blockIdx.y];
+  const int slot = B.slot ? B.slot[p] : p;
+  const int nr = L.nr, nt = L.nt;
+  const int SW = TW + 3;
+  V* se = reinterpret_cast<V*>(sraw);   // [nt][SW], column cc <-> i0 - 1 + cc
+  V* sf = se + size_t(nt) * SW;          // same layout for f
+  const size_t base = size_t(p) * nr * nt;
+  const int i0 = blockIdx.x * TW;
+  for (int idx = threadIdx.x; idx < nt * SW; idx += blockDim.x) {
+    const int j = idx / SW, cc = idx - j * SW, i = i0 - 1 + cc;
+    const bool in = i >= 0 && i < nr;
+    se[idx] = in ? ein[base + size_t(j) * nr + i] : z2<V>();
+    sf[idx] = in ? f[base + size_t(j) * nr + i] : z2<V>();
+  }
+  __syncthreads();
+  const T* rt = rt_<T>(L);
+  const T* tt = tt_<T>(L);
+  const T s2 = s2_<T>(B, slot);
+  const T* om = omt_<T>(L) + size_t(slot) * nr;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int color = 0; color < 2; ++color) {
+    const int ncol = color == 0 ? TW / 2 + 1 : TW / 2;   // colour 0 includes column i0+TW
+    for (int k = warp; k < ncol; k += nw) {
+      const int i = i0 + color + 2 * k;
+      if (i >= nr) continue;
+      const int cc = i - i0 + 1;
+      V ev[CPL];
+      relax_tcol<T, CPL>(L, rt, tt, s2, om[i], i, se + cc, se + cc - 1, se + cc + 1, sf + cc, SW,
+                         n_sor, ev);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c)
+        if (lane + 32 * c < nt) se[(lane + 32 * c) * SW + cc] = ev[c];
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < nt * TW; idx += blockDim.x) {
+    const int j = idx / TW, cc = idx - j * TW;
+    eout[base + size_t(j) * nr + i0 + cc] = se[j * SW + cc + 1];
+  }
+}
+
+static int tile_w(int nr, int nt, size_t vb) {
+  int tw = nr < 32 ? nr : 32;
+  while (tw > 2 && size_t(nt) * 2 * (tw + 3) * vb > 160 * 1024) tw /= 2;
+  return tw;
+}
+
+template <typename T, int CPL>
+static void rpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
+                   const vec2_t<T>* f, bool zi, int n_sor, cudaStream_t st) {
+  dim3 grid((L.nt + 7) / 8, B.max_planes);
+  k_rpass2<T, CPL><<<grid, 256, 5 * L.nr * sizeof(vec2_t<T>), st>>>(L, B, ein, eout, f, zi ? 1 : 0, n_sor);
+}
+
+template <typename T, int CPL>
+static void tpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
+                   const vec2_t<T>* f, int n_sor, cudaStream_t st) {
+  const int TW = tile_w(L.nr, L.nt, sizeof(vec2_t<T>));
+  const size_t sm = size_t(L.nt) * 2 * (TW + 3) * sizeof(vec2_t<T>);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tpass2<T, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  dim3 grid(L.nr / TW, B.max_planes);
+  k_tpass2<T, CPL><<<grid, 256, sm, st>>>(L, B, ein, eout, f, n_sor, TW);
+}
+
+template <typename T>
+static void rpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
+                       const vec2_t<T>* f, bool zi, int n_sor, cudaStream_t st) {
+  switch (L.nr <= 32 ? 1 : L.nr / 32) {
+    case 1: rpass2<T, 1>(L, B, ein, eout, f, zi, n_sor, st); break;
+    case 2: rpass2<T, 2>(L, B, ein, eout, f, zi, n_sor, st); break;
+    case 4: rpass2<T, 4>(L, B, ein, eout, f, zi, n_sor, st); break;
+    case 8: rpass2<T, 8>(L, B, ein, eout, f, zi, n_sor, st); break;
+    case 16: rpass2<T, 16>(L, B, ein, eout, f, zi, n_sor, st); break;
+    case 32: rpass2<T, 32>(L, B, ein, eout, f, zi, n_sor, st); break;
+    default: std::fprintf(stderr, "psolve: radial size %d unsupported\n", L.nr);
+  }
+}
+
+template <typename T>
+static void tpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
+                       const vec2_t<T>* f, int n_sor, cudaStream_t st) {
+  switch (L.nt <= 32 ? 1 : L.nt / 32) {
+    case 1: tpass2<T, 1>(L, B, ein, eout, f, n_sor, st); break;
+    case 2: tpass2<T, 2>(L, B, ein, eout, f, n_sor, st); break;
+    case 4: tpass2<T, 4>(L, B, ein, eout, f, n_sor, st); break;
+    case 8: tpass2<T, 8>(L, B, ein, eout, f, n_sor, st); break;
+    case 16: tpass2<T, 16>(L, B, ein, eout, f, n_sor, st); break;
+    case 32: tpass2<T, 32>(L, B, ein, eout, f, n_sor, st); break;
+    default: std::fprintf(stderr, "psolve: polar size %d unsupported\n", L.nt);
+  }
+}
+
+template <typename T>
+void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
+                   vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, cudaStream_t st) {
+  for (int c = 0; c < cycles; ++c) {
+    rpass2_any<T>(L, B, e, tmp, f, zero_init && c == 0, n_sor, st);
+    tpass2_any<T>(L, B, tmp, e, f, n_sor, st);
+  }
+}
+
+template void launch_smooth<float>(const LevelDev&, const Batch&, float2*, const float2*, float2*,
+                                   int, int, bool, cudaStream_t);
+template void launch_smooth<double>(const LevelDev&, const Batch&, double2*, const double2*,
+                                    double2*, int, int, bool, cudaStream_t);
+
+}  // namespace ps

@@ -1,0 +1,225 @@
+// The lower part of a V-cycle (Sec. 3) in one kernel: one block per mode
+// plane keeps the error and right-hand side of every level from `first`
+// down to the coarsest in shared memory (rows padded to nr + 1 elements so
+// that column accesses hit distinct banks) and runs smoothing (the same
+// alternating zebra line relaxation), defect restriction, the coarsest
+// exact solve, prolongation and post-smoothing with block barriers instead
+// of kernel boundaries.  Input f[first] and output e[first] live in global
+// memory.
+#include <cstdio>
+
+#include "lines.cuh"
+
+namespace ps {
+
+#define R_(id, i) rt[(id) * (L.nr + 2) + (i)]
+#define T_(id, j) tt[(id) * (L.nt + 2) + (j)]
+
+template <typename T, int CPL>
+__device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int slot, int n_sor,
+                         int color) {
+  typedef vec2_t<T> V;
+  const int nr = L.nr, nt = L.nt;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const T* rt = rt_<T>(L);
+  const T* tt = tt_<T>(L);
+  const T* om = omr_<T>(L) + size_t(slot) * nt;
+  for (int line = warp; 2 * line + color < nt; line += nw) {
+    const int j = 2 * line + color;
+    V ev[CPL];
+    const int ld = nr + 1;
+    relax_rline<T, CPL, false>(L, rt, tt, s2, om[j], j, e + j * ld, j + 1 < nt ? e + (j + 1) * ld : nullptr,
+                               j > 0 ? e + (j - 1) * ld : nullptr, f + j * ld, n_sor, ev);
+    if (lane * CPL < nr) {
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) e[j * ld + lane * CPL + c] = ev[c];
+    }
+  }
+}
+
+template <typename T, int CPL>
+__device__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int slot, int n_sor,
+                        int color) {
+  typedef vec2_t<T> V;
+  const int nr = L.nr, nt = L.nt;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const T* rt = rt_<T>(L);
+  const T* tt = tt_<T>(L);
+  const T* om = omt_<T>(L) + size_t(slot) * nr;
+  for (int col = warp; 2 * col + color < nr; col += nw) {
+    const int i = 2 * col + color;
+    V ev[CPL];
+    relax_tcol<T, CPL>(L, rt, tt, s2, om[i], i, e + i, i > 0 ? e + i - 1 : nullptr,
+                       i + 1 < nr ? e + i + 1 : nullptr, f + i, nr + 1, n_sor, ev);
+#pragma unroll
+    for (int c = 0; c < CPL; ++c)
+      if (lane + 32 * c < nt) e[(lane + 32 * c) * (nr + 1) + i] = ev[c];
+  }
+}
+
+// `cycles` alternating-line smoothing cycles of a level held in shared memory.
+template <typename T>
+__device__ void s_smooth(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int slot,
+                         int cycles, int n_sor) {
+  const int cr = L.nr <= 32 ? 1 : L.nr / 32, ct = L.nt <= 32 ? 1 : L.nt / 32;
+  for (int cyc = 0; cyc < cycles; ++cyc) {
+    for (int color = 0; color < 2; ++color) {
+      if (cr == 1) s_rlines<T, 1>(L, e, f, s2, slot, n_sor, color);
+      else if (cr == 2) s_rlines<T, 2>(L, e, f, s2, slot, n_sor, color);
+      else s_rlines<T, 4>(L, e, f, s2, slot, n_sor, color);
+      __syncthreads();
+    }
+    for (int color = 0; color < 2; ++color) {
+      if (ct == 1) s_tcols<T, 1>(L, e, f, s2, slot, n_sor, color);
+      else if (ct == 2) s_tcols<T, 2>(L, e, f, s2, slot, n_sor, color);
+      else s_tcols<T, 4>(L, e, f, s2, slot, n_sor, color);
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+__device__ void s_restrict(const LevelDev& L, const LevelDev& C, const vec2_t<T>* e,
+                           const vec2_t<T>* f, vec2_t<T>* fc, T s2) {
+  typedef vec2_t<T> V;
+  const int nr = L.nr, nt = L.nt, ld = nr + 1, ldc = C.nr + 1;
+  const T* rt = rt_<T>(L);
+  const T* tt = tt_<T>(L);
+  for (int cidx = threadIdx.x; cidx < C.nr * C.nt; cidx += blockDim.x) {
+    const int J = cidx / C.nr, I = cidx - J * C.nr;
+    T ax = 0, ay = 0;
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        const int i = 2 * I + a, j = 2 * J + b;
+        const V c = e[j * ld + i];
+        const V E = (i + 1 < nr) ? e[j * ld + i + 1] : V{0, 0};
+        const V W = (i > 0) ? e[j * ld + i - 1] : V{0, 0};
+        const V N = (j + 1 < nt) ? e[(j + 1) * ld + i] : V{0, 0};
+        const V S = (j > 0) ? e[(j - 1) * ld + i] : V{0, 0};
+        const T aE = R_(RT_AE, i + 1), aW = R_(RT_AW, i + 1), P = R_(RT_P, i + 1);
+        const T aN = P * T_(TT_AN, j + 1), aS = P * T_(TT_AS, j + 1);
+        const T d = R_(RT_DR, i + 1) + P * T_(TT_DT, j + 1) - s2 * R_(RT_Q, i + 1) * T_(TT_T, j + 1);
+        const V fv = f[j * ld + i];
+        const T rx = fv.x - (aE * E.x + aW * W.x + aN * N.x + aS * S.x + d * c.x);
+        const T ry = fv.y - (aE * E.y + aW * W.y + aN * N.y + aS * S.y + d * c.y);
+        const T wgt = R_(RT_RW, i + 1) * T_(TT_RW, j + 1);
+        ax += wgt * rx;
+        ay += wgt * ry;
+      }
+    fc[J * ldc + I] = V{ax, ay};
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ vec2_t<T> s_cval(const LevelDev& C, const vec2_t<T>* ec, int I, int J, int m) {
+  typedef vec2_t<T> V;
+  T fac = T(1);
+  const T sgn = (m & 1) ? T(-1) : T(1);
+  int Ic = I, Jc = J;
+  if (I == 0) { if (C.gL == GH_ZERO) return V{0, 0}; Ic = 1; if (C.gL == GH_PARITY) fac *= sgn; }
+  if (I == C.nr + 1) { if (C.gR == GH_ZERO) return V{0, 0}; Ic = C.nr; if (C.gR == GH_PARITY) fac *= sgn; }
+  if (J == 0) { if (C.gB == GH_ZERO) return V{0, 0}; Jc = 1; if (C.gB == GH_PARITY) fac *= sgn; }
+  if (J == C.nt + 1) { if (C.gT == GH_ZERO) return V{0, 0}; Jc = C.nt; if (C.gT == GH_PARITY) fac *= sgn; }
+  const V v = ec[(Jc - 1) * (C.nr + 1) + (Ic - 1)];
+  return V{fac * v.x, fac * v.y};
+}
+
+template <typename T>
+__device__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, const vec2_t<T>* ec, int m) {
+  typedef vec2_t<T> V;
+  const T* rt = rt_<T>(L);
+  const T* tt = tt_<T>(L);
+  for (int idx = threadIdx.x; idx < L.nr * L.nt; idx += blockDim.x) {
+    const int j = idx / L.nr, i = idx - j * L.nr;
+    const int i1 = i + 1, j1 = j + 1;
+    const int I1 = (i1 & 1) ? (i1 + 1) / 2 - 1 : i1 / 2, J1 = (j1 & 1) ? (j1 + 1) / 2 - 1 : j1 / 2;
+    const T p1 = R_(RT_P1, i1), p2 = R_(RT_P2, i1), q1 = T_(TT_P1, j1), q2 = T_(TT_P2, j1);
+    const V a = s_cval<T>(C, ec, I1, J1, m), b = s_cval<T>(C, ec, I1 + 1, J1, m);
+    const V c = s_cval<T>(C, ec, I1, J1 + 1, m), d = s_cval<T>(C, ec, I1 + 1, J1 + 1, m);
+    V u = e[j * (L.nr + 1) + i];
+    u.x += p1 * q1 * a.x + p2 * q1 * b.x + p1 * q2 * c.x + p2 * q2 * d.x;
+    u.y += p1 * q1 * a.y + p2 * q1 * b.y + p1 * q2 * c.y + p2 * q2 * d.y;
+    e[j * (L.nr + 1) + i] = u;
+  }
+  __syncthreads();
+}
+
+template <typename T, int NTH>
+__global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const vec2_t<T>* __restrict__ gf,
+                                               vec2_t<T>* __restrict__ ge) {
+  typedef vec2_t<T> V;
+  extern __shared__ __align__(16) unsigned char vraw[];
+  V* sm = reinterpret_cast<V*>(vraw);
+  if (blockIdx.x >= *B.nact) return;
+  const int p = B.act[blockIdx.x];
+  const int slot = B.slot ? B.slot[p] : p;
+  const int m = B.mode[slot];
+  T s2;
+  if constexpr (sizeof(T) == 8) s2 = B.s2d[slot]; else s2 = B.s2f[slot];
+  const int K = a.nlev;
+  const int nr0 = a.L[0].nr, n0 = nr0 * a.L[0].nt;
+  // load f of the first level (rows padded to nr + 1), zero all errors
+  for (int k = threadIdx.x; k < n0; k += blockDim.x)
+    sm[a.off_f[0] + (k / nr0) * (nr0 + 1) + k % nr0] = gf[size_t(p) * n0 + k];
+  for (int l = 0; l < K; ++l) {
+    const int n = (a.L[l].nr + 1) * a.L[l].nt;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) sm[a.off_e[l] + k] = V{0, 0};
+  }
+  __syncthreads();
+  for (int l = 0; l < K - 1; ++l) {
+    s_smooth<T>(a.L[l], sm + a.off_e[l], sm + a.off_f[l], s2, slot, a.nu1, a.n_sor);
+    s_restrict<T>(a.L[l], a.L[l + 1], sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
+  }
+  {   // coarsest level: e = L^{-1} f, FP64 dot products, g threads per row
+    const int nc = a.nc;
+    const double* A = a.inv + size_t(slot) * nc * nc;
+    const V* fc = sm + a.off_f[K - 1];
+    V* ec = sm + a.off_e[K - 1];
+    const int ldc = a.L[K - 1].nr + 1, ncr = a.L[K - 1].nr;
+    // g lanes per row; nc is a power of two >= 16, so g * nc is a whole
+    // number of warps and every warp below it takes part in the shuffles
+    int g = 1;
+    while (g < 32 && g * 2 * nc <= int(blockDim.x)) g *= 2;
+    if (int(threadIdx.x) < g * nc) {
+      const int row = threadIdx.x / g, sub = threadIdx.x & (g - 1);
+      double sx = 0.0, sy = 0.0;
+      for (int k = sub; k < nc; k += g) {
+        const double c = A[size_t(row) * nc + k];
+        const V fk = fc[(k / ncr) * ldc + k % ncr];
+        sx += c * double(fk.x);
+        sy += c * double(fk.y);
+      }
+      for (int o = g >> 1; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      }
+      if (sub == 0) ec[(row / ncr) * ldc + row % ncr] = V{T(sx), T(sy)};
+    }
+    __syncthreads();
+  }
+  for (int l = K - 2; l >= 0; --l) {
+    s_prolong<T>(a.L[l], a.L[l + 1], sm + a.off_e[l], sm + a.off_e[l + 1], m);
+    s_smooth<T>(a.L[l], sm + a.off_e[l], sm + a.off_f[l], s2, slot, a.nu2, a.n_sor);
+  }
+  for (int k = threadIdx.x; k < n0; k += blockDim.x)
+    ge[size_t(p) * n0 + k] = sm[a.off_e[0] + (k / nr0) * (nr0 + 1) + k % nr0];
+}
+
+// FP32 planes: 1024 threads (64 registers each); FP64 planes: 512 threads.
+template <typename T>
+void launch_vsmem(const VSmemArgs& a, const Batch& B, const vec2_t<T>* gf, vec2_t<T>* ge,
+                  cudaStream_t st) {
+  constexpr int NTH = sizeof(T) == 4 ? 1024 : 512;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_vsmem<T, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  k_vsmem<T, NTH><<<B.max_planes, NTH, a.smem_bytes, st>>>(a, B, gf, ge);
+}
+
+template void launch_vsmem<float>(const VSmemArgs&, const Batch&, const float2*, float2*, cudaStream_t);
+template void launch_vsmem<double>(const VSmemArgs&, const Batch&, const double2*, double2*, cudaStream_t);
+
+}  // namespace ps

@@ -47,10 +47,25 @@ void launch_fft_inverse(const double2* fh, double* phi, int nr, int nt, int N,
                         const double2* tw, cudaStream_t st);
 
 // ---- multigrid (k_mg.cu), T = float or double ---------------------------------
+// `cycles` alternating-line smoothing cycles (k_smooth.cu); tmp is a
+// scratch buffer of the level's size (ping-pong between the two passes).
 template <typename T>
-void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e,
-                   const vec2_t<T>* f,
-                   int cycles, int n_sor, bool zero_init, cudaStream_t st);
+void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
+                   vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, cudaStream_t st);
+
+// Lower part of a V-cycle in shared memory, one block per plane (k_vsmem.cu).
+struct VSmemArgs {
+  int nlev;              // levels first .. coarsest
+  LevelDev L[8];
+  int off_e[8], off_f[8];   // shared-memory offsets (complex elements)
+  const double* inv;     // coarsest-level inverse [slots][nc][nc]
+  int nc;
+  int nu1, nu2, n_sor;
+  size_t smem_bytes;
+};
+template <typename T>
+void launch_vsmem(const VSmemArgs& a, const Batch& B, const vec2_t<T>* gf, vec2_t<T>* ge,
+                  cudaStream_t st);
 template <typename T>
 void launch_restrict(const LevelDev& F, const LevelDev& C, const Batch& B,
                      const vec2_t<T>* e,
@@ -62,11 +77,6 @@ void launch_prolong(const LevelDev& F, const LevelDev& C, const Batch& B,
                     vec2_t<T>* e,
                     const vec2_t<T>* ec,
                     cudaStream_t st);
-template <typename T>
-void launch_coarse(const LevelDev& C, const Batch& B, const double* inv, int nc,
-                   const vec2_t<T>* fc,
-                   vec2_t<T>* ec,
-                   cudaStream_t st);
 // u += e over the planes of the batch (level-0 sizes)
 template <typename T>
 void launch_update(const LevelDev& L, const Batch& B, double2* u,

@@ -171,7 +171,10 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
     L.g = g;
     if (neumann) L.g.aW[1] = 0.0;
     H.lv.push_back(L);
-    if (std::min(g.r.n, g.t.n) <= 4) break;
+    // coarsen while the short side exceeds 8 cells, or exceeds 4 cells while
+    // the plane has more than 256 (coarsest exact solve stays small)
+    const int mn = std::min(g.r.n, g.t.n);
+    if (!(mn > 8 || (mn > 4 && g.r.n * g.t.n > 256))) break;
     if (g.r.n % 2 || g.t.n % 2) { err = "grid sizes must be powers of two"; return false; }
     PlaneGeo c;
     c.geometry = g.geometry; c.n_phi = g.n_phi; c.G = g.G;

@@ -69,7 +69,8 @@ struct Hierarchy {
   int nc = 0;
 };
 
-// Build levels down to min(n_r, n_t) == 4; neumann zeroes the inner radial
+// Build levels (coarsening stops at a short side of 8 cells, or 4 cells when
+// the plane would exceed 256 cells); neumann zeroes the inner radial
 // face coefficient on every level.  modes: list of azimuthal mode numbers
 // whose omega tables / coarse inverses are needed (index = plane-mode slot).
 bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,

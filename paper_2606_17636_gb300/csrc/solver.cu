@@ -83,6 +83,36 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
     f[l] = A.get(n);
     if (!e[l] || !f[l]) { err = "out of device memory"; return false; }
   }
+  tmp = A.get(size_t(mp) * lv[0].nr * lv[0].nt * vb);
+  if (!tmp) { err = "out of device memory"; return false; }
+  // shared-memory V-cycle: the deepest levels whose error and right-hand
+  // side fit in 200 KB (lines of at most 128 cells)
+  first = nl - 1;
+  {
+    size_t bytes = 0;
+    for (int l = nl - 1; l >= 0; --l) {
+      bytes += 2 * size_t(lv[l].nr + 1) * lv[l].nt * vb;
+      if (bytes > 200 * 1024 || lv[l].nr > 128 || lv[l].nt > 128 || nl - l > 8) break;
+      first = l;
+    }
+    vs.nlev = nl - first;
+    size_t off = 0;
+    for (int k = 0; k < vs.nlev; ++k) {
+      const LevelDev& d = lv[first + k];
+      vs.L[k] = d;
+      vs.off_e[k] = int(off);
+      off += size_t(d.nr + 1) * d.nt;
+      vs.off_f[k] = int(off);
+      off += size_t(d.nr + 1) * d.nt;
+    }
+    vs.smem_bytes = off * vb;
+    vs.inv = d_inv;
+    vs.nc = H.nc;
+    if (H.nc < 16 || (H.nc & (H.nc - 1))) { err = "coarsest level must have a power-of-two size >= 16"; return false; }
+    vs.nu1 = opt.nu1;
+    vs.nu2 = opt.nu2;
+    vs.n_sor = opt.n_sor;
+  }
   const int nblk = residual_blocks(lv[0].nr, lv[0].nt);
   d_act = static_cast<int*>(A.get(sizeof(int) * mp));
   d_nact = static_cast<int*>(A.get(sizeof(int)));
@@ -119,9 +149,11 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
 // ---- typed dispatch -----------------------------------------------------------
 void MGSolver::smooth(int l, void* ee, const void* ff, int cycles, bool zi, cudaStream_t st) {
   if (opt.precision)
-    launch_smooth<float>(lv[l], batch, (float2*)ee, (const float2*)ff, cycles, opt.n_sor, zi, st);
+    launch_smooth<float>(lv[l], batch, (float2*)ee, (const float2*)ff, (float2*)tmp, cycles,
+                         opt.n_sor, zi, st);
   else
-    launch_smooth<double>(lv[l], batch, (double2*)ee, (const double2*)ff, cycles, opt.n_sor, zi, st);
+    launch_smooth<double>(lv[l], batch, (double2*)ee, (const double2*)ff, (double2*)tmp, cycles,
+                          opt.n_sor, zi, st);
 }
 void MGSolver::restrict_(int l, const void* ee, const void* ff, void* fc, cudaStream_t st) {
   if (opt.precision)
@@ -135,12 +167,11 @@ void MGSolver::prolong(int l, void* ee, const void* ec, cudaStream_t st) {
   else
     launch_prolong<double>(lv[l], lv[l + 1], batch, (double2*)ee, (const double2*)ec, st);
 }
-void MGSolver::coarse(const void* fc, void* ec, cudaStream_t st) {
-  const LevelDev& C = lv.back();
+void MGSolver::fused(cudaStream_t st) {
   if (opt.precision)
-    launch_coarse<float>(C, batch, d_inv, H.nc, (const float2*)fc, (float2*)ec, st);
+    launch_vsmem<float>(vs, batch, (const float2*)f[first], (float2*)e[first], st);
   else
-    launch_coarse<double>(C, batch, d_inv, H.nc, (const double2*)fc, (double2*)ec, st);
+    launch_vsmem<double>(vs, batch, (const double2*)f[first], (double2*)e[first], st);
 }
 void MGSolver::residual(const double2* ff, const double2* u, cudaStream_t st) {
   if (opt.precision)
@@ -150,17 +181,18 @@ void MGSolver::residual(const double2* ff, const double2* u, cudaStream_t st) {
 }
 
 // One V-cycle on the error equation L e_0 = f_0 (f_0 = FP64 residual in the
-// buffer precision), e_0 starting from zero (Sec. 3: pre-smoothing,
-// defect restriction, coarse correction, prolongation, post-smoothing).
+// buffer precision), e_0 starting from zero (Sec. 3: pre-smoothing, defect
+// restriction, coarse correction, prolongation, post-smoothing).  Levels
+// below `first` run as level-wide kernels over all active planes; the rest
+// runs in the shared-memory kernel, one block per plane.
 void MGSolver::vcycle(cudaStream_t st) {
-  const int nl = int(lv.size());
-  for (int l = 0; l < nl - 1; ++l) {
+  for (int l = 0; l < first; ++l) {
     if (opt.nu1 > 0) smooth(l, e[l], f[l], opt.nu1, true, st);
     else cudaMemsetAsync(e[l], 0, size_t(max_planes) * lv[l].nr * lv[l].nt * vbytes(), st);
     restrict_(l, e[l], f[l], f[l + 1], st);
   }
-  coarse(f[nl - 1], e[nl - 1], st);
-  for (int l = nl - 2; l >= 0; --l) {
+  fused(st);
+  for (int l = first - 1; l >= 0; --l) {
     prolong(l, e[l], e[l + 1], st);
     if (opt.nu2 > 0) smooth(l, e[l], f[l], opt.nu2, false, st);
   }

@@ -56,11 +56,14 @@ class MGSolver {
   int max_planes = 0;
   // level buffers (T2 of the precision): e[l], f[l]
   std::vector<void*> e, f;
+  void* tmp = nullptr;             // ping-pong buffer of the global-memory smoother
+  int first = 0;                   // first level handled by the shared-memory kernel
+  VSmemArgs vs{};
   // stage helpers on explicit buffers
   void smooth(int level, void* e, const void* f, int cycles, bool zero_init, cudaStream_t st);
   void restrict_(int level, const void* e, const void* f, void* fc, cudaStream_t st);
   void prolong(int level, void* e, const void* ec, cudaStream_t st);
-  void coarse(const void* fc, void* ec, cudaStream_t st);
+  void fused(cudaStream_t st);   // levels first .. coarsest in shared memory
   void residual(const double2* f, const double2* u, cudaStream_t st);
   int* d_act = nullptr;
   int* d_nact = nullptr;

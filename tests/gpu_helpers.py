@@ -26,10 +26,10 @@ def rel_l2(plane, a, ref):
 
 
 SMALL = {
-    "cyl_axis": workloads.spec(workloads.CYLINDRICAL, 32, 16, 16, workloads.UNIFORM, 0.0, 1.0, -0.5, 0.5),
-    "sph_log": workloads.spec(workloads.SPHERICAL, 32, 16, 16, workloads.LOG, 0.1, 10.0),
-    "cyl_cavity": workloads.spec(workloads.CYLINDRICAL, 16, 32, 8, workloads.UNIFORM, 0.2, 1.0),
-    "sph_partial": workloads.spec(workloads.SPHERICAL, 16, 16, 8, workloads.UNIFORM, 1.0, 2.0,
+    "cyl_axis": workloads.spec(workloads.CYLINDRICAL, 32, 32, 16, workloads.UNIFORM, 0.0, 1.0, -0.5, 0.5),
+    "sph_log": workloads.spec(workloads.SPHERICAL, 64, 32, 16, workloads.LOG, 0.1, 10.0),
+    "cyl_cavity": workloads.spec(workloads.CYLINDRICAL, 32, 64, 8, workloads.UNIFORM, 0.2, 1.0),
+    "sph_partial": workloads.spec(workloads.SPHERICAL, 32, 32, 8, workloads.UNIFORM, 1.0, 2.0,
                                   0.25 * np.pi, 0.75 * np.pi),
 }
 

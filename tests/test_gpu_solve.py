@@ -80,7 +80,7 @@ def test_graph_and_eager_paths_agree_bitwise(ps):
 
 def test_mode_retirement_counts_follow_appendix_b(ps):
     """Higher modes retire after fewer V-cycles than m = 0 (App. B)."""
-    sp = dict(SMALL["sph_log"], n_r=64, n_tz=32, n_phi=64)
+    sp = dict(SMALL["sph_log"], n_r=128, n_tz=64, n_phi=64)
     rho = clumps(sp, 3)
     s = ps.Solver.from_spec(sp, precision=ps.MIXED)
     s.solve(torch.from_numpy(rho).cuda(), tol=1e-8)

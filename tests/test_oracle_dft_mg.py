@@ -76,7 +76,7 @@ def test_prolongation_is_exact_for_bilinear_fields():
     """Eq. prolongation_sph is bilinear in (r^2, theta): a field a + b xi +
     c eta + d xi eta on the coarse centres is reproduced at the fine centres
     that have four coarse neighbours inside the domain."""
-    p = Plane.make(SPHERICAL, 16, 8, 8, LOG, 0.5, 4.0, t_min=0.2, t_max=2.0)
+    p = Plane.make(SPHERICAL, 32, 16, 8, LOG, 0.5, 4.0, t_min=0.2, t_max=2.0)
     H = mg.Hierarchy(p)
     F, C = H.levels[0], H.levels[1]
     fn = lambda xi, eta: 1.0 + 0.3 * xi - 2.0 * eta + 0.7 * xi * eta
@@ -87,16 +87,16 @@ def test_prolongation_is_exact_for_bilinear_fields():
 
 
 def test_restriction_preserves_constants_and_area_integral():
-    p = Plane.make(CYLINDRICAL, 16, 8, 8, LOG, 0.05, 3.0)
+    p = Plane.make(CYLINDRICAL, 32, 16, 8, LOG, 0.05, 3.0)
     H = mg.Hierarchy(p)
-    assert np.allclose(H.restrict(0, np.ones((16, 8)) + 0j), 1.0, atol=1e-14)
-    r = np.random.default_rng(0).standard_normal((16, 8)) + 0j
-    a = np.diff(p.r.F)[1:17]
-    b = np.diff(p.t.F)[1:9]
+    assert np.allclose(H.restrict(0, np.ones((32, 16)) + 0j), 1.0, atol=1e-14)
+    r = np.random.default_rng(0).standard_normal((32, 16)) + 0j
+    a = np.diff(p.r.F)[1:33]
+    b = np.diff(p.t.F)[1:17]
     c = H.restrict(0, r)
     C = H.levels[1].plane
-    ac = np.diff(C.r.F)[1:9]
-    bc = np.diff(C.t.F)[1:5]
+    ac = np.diff(C.r.F)[1:17]
+    bc = np.diff(C.t.F)[1:9]
     assert abs((a[:, None] * b[None, :] * r).sum() - (ac[:, None] * bc[None, :] * c).sum()) < 1e-12
 
 
