@@ -158,7 +158,9 @@ static bool build_extended(const PlaneGeo& g, const Law& rlaw, const Law& tlaw,
   }
   cudaStreamSynchronize(st);
   if (mg.h_cont) cudaFreeHost(mg.h_cont);
-  return cudaGetLastError() == cudaSuccess;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { err = std::string("extended-domain DGF: ") + cudaGetErrorString(e); return false; }
+  return true;
 }
 
 // Cells c_first..c_last of a law kept in the auxiliary windows: radial cells
@@ -313,7 +315,9 @@ static bool build_aux(const PlaneGeo& g, const Law& rlaw, const Law& tlaw,
   cudaMemcpyAsync(&fails, a.fail, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
   if (fails) { err = "auxiliary DGF window solves did not converge"; return false; }
-  return cudaGetLastError() == cudaSuccess;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { err = std::string("auxiliary DGF: ") + cudaGetErrorString(e); return false; }
+  return true;
 }
 
 bool build_dgf(const PlaneGeo& g, const Law& rlaw, const Law& tlaw, const std::vector<BPoint>& bp,

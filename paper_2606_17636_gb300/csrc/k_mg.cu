@@ -41,6 +41,8 @@ template <typename V, typename T> __device__ __forceinline__ V vmk(T a, T b);
 template <> __device__ __forceinline__ float2 vmk<float2, float>(float a, float b) { return make_float2(a, b); }
 template <> __device__ __forceinline__ double2 vmk<double2, double>(double a, double b) { return make_double2(a, b); }
 
+enum { ST_ACTIVE = 1, ST_OK = 0, ST_STAGNATED = 2, ST_NOTCONV = -4, ST_NONFINITE = -5 };
+
 __device__ __forceinline__ bool plane_of(const Batch& B, int k, int& p, int& slot) {
   if (k >= *B.nact) return false;
   p = B.act[k];
@@ -209,29 +211,62 @@ __device__ double4 block_sum4(double4 v, double4* sh) {
   return s;
 }
 
+__device__ void retire_block(int* act, int* nact, const double4* __restrict__ psum, RetireState S,
+                             double tol, int max_cycles, int stagnation, int use_cond,
+                             unsigned long long handle, int* scan);
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const double2* __restrict__ f,
                                                   const double2* __restrict__ u,
                                                   vec2_t<T>* __restrict__ r, double4* part,
-                                                  double4* psum, int* cnt) {
+                                                  double4* psum, int* cnt, RetireArgs ra) {
   __shared__ double4 sh[8];
-  __shared__ int last;
+  __shared__ int last, glast;
+  __shared__ int scan[256];
   int p, slot;
   if (!plane_of(B, blockIdx.y, p, slot)) return;
   const int nr = L.nr, nt = L.nt, n = nr * nt;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  double4 acc = make_double4(0, 0, 0, 0);
+  const bool want_f = *ra.S.iter == 0;     // |f| is needed on the first iteration only
+  // the residual is FP64; its norm only drives the convergence test, so the
+  // volume-weighted squares are accumulated in FP32 within the block
+  float4 accf = make_float4(0.f, 0.f, 0.f, 0.f);
   if (idx < n) {
     const int j = idx / nr, i = idx - j * nr;
     const size_t base = size_t(p) * n;
     const double s2 = B.s2d[slot];
     const double2 rv = defect<double>(L, L.rd, L.td, s2, u + base, f + base, i, j);
-    const double2 fv = f[base + idx];
-    r[base + idx] = vmk<vec2_t<T>, T>(T(rv.x), T(rv.y));
-    const double dv = L.rd[RT_V * (nr + 2) + i + 1] * L.td[TT_V * (nt + 2) + j + 1];
-    acc = make_double4(dv * rv.x * rv.x, dv * rv.y * rv.y, dv * fv.x * fv.x, dv * fv.y * fv.y);
+    const vec2_t<T> ro = vmk<vec2_t<T>, T>(T(rv.x), T(rv.y));
+    r[base + idx] = ro;
+    const float dv = L.rf[RT_V * (nr + 2) + i + 1] * L.tf[TT_V * (nt + 2) + j + 1];
+    const float rx = float(ro.x), ry = float(ro.y);
+    accf.x = dv * rx * rx;
+    accf.y = dv * ry * ry;
+    if (want_f) {
+      const double2 fv = f[base + idx];
+      const float fx = float(fv.x), fy = float(fv.y);
+      accf.z = dv * fx * fx;
+      accf.w = dv * fy * fy;
+    }
   }
-  const double4 s = block_sum4(acc, sh);
+  double4 acc;
+  {
+    for (int o = 16; o > 0; o >>= 1) {
+      accf.x += __shfl_down_sync(0xffffffffu, accf.x, o);
+      accf.y += __shfl_down_sync(0xffffffffu, accf.y, o);
+      accf.z += __shfl_down_sync(0xffffffffu, accf.z, o);
+      accf.w += __shfl_down_sync(0xffffffffu, accf.w, o);
+    }
+    __shared__ float4 shf[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) shf[warp] = accf;
+    __syncthreads();
+    acc = make_double4(0, 0, 0, 0);
+    if (threadIdx.x == 0)
+      for (int w = 0; w < int(blockDim.x >> 5); ++w)
+        acc = add4(acc, make_double4(shf[w].x, shf[w].y, shf[w].z, shf[w].w));
+  }
+  const double4 s = acc;
   const int nblk = gridDim.x;
   if (threadIdx.x == 0) {
     part[size_t(p) * nblk + blockIdx.x] = s;
@@ -252,28 +287,35 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
     if (threadIdx.x == 0) {
       psum[p] = tot;
       cnt[p] = 0;
+      __threadfence();
+      glast = (atomicAdd(ra.gcnt, 1) == *B.nact - 1);
+    }
+    __syncthreads();
+    if (glast) {   // every plane's sum is in: retire converged planes (App. B)
+      __threadfence();
+      retire_block(const_cast<int*>(B.act), const_cast<int*>(B.nact), psum, ra.S, ra.tol,
+                   ra.max_cycles, ra.stagnation, ra.use_cond, ra.handle, scan);
+      if (threadIdx.x == 0) *ra.gcnt = 0;
     }
   }
 }
 
 template <typename T>
 void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
-                     vec2_t<T>* r, double4* part, double4* psum, int* cnt, cudaStream_t st) {
+                     vec2_t<T>* r, double4* part, double4* psum, int* cnt, const RetireArgs& ra,
+                     cudaStream_t st) {
   dim3 grid(residual_blocks(L.nr, L.nt), B.max_planes);
-  k_residual<T><<<grid, 256, 0, st>>>(L, B, f, u, r, part, psum, cnt);
+  k_residual<T><<<grid, 256, 0, st>>>(L, B, f, u, r, part, psum, cnt, ra);
 }
 
 // ---------------------------------------------------------------------------
 // Retirement (App. B criterion, per mode and component) and compaction.
 // ---------------------------------------------------------------------------
-enum { ST_ACTIVE = 1, ST_OK = 0, ST_STAGNATED = 2, ST_NOTCONV = -4, ST_NONFINITE = -5 };
 
-__global__ void __launch_bounds__(1024) k_retire(int* act, int* nact, const double4* __restrict__ psum,
-                                                  RetireState S, double tol, int max_cycles,
-                                                  int stagnation, int use_cond,
-                                                  unsigned long long handle) {
+__device__ void retire_block(int* act, int* nact, const double4* __restrict__ psum, RetireState S,
+                             double tol, int max_cycles, int stagnation, int use_cond,
+                             unsigned long long handle, int* scan) {
   __shared__ double smax[32];
-  __shared__ int scan[1024];
   __shared__ int base_out;
   const int n = *nact;
   const int iter = *S.iter;
@@ -341,12 +383,6 @@ __global__ void __launch_bounds__(1024) k_retire(int* act, int* nact, const doub
   }
 }
 
-void launch_retire(int* act, int* nact, const double4* psum, RetireState S, double tol,
-                   int max_cycles, int stagnation, int use_cond, unsigned long long handle,
-                   cudaStream_t st) {
-  k_retire<<<1, 1024, 0, st>>>(act, nact, psum, S, tol, max_cycles, stagnation, use_cond, handle);
-}
-
 __global__ void k_init_active(int* act, int* nact, int n, RetireState S) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     act[k] = k;
@@ -374,7 +410,7 @@ void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t 
                                  cudaStream_t);                                                  \
   template void launch_residual<T>(const LevelDev&, const Batch&, const double2*,               \
                                    const double2*, vec2_t<T>*, double4*, double4*, int*,        \
-                                   cudaStream_t);
+                                   const RetireArgs&, cudaStream_t);
 INST(float)
 INST(double)
 

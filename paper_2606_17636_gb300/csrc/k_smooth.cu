@@ -6,27 +6,53 @@
 // the next block is recomputed from e_in (one extra line or column per block),
 // giving exactly the values the two-launch ordering produces.  A smoothing
 // cycle is a radial pass e -> tmp followed by a polar pass tmp -> e.
+//
+// Re-tiling: grids are sized for all planes with the widest tiles; when only
+// a few planes are active the blocks are spread over them with narrower
+// tiles (up to 4x more blocks per plane), so a lone slow mode still uses
+// many SMs.  The first post-smoothing radial pass of a level can add the
+// bilinear coarse correction to every value it loads (prolongation fused).
 #include <cstdio>
 
 #include "lines.cuh"
 
 namespace ps {
 
-// Radial pass, both colours: a block owns 8 lines [j0, j0+8) (8 warps).
+// Blocks per plane for the active count: base * mult, mult in {1, 2, 4}.
+__device__ __forceinline__ int spread(int base, int nact) {
+  const int G = int(gridDim.x * gridDim.y);
+  int mult = 1;
+  while (mult < 4 && nact * base * mult * 2 <= G) mult *= 2;
+  return mult;
+}
+
+struct Corr {          // fused prolongation source (ec == nullptr: none)
+  LevelDev C;
+  const void* ec;
+};
+
+// Radial pass, both colours: a block owns W lines [j0, j0+W), W = 8 / mult.
 template <typename T, int CPL>
 __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_t<T>* __restrict__ ein,
                                                 vec2_t<T>* __restrict__ eout,
                                                 const vec2_t<T>* __restrict__ f, int zero_init,
-                                                int n_sor) {
+                                                int n_sor, Corr corr) {
   typedef vec2_t<T> V;
   extern __shared__ __align__(16) unsigned char sraw[];
-  V* s0 = reinterpret_cast<V*>(sraw);   // 5 colour-0 lines (4 own + 1 recomputed)
-  if (blockIdx.y >= *B.nact) return;
-  const int p = B.act[blockIdx.y];
+  V* s0 = reinterpret_cast<V*>(sraw);   // up to 5 colour-0 lines (own + 1 recomputed)
+  const int nact = *B.nact;
+  const int mult = spread(int(gridDim.x), nact);
+  const int per = int(gridDim.x) * mult;
+  const int b = int(blockIdx.y * gridDim.x + blockIdx.x);
+  const int k = b / per;
+  if (k >= nact) return;
+  const int W = 8 / mult;
+  const int j0 = (b - k * per) * W;
+  const int p = B.act[k];
   const int slot = B.slot ? B.slot[p] : p;
+  const int m = B.mode[slot];
   const int nr = L.nr, nt = L.nt;
-  const int warp = threadIdx.x >> 5;
-  const int j0 = blockIdx.x * 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t base = size_t(p) * nr * nt;
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
@@ -34,57 +60,88 @@ __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_
   const T* om = omr_<T>(L) + size_t(slot) * nt;
   const V* ei = ein + base;
   const V* fi = f + base;
-  if (warp < 5) {                 // colour 0: lines j0, j0+2, .., j0+8
+  const V* ec = corr.ec ? static_cast<const V*>(corr.ec) + size_t(p) * corr.C.nr * corr.C.nt : nullptr;
+  const int i0 = lane * CPL;
+  const bool on = i0 < nr;
+  // line j of e_in (+ coarse correction), or zero
+  auto load = [&](V (&x)[CPL], int j) {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) x[c] = z2<V>();
+    if (zero_init || j < 0 || j >= nt || !on) return;
+    ld_run<V, CPL>(x, ei + size_t(j) * nr + i0);
+    if (ec) {
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const V d = prolong_at<T>(L, rt, tt, corr.C, ec, i0 + c, j, m);
+        x[c].x += d.x;
+        x[c].y += d.y;
+      }
+    }
+  };
+  if (warp <= W / 2) {            // colour 0: lines j0, j0+2, .., j0+W
     const int j = j0 + 2 * warp;
     if (j < nt) {
-      V ev[CPL];
-      const V* nn = (!zero_init && j + 1 < nt) ? ei + size_t(j + 1) * nr : nullptr;
-      const V* ss = (!zero_init && j > 0) ? ei + size_t(j - 1) * nr : nullptr;
-      relax_rline<T, CPL>(L, rt, tt, s2, om[j], j, zero_init ? nullptr : ei + size_t(j) * nr, nn, ss,
-                          fi + size_t(j) * nr, n_sor, ev);
-      const int lane = threadIdx.x & 31;
-      if (lane * CPL < nr) st_run<V, CPL>(s0 + warp * nr + lane * CPL, ev);
+      V ev[CPL], g[CPL], un[CPL], us[CPL];
+      load(ev, j);
+      load(un, j + 1);
+      load(us, j - 1);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) g[c] = z2<V>();
+      if (on) ld_run<V, CPL>(g, fi + size_t(j) * nr + i0);
+      relax_rline_regs<T, CPL>(L, rt, tt, s2, om[j], j, g, un, us, n_sor, ev);
+      if (on) st_run<V, CPL>(s0 + warp * nr + i0, ev);
     }
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  if (warp < 4) {                 // colour 1: lines j0+1, .., j0+7
+  if (warp < W / 2) {             // colour 1: lines j0+1, .., j0+W-1
     const int j = j0 + 1 + 2 * warp;
     if (j < nt) {
-      V ev[CPL];
-      const V* nn = (j + 1 < nt) ? s0 + (warp + 1) * nr : nullptr;
-      const V* ss = s0 + warp * nr;
-      relax_rline<T, CPL>(L, rt, tt, s2, om[j], j, zero_init ? nullptr : ei + size_t(j) * nr, nn, ss,
-                          fi + size_t(j) * nr, n_sor, ev);
-      if (lane * CPL < nr) st_run<V, CPL>(eout + base + size_t(j) * nr + lane * CPL, ev);
+      V ev[CPL], g[CPL], un[CPL], us[CPL];
+      load(ev, j);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) { g[c] = z2<V>(); un[c] = z2<V>(); us[c] = z2<V>(); }
+      if (on) {
+        ld_run<V, CPL>(g, fi + size_t(j) * nr + i0);
+        ld_run<V, CPL>(us, s0 + warp * nr + i0);
+        if (j + 1 < nt) ld_run<V, CPL>(un, s0 + (warp + 1) * nr + i0);
+      }
+      relax_rline_regs<T, CPL>(L, rt, tt, s2, om[j], j, g, un, us, n_sor, ev);
+      if (on) st_run<V, CPL>(eout + base + size_t(j) * nr + i0, ev);
     }
-  } else {                        // store the block's colour-0 lines
-    const int k = warp - 4, j = j0 + 2 * k;
-    if (j < nt && lane * CPL < nr) {
+  } else if (warp >= 4 && warp < 4 + W / 2) {   // store the block's colour-0 lines
+    const int q = warp - 4, j = j0 + 2 * q;
+    if (j < nt && on) {
       V ev[CPL];
-      ld_run<V, CPL>(ev, s0 + k * nr + lane * CPL);
-      st_run<V, CPL>(eout + base + size_t(j) * nr + lane * CPL, ev);
+      ld_run<V, CPL>(ev, s0 + q * nr + i0);
+      st_run<V, CPL>(eout + base + size_t(j) * nr + i0, ev);
     }
   }
 }
 
-// Polar pass, both colours: a block owns TW columns [i0, i0+TW); shared
-// memory holds columns i0-1 .. i0+TW+1 of e_in and of f (row stride TW+3).
+// Polar pass, both colours: a block owns TW columns [i0, i0+TW), TW =
+// TWmax / mult; shared memory holds columns i0-1 .. i0+TW+1 of e_in and f
+// (row stride TW+3, odd, so interleaved column accesses are conflict-free).
 template <typename T, int CPL>
 __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_t<T>* __restrict__ ein,
                                                 vec2_t<T>* __restrict__ eout,
-                                                const vec2_t<T>* __restrict__ f, int n_sor, int TW) {
+                                                const vec2_t<T>* __restrict__ f, int n_sor, int TWmax) {
   typedef vec2_t<T> V;
   extern __shared__ __align__(16) unsigned char sraw[];
-  if (blockIdx.y >= *B.nact) return;
-  const int p = B.act[blockIdx.y];
+  const int nact = *B.nact;
+  const int mult = TWmax >= 8 ? spread(int(gridDim.x), nact) : 1;
+  const int per = int(gridDim.x) * mult;
+  const int b = int(blockIdx.y * gridDim.x + blockIdx.x);
+  const int kp = b / per;
+  if (kp >= nact) return;
+  const int TW = TWmax / mult;
+  const int i0 = (b - kp * per) * TW;
+  const int p = B.act[kp];
   const int slot = B.slot ? B.slot[p] : p;
   const int nr = L.nr, nt = L.nt;
   const int SW = TW + 3;
   V* se = reinterpret_cast<V*>(sraw);   // [nt][SW], column cc <-> i0 - 1 + cc
   V* sf = se + size_t(nt) * SW;          // same layout for f
   const size_t base = size_t(p) * nr * nt;
-  const int i0 = blockIdx.x * TW;
   for (int idx = threadIdx.x; idx < nt * SW; idx += blockDim.x) {
     const int j = idx / SW, cc = idx - j * SW, i = i0 - 1 + cc;
     const bool in = i >= 0 && i < nr;
@@ -106,9 +163,10 @@ __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_
       V ev[CPL];
       relax_tcol<T, CPL>(L, rt, tt, s2, om[i], i, se + cc, se + cc - 1, se + cc + 1, sf + cc, SW,
                          n_sor, ev);
+      if (lane * CPL < nt) {
 #pragma unroll
-      for (int c = 0; c < CPL; ++c)
-        if (lane + 32 * c < nt) se[(lane + 32 * c) * SW + cc] = ev[c];
+        for (int c = 0; c < CPL; ++c) se[(lane * CPL + c) * SW + cc] = ev[c];
+      }
     }
     __syncthreads();
   }
@@ -126,9 +184,10 @@ static int tile_w(int nr, int nt, size_t vb) {
 
 template <typename T, int CPL>
 static void rpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                   const vec2_t<T>* f, bool zi, int n_sor, cudaStream_t st) {
+                   const vec2_t<T>* f, bool zi, int n_sor, const Corr& corr, cudaStream_t st) {
   dim3 grid((L.nt + 7) / 8, B.max_planes);
-  k_rpass2<T, CPL><<<grid, 256, 5 * L.nr * sizeof(vec2_t<T>), st>>>(L, B, ein, eout, f, zi ? 1 : 0, n_sor);
+  k_rpass2<T, CPL><<<grid, 256, 5 * L.nr * sizeof(vec2_t<T>), st>>>(L, B, ein, eout, f, zi ? 1 : 0,
+                                                                    n_sor, corr);
 }
 
 template <typename T, int CPL>
@@ -147,14 +206,14 @@ static void tpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2
 
 template <typename T>
 static void rpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                       const vec2_t<T>* f, bool zi, int n_sor, cudaStream_t st) {
+                       const vec2_t<T>* f, bool zi, int n_sor, const Corr& corr, cudaStream_t st) {
   switch (L.nr <= 32 ? 1 : L.nr / 32) {
-    case 1: rpass2<T, 1>(L, B, ein, eout, f, zi, n_sor, st); break;
-    case 2: rpass2<T, 2>(L, B, ein, eout, f, zi, n_sor, st); break;
-    case 4: rpass2<T, 4>(L, B, ein, eout, f, zi, n_sor, st); break;
-    case 8: rpass2<T, 8>(L, B, ein, eout, f, zi, n_sor, st); break;
-    case 16: rpass2<T, 16>(L, B, ein, eout, f, zi, n_sor, st); break;
-    case 32: rpass2<T, 32>(L, B, ein, eout, f, zi, n_sor, st); break;
+    case 1: rpass2<T, 1>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
+    case 2: rpass2<T, 2>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
+    case 4: rpass2<T, 4>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
+    case 8: rpass2<T, 8>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
+    case 16: rpass2<T, 16>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
+    case 32: rpass2<T, 32>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
     default: std::fprintf(stderr, "psolve: radial size %d unsupported\n", L.nr);
   }
 }
@@ -175,16 +234,23 @@ static void tpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, 
 
 template <typename T>
 void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
-                   vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, cudaStream_t st) {
+                   vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, const LevelDev* C,
+                   const vec2_t<T>* ec, cudaStream_t st) {
   for (int c = 0; c < cycles; ++c) {
-    rpass2_any<T>(L, B, e, tmp, f, zero_init && c == 0, n_sor, st);
+    Corr corr{};
+    if (c == 0 && ec) {
+      corr.C = *C;
+      corr.ec = ec;
+    }
+    rpass2_any<T>(L, B, e, tmp, f, zero_init && c == 0, n_sor, corr, st);
     tpass2_any<T>(L, B, tmp, e, f, n_sor, st);
   }
 }
 
 template void launch_smooth<float>(const LevelDev&, const Batch&, float2*, const float2*, float2*,
-                                   int, int, bool, cudaStream_t);
+                                   int, int, bool, const LevelDev*, const float2*, cudaStream_t);
 template void launch_smooth<double>(const LevelDev&, const Batch&, double2*, const double2*,
-                                    double2*, int, int, bool, cudaStream_t);
+                                    double2*, int, int, bool, const LevelDev*, const double2*,
+                                    cudaStream_t);
 
 }  // namespace ps

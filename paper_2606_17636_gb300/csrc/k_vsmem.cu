@@ -16,14 +16,14 @@ namespace ps {
 #define T_(id, j) tt[(id) * (L.nt + 2) + (j)]
 
 template <typename T, int CPL>
-__device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int slot, int n_sor,
+__device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int n_sor,
                          int color) {
   typedef vec2_t<T> V;
   const int nr = L.nr, nt = L.nt;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
-  const T* om = omr_<T>(L) + size_t(slot) * nt;
+  const T* om = omr_<T>(L);
   for (int line = warp; 2 * line + color < nt; line += nw) {
     const int j = 2 * line + color;
     V ev[CPL];
@@ -38,41 +38,44 @@ __device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T 
 }
 
 template <typename T, int CPL>
-__device__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int slot, int n_sor,
+__device__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int n_sor,
                         int color) {
   typedef vec2_t<T> V;
   const int nr = L.nr, nt = L.nt;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
-  const T* om = omt_<T>(L) + size_t(slot) * nr;
+  const T* om = omt_<T>(L);
   for (int col = warp; 2 * col + color < nr; col += nw) {
     const int i = 2 * col + color;
     V ev[CPL];
     relax_tcol<T, CPL>(L, rt, tt, s2, om[i], i, e + i, i > 0 ? e + i - 1 : nullptr,
                        i + 1 < nr ? e + i + 1 : nullptr, f + i, nr + 1, n_sor, ev);
+    if (lane * CPL < nt) {
 #pragma unroll
-    for (int c = 0; c < CPL; ++c)
-      if (lane + 32 * c < nt) e[(lane + 32 * c) * (nr + 1) + i] = ev[c];
+      for (int c = 0; c < CPL; ++c) e[(lane * CPL + c) * (nr + 1) + i] = ev[c];
+    }
   }
 }
 
-// `cycles` alternating-line smoothing cycles of a level held in shared memory.
+// `cycles` alternating-line smoothing cycles of a level held in shared memory
+// (L's table and omega pointers point at shared-memory copies; the omega
+// rows are those of this block's mode).
 template <typename T>
-__device__ void s_smooth(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int slot,
-                         int cycles, int n_sor) {
+__device__ void s_smooth(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int cycles,
+                         int n_sor) {
   const int cr = L.nr <= 32 ? 1 : L.nr / 32, ct = L.nt <= 32 ? 1 : L.nt / 32;
   for (int cyc = 0; cyc < cycles; ++cyc) {
     for (int color = 0; color < 2; ++color) {
-      if (cr == 1) s_rlines<T, 1>(L, e, f, s2, slot, n_sor, color);
-      else if (cr == 2) s_rlines<T, 2>(L, e, f, s2, slot, n_sor, color);
-      else s_rlines<T, 4>(L, e, f, s2, slot, n_sor, color);
+      if (cr == 1) s_rlines<T, 1>(L, e, f, s2, n_sor, color);
+      else if (cr == 2) s_rlines<T, 2>(L, e, f, s2, n_sor, color);
+      else s_rlines<T, 4>(L, e, f, s2, n_sor, color);
       __syncthreads();
     }
     for (int color = 0; color < 2; ++color) {
-      if (ct == 1) s_tcols<T, 1>(L, e, f, s2, slot, n_sor, color);
-      else if (ct == 2) s_tcols<T, 2>(L, e, f, s2, slot, n_sor, color);
-      else s_tcols<T, 4>(L, e, f, s2, slot, n_sor, color);
+      if (ct == 1) s_tcols<T, 1>(L, e, f, s2, n_sor, color);
+      else if (ct == 2) s_tcols<T, 2>(L, e, f, s2, n_sor, color);
+      else s_tcols<T, 4>(L, e, f, s2, n_sor, color);
       __syncthreads();
     }
   }
@@ -159,6 +162,36 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
   if constexpr (sizeof(T) == 8) s2 = B.s2d[slot]; else s2 = B.s2f[slot];
   const int K = a.nlev;
   const int nr0 = a.L[0].nr, n0 = nr0 * a.L[0].nt;
+  // stage every level's coefficient tables and this mode's omega rows in
+  // shared memory (after the error / right-hand-side arrays) and point a
+  // block-local copy of the level descriptors at them
+  __shared__ LevelDev sL[8];
+  {
+    T* tb = reinterpret_cast<T*>(sm + a.tab_off);
+    for (int l = 0; l < K; ++l) {
+      const LevelDev& G = a.L[l];
+      const int NR = G.nr + 2, NT = G.nt + 2;
+      const T* grt = rt_<T>(G);
+      const T* gtt = tt_<T>(G);
+      const T* gor = omr_<T>(G) + size_t(slot) * G.nt;
+      const T* got = omt_<T>(G) + size_t(slot) * G.nr;
+      T* srt = tb;
+      T* stt = srt + RT_N * NR;
+      T* sor = stt + TT_N * NT;
+      T* sot = sor + G.nt;
+      for (int k = threadIdx.x; k < RT_N * NR; k += blockDim.x) srt[k] = grt[k];
+      for (int k = threadIdx.x; k < TT_N * NT; k += blockDim.x) stt[k] = gtt[k];
+      for (int k = threadIdx.x; k < G.nt; k += blockDim.x) sor[k] = gor[k];
+      for (int k = threadIdx.x; k < G.nr; k += blockDim.x) sot[k] = got[k];
+      if (threadIdx.x == 0) {
+        LevelDev d = G;
+        if constexpr (sizeof(T) == 8) { d.rd = srt; d.td = stt; d.omr_d = sor; d.omt_d = sot; }
+        else { d.rf = srt; d.tf = stt; d.omr_f = sor; d.omt_f = sot; }
+        sL[l] = d;
+      }
+      tb = sot + G.nr;
+    }
+  }
   // load f of the first level (rows padded to nr + 1), zero all errors
   for (int k = threadIdx.x; k < n0; k += blockDim.x)
     sm[a.off_f[0] + (k / nr0) * (nr0 + 1) + k % nr0] = gf[size_t(p) * n0 + k];
@@ -168,8 +201,8 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
   }
   __syncthreads();
   for (int l = 0; l < K - 1; ++l) {
-    s_smooth<T>(a.L[l], sm + a.off_e[l], sm + a.off_f[l], s2, slot, a.nu1, a.n_sor);
-    s_restrict<T>(a.L[l], a.L[l + 1], sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
+    s_smooth<T>(sL[l], sm + a.off_e[l], sm + a.off_f[l], s2, a.nu1, a.n_sor);
+    s_restrict<T>(sL[l], sL[l + 1], sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
   }
   {   // coarsest level: e = L^{-1} f, FP64 dot products, g threads per row
     const int nc = a.nc;
@@ -180,7 +213,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     // g lanes per row; nc is a power of two >= 16, so g * nc is a whole
     // number of warps and every warp below it takes part in the shuffles
     int g = 1;
-    while (g < 32 && g * 2 * nc <= int(blockDim.x)) g *= 2;
+    while (g < 32 && g * 2 * nc <= int(blockDim.x)) g *= 2;   // uses all threads when nc >= 32
     if (int(threadIdx.x) < g * nc) {
       const int row = threadIdx.x / g, sub = threadIdx.x & (g - 1);
       double sx = 0.0, sy = 0.0;
@@ -199,8 +232,8 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     __syncthreads();
   }
   for (int l = K - 2; l >= 0; --l) {
-    s_prolong<T>(a.L[l], a.L[l + 1], sm + a.off_e[l], sm + a.off_e[l + 1], m);
-    s_smooth<T>(a.L[l], sm + a.off_e[l], sm + a.off_f[l], s2, slot, a.nu2, a.n_sor);
+    s_prolong<T>(sL[l], sL[l + 1], sm + a.off_e[l], sm + a.off_e[l + 1], m);
+    s_smooth<T>(sL[l], sm + a.off_e[l], sm + a.off_f[l], s2, a.nu2, a.n_sor);
   }
   for (int k = threadIdx.x; k < n0; k += blockDim.x)
     ge[size_t(p) * n0 + k] = sm[a.off_e[0] + (k / nr0) * (nr0 + 1) + k % nr0];
@@ -212,8 +245,11 @@ void launch_vsmem(const VSmemArgs& a, const Batch& B, const vec2_t<T>* gf, vec2_
                   cudaStream_t st) {
   constexpr int NTH = sizeof(T) == 4 ? 1024 : 512;
   static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_vsmem<T, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (!attr) {   // opt in to the largest dynamic size the kernel's static usage leaves
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_vsmem<T, NTH>) == cudaSuccess)
+      cudaFuncSetAttribute(k_vsmem<T, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(227 * 1024 - fa.sharedSizeBytes));
     attr = true;
   }
   k_vsmem<T, NTH><<<B.max_planes, NTH, a.smem_bytes, st>>>(a, B, gf, ge);

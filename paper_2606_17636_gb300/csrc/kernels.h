@@ -49,9 +49,12 @@ void launch_fft_inverse(const double2* fh, double* phi, int nr, int nt, int N,
 // ---- multigrid (k_mg.cu), T = float or double ---------------------------------
 // `cycles` alternating-line smoothing cycles (k_smooth.cu); tmp is a
 // scratch buffer of the level's size (ping-pong between the two passes).
+// When ec != nullptr the first radial pass adds the bilinear correction
+// from the coarser level C (prolongation fused into post-smoothing).
 template <typename T>
 void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
-                   vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, cudaStream_t st);
+                   vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, const LevelDev* C,
+                   const vec2_t<T>* ec, cudaStream_t st);
 
 // Lower part of a V-cycle in shared memory, one block per plane (k_vsmem.cu).
 struct VSmemArgs {
@@ -61,6 +64,7 @@ struct VSmemArgs {
   const double* inv;     // coarsest-level inverse [slots][nc][nc]
   int nc;
   int nu1, nu2, n_sor;
+  int tab_off;           // shared-memory offset (complex elements) of the staged tables
   size_t smem_bytes;
 };
 template <typename T>
@@ -82,19 +86,7 @@ template <typename T>
 void launch_update(const LevelDev& L, const Batch& B, double2* u,
                    const vec2_t<T>* e,
                    cudaStream_t st);
-// r = f - L u (FP64), stored as T2; per-block partial sums of dV r^2 (and
-// dV f^2 when want_f) into part[p * nblk + b] as (rr_re, rr_im, ff_re, ff_im).
-// Deterministic per-plane sums: each block writes its partial to
-// part[p * nblk + b]; the last block of a plane (counter cnt[p]) adds the
-// partials in block order into psum[p] and resets the counter.
-template <typename T>
-void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
-                     vec2_t<T>* r, double4* part, double4* psum, int* cnt, cudaStream_t st);
-int residual_blocks(int nr, int nt);
-
-// Convergence bookkeeping: sums partials, retires converged planes, compacts
-// the active list, counts cycles and sets status; writes *cont (and the
-// graph conditional when handle != 0).
+// Convergence bookkeeping state (per plane) and the retirement parameters.
 struct RetireState {
   double2* nf2;      // [planes] |f|^2 per component (set on iteration 0)
   double2* nr2;      // [planes] latest |r|^2
@@ -104,9 +96,26 @@ struct RetireState {
   int* cont;         // scalar: 1 while planes remain
   double* fmax2;     // scalar: max over planes of |f|^2 (iteration 0)
 };
-void launch_retire(int* act, int* nact, const double4* psum, RetireState S, double tol,
-                   int max_cycles, int stagnation, int use_cond, unsigned long long cond_handle,
-                   cudaStream_t st);
+struct RetireArgs {
+  RetireState S;
+  double tol;
+  int max_cycles, stagnation, use_cond;
+  unsigned long long handle;   // graph conditional (use_cond)
+  int* gcnt;                   // completion counter, zero between launches
+};
+
+// r = f - L u (FP64), stored as T2, and the volume-weighted norms per plane
+// (deterministic: each block writes its partial to part[p * nblk + b]; the
+// last block of a plane adds them in block order into psum[p]).  The last
+// plane to finish then applies the App. B criterion to every active plane,
+// counts cycles, sets the status, compacts the active list and sets the
+// continue flag (and the graph conditional).
+template <typename T>
+void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
+                     vec2_t<T>* r, double4* part, double4* psum, int* cnt, const RetireArgs& ra,
+                     cudaStream_t st);
+int residual_blocks(int nr, int nt);
+
 void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t st);
 
 // ---- boundary treatment (k_bc.cu) ---------------------------------------------

@@ -94,6 +94,34 @@ __device__ __forceinline__ void sor_line(vec2_t<T> (&ev)[CPL], const vec2_t<T> (
   }
 }
 
+// Radial line j from registers: g = source line, un / us = neighbour lines
+// j+1 / j-1, ev = own line on entry, relaxed line on exit (lane holds cells
+// lane*CPL ..).
+template <typename T, int CPL>
+__device__ __forceinline__ void relax_rline_regs(const LevelDev& L, const T* rt, const T* tt, T s2,
+                                                 T w, int j, vec2_t<T> (&g)[CPL],
+                                                 const vec2_t<T> (&un)[CPL],
+                                                 const vec2_t<T> (&us)[CPL], int n_sor,
+                                                 vec2_t<T> (&ev)[CPL]) {
+  const int lane = threadIdx.x & 31, nr = L.nr, NR = nr + 2, NT = L.nt + 2;
+  const int i0 = lane * CPL;
+  const bool on = i0 < nr;
+  const T aN = tt[TT_AN * NT + j + 1], aS = tt[TT_AS * NT + j + 1];
+  const T Tj = tt[TT_T * NT + j + 1], dtj = tt[TT_DT * NT + j + 1];
+  T up[CPL], dn[CPL], id[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    const int i = i0 + c + 1;
+    const T P = on ? rt[RT_P * NR + i] : T(0);
+    g[c].x = g[c].x - P * (aN * un[c].x + aS * us[c].x);
+    g[c].y = g[c].y - P * (aN * un[c].y + aS * us[c].y);
+    up[c] = on ? rt[RT_AE * NR + i] : T(0);
+    dn[c] = on ? rt[RT_AW * NR + i] : T(0);
+    id[c] = on ? T(1) / (rt[RT_DR * NR + i] + P * dtj - s2 * rt[RT_Q * NR + i] * Tj) : T(0);
+  }
+  sor_line<T, CPL>(ev, g, up, dn, id, w, i0, on, i0 + CPL >= nr, n_sor);
+}
+
 // Radial line j: own line (nullptr = 0), neighbour lines j+1 / j-1 (nullptr =
 // ghost 0), source line; contiguous storage.  Result in ev.
 template <typename T, int CPL, bool VEC = true>
@@ -102,13 +130,10 @@ __device__ __forceinline__ void relax_rline(const LevelDev& L, const T* rt, cons
                                             const vec2_t<T>* ss, const vec2_t<T>* fl_, int n_sor,
                                             vec2_t<T> (&ev)[CPL]) {
   typedef vec2_t<T> V;
-  const int lane = threadIdx.x & 31, nr = L.nr, NR = nr + 2, NT = L.nt + 2;
+  const int lane = threadIdx.x & 31, nr = L.nr;
   const int i0 = lane * CPL;
   const bool on = i0 < nr;
-  const T aN = tt[TT_AN * NT + j + 1], aS = tt[TT_AS * NT + j + 1];
-  const T Tj = tt[TT_T * NT + j + 1], dtj = tt[TT_DT * NT + j + 1];
   V g[CPL], un[CPL], us[CPL];
-  T up[CPL], dn[CPL], id[CPL];
 #pragma unroll
   for (int c = 0; c < CPL; ++c) { ev[c] = z2<V>(); g[c] = z2<V>(); un[c] = z2<V>(); us[c] = z2<V>(); }
   if (on) {
@@ -127,68 +152,50 @@ __device__ __forceinline__ void relax_rline(const LevelDev& L, const T* rt, cons
       }
     }
   }
-#pragma unroll
-  for (int c = 0; c < CPL; ++c) {
-    const int i = i0 + c + 1;
-    const T P = on ? rt[RT_P * NR + i] : T(0);
-    g[c].x = g[c].x - P * (aN * un[c].x + aS * us[c].x);
-    g[c].y = g[c].y - P * (aN * un[c].y + aS * us[c].y);
-    up[c] = on ? rt[RT_AE * NR + i] : T(0);
-    dn[c] = on ? rt[RT_AW * NR + i] : T(0);
-    id[c] = on ? T(1) / (rt[RT_DR * NR + i] + P * dtj - s2 * rt[RT_Q * NR + i] * Tj) : T(0);
-  }
-  sor_line<T, CPL>(ev, g, up, dn, id, w, i0, on, i0 + CPL >= nr, n_sor);
+  relax_rline_regs<T, CPL>(L, rt, tt, s2, w, j, g, un, us, n_sor, ev);
 }
 
-// Interleaved variant of sor_line: lane k holds cells k + 32 c (c < CPL), so
-// all cells of a lane share one parity; neighbours across the 32-cell chunks
-// come from lanes 31 / 0 of the adjacent chunk.
-template <typename T, int CPL>
-__device__ __forceinline__ void sor_line_il(vec2_t<T> (&ev)[CPL], const vec2_t<T> (&g)[CPL],
-                                            const T (&up)[CPL], const T (&dn)[CPL],
-                                            const T (&id)[CPL], T w, int n, int n_sor) {
+// Bilinear coarse correction (Sec. 3.1, Eq. prolongation_sph) at fine cell
+// (i, j): coarse level C of plane p, parity sign of mode m at poles / axis.
+template <typename T>
+__device__ __forceinline__ vec2_t<T> coarse_at(const LevelDev& C, const vec2_t<T>* __restrict__ ec,
+                                               int I, int J, int m) {
   typedef vec2_t<T> V;
-  const int lane = threadIdx.x & 31;
-  const T w1 = T(1) - w;
-  for (int it = 0; it < n_sor; ++it) {
-#pragma unroll
-    for (int par = 0; par < 2; ++par) {
-      V lo[CPL], hi[CPL];
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        lo[c] = shup(ev[c]);     // from lane - 1
-        hi[c] = shdn(ev[c]);     // from lane + 1
-      }
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        V last_prev, first_next;   // lane 31 of chunk c-1, lane 0 of chunk c+1
-        last_prev.x = __shfl_sync(0xffffffffu, c > 0 ? ev[c > 0 ? c - 1 : 0].x : T(0), 31);
-        last_prev.y = __shfl_sync(0xffffffffu, c > 0 ? ev[c > 0 ? c - 1 : 0].y : T(0), 31);
-        first_next.x = __shfl_sync(0xffffffffu, c + 1 < CPL ? ev[c + 1 < CPL ? c + 1 : 0].x : T(0), 0);
-        first_next.y = __shfl_sync(0xffffffffu, c + 1 < CPL ? ev[c + 1 < CPL ? c + 1 : 0].y : T(0), 0);
-        if (lane == 0) lo[c] = last_prev;
-        if (lane == 31) hi[c] = first_next;
-      }
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        const int k = lane + 32 * c;
-        if (k < n && (lane & 1) == par) {
-          const V em = lo[c];
-          const V ep = (k + 1 < n) ? hi[c] : z2<V>();
-          const T tx = (g[c].x - up[c] * ep.x - dn[c] * em.x) * id[c];
-          const T ty = (g[c].y - up[c] * ep.y - dn[c] * em.y) * id[c];
-          ev[c].x = w1 * ev[c].x + w * tx;
-          ev[c].y = w1 * ev[c].y + w * ty;
-        }
-      }
-    }
-  }
+  T fac = T(1);
+  const T sgn = (m & 1) ? T(-1) : T(1);
+  int Ic = I, Jc = J;
+  if (I == 0) { if (C.gL == GH_ZERO) return z2<V>(); Ic = 1; if (C.gL == GH_PARITY) fac *= sgn; }
+  if (I == C.nr + 1) { if (C.gR == GH_ZERO) return z2<V>(); Ic = C.nr; if (C.gR == GH_PARITY) fac *= sgn; }
+  if (J == 0) { if (C.gB == GH_ZERO) return z2<V>(); Jc = 1; if (C.gB == GH_PARITY) fac *= sgn; }
+  if (J == C.nt + 1) { if (C.gT == GH_ZERO) return z2<V>(); Jc = C.nt; if (C.gT == GH_PARITY) fac *= sgn; }
+  V v = ec[size_t(Jc - 1) * C.nr + (Ic - 1)];
+  v.x *= fac;
+  v.y *= fac;
+  return v;
 }
 
-// Polar / vertical line i stored with row stride `ld` (odd strides make the
-// interleaved accesses free of shared-memory bank conflicts): own column,
-// west and east neighbour columns (nullptr = ghost 0), source column.  Lane
-// k holds cells j = k + 32 c; result in ev.
+template <typename T>
+__device__ __forceinline__ vec2_t<T> prolong_at(const LevelDev& L, const T* rt, const T* tt,
+                                                const LevelDev& C, const vec2_t<T>* __restrict__ ec,
+                                                int i, int j, int m) {
+  typedef vec2_t<T> V;
+  const int i1 = i + 1, j1 = j + 1, NR = L.nr + 2, NT = L.nt + 2;
+  const int I1 = (i1 & 1) ? (i1 + 1) / 2 - 1 : i1 / 2, J1 = (j1 & 1) ? (j1 + 1) / 2 - 1 : j1 / 2;
+  const T p1 = rt[RT_P1 * NR + i1], p2 = rt[RT_P2 * NR + i1];
+  const T q1 = tt[TT_P1 * NT + j1], q2 = tt[TT_P2 * NT + j1];
+  const V a = coarse_at<T>(C, ec, I1, J1, m), b = coarse_at<T>(C, ec, I1 + 1, J1, m);
+  const V c = coarse_at<T>(C, ec, I1, J1 + 1, m), d = coarse_at<T>(C, ec, I1 + 1, J1 + 1, m);
+  V r;
+  r.x = p1 * q1 * a.x + p2 * q1 * b.x + p1 * q2 * c.x + p2 * q2 * d.x;
+  r.y = p1 * q1 * a.y + p2 * q1 * b.y + p1 * q2 * c.y + p2 * q2 * d.y;
+  return r;
+}
+
+// Polar / vertical line i stored with row stride `ld` (an odd stride keeps
+// the strided column loads to at most CPL-way shared-memory bank conflicts;
+// they happen once per line, the SOR sweeps run in registers): own column,
+// west and east neighbour columns (nullptr = ghost 0), source column.  Lane k
+// holds cells j = k*CPL .. k*CPL+CPL-1; result in ev.
 template <typename T, int CPL>
 __device__ __forceinline__ void relax_tcol(const LevelDev& L, const T* rt, const T* tt, T s2, T w,
                                            int i, const vec2_t<T>* own, const vec2_t<T>* west,
@@ -196,17 +203,19 @@ __device__ __forceinline__ void relax_tcol(const LevelDev& L, const T* rt, const
                                            int n_sor, vec2_t<T> (&ev)[CPL]) {
   typedef vec2_t<T> V;
   const int lane = threadIdx.x & 31, nt = L.nt, NR = L.nr + 2, NT = nt + 2;
+  const int j0 = lane * CPL;
+  const bool on = j0 < nt;
   const T P = rt[RT_P * NR + i + 1], aE = rt[RT_AE * NR + i + 1], aW = rt[RT_AW * NR + i + 1];
   const T dr = rt[RT_DR * NR + i + 1], Qi = rt[RT_Q * NR + i + 1];
   V g[CPL];
   T up[CPL], dn[CPL], id[CPL];
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
-    const int j = lane + 32 * c;
+    const int j = j0 + c;
     ev[c] = z2<V>();
     g[c] = z2<V>();
     up[c] = dn[c] = id[c] = T(0);
-    if (j < nt) {
+    if (on) {
       const V fv = fcol[size_t(j) * ld];
       const V ue = east ? east[size_t(j) * ld] : z2<V>();
       const V uw = west ? west[size_t(j) * ld] : z2<V>();
@@ -218,7 +227,7 @@ __device__ __forceinline__ void relax_tcol(const LevelDev& L, const T* rt, const
       id[c] = T(1) / (dr + P * tt[TT_DT * NT + j + 1] - s2 * Qi * tt[TT_T * NT + j + 1]);
     }
   }
-  sor_line_il<T, CPL>(ev, g, up, dn, id, w, nt, n_sor);
+  sor_line<T, CPL>(ev, g, up, dn, id, w, j0, on, j0 + CPL >= nt, n_sor);
 }
 
 }  // namespace ps

@@ -4,6 +4,7 @@
 #include "solver.h"
 
 #include <cstring>
+#include <string>
 
 namespace ps {
 
@@ -90,9 +91,11 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   first = nl - 1;
   {
     size_t bytes = 0;
+    const size_t tb = vb / 2;   // bytes of one real table entry
     for (int l = nl - 1; l >= 0; --l) {
       bytes += 2 * size_t(lv[l].nr + 1) * lv[l].nt * vb;
-      if (bytes > 200 * 1024 || lv[l].nr > 128 || lv[l].nt > 128 || nl - l > 8) break;
+      bytes += (size_t(RT_N) * (lv[l].nr + 2) + size_t(TT_N) * (lv[l].nt + 2) + lv[l].nr + lv[l].nt) * tb;
+      if (bytes > 210 * 1024 || lv[l].nr > 128 || lv[l].nt > 128 || nl - l > 8) break;
       first = l;
     }
     vs.nlev = nl - first;
@@ -105,7 +108,13 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
       vs.off_f[k] = int(off);
       off += size_t(d.nr + 1) * d.nt;
     }
-    vs.smem_bytes = off * vb;
+    vs.tab_off = int(off);
+    size_t tab = 0;
+    for (int k = 0; k < vs.nlev; ++k) {
+      const LevelDev& d = lv[first + k];
+      tab += size_t(RT_N) * (d.nr + 2) + size_t(TT_N) * (d.nt + 2) + d.nr + d.nt;
+    }
+    vs.smem_bytes = off * vb + tab * (vb / 2) + 16;
     vs.inv = d_inv;
     vs.nc = H.nc;
     if (H.nc < 16 || (H.nc & (H.nc - 1))) { err = "coarsest level must have a power-of-two size >= 16"; return false; }
@@ -126,8 +135,10 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   d_iter = static_cast<int*>(A.get(sizeof(int)));
   d_cont = static_cast<int*>(A.get(sizeof(int)));
   d_fmax2 = static_cast<double*>(A.get(sizeof(double)));
-  if (!d_fmax2 || !d_cnt) { err = "out of device memory"; return false; }
+  d_gcnt = static_cast<int*>(A.get(sizeof(int)));
+  if (!d_fmax2 || !d_cnt || !d_gcnt) { err = "out of device memory"; return false; }
   cudaMemset(d_cnt, 0, sizeof(int) * mp);
+  cudaMemset(d_gcnt, 0, sizeof(int));
   if (cudaMallocHost(&h_cont, sizeof(int)) != cudaSuccess) { err = "pinned allocation failed"; return false; }
   batch.act = d_act;
   batch.nact = d_nact;
@@ -143,17 +154,21 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   S.iter = d_iter;
   S.cont = d_cont;
   S.fmax2 = d_fmax2;
-  return cudaGetLastError() == cudaSuccess;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { err = std::string("multigrid setup: ") + cudaGetErrorString(e); return false; }
+  return true;
 }
 
 // ---- typed dispatch -----------------------------------------------------------
-void MGSolver::smooth(int l, void* ee, const void* ff, int cycles, bool zi, cudaStream_t st) {
+void MGSolver::smooth(int l, void* ee, const void* ff, int cycles, bool zi, cudaStream_t st,
+                      const void* ec) {
+  const LevelDev* C = ec ? &lv[l + 1] : nullptr;
   if (opt.precision)
     launch_smooth<float>(lv[l], batch, (float2*)ee, (const float2*)ff, (float2*)tmp, cycles,
-                         opt.n_sor, zi, st);
+                         opt.n_sor, zi, C, (const float2*)ec, st);
   else
     launch_smooth<double>(lv[l], batch, (double2*)ee, (const double2*)ff, (double2*)tmp, cycles,
-                          opt.n_sor, zi, st);
+                          opt.n_sor, zi, C, (const double2*)ec, st);
 }
 void MGSolver::restrict_(int l, const void* ee, const void* ff, void* fc, cudaStream_t st) {
   if (opt.precision)
@@ -173,11 +188,20 @@ void MGSolver::fused(cudaStream_t st) {
   else
     launch_vsmem<double>(vs, batch, (const double2*)f[first], (double2*)e[first], st);
 }
-void MGSolver::residual(const double2* ff, const double2* u, cudaStream_t st) {
+void MGSolver::residual(const double2* ff, const double2* u, double tol, cudaStream_t st,
+                        int use_cond, unsigned long long cond) {
+  RetireArgs ra;
+  ra.S = S;
+  ra.tol = tol;
+  ra.max_cycles = opt.max_cycles;
+  ra.stagnation = opt.stagnation;
+  ra.use_cond = use_cond;
+  ra.handle = cond;
+  ra.gcnt = d_gcnt;
   if (opt.precision)
-    launch_residual<float>(lv[0], batch, ff, u, (float2*)f[0], d_part, d_psum, d_cnt, st);
+    launch_residual<float>(lv[0], batch, ff, u, (float2*)f[0], d_part, d_psum, d_cnt, ra, st);
   else
-    launch_residual<double>(lv[0], batch, ff, u, (double2*)f[0], d_part, d_psum, d_cnt, st);
+    launch_residual<double>(lv[0], batch, ff, u, (double2*)f[0], d_part, d_psum, d_cnt, ra, st);
 }
 
 // One V-cycle on the error equation L e_0 = f_0 (f_0 = FP64 residual in the
@@ -202,8 +226,7 @@ void MGSolver::init_loop(cudaStream_t st) { launch_init_active(d_act, d_nact, ma
 
 void MGSolver::loop_body(const double2* ff, double2* u, double tol, cudaStream_t st, int use_cond,
                          unsigned long long cond) {
-  residual(ff, u, st);
-  launch_retire(d_act, d_nact, d_psum, S, tol, opt.max_cycles, opt.stagnation, use_cond, cond, st);
+  residual(ff, u, tol, st, use_cond, cond);
   vcycle(st);
   if (opt.precision)
     launch_update<float>(lv[0], batch, u, (const float2*)e[0], st);
@@ -215,11 +238,12 @@ int MGSolver::eager_solve(const double2* ff, double2* u, double tol, cudaStream_
                           std::string& err) {
   init_loop(st);
   for (int it = 0; it <= opt.max_cycles + 1; ++it) {
-    residual(ff, u, st);
-    launch_retire(d_act, d_nact, d_psum, S, tol, opt.max_cycles, opt.stagnation, 0, 0, st);
+    residual(ff, u, tol, st, 0, 0);
     cudaMemcpyAsync(h_cont, d_cont, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) {
-      err = cudaGetErrorString(cudaGetLastError());
+    const cudaError_t le = cudaGetLastError();
+    const cudaError_t se = cudaStreamSynchronize(st);
+    if (le != cudaSuccess || se != cudaSuccess) {
+      err = std::string("multigrid iteration: ") + cudaGetErrorString(le != cudaSuccess ? le : se);
       return -2;
     }
     if (!*h_cont) return 0;

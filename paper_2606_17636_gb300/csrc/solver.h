@@ -60,11 +60,13 @@ class MGSolver {
   int first = 0;                   // first level handled by the shared-memory kernel
   VSmemArgs vs{};
   // stage helpers on explicit buffers
-  void smooth(int level, void* e, const void* f, int cycles, bool zero_init, cudaStream_t st);
+  void smooth(int level, void* e, const void* f, int cycles, bool zero_init, cudaStream_t st,
+              const void* ec = nullptr);
   void restrict_(int level, const void* e, const void* f, void* fc, cudaStream_t st);
   void prolong(int level, void* e, const void* ec, cudaStream_t st);
   void fused(cudaStream_t st);   // levels first .. coarsest in shared memory
-  void residual(const double2* f, const double2* u, cudaStream_t st);
+  void residual(const double2* f, const double2* u, double tol, cudaStream_t st, int use_cond,
+                unsigned long long cond);
   int* d_act = nullptr;
   int* d_nact = nullptr;
   int* d_slot = nullptr;
@@ -75,6 +77,7 @@ class MGSolver {
   double4* d_part = nullptr;
   double4* d_psum = nullptr;
   int* d_cnt = nullptr;
+  int* d_gcnt = nullptr;
   double* d_fmax2 = nullptr;
   RetireState S{};
   int precision_of_buffers = 1;
