@@ -148,6 +148,37 @@ int psolve_stage_boundary(psolve_t h, const double* sigma, double* theta);
 /* Copy the DGF table Gt[m][t][s] (FP64, M * nb * nb) to device memory dst. */
 int psolve_get_dgf(psolve_t h, double* dst);
 
+/* ---- allocation-free variant (the paper has no counterpart) ---- */
+
+/* Size in bytes of the library's static device scratch array.  Every GPU on
+ * which the library's kernels are loaded holds this much device memory until
+ * the process exits. */
+#define PSOLVE_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* psolve_stage_smooth computed with no device allocation and without the
+ * handle's workspaces: for callers that must not allocate device memory at
+ * the point of the call -- a host code that has given all remaining device
+ * memory to its own pool after creating the handle, or one that cannot afford
+ * the device-wide synchronisation cudaMalloc / cudaFree may imply.  Same
+ * arguments, layout and result as psolve_stage_smooth (e in/out, f in, both
+ * device pointers owned by the caller).  The step's working memory (an
+ * active-plane list and one ping-pong copy of the level's planes, 256-byte
+ * aligned) is taken from the static array; the handle supplies only its
+ * read-only tables, so the call does not touch a solve in flight on the same
+ * handle.
+ *   Size limit: round_up_256(4 (M + 1)) + M n_tz_l n_r_l (16 for precision 0,
+ *   8 for precision 1) bytes must not exceed PSOLVE_STATIC_SCRATCH_BYTES;
+ *   larger levels return PSOLVE_ERR_ARG with a message naming the need.
+ *   First call per device: looks up the array's device address with that
+ *   device current (the handle's device must be current); make this first
+ *   call before any stream capture begins.
+ *   Sharing: all calls on a device use the same array, which keeps the last
+ *   call's contents; each call rewrites what it reads.  Calls whose work
+ *   overlaps on one GPU (other streams, threads or handles) race.
+ * Returns PSOLVE_OK, PSOLVE_ERR_ARG or PSOLVE_ERR_CUDA. */
+int psolve_stage_smooth_static(psolve_t h, int level, int precision, void* e, const void* f,
+                               int cycles);
+
 #ifdef __cplusplus
 }
 #endif

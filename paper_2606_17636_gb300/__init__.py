@@ -14,6 +14,7 @@ SPHERICAL, CYLINDRICAL = 0, 1
 UNIFORM, LOG = 0, 1
 FP64, MIXED = 0, 1
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NOT_CONVERGED, ERR_NONFINITE = 0, -1, -2, -3, -4, -5
+STATIC_SCRATCH_BYTES = 32 * 1024 * 1024   # PSOLVE_STATIC_SCRATCH_BYTES
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpsolve.so")
@@ -65,6 +66,7 @@ def lib():
             "psolve_stage_inverse": (I, [P, P, P]),
             "psolve_stage_mg_solve": (I, [P, P, P, D, I, ctypes.POINTER(I)]),
             "psolve_stage_smooth": (I, [P, I, I, P, P, I]),
+            "psolve_stage_smooth_static": (I, [P, I, I, P, P, I]),
             "psolve_stage_restrict": (I, [P, I, I, P, P, P]),
             "psolve_stage_prolong": (I, [P, I, I, P, P]),
             "psolve_stage_screening": (I, [P, P, P]),
@@ -228,6 +230,14 @@ class Solver:
         prec = 1 if self.desc.precision == MIXED else 0
         check(lib().psolve_stage_smooth(self.h, level, prec, _ptr(e), _ptr(f), cycles),
               "psolve_stage_smooth")
+        return e
+
+    def stage_smooth_static(self, level, e, f, cycles=1):
+        """stage_smooth with its working memory in the library's static
+        device array (no allocation; concurrent calls on one GPU race)."""
+        prec = 1 if self.desc.precision == MIXED else 0
+        check(lib().psolve_stage_smooth_static(self.h, level, prec, _ptr(e), _ptr(f), cycles),
+              "psolve_stage_smooth_static")
         return e
 
     def stage_restrict(self, level, e, f):

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -585,4 +586,91 @@ extern "C" int psolve_get_dgf(psolve_t h, double* dst) {
                   cudaMemcpyDeviceToDevice, h->st);
   return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("dgf") ? PSOLVE_OK
                                                                          : PSOLVE_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free smoothing step (psolve_stage_smooth_static)
+//
+// For callers that must not allocate device memory when they run a step: a
+// host code that has handed all remaining device memory to its own pool
+// after creating the handle, or that cannot afford the device-wide
+// synchronisation cudaMalloc / cudaFree may imply.  The step's working
+// memory -- the active-plane list and the ping-pong plane buffer of the
+// radial -> polar passes -- lives in the file-scope array below instead of
+// the handle's workspaces; the handle contributes only read-only tables.
+// Every GPU that loads this library holds the array until the process exits.
+// Calls share it and it keeps the last call's contents, so calls whose work
+// overlaps on one GPU (different streams, threads or handles) race.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_static_scratch[PSOLVE_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_dev[kMaxDevices] = {};   // device address of g_static_scratch, per device
+
+// In host code g_static_scratch names a host-side stand-in; the device
+// address is looked up once per device, with that device current.
+int static_scratch(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(PSOLVE_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(PSOLVE_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_dev[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(PSOLVE_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") +
+                                       cudaGetErrorString(e));
+    g_scratch_dev[dev] = p;
+  }
+  *out = g_scratch_dev[dev];
+  return PSOLVE_OK;
+}
+
+__global__ void k_static_active(int* act, int* nact, int n) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) act[k] = k;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *nact = n;
+}
+}  // namespace
+
+extern "C" int psolve_stage_smooth_static(psolve_t h, int level, int precision, void* e,
+                                          const void* f, int cycles) {
+  if (!h || !e || !f) return fail(PSOLVE_ERR_ARG, "null argument");
+  if (cycles < 0) return fail(PSOLVE_ERR_ARG, "cycles must be >= 0");
+  int rc = check_level(h, level, precision, false);
+  if (rc) return rc;
+  const LevelDev& L = h->mg.lv[level];
+  const size_t list_bytes = (sizeof(int) * (size_t(h->M) + 1) + 255) / 256 * 256;
+  const size_t plane_bytes =
+      size_t(h->M) * L.nr * L.nt * (precision ? sizeof(float2) : sizeof(double2));
+  if (list_bytes + plane_bytes > PSOLVE_STATIC_SCRATCH_BYTES)
+    return fail(PSOLVE_ERR_ARG,
+                "psolve_stage_smooth_static: this level needs " +
+                    std::to_string(list_bytes + plane_bytes) +
+                    " bytes of scratch, above the static limit of " +
+                    std::to_string(size_t(PSOLVE_STATIC_SCRATCH_BYTES)) +
+                    " bytes; use psolve_stage_smooth");
+  unsigned char* base = nullptr;
+  rc = static_scratch(reinterpret_cast<void**>(&base));
+  if (rc) return rc;
+  int* act = reinterpret_cast<int*>(base);
+  // The active list is rewritten on every call (the array holds the last
+  // call's list).  The plane buffer needs no clearing: each cycle's radial
+  // pass writes every cell of it that the polar pass then reads.
+  k_static_active<<<(h->M + 255) / 256, 256, 0, h->st>>>(act, act + h->M, h->M);
+  Batch B = h->mg.batch;
+  B.act = act;
+  B.nact = act + h->M;
+  if (precision)
+    launch_smooth<float>(L, B, static_cast<float2*>(e), static_cast<const float2*>(f),
+                         reinterpret_cast<float2*>(base + list_bytes), cycles, h->mg.opt.n_sor,
+                         false, nullptr, nullptr, h->st);
+  else
+    launch_smooth<double>(L, B, static_cast<double2*>(e), static_cast<const double2*>(f),
+                          reinterpret_cast<double2*>(base + list_bytes), cycles, h->mg.opt.n_sor,
+                          false, nullptr, nullptr, h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("smooth_static") ? PSOLVE_OK
+                                                                                   : PSOLVE_ERR_CUDA;
 }

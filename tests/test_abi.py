@@ -48,3 +48,17 @@ def test_invalid_arguments_fail_without_a_gpu(libpath):
     assert L.psolve_create(ctypes.byref(h), 0, 32, 16, 16, 1, 0.0, 10.0) == ps.ERR_ARG
     assert L.psolve_solve(None, None, None, 1e-8) == ps.ERR_ARG
     L.psolve_destroy(None)
+
+
+def test_static_scratch_limit_matches_the_header():
+    import paper_2606_17636_gb300 as ps
+    src = open(os.path.join(ROOT, "include", "psolve.h")).read()
+    m = re.search(r"#define PSOLVE_STATIC_SCRATCH_BYTES \((\d+)u \* 1024u \* 1024u\)", src)
+    assert m and int(m.group(1)) * 1024 * 1024 == ps.STATIC_SCRATCH_BYTES
+
+
+def test_static_entry_point_rejects_bad_arguments_without_a_gpu(libpath):
+    import paper_2606_17636_gb300 as ps
+    L = ps.lib()
+    assert L.psolve_stage_smooth_static(None, 0, 0, None, None, 1) == ps.ERR_ARG
+    assert "null" in ps.last_error()
