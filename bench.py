@@ -162,21 +162,30 @@ def oracle_sample(rho, spec):
     return est, t3 - t0
 
 
-def _oracle_child(q, rho, spec):
-    q.put(oracle_sample(rho, spec))
+def _oracle_child(q, rho, spec, warmup, steps, min_seconds, max_seconds):
+    for _ in range(warmup):
+        oracle_sample(rho, spec)
+    ests, spent = [], 0.0
+    while len(ests) < steps or (spent < min_seconds and spent < max_seconds):
+        est, sp = oracle_sample(rho, spec)
+        ests.append(est)
+        spent += sp
+    q.put((ests, spent))
 
 
-def run_oracle_sample(rho, spec):
-    """Run the sample in a spawned single-threaded process; returns
-    (estimated seconds per full solve, seconds spent)."""
+def run_oracle_samples(rho, spec, warmup=0, steps=1, min_seconds=0.0, max_seconds=30.0):
+    """Run oracle samples in one spawned single-threaded process: `warmup`
+    untimed, then at least `steps`, continuing while under `min_seconds` of
+    CPU time (at most `max_seconds`).  Returns (per-sample estimated seconds
+    per full solve, seconds spent in the timed samples)."""
     import multiprocessing as mp
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    pr = ctx.Process(target=_oracle_child, args=(q, rho, spec))
+    pr = ctx.Process(target=_oracle_child, args=(q, rho, spec, warmup, steps, min_seconds, max_seconds))
     pr.start()
-    res = q.get(timeout=600)
+    res = q.get(timeout=1800)
     pr.join(timeout=60)
     return res
 
@@ -196,14 +205,7 @@ def reference_arm(a, ws, rank):
         return
     from paper_2606_17636_gb300 import workloads
     w = workloads.workload(WORKLOAD)
-    for _ in range(a.warmup):
-        run_oracle_sample(w["rho"], w["spec"])
-    times = []
-    spent = 0.0
-    for _ in range(a.steps):
-        est, sp = run_oracle_sample(w["rho"], w["spec"])
-        times.append(est)
-        spent += sp
+    times, spent = run_oracle_samples(w["rho"], w["spec"], warmup=a.warmup, steps=a.steps)
     per = statistics.mean(times)
     v = 1.0 / per
     sample = ("full forward/inverse DFT + per-mode work of modes %s of %d, scaled to all modes; "
@@ -244,7 +246,8 @@ def ours(a, ws, rank, local):
     torch.cuda.set_device(dev)
     if rank == 0 and not a.no_baseline:      # CPU baseline first: spawned before heavy GPU work
         w0 = workloads.workload(WORKLOAD)
-        base_s, base_spent = run_oracle_sample(w0["rho"], w0["spec"])
+        ests, base_spent = run_oracle_samples(w0["rho"], w0["spec"], min_seconds=10.0)
+        base_s = statistics.mean(ests)
     w = workloads.workload(WORKLOAD)
     spec = w["spec"]
     stream = torch.cuda.current_stream()
@@ -320,9 +323,10 @@ def ours(a, ws, rank, local):
     }
     if not a.no_baseline:
         line["cpu_baseline"] = {"value": 1.0 / base_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                "sample": "full DFT + modes %s of %d scaled to all modes (%.1f s of CPU); "
-                                          "DGF setup excluded" % (list(ORACLE_SAMPLE_MODES),
-                                                                  spec["n_phi"] // 2 + 1, base_spent),
+                                "sample": "%d samples of: full forward/inverse DFT + per-mode work of modes %s of "
+                                          "%d, scaled to all modes (%.1f s of CPU); DGF setup excluded"
+                                          % (len(ests), list(ORACLE_SAMPLE_MODES), spec["n_phi"] // 2 + 1,
+                                             base_spent),
                                 "cpu": cpu_info()}
     print(json.dumps(line), flush=True)
 
