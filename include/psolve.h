@@ -49,7 +49,9 @@ enum {
 
 /* Allocation hooks: when set, every device workspace of a handle is obtained
  * from alloc(bytes, user) and returned with free(ptr, user); otherwise
- * cudaMalloc / cudaFree are used.  alloc returns NULL on failure. */
+ * cudaMalloc / cudaFree are used.  alloc returns NULL on failure, and
+ * 256-byte aligned memory otherwise (as cudaMalloc does); a block that is not
+ * so aligned is handed back to free and counts as a failed allocation. */
 typedef void* (*psolve_alloc_fn)(size_t bytes, void* user);
 typedef void (*psolve_free_fn)(void* ptr, void* user);
 

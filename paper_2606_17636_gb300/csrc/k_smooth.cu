@@ -61,18 +61,16 @@ __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_
   const V* ei = ein + base;
   const V* fi = f + base;
   const V* ec = corr.ec ? static_cast<const V*>(corr.ec) + size_t(p) * corr.C.nr * corr.C.nt : nullptr;
-  const int i0 = lane * CPL;
-  const bool on = i0 < nr;
   // line j of e_in (+ coarse correction), or zero
   auto load = [&](V (&x)[CPL], int j) {
 #pragma unroll
     for (int c = 0; c < CPL; ++c) x[c] = z2<V>();
-    if (zero_init || j < 0 || j >= nt || !on) return;
-    ld_run<V, CPL>(x, ei + size_t(j) * nr + i0);
-    if (ec) {
+    if (zero_init || j < 0 || j >= nt) return;
+    ld_line<V, CPL>(x, ei + size_t(j) * nr, lane, nr);
+    if (ec && (CPL > 1 || lane < nr)) {
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {
-        const V d = prolong_at<T>(L, rt, tt, corr.C, ec, i0 + c, j, m);
+        const V d = prolong_at<T>(L, rt, tt, corr.C, ec, lcell<CPL>(lane, c), j, m);
         x[c].x += d.x;
         x[c].y += d.y;
       }
@@ -85,11 +83,9 @@ __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_
       load(ev, j);
       load(un, j + 1);
       load(us, j - 1);
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) g[c] = z2<V>();
-      if (on) ld_run<V, CPL>(g, fi + size_t(j) * nr + i0);
-      relax_rline_regs<T, CPL>(L, rt, tt, s2, om[j], j, g, un, us, n_sor, ev);
-      if (on) st_run<V, CPL>(s0 + warp * nr + i0, ev);
+      ld_line<V, CPL>(g, fi + size_t(j) * nr, lane, nr);
+      relax_r<T, CPL>(L, rt, tt, s2, om[j], j, g, un, us, n_sor, ev);
+      st_line<V, CPL>(s0 + warp * nr, ev, lane, nr);
     }
   }
   __syncthreads();
@@ -98,29 +94,38 @@ __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_
     if (j < nt) {
       V ev[CPL], g[CPL], un[CPL], us[CPL];
       load(ev, j);
+      ld_line<V, CPL>(g, fi + size_t(j) * nr, lane, nr);
+      ld_line<V, CPL>(us, s0 + warp * nr, lane, nr);
+      if (j + 1 < nt) {
+        ld_line<V, CPL>(un, s0 + (warp + 1) * nr, lane, nr);
+      } else {
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) { g[c] = z2<V>(); un[c] = z2<V>(); us[c] = z2<V>(); }
-      if (on) {
-        ld_run<V, CPL>(g, fi + size_t(j) * nr + i0);
-        ld_run<V, CPL>(us, s0 + warp * nr + i0);
-        if (j + 1 < nt) ld_run<V, CPL>(un, s0 + (warp + 1) * nr + i0);
+        for (int c = 0; c < CPL; ++c) un[c] = z2<V>();
       }
-      relax_rline_regs<T, CPL>(L, rt, tt, s2, om[j], j, g, un, us, n_sor, ev);
-      if (on) st_run<V, CPL>(eout + base + size_t(j) * nr + i0, ev);
+      relax_r<T, CPL>(L, rt, tt, s2, om[j], j, g, un, us, n_sor, ev);
+      st_line<V, CPL>(eout + base + size_t(j) * nr, ev, lane, nr);
     }
   } else if (warp >= 4 && warp < 4 + W / 2) {   // store the block's colour-0 lines
     const int q = warp - 4, j = j0 + 2 * q;
-    if (j < nt && on) {
+    if (j < nt) {
       V ev[CPL];
-      ld_run<V, CPL>(ev, s0 + q * nr + i0);
-      st_run<V, CPL>(eout + base + size_t(j) * nr + i0, ev);
+      ld_line<V, CPL>(ev, s0 + q * nr, lane, nr);
+      st_line<V, CPL>(eout + base + size_t(j) * nr, ev, lane, nr);
     }
   }
 }
 
 // Polar pass, both colours: a block owns TW columns [i0, i0+TW), TW =
-// TWmax / mult; shared memory holds columns i0-1 .. i0+TW+1 of e_in and f
-// (row stride TW+3, odd, so interleaved column accesses are conflict-free).
+// TWmax / mult; shared memory holds columns i0-1 .. i0+TW+1 of e_in and f.
+// Tile layout: cell (j, cc) at j * SW + (cc ^ x(j)) with the odd stride
+// SW = TW + 5 and x(j) = bit 4 of j under the pair lane mapping (else 0), so
+// the 16 rows a half-warp reads fall on 16 distinct 8-byte bank slots.
+__device__ __forceinline__ int tile_sw(int tw) { return tw + 5; }
+template <int CPL>
+__device__ __forceinline__ int tslot(int j, int cc, int SW) {
+  return j * SW + (CPL == 1 ? cc : (cc ^ ((j >> 4) & 1)));
+}
+
 template <typename T, int CPL>
 __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_t<T>* __restrict__ ein,
                                                 vec2_t<T>* __restrict__ eout,
@@ -138,15 +143,16 @@ __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_
   const int p = B.act[kp];
   const int slot = B.slot ? B.slot[p] : p;
   const int nr = L.nr, nt = L.nt;
-  const int SW = TW + 3;
+  const int SW = tile_sw(TW), TC = TW + 3;
   V* se = reinterpret_cast<V*>(sraw);   // [nt][SW], column cc <-> i0 - 1 + cc
   V* sf = se + size_t(nt) * SW;          // same layout for f
   const size_t base = size_t(p) * nr * nt;
-  for (int idx = threadIdx.x; idx < nt * SW; idx += blockDim.x) {
-    const int j = idx / SW, cc = idx - j * SW, i = i0 - 1 + cc;
+  for (int idx = threadIdx.x; idx < nt * TC; idx += blockDim.x) {
+    const int j = idx / TC, cc = idx - j * TC, i = i0 - 1 + cc;
     const bool in = i >= 0 && i < nr;
-    se[idx] = in ? ein[base + size_t(j) * nr + i] : z2<V>();
-    sf[idx] = in ? f[base + size_t(j) * nr + i] : z2<V>();
+    const int o = tslot<CPL>(j, cc, SW);
+    se[o] = in ? ein[base + size_t(j) * nr + i] : z2<V>();
+    sf[o] = in ? f[base + size_t(j) * nr + i] : z2<V>();
   }
   __syncthreads();
   const T* rt = rt_<T>(L);
@@ -154,31 +160,42 @@ __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_
   const T s2 = s2_<T>(B, slot);
   const T* om = omt_<T>(L) + size_t(slot) * nr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const bool on = CPL > 1 || lane < nt;
   for (int color = 0; color < 2; ++color) {
     const int ncol = color == 0 ? TW / 2 + 1 : TW / 2;   // colour 0 includes column i0+TW
     for (int k = warp; k < ncol; k += nw) {
       const int i = i0 + color + 2 * k;
       if (i >= nr) continue;
       const int cc = i - i0 + 1;
-      V ev[CPL];
-      relax_tcol<T, CPL>(L, rt, tt, s2, om[i], i, se + cc, se + cc - 1, se + cc + 1, sf + cc, SW,
-                         n_sor, ev);
-      if (lane * CPL < nt) {
+      V ev[CPL], g[CPL], ue[CPL], uw[CPL];
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) se[(lane * CPL + c) * SW + cc] = ev[c];
+      for (int c = 0; c < CPL; ++c) {
+        const int j = lcell<CPL>(lane, c);
+        ev[c] = g[c] = ue[c] = uw[c] = z2<V>();
+        if (on) {
+          ev[c] = se[tslot<CPL>(j, cc, SW)];
+          uw[c] = se[tslot<CPL>(j, cc - 1, SW)];
+          ue[c] = se[tslot<CPL>(j, cc + 1, SW)];
+          g[c] = sf[tslot<CPL>(j, cc, SW)];
+        }
+      }
+      relax_t<T, CPL>(L, rt, tt, s2, om[i], i, g, ue, uw, n_sor, ev);
+      if (on) {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) se[tslot<CPL>(lcell<CPL>(lane, c), cc, SW)] = ev[c];
       }
     }
     __syncthreads();
   }
   for (int idx = threadIdx.x; idx < nt * TW; idx += blockDim.x) {
     const int j = idx / TW, cc = idx - j * TW;
-    eout[base + size_t(j) * nr + i0 + cc] = se[j * SW + cc + 1];
+    eout[base + size_t(j) * nr + i0 + cc] = se[tslot<CPL>(j, cc + 1, SW)];
   }
 }
 
 static int tile_w(int nr, int nt, size_t vb) {
   int tw = nr < 32 ? nr : 32;
-  while (tw > 2 && size_t(nt) * 2 * (tw + 3) * vb > 160 * 1024) tw /= 2;
+  while (tw > 2 && size_t(nt) * 2 * (tw + 5) * vb > 160 * 1024) tw /= 2;
   return tw;
 }
 
@@ -194,7 +211,7 @@ template <typename T, int CPL>
 static void tpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
                    const vec2_t<T>* f, int n_sor, cudaStream_t st) {
   const int TW = tile_w(L.nr, L.nt, sizeof(vec2_t<T>));
-  const size_t sm = size_t(L.nt) * 2 * (TW + 3) * sizeof(vec2_t<T>);
+  const size_t sm = size_t(L.nt) * 2 * (TW + 5) * sizeof(vec2_t<T>);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_tpass2<T, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

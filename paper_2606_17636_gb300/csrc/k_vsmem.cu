@@ -1,11 +1,16 @@
 // The lower part of a V-cycle (Sec. 3) in one kernel: one block per mode
 // plane keeps the error and right-hand side of every level from `first`
-// down to the coarsest in shared memory (rows padded to nr + 1 elements so
-// that column accesses hit distinct banks) and runs smoothing (the same
+// down to the coarsest in shared memory and runs smoothing (the same
 // alternating zebra line relaxation), defect restriction, the coarsest
 // exact solve, prolongation and post-smoothing with block barriers instead
 // of kernel boundaries.  Input f[first] and output e[first] live in global
 // memory.
+//
+// Shared-memory layout of a level (nr x nt, unpadded rows): cell (j, i) sits
+// at j * nr + (i ^ h(j)).  The row swizzle h(j) < min(16, nr) is (j >> 1) or j
+// (masked), matching the rows a half-warp holds in a polar line (pairs or
+// single cells), so both the row-wise vector accesses of radial lines and the
+// column accesses of polar lines are free of bank conflicts.
 #include <cstdio>
 
 #include "lines.cuh"
@@ -14,6 +19,14 @@ namespace ps {
 
 #define R_(id, i) rt[(id) * (L.nr + 2) + (i)]
 #define T_(id, j) tt[(id) * (L.nt + 2) + (j)]
+
+__device__ __forceinline__ int vswz(const LevelDev& L, int j) {
+  const int mask = (L.nr < 16 ? L.nr : 16) - 1;
+  return ((L.nt > 32 ? j >> 1 : j)) & mask;
+}
+__device__ __forceinline__ int vslot(const LevelDev& L, int j, int i) {
+  return j * L.nr + (i ^ vswz(L, j));
+}
 
 template <typename T, int CPL>
 __device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int n_sor,
@@ -26,14 +39,24 @@ __device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T 
   const T* om = omr_<T>(L);
   for (int line = warp; 2 * line + color < nt; line += nw) {
     const int j = 2 * line + color;
-    V ev[CPL];
-    const int ld = nr + 1;
-    relax_rline<T, CPL, false>(L, rt, tt, s2, om[j], j, e + j * ld, j + 1 < nt ? e + (j + 1) * ld : nullptr,
-                               j > 0 ? e + (j - 1) * ld : nullptr, f + j * ld, n_sor, ev);
-    if (lane * CPL < nr) {
+    const int sj = vswz(L, j);
+    V ev[CPL], g[CPL], un[CPL], us[CPL];
+    ld_line_swz<V, CPL>(ev, e + j * nr, sj, lane, nr);
+    ld_line_swz<V, CPL>(g, f + j * nr, sj, lane, nr);
+    if (j + 1 < nt) {
+      ld_line_swz<V, CPL>(un, e + (j + 1) * nr, vswz(L, j + 1), lane, nr);
+    } else {
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) e[j * ld + lane * CPL + c] = ev[c];
+      for (int c = 0; c < CPL; ++c) un[c] = z2<V>();
     }
+    if (j > 0) {
+      ld_line_swz<V, CPL>(us, e + (j - 1) * nr, vswz(L, j - 1), lane, nr);
+    } else {
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) us[c] = z2<V>();
+    }
+    relax_r<T, CPL>(L, rt, tt, s2, om[j], j, g, un, us, n_sor, ev);
+    st_line_swz<V, CPL>(e + j * nr, sj, ev, lane, nr);
   }
 }
 
@@ -46,14 +69,28 @@ __device__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
   const T* om = omt_<T>(L);
+  const bool on = CPL > 1 || lane < nt;
   for (int col = warp; 2 * col + color < nr; col += nw) {
     const int i = 2 * col + color;
-    V ev[CPL];
-    relax_tcol<T, CPL>(L, rt, tt, s2, om[i], i, e + i, i > 0 ? e + i - 1 : nullptr,
-                       i + 1 < nr ? e + i + 1 : nullptr, f + i, nr + 1, n_sor, ev);
-    if (lane * CPL < nt) {
+    V ev[CPL], g[CPL], ue[CPL], uw[CPL];
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) e[(lane * CPL + c) * (nr + 1) + i] = ev[c];
+    for (int c = 0; c < CPL; ++c) {
+      ev[c] = g[c] = ue[c] = uw[c] = z2<V>();
+      if (on) {
+        const int j = lcell<CPL>(lane, c), row = j * nr, s = vswz(L, j);
+        ev[c] = e[row + (i ^ s)];
+        g[c] = f[row + (i ^ s)];
+        if (i > 0) uw[c] = e[row + ((i - 1) ^ s)];
+        if (i + 1 < nr) ue[c] = e[row + ((i + 1) ^ s)];
+      }
+    }
+    relax_t<T, CPL>(L, rt, tt, s2, om[i], i, g, ue, uw, n_sor, ev);
+    if (on) {
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const int j = lcell<CPL>(lane, c);
+        e[j * nr + (i ^ vswz(L, j))] = ev[c];
+      }
     }
   }
 }
@@ -85,7 +122,7 @@ template <typename T>
 __device__ void s_restrict(const LevelDev& L, const LevelDev& C, const vec2_t<T>* e,
                            const vec2_t<T>* f, vec2_t<T>* fc, T s2) {
   typedef vec2_t<T> V;
-  const int nr = L.nr, nt = L.nt, ld = nr + 1, ldc = C.nr + 1;
+  const int nr = L.nr, nt = L.nt;
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
   for (int cidx = threadIdx.x; cidx < C.nr * C.nt; cidx += blockDim.x) {
@@ -94,22 +131,22 @@ __device__ void s_restrict(const LevelDev& L, const LevelDev& C, const vec2_t<T>
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) {
         const int i = 2 * I + a, j = 2 * J + b;
-        const V c = e[j * ld + i];
-        const V E = (i + 1 < nr) ? e[j * ld + i + 1] : V{0, 0};
-        const V W = (i > 0) ? e[j * ld + i - 1] : V{0, 0};
-        const V N = (j + 1 < nt) ? e[(j + 1) * ld + i] : V{0, 0};
-        const V S = (j > 0) ? e[(j - 1) * ld + i] : V{0, 0};
+        const V c = e[vslot(L, j, i)];
+        const V E = (i + 1 < nr) ? e[vslot(L, j, i + 1)] : V{0, 0};
+        const V W = (i > 0) ? e[vslot(L, j, i - 1)] : V{0, 0};
+        const V N = (j + 1 < nt) ? e[vslot(L, j + 1, i)] : V{0, 0};
+        const V S = (j > 0) ? e[vslot(L, j - 1, i)] : V{0, 0};
         const T aE = R_(RT_AE, i + 1), aW = R_(RT_AW, i + 1), P = R_(RT_P, i + 1);
         const T aN = P * T_(TT_AN, j + 1), aS = P * T_(TT_AS, j + 1);
         const T d = R_(RT_DR, i + 1) + P * T_(TT_DT, j + 1) - s2 * R_(RT_Q, i + 1) * T_(TT_T, j + 1);
-        const V fv = f[j * ld + i];
+        const V fv = f[vslot(L, j, i)];
         const T rx = fv.x - (aE * E.x + aW * W.x + aN * N.x + aS * S.x + d * c.x);
         const T ry = fv.y - (aE * E.y + aW * W.y + aN * N.y + aS * S.y + d * c.y);
         const T wgt = R_(RT_RW, i + 1) * T_(TT_RW, j + 1);
         ax += wgt * rx;
         ay += wgt * ry;
       }
-    fc[J * ldc + I] = V{ax, ay};
+    fc[vslot(C, J, I)] = V{ax, ay};
   }
   __syncthreads();
 }
@@ -124,7 +161,7 @@ __device__ __forceinline__ vec2_t<T> s_cval(const LevelDev& C, const vec2_t<T>* 
   if (I == C.nr + 1) { if (C.gR == GH_ZERO) return V{0, 0}; Ic = C.nr; if (C.gR == GH_PARITY) fac *= sgn; }
   if (J == 0) { if (C.gB == GH_ZERO) return V{0, 0}; Jc = 1; if (C.gB == GH_PARITY) fac *= sgn; }
   if (J == C.nt + 1) { if (C.gT == GH_ZERO) return V{0, 0}; Jc = C.nt; if (C.gT == GH_PARITY) fac *= sgn; }
-  const V v = ec[(Jc - 1) * (C.nr + 1) + (Ic - 1)];
+  const V v = ec[vslot(C, Jc - 1, Ic - 1)];
   return V{fac * v.x, fac * v.y};
 }
 
@@ -140,10 +177,10 @@ __device__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, co
     const T p1 = R_(RT_P1, i1), p2 = R_(RT_P2, i1), q1 = T_(TT_P1, j1), q2 = T_(TT_P2, j1);
     const V a = s_cval<T>(C, ec, I1, J1, m), b = s_cval<T>(C, ec, I1 + 1, J1, m);
     const V c = s_cval<T>(C, ec, I1, J1 + 1, m), d = s_cval<T>(C, ec, I1 + 1, J1 + 1, m);
-    V u = e[j * (L.nr + 1) + i];
+    V u = e[vslot(L, j, i)];
     u.x += p1 * q1 * a.x + p2 * q1 * b.x + p1 * q2 * c.x + p2 * q2 * d.x;
     u.y += p1 * q1 * a.y + p2 * q1 * b.y + p1 * q2 * c.y + p2 * q2 * d.y;
-    e[j * (L.nr + 1) + i] = u;
+    e[vslot(L, j, i)] = u;
   }
   __syncthreads();
 }
@@ -167,7 +204,10 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
   // block-local copy of the level descriptors at them
   __shared__ LevelDev sL[8];
   {
+    // each table block starts one element past an even element offset, so
+    // the two entries of a cell pair are one aligned vector load
     T* tb = reinterpret_cast<T*>(sm + a.tab_off);
+    int toff = 0;
     for (int l = 0; l < K; ++l) {
       const LevelDev& G = a.L[l];
       const int NR = G.nr + 2, NT = G.nt + 2;
@@ -175,7 +215,8 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
       const T* gtt = tt_<T>(G);
       const T* gor = omr_<T>(G) + size_t(slot) * G.nt;
       const T* got = omt_<T>(G) + size_t(slot) * G.nr;
-      T* srt = tb;
+      toff = (toff + 1) / 2 * 2 + 1;
+      T* srt = tb + toff;
       T* stt = srt + RT_N * NR;
       T* sor = stt + TT_N * NT;
       T* sot = sor + G.nt;
@@ -189,14 +230,14 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
         else { d.rf = srt; d.tf = stt; d.omr_f = sor; d.omt_f = sot; }
         sL[l] = d;
       }
-      tb = sot + G.nr;
+      toff += RT_N * NR + TT_N * NT + G.nt + G.nr;
     }
   }
-  // load f of the first level (rows padded to nr + 1), zero all errors
+  // load f of the first level, zero all errors
   for (int k = threadIdx.x; k < n0; k += blockDim.x)
-    sm[a.off_f[0] + (k / nr0) * (nr0 + 1) + k % nr0] = gf[size_t(p) * n0 + k];
+    sm[a.off_f[0] + vslot(a.L[0], k / nr0, k % nr0)] = gf[size_t(p) * n0 + k];
   for (int l = 0; l < K; ++l) {
-    const int n = (a.L[l].nr + 1) * a.L[l].nt;
+    const int n = a.L[l].nr * a.L[l].nt;
     for (int k = threadIdx.x; k < n; k += blockDim.x) sm[a.off_e[l] + k] = V{0, 0};
   }
   __syncthreads();
@@ -209,7 +250,8 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     const double* A = a.inv + size_t(slot) * nc * nc;
     const V* fc = sm + a.off_f[K - 1];
     V* ec = sm + a.off_e[K - 1];
-    const int ldc = a.L[K - 1].nr + 1, ncr = a.L[K - 1].nr;
+    const LevelDev& Lc = a.L[K - 1];
+    const int ncr = Lc.nr;
     // g lanes per row; nc is a power of two >= 16, so g * nc is a whole
     // number of warps and every warp below it takes part in the shuffles
     int g = 1;
@@ -219,7 +261,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
       double sx = 0.0, sy = 0.0;
       for (int k = sub; k < nc; k += g) {
         const double c = A[size_t(row) * nc + k];
-        const V fk = fc[(k / ncr) * ldc + k % ncr];
+        const V fk = fc[vslot(Lc, k / ncr, k % ncr)];
         sx += c * double(fk.x);
         sy += c * double(fk.y);
       }
@@ -227,7 +269,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
       }
-      if (sub == 0) ec[(row / ncr) * ldc + row % ncr] = V{T(sx), T(sy)};
+      if (sub == 0) ec[vslot(Lc, row / ncr, row % ncr)] = V{T(sx), T(sy)};
     }
     __syncthreads();
   }
@@ -236,7 +278,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     s_smooth<T>(sL[l], sm + a.off_e[l], sm + a.off_f[l], s2, a.nu2, a.n_sor);
   }
   for (int k = threadIdx.x; k < n0; k += blockDim.x)
-    ge[size_t(p) * n0 + k] = sm[a.off_e[0] + (k / nr0) * (nr0 + 1) + k % nr0];
+    ge[size_t(p) * n0 + k] = sm[a.off_e[0] + vslot(a.L[0], k / nr0, k % nr0)];
 }
 
 // FP32 planes: 1024 threads (64 registers each); FP64 planes: 512 threads.

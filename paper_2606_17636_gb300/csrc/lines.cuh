@@ -1,7 +1,19 @@
 // Line relaxation building blocks shared by the smoothing kernels (Sec. 3.2):
-// one warp relaxes one radial line or one polar / vertical line; each lane
-// holds CPL consecutive cells in registers, neighbours across lanes come by
-// shuffles, so the n_sor even-odd SOR sweeps touch no memory.
+// one warp relaxes one radial line or one polar / vertical line held in
+// registers; neighbours across lanes come by shuffles, so the n_sor even-odd
+// SOR sweeps touch no memory.
+//
+// Lane mapping of a line of n cells (n <= 32, or n = 32 CPL with CPL even):
+//   CPL == 1   lane k holds cell k (lanes k >= n hold nothing);
+//   CPL even   lane k holds the pairs (2k + 64q, 2k + 1 + 64q), q < CPL / 2,
+//              in register slots 2q and 2q + 1.
+// A warp's access to a contiguous line then covers whole 128-byte rows (no
+// shared-memory bank conflicts, full global sectors), and each SOR half-sweep
+// needs one shuffle per pair.
+//
+// Coefficient tables hold the entry of cell i at index i + 1 and start one
+// element past an even element boundary, so the two entries of a pair are one
+// aligned vector load.
 #pragma once
 #include "kernels.h"
 
@@ -35,124 +47,222 @@ template <typename V> __device__ __forceinline__ V shdn(V v) {
   v.y = __shfl_down_sync(0xffffffffu, v.y, 1);
   return v;
 }
+template <typename V> __device__ __forceinline__ V shidx(V v, int src) {
+  v.x = __shfl_sync(0xffffffffu, v.x, src);
+  v.y = __shfl_sync(0xffffffffu, v.y, src);
+  return v;
+}
 
-// CPL consecutive complex values at p (16-byte vector accesses when possible).
+// Cell index held in register slot c of `lane`.
+template <int CPL> __device__ __forceinline__ int lcell(int lane, int c) {
+  if constexpr (CPL == 1) return lane;
+  else return 2 * lane + 64 * (c >> 1) + (c & 1);
+}
+
+// Two consecutive complex values (one 16-byte access for float2).
+template <typename V> __device__ __forceinline__ void ld_pair(V& a, V& b, const V* p) {
+  if constexpr (sizeof(V) == 8) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a.x = v.x; a.y = v.y; b.x = v.z; b.y = v.w;
+  } else {
+    a = p[0];
+    b = p[1];
+  }
+}
+template <typename V> __device__ __forceinline__ void st_pair(V* p, const V& a, const V& b) {
+  if constexpr (sizeof(V) == 8) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    p[0] = a;
+    p[1] = b;
+  }
+}
+
+// The lane's cells of a line of n cells stored contiguously at p.
 template <typename V, int CPL>
-__device__ __forceinline__ void ld_run(V (&d)[CPL], const V* p) {
-  if constexpr (sizeof(V) == 8 && CPL % 2 == 0) {
-    const float4* q = reinterpret_cast<const float4*>(p);
+__device__ __forceinline__ void ld_line(V (&d)[CPL], const V* p, int lane, int n) {
+  if constexpr (CPL == 1) {
+    d[0] = lane < n ? p[lane] : z2<V>();
+  } else {
 #pragma unroll
-    for (int c = 0; c < CPL / 2; ++c) {
-      const float4 v = q[c];
-      d[2 * c].x = v.x; d[2 * c].y = v.y; d[2 * c + 1].x = v.z; d[2 * c + 1].y = v.w;
+    for (int q = 0; q < CPL / 2; ++q) ld_pair(d[2 * q], d[2 * q + 1], p + 2 * lane + 64 * q);
+  }
+}
+template <typename V, int CPL>
+__device__ __forceinline__ void st_line(V* p, const V (&d)[CPL], int lane, int n) {
+  if constexpr (CPL == 1) {
+    if (lane < n) p[lane] = d[0];
+  } else {
+#pragma unroll
+    for (int q = 0; q < CPL / 2; ++q) st_pair(p + 2 * lane + 64 * q, d[2 * q], d[2 * q + 1]);
+  }
+}
+
+// Same for a row whose cell i is stored at row[i ^ s] (s < n, n a power of
+// two): a pair stays one aligned vector, swapped when s is odd.
+template <typename V, int CPL>
+__device__ __forceinline__ void ld_line_swz(V (&d)[CPL], const V* row, int s, int lane, int n) {
+  if constexpr (CPL == 1) {
+    d[0] = lane < n ? row[lane ^ s] : z2<V>();
+  } else {
+#pragma unroll
+    for (int q = 0; q < CPL / 2; ++q) {
+      V a, b;
+      ld_pair(a, b, row + ((2 * lane + 64 * q) ^ (s & ~1)));
+      d[2 * q] = (s & 1) ? b : a;
+      d[2 * q + 1] = (s & 1) ? a : b;
     }
-  } else {
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) d[c] = p[c];
   }
 }
 template <typename V, int CPL>
-__device__ __forceinline__ void st_run(V* p, const V (&d)[CPL]) {
-  if constexpr (sizeof(V) == 8 && CPL % 2 == 0) {
-    float4* q = reinterpret_cast<float4*>(p);
-#pragma unroll
-    for (int c = 0; c < CPL / 2; ++c) q[c] = make_float4(d[2 * c].x, d[2 * c].y, d[2 * c + 1].x, d[2 * c + 1].y);
+__device__ __forceinline__ void st_line_swz(V* row, int s, const V (&d)[CPL], int lane, int n) {
+  if constexpr (CPL == 1) {
+    if (lane < n) row[lane ^ s] = d[0];
   } else {
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) p[c] = d[c];
+    for (int q = 0; q < CPL / 2; ++q) {
+      const V a = (s & 1) ? d[2 * q + 1] : d[2 * q];
+      const V b = (s & 1) ? d[2 * q] : d[2 * q + 1];
+      st_pair(row + ((2 * lane + 64 * q) ^ (s & ~1)), a, b);
+    }
   }
 }
 
-// n_sor even-odd SOR sweeps of a line held in registers: x_k <- (1-w) x_k +
-// w (g_k - up_k x_{k+1} - dn_k x_{k-1}) id_k, cells of even position first.
+// Table entries of the lane's cells (entry of cell i at tab[i + 1]; 0 for
+// cells beyond n).
+template <typename T, int CPL>
+__device__ __forceinline__ void ld_tab(T (&d)[CPL], const T* tab, int lane, int n) {
+  if constexpr (CPL == 1) {
+    d[0] = lane < n ? tab[lane + 1] : T(0);
+  } else {
+#pragma unroll
+    for (int q = 0; q < CPL / 2; ++q) {
+      const vec2_t<T> v = *reinterpret_cast<const vec2_t<T>*>(tab + 2 * lane + 64 * q + 1);
+      d[2 * q] = v.x;
+      d[2 * q + 1] = v.y;
+    }
+  }
+}
+
+// n_sor even-odd SOR sweeps of a line of n cells held in registers:
+// x_k <- (1-w) x_k + w (g_k - up_k x_{k+1} - dn_k x_{k-1}) id_k, cells of even
+// index first; the ghosts beyond both ends are zero.
 template <typename T, int CPL>
 __device__ __forceinline__ void sor_line(vec2_t<T> (&ev)[CPL], const vec2_t<T> (&g)[CPL],
                                          const T (&up)[CPL], const T (&dn)[CPL], const T (&id)[CPL],
-                                         T w, int k0, bool on, bool last, int n_sor) {
+                                         T w, int n, int n_sor) {
   typedef vec2_t<T> V;
   const int lane = threadIdx.x & 31;
   const T w1 = T(1) - w;
-  for (int it = 0; it < n_sor; ++it) {
+  auto upd = [&](int c, const V& em, const V& ep) {
+    const T tx = (g[c].x - up[c] * ep.x - dn[c] * em.x) * id[c];
+    const T ty = (g[c].y - up[c] * ep.y - dn[c] * em.y) * id[c];
+    ev[c].x = w1 * ev[c].x + w * tx;
+    ev[c].y = w1 * ev[c].y + w * ty;
+  };
+  if constexpr (CPL == 1) {
+    const bool on = lane < n, last = lane == n - 1;
+    for (int it = 0; it < n_sor; ++it) {
 #pragma unroll
-    for (int par = 0; par < 2; ++par) {
-      V left = shup(ev[CPL - 1]);
-      V right = shdn(ev[0]);
-      if (lane == 0) left = z2<V>();
-      if (last) right = z2<V>();
+      for (int par = 0; par < 2; ++par) {
+        V left = shup(ev[0]);
+        V right = shdn(ev[0]);
+        if (lane == 0) left = z2<V>();
+        if (last) right = z2<V>();
+        if (on && (lane & 1) == par) upd(0, left, right);
+      }
+    }
+  } else {
+    constexpr int NP = CPL / 2;
+    const int prv = (lane + 31) & 31, nxt = (lane + 1) & 31;
+    for (int it = 0; it < n_sor; ++it) {
+      V r[NP];
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        if (on && ((k0 + c) & 1) == par) {
-          const V em = (c > 0) ? ev[c - 1] : left;
-          const V ep = (c < CPL - 1) ? ev[c + 1] : right;
-          const T tx = (g[c].x - up[c] * ep.x - dn[c] * em.x) * id[c];
-          const T ty = (g[c].y - up[c] * ep.y - dn[c] * em.y) * id[c];
-          ev[c].x = w1 * ev[c].x + w * tx;
-          ev[c].y = w1 * ev[c].y + w * ty;
-        }
+      for (int q = 0; q < NP; ++q) r[q] = shidx(ev[2 * q + 1], prv);   // odd cell 2k - 1 + 64q
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        V left = r[q];
+        if (lane == 0) left = q == 0 ? z2<V>() : r[q > 0 ? q - 1 : 0];
+        upd(2 * q, left, ev[2 * q + 1]);
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) r[q] = shidx(ev[2 * q], nxt);       // even cell 2k + 2 + 64q
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        V right = r[q];
+        if (lane == 31) right = q == NP - 1 ? z2<V>() : r[q + 1 < NP ? q + 1 : q];
+        upd(2 * q + 1, ev[2 * q], right);
       }
     }
   }
 }
 
-// Radial line j from registers: g = source line, un / us = neighbour lines
-// j+1 / j-1, ev = own line on entry, relaxed line on exit (lane holds cells
-// lane*CPL ..).
+// Radial line j: g = source values of the lane's cells (clobbered), un / us =
+// lines j+1 / j-1 (zero beyond the plane), ev = own line on entry, relaxed
+// line on exit.
 template <typename T, int CPL>
-__device__ __forceinline__ void relax_rline_regs(const LevelDev& L, const T* rt, const T* tt, T s2,
-                                                 T w, int j, vec2_t<T> (&g)[CPL],
-                                                 const vec2_t<T> (&un)[CPL],
-                                                 const vec2_t<T> (&us)[CPL], int n_sor,
-                                                 vec2_t<T> (&ev)[CPL]) {
+__device__ __forceinline__ void relax_r(const LevelDev& L, const T* rt, const T* tt, T s2, T w,
+                                        int j, vec2_t<T> (&g)[CPL], const vec2_t<T> (&un)[CPL],
+                                        const vec2_t<T> (&us)[CPL], int n_sor,
+                                        vec2_t<T> (&ev)[CPL]) {
   const int lane = threadIdx.x & 31, nr = L.nr, NR = nr + 2, NT = L.nt + 2;
-  const int i0 = lane * CPL;
-  const bool on = i0 < nr;
   const T aN = tt[TT_AN * NT + j + 1], aS = tt[TT_AS * NT + j + 1];
   const T Tj = tt[TT_T * NT + j + 1], dtj = tt[TT_DT * NT + j + 1];
+  const bool on = CPL > 1 || lane < nr;
+  // neighbour lines first (they die here), then the diagonal, then the
+  // along-line couplings: keeps the live register set small
+  T P[CPL], up[CPL], dn[CPL], id[CPL];
+  ld_tab<T, CPL>(P, rt + RT_P * NR, lane, nr);
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    g[c].x = g[c].x - P[c] * (aN * un[c].x + aS * us[c].x);
+    g[c].y = g[c].y - P[c] * (aN * un[c].y + aS * us[c].y);
+  }
+  {
+    T dr[CPL], q[CPL];
+    ld_tab<T, CPL>(dr, rt + RT_DR * NR, lane, nr);
+    ld_tab<T, CPL>(q, rt + RT_Q * NR, lane, nr);
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) id[c] = on ? T(1) / (dr[c] + P[c] * dtj - s2 * q[c] * Tj) : T(0);
+  }
+  ld_tab<T, CPL>(up, rt + RT_AE * NR, lane, nr);
+  ld_tab<T, CPL>(dn, rt + RT_AW * NR, lane, nr);
+  sor_line<T, CPL>(ev, g, up, dn, id, w, nr, n_sor);
+}
+
+// Polar / vertical line i: g = source values of the lane's cells (clobbered),
+// ue / uw = columns i+1 / i-1 (zero beyond the plane), ev = own column on
+// entry, relaxed column on exit.
+template <typename T, int CPL>
+__device__ __forceinline__ void relax_t(const LevelDev& L, const T* rt, const T* tt, T s2, T w,
+                                        int i, vec2_t<T> (&g)[CPL], const vec2_t<T> (&ue)[CPL],
+                                        const vec2_t<T> (&uw)[CPL], int n_sor,
+                                        vec2_t<T> (&ev)[CPL]) {
+  const int lane = threadIdx.x & 31, nt = L.nt, NR = L.nr + 2, NT = nt + 2;
+  const T P = rt[RT_P * NR + i + 1], aE = rt[RT_AE * NR + i + 1], aW = rt[RT_AW * NR + i + 1];
+  const T dr = rt[RT_DR * NR + i + 1], Qi = rt[RT_Q * NR + i + 1];
+  const bool on = CPL > 1 || lane < nt;
   T up[CPL], dn[CPL], id[CPL];
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
-    const int i = i0 + c + 1;
-    const T P = on ? rt[RT_P * NR + i] : T(0);
-    g[c].x = g[c].x - P * (aN * un[c].x + aS * us[c].x);
-    g[c].y = g[c].y - P * (aN * un[c].y + aS * us[c].y);
-    up[c] = on ? rt[RT_AE * NR + i] : T(0);
-    dn[c] = on ? rt[RT_AW * NR + i] : T(0);
-    id[c] = on ? T(1) / (rt[RT_DR * NR + i] + P * dtj - s2 * rt[RT_Q * NR + i] * Tj) : T(0);
+    g[c].x = g[c].x - aE * ue[c].x - aW * uw[c].x;
+    g[c].y = g[c].y - aE * ue[c].y - aW * uw[c].y;
   }
-  sor_line<T, CPL>(ev, g, up, dn, id, w, i0, on, i0 + CPL >= nr, n_sor);
-}
-
-// Radial line j: own line (nullptr = 0), neighbour lines j+1 / j-1 (nullptr =
-// ghost 0), source line; contiguous storage.  Result in ev.
-template <typename T, int CPL, bool VEC = true>
-__device__ __forceinline__ void relax_rline(const LevelDev& L, const T* rt, const T* tt, T s2, T w,
-                                            int j, const vec2_t<T>* own, const vec2_t<T>* nn,
-                                            const vec2_t<T>* ss, const vec2_t<T>* fl_, int n_sor,
-                                            vec2_t<T> (&ev)[CPL]) {
-  typedef vec2_t<T> V;
-  const int lane = threadIdx.x & 31, nr = L.nr;
-  const int i0 = lane * CPL;
-  const bool on = i0 < nr;
-  V g[CPL], un[CPL], us[CPL];
+  {
+    T dt[CPL], tj[CPL];
+    ld_tab<T, CPL>(dt, tt + TT_DT * NT, lane, nt);
+    ld_tab<T, CPL>(tj, tt + TT_T * NT, lane, nt);
 #pragma unroll
-  for (int c = 0; c < CPL; ++c) { ev[c] = z2<V>(); g[c] = z2<V>(); un[c] = z2<V>(); us[c] = z2<V>(); }
-  if (on) {
-    if constexpr (VEC) {
-      ld_run<V, CPL>(g, fl_ + i0);
-      if (own) ld_run<V, CPL>(ev, own + i0);
-      if (nn) ld_run<V, CPL>(un, nn + i0);
-      if (ss) ld_run<V, CPL>(us, ss + i0);
-    } else {
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        g[c] = fl_[i0 + c];
-        if (own) ev[c] = own[i0 + c];
-        if (nn) un[c] = nn[i0 + c];
-        if (ss) us[c] = ss[i0 + c];
-      }
-    }
+    for (int c = 0; c < CPL; ++c) id[c] = on ? T(1) / (dr + P * dt[c] - s2 * Qi * tj[c]) : T(0);
   }
-  relax_rline_regs<T, CPL>(L, rt, tt, s2, w, j, g, un, us, n_sor, ev);
+  ld_tab<T, CPL>(up, tt + TT_AN * NT, lane, nt);
+  ld_tab<T, CPL>(dn, tt + TT_AS * NT, lane, nt);
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    up[c] = P * up[c];
+    dn[c] = P * dn[c];
+  }
+  sor_line<T, CPL>(ev, g, up, dn, id, w, nt, n_sor);
 }
 
 // Bilinear coarse correction (Sec. 3.1, Eq. prolongation_sph) at fine cell
@@ -189,45 +299,6 @@ __device__ __forceinline__ vec2_t<T> prolong_at(const LevelDev& L, const T* rt, 
   r.x = p1 * q1 * a.x + p2 * q1 * b.x + p1 * q2 * c.x + p2 * q2 * d.x;
   r.y = p1 * q1 * a.y + p2 * q1 * b.y + p1 * q2 * c.y + p2 * q2 * d.y;
   return r;
-}
-
-// Polar / vertical line i stored with row stride `ld` (an odd stride keeps
-// the strided column loads to at most CPL-way shared-memory bank conflicts;
-// they happen once per line, the SOR sweeps run in registers): own column,
-// west and east neighbour columns (nullptr = ghost 0), source column.  Lane k
-// holds cells j = k*CPL .. k*CPL+CPL-1; result in ev.
-template <typename T, int CPL>
-__device__ __forceinline__ void relax_tcol(const LevelDev& L, const T* rt, const T* tt, T s2, T w,
-                                           int i, const vec2_t<T>* own, const vec2_t<T>* west,
-                                           const vec2_t<T>* east, const vec2_t<T>* fcol, int ld,
-                                           int n_sor, vec2_t<T> (&ev)[CPL]) {
-  typedef vec2_t<T> V;
-  const int lane = threadIdx.x & 31, nt = L.nt, NR = L.nr + 2, NT = nt + 2;
-  const int j0 = lane * CPL;
-  const bool on = j0 < nt;
-  const T P = rt[RT_P * NR + i + 1], aE = rt[RT_AE * NR + i + 1], aW = rt[RT_AW * NR + i + 1];
-  const T dr = rt[RT_DR * NR + i + 1], Qi = rt[RT_Q * NR + i + 1];
-  V g[CPL];
-  T up[CPL], dn[CPL], id[CPL];
-#pragma unroll
-  for (int c = 0; c < CPL; ++c) {
-    const int j = j0 + c;
-    ev[c] = z2<V>();
-    g[c] = z2<V>();
-    up[c] = dn[c] = id[c] = T(0);
-    if (on) {
-      const V fv = fcol[size_t(j) * ld];
-      const V ue = east ? east[size_t(j) * ld] : z2<V>();
-      const V uw = west ? west[size_t(j) * ld] : z2<V>();
-      g[c].x = fv.x - aE * ue.x - aW * uw.x;
-      g[c].y = fv.y - aE * ue.y - aW * uw.y;
-      if (own) ev[c] = own[size_t(j) * ld];
-      up[c] = P * tt[TT_AN * NT + j + 1];
-      dn[c] = P * tt[TT_AS * NT + j + 1];
-      id[c] = T(1) / (dr + P * tt[TT_DT * NT + j + 1] - s2 * Qi * tt[TT_T * NT + j + 1]);
-    }
-  }
-  sor_line<T, CPL>(ev, g, up, dn, id, w, j0, on, j0 + CPL >= nt, n_sor);
 }
 
 }  // namespace ps

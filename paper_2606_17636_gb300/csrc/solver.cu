@@ -3,6 +3,8 @@
 // mode-by-mode iteration replaced by a batch that drops converged modes).
 #include "solver.h"
 
+#include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <string>
 
@@ -14,6 +16,10 @@ void* Arena::get(size_t n) {
   void* p = nullptr;
   if (alloc_fn) {
     p = alloc_fn(n, user);
+    if (p && (reinterpret_cast<uintptr_t>(p) & 255)) {   // kernels rely on 256-byte alignment
+      if (free_fn) free_fn(p, user);
+      p = nullptr;
+    }
   } else if (cudaMalloc(&p, n) != cudaSuccess) {
     p = nullptr;
   }
@@ -40,6 +46,17 @@ static X* upload(Arena& A, const std::vector<X>& v) {
   return d;
 }
 
+// A coefficient table with one leading pad element: the returned pointer is
+// one element past the (256-byte aligned) block start, so entry i + 1 of cell
+// i puts every even cell at an even element offset (aligned pair loads).
+template <typename X>
+static X* upload_tab(Arena& A, const std::vector<X>& v) {
+  std::vector<X> pad(v.size() + 1, X(0));
+  std::copy(v.begin(), v.end(), pad.begin() + 1);
+  X* d = upload(A, pad);
+  return d ? d + 1 : nullptr;
+}
+
 static std::vector<float> to_f(const std::vector<double>& v) {
   return std::vector<float>(v.begin(), v.end());
 }
@@ -57,10 +74,10 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
     LevelDev& d = lv[l];
     d.nr = h.g.r.n;
     d.nt = h.g.t.n;
-    d.rd = upload(A, h.rtab);
-    d.td = upload(A, h.ttab);
-    d.rf = upload(A, to_f(h.rtab));
-    d.tf = upload(A, to_f(h.ttab));
+    d.rd = upload_tab(A, h.rtab);
+    d.td = upload_tab(A, h.ttab);
+    d.rf = upload_tab(A, to_f(h.rtab));
+    d.tf = upload_tab(A, to_f(h.ttab));
     d.omr_d = upload(A, h.om_r);
     d.omt_d = upload(A, h.om_t);
     d.omr_f = upload(A, to_f(h.om_r));
@@ -93,8 +110,8 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
     size_t bytes = 0;
     const size_t tb = vb / 2;   // bytes of one real table entry
     for (int l = nl - 1; l >= 0; --l) {
-      bytes += 2 * size_t(lv[l].nr + 1) * lv[l].nt * vb;
-      bytes += (size_t(RT_N) * (lv[l].nr + 2) + size_t(TT_N) * (lv[l].nt + 2) + lv[l].nr + lv[l].nt) * tb;
+      bytes += 2 * size_t(lv[l].nr) * lv[l].nt * vb;
+      bytes += (size_t(RT_N) * (lv[l].nr + 2) + size_t(TT_N) * (lv[l].nt + 2) + lv[l].nr + lv[l].nt + 2) * tb;
       if (bytes > 210 * 1024 || lv[l].nr > 128 || lv[l].nt > 128 || nl - l > 8) break;
       first = l;
     }
@@ -104,15 +121,15 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
       const LevelDev& d = lv[first + k];
       vs.L[k] = d;
       vs.off_e[k] = int(off);
-      off += size_t(d.nr + 1) * d.nt;
+      off += size_t(d.nr) * d.nt;
       vs.off_f[k] = int(off);
-      off += size_t(d.nr + 1) * d.nt;
+      off += size_t(d.nr) * d.nt;
     }
     vs.tab_off = int(off);
     size_t tab = 0;
     for (int k = 0; k < vs.nlev; ++k) {
       const LevelDev& d = lv[first + k];
-      tab += size_t(RT_N) * (d.nr + 2) + size_t(TT_N) * (d.nt + 2) + d.nr + d.nt;
+      tab += size_t(RT_N) * (d.nr + 2) + size_t(TT_N) * (d.nt + 2) + d.nr + d.nt + 2;
     }
     vs.smem_bytes = off * vb + tab * (vb / 2) + 16;
     vs.inv = d_inv;
