@@ -233,6 +233,13 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
       toff += RT_N * NR + TT_N * NT + G.nt + G.nr;
     }
   }
+  // this mode's coarsest-level block factors (when they fit)
+  const size_t blk_stride = size_t(a.blk_nt) * a.blk_n * (a.blk_n + 2);
+  if (a.blk_smem) {
+    const double2* src = reinterpret_cast<const double2*>(a.blk + size_t(slot) * blk_stride);
+    double2* dst = reinterpret_cast<double2*>(vraw + a.blk_off);
+    for (int k = threadIdx.x; k < int(blk_stride / 2); k += blockDim.x) dst[k] = src[k];
+  }
   // load f of the first level, zero all errors
   for (int k = threadIdx.x; k < n0; k += blockDim.x)
     sm[a.off_f[0] + vslot(a.L[0], k / nr0, k % nr0)] = gf[size_t(p) * n0 + k];
@@ -245,7 +252,64 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     s_smooth<T>(sL[l], sm + a.off_e[l], sm + a.off_f[l], s2, a.nu1, a.n_sor);
     s_restrict<T>(sL[l], sL[l + 1], sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
   }
-  {   // coarsest level: e = L^{-1} f, FP64 dot products, g threads per row
+  if (a.blk_n > 0) {
+    // coarsest level, exact FP64 block-tridiagonal solve (Schur complements
+    // of the polar rows): forward z_J = f_J - b_J (S_{J-1}^{-1} z_{J-1}),
+    // backward x_J = S_J^{-1} (z_J - c_J x_{J+1}).  Four warps (128 threads:
+    // 2 components x n rows x g lanes per row) step through the 2 nt - 1
+    // block products, joined by a named barrier.
+    const int n = a.blk_n, nb = a.blk_nt, nc = a.nc;
+    const LevelDev& Lc = a.L[K - 1];
+    const V* fc = sm + a.off_f[K - 1];
+    V* ec = sm + a.off_e[K - 1];
+    double* z = reinterpret_cast<double*>(vraw + a.dbl_off);   // [2][nc]
+    double* x = z + 2 * nc;                                     // [2][nc]
+    const double* S = a.blk_smem ? reinterpret_cast<const double*>(vraw + a.blk_off)
+                                 : a.blk + size_t(slot) * blk_stride;
+    const double* bsub = S + size_t(nb) * n * n;
+    const double* csup = bsub + size_t(nb) * n;
+    const int t = threadIdx.x;
+    if (t < 128) {
+      const int g = 64 / n;
+      const int sub = t & (g - 1), r = (t / g) % n, c = t / (n * g);
+      auto fval = [&](int J) {
+        const V v = fc[vslot(Lc, J, r)];
+        return double(c ? v.y : v.x);
+      };
+      if (sub == 0) z[c * nc + r] = fval(0);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      for (int J = 1; J < nb; ++J) {
+        const double* Sr = S + size_t(J - 1) * n * n + size_t(r) * n;
+        const double* zp = z + c * nc + (J - 1) * n;
+        double acc = 0.0;
+        for (int k = sub; k < n; k += g) acc += Sr[k] * zp[k];
+        for (int o = g >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (sub == 0) z[c * nc + J * n + r] = fval(J) - bsub[J * n + r] * acc;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      }
+      for (int J = nb - 1; J >= 0; --J) {
+        const double* Sr = S + size_t(J) * n * n + size_t(r) * n;
+        const double* zJ = z + c * nc + J * n;
+        double acc = 0.0;
+        if (J == nb - 1) {
+          for (int k = sub; k < n; k += g) acc += Sr[k] * zJ[k];
+        } else {
+          const double* xn = x + c * nc + (J + 1) * n;
+          const double* cJ = csup + J * n;
+          for (int k = sub; k < n; k += g) acc += Sr[k] * (zJ[k] - cJ[k] * xn[k]);
+        }
+        for (int o = g >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (sub == 0) x[c * nc + J * n + r] = acc;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      const int J = q / n, i = q - J * n;
+      ec[vslot(Lc, J, i)] = V{T(x[q]), T(x[nc + q])};
+    }
+    __syncthreads();
+  } else {   // coarsest level: e = L^{-1} f, FP64 dot products, g threads per row
     const int nc = a.nc;
     const double* A = a.inv + size_t(slot) * nc * nc;
     const V* fc = sm + a.off_f[K - 1];

@@ -61,8 +61,12 @@ struct VSmemArgs {
   int nlev;              // levels first .. coarsest
   LevelDev L[8];
   int off_e[8], off_f[8];   // shared-memory offsets (complex elements)
-  const double* inv;     // coarsest-level inverse [slots][nc][nc]
+  const double* inv;     // dense coarsest-level inverse [slots][nc][nc] (blk_n == 0)
+  const double* blk;     // coarsest-level block factors [slots][blk_stride] (blk_n > 0)
   int nc;
+  int blk_n, blk_nt;     // block size (= coarsest nr) and block count (= coarsest nt)
+  int blk_smem;          // 1: this slot's factors are staged in shared memory at blk_off
+  int dbl_off, blk_off;  // byte offsets in shared memory: FP64 solve scratch, staged factors
   int nu1, nu2, n_sor;
   int tab_off;           // shared-memory offset (complex elements) of the staged tables
   size_t smem_bytes;

@@ -274,8 +274,13 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
   const LevelHost& C = H.lv.back();
   const int nr = C.g.r.n, nt = C.g.t.n, nc = nr * nt;
   H.nc = nc;
-  H.coarse_inv.assign(size_t(M) * nc * nc, 0.0);
-  std::vector<double> A(size_t(nc) * nc);
+  const bool blocks = nr <= 64;
+  H.blk_n = blocks ? nr : 0;
+  H.blk_nt = blocks ? nt : 0;
+  const size_t bstride = size_t(nt) * nr * (nr + 2);
+  if (blocks) H.coarse_blk.assign(size_t(M) * bstride, 0.0);
+  else H.coarse_inv.assign(size_t(M) * nc * nc, 0.0);
+  std::vector<double> A(size_t(nc) * nc), S(size_t(nr) * nr);
   for (int k = 0; k < M; ++k) {
     std::fill(A.begin(), A.end(), 0.0);
     int m = modes[k];
@@ -288,8 +293,30 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
         if (j < nt) A[size_t(row) * nc + row + nr] = C.g.P[i] * C.g.aN[j];
         if (j > 1) A[size_t(row) * nc + row - nr] = C.g.P[i] * C.g.aS[j];
       }
-    if (!invert(A, nc)) { err = "singular coarsest-level operator"; return false; }
-    std::copy(A.begin(), A.end(), H.coarse_inv.begin() + size_t(k) * nc * nc);
+    if (!blocks) {
+      if (!invert(A, nc)) { err = "singular coarsest-level operator"; return false; }
+      std::copy(A.begin(), A.end(), H.coarse_inv.begin() + size_t(k) * nc * nc);
+      continue;
+    }
+    double* out = H.coarse_blk.data() + size_t(k) * bstride;
+    double* bsub = out + size_t(nt) * nr * nr;
+    double* csup = bsub + size_t(nt) * nr;
+    auto a = [&](int J, int r, int J2, int r2) { return A[size_t(J * nr + r) * nc + J2 * nr + r2]; };
+    for (int J = 0; J < nt; ++J) {
+      for (int r = 0; r < nr; ++r) {
+        bsub[J * nr + r] = J > 0 ? a(J, r, J - 1, r) : 0.0;
+        csup[J * nr + r] = J + 1 < nt ? a(J, r, J + 1, r) : 0.0;
+      }
+      for (int r = 0; r < nr; ++r)
+        for (int q = 0; q < nr; ++q) {
+          double v = a(J, r, J, q);
+          if (J > 0)
+            v -= bsub[J * nr + r] * out[size_t(J - 1) * nr * nr + r * nr + q] * csup[(J - 1) * nr + q];
+          S[size_t(r) * nr + q] = v;
+        }
+      if (!invert(S, nr)) { err = "singular coarsest-level operator"; return false; }
+      std::copy(S.begin(), S.end(), out + size_t(J) * nr * nr);
+    }
   }
   return true;
 }

@@ -65,8 +65,17 @@ struct LevelHost {
 
 struct Hierarchy {
   std::vector<LevelHost> lv;
-  std::vector<double> coarse_inv;   // [M][nc][nc] inverse of L_m on the coarsest level
-  int nc = 0;
+  int nc = 0;                       // cells of the coarsest level
+  // Block factors of L_m on the coarsest level (blocks = polar rows J of
+  // nb = nr cells, L_m block tridiagonal with diagonal couplings), per mode
+  // slot: [nt][nb][nb] inverses of the Schur complements
+  // S_0 = D_0, S_J = D_J - B_J S_{J-1}^{-1} C_{J-1}; then [nt][nb] sub-diagonal
+  // couplings b_J (row J to J-1) and [nt][nb] super-diagonal couplings c_J
+  // (row J to J+1).  Used when nb <= 64; otherwise coarse_inv holds the dense
+  // inverse [M][nc][nc].
+  std::vector<double> coarse_blk;
+  std::vector<double> coarse_inv;
+  int blk_n = 0, blk_nt = 0;
 };
 
 // Build levels (coarsening stops at a short side of 8 cells, or 4 cells when

@@ -91,7 +91,8 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   d_s2f = upload(A, to_f(s2));
   d_mode = upload(A, modes);
   d_slot = plane_slot.empty() ? nullptr : upload(A, plane_slot);
-  d_inv = upload(A, H.coarse_inv);
+  if (!H.coarse_inv.empty()) d_inv = upload(A, H.coarse_inv);
+  if (!H.coarse_blk.empty()) d_blk = upload(A, H.coarse_blk);
   const size_t vb = vbytes();
   e.assign(nl, nullptr);
   f.assign(nl, nullptr);
@@ -107,7 +108,8 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   // side fit in 200 KB (lines of at most 128 cells)
   first = nl - 1;
   {
-    size_t bytes = 0;
+    const size_t zx_bytes = 4 * size_t(H.nc) * sizeof(double) + 16;   // FP64 coarse-solve scratch
+    size_t bytes = zx_bytes;
     const size_t tb = vb / 2;   // bytes of one real table entry
     for (int l = nl - 1; l >= 0; --l) {
       bytes += 2 * size_t(lv[l].nr) * lv[l].nt * vb;
@@ -131,9 +133,19 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
       const LevelDev& d = lv[first + k];
       tab += size_t(RT_N) * (d.nr + 2) + size_t(TT_N) * (d.nt + 2) + d.nr + d.nt + 2;
     }
-    vs.smem_bytes = off * vb + tab * (vb / 2) + 16;
+    size_t sbytes = (off * vb + tab * (vb / 2) + 15) / 16 * 16;
+    vs.dbl_off = int(sbytes);
+    sbytes += 4 * size_t(H.nc) * sizeof(double);
     vs.inv = d_inv;
+    vs.blk = d_blk;
     vs.nc = H.nc;
+    vs.blk_n = H.blk_n;
+    vs.blk_nt = H.blk_nt;
+    const size_t blk_bytes = size_t(H.blk_nt) * H.blk_n * (H.blk_n + 2) * sizeof(double);
+    vs.blk_smem = (H.blk_n > 0 && sbytes + blk_bytes <= 220 * 1024) ? 1 : 0;
+    vs.blk_off = int(sbytes);
+    if (vs.blk_smem) sbytes += blk_bytes;
+    vs.smem_bytes = sbytes + 16;
     if (H.nc < 16 || (H.nc & (H.nc - 1))) { err = "coarsest level must have a power-of-two size >= 16"; return false; }
     vs.nu1 = opt.nu1;
     vs.nu2 = opt.nu2;

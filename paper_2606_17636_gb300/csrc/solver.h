@@ -74,6 +74,7 @@ class MGSolver {
   double* d_s2 = nullptr;
   float* d_s2f = nullptr;
   double* d_inv = nullptr;
+  double* d_blk = nullptr;
   double4* d_part = nullptr;
   double4* d_psum = nullptr;
   int* d_cnt = nullptr;
