@@ -43,6 +43,21 @@ template <> __device__ __forceinline__ double2 vmk<double2, double>(double a, do
 
 enum { ST_ACTIVE = 1, ST_OK = 0, ST_STAGNATED = 2, ST_NOTCONV = -4, ST_NONFINITE = -5 };
 
+// Grids of the per-plane kernels are bounded (a few blocks per SM) and loop
+// over work items w = k * bpp + b (active plane k, block b of bpp), so the
+// cost of a launch follows the active planes, not the planes allocated.
+static int work_grid(long items) {
+  static int sms = 0;   // cached on first use (the solver's set-up, before any capture)
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 132;
+  }
+  const long cap = long(sms) * 8;
+  return int(items < cap ? (items > 0 ? items : 1) : cap);
+}
+
 __device__ __forceinline__ bool plane_of(const Batch& B, int k, int& p, int& slot) {
   if (k >= *B.nact) return false;
   p = B.act[k];
@@ -80,35 +95,38 @@ __global__ void __launch_bounds__(256) k_restrict(LevelDev L, LevelDev C, Batch 
                                                   const vec2_t<T>* __restrict__ f,
                                                   vec2_t<T>* __restrict__ fc) {
   typedef vec2_t<T> V;
-  int p, slot;
-  if (!plane_of(B, blockIdx.y, p, slot)) return;
-  const int cidx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cidx >= C.nr * C.nt) return;
-  const int J = cidx / C.nr, I = cidx - J * C.nr;
+  const int nact = *B.nact, nc = C.nr * C.nt, bpp = (nc + blockDim.x - 1) / blockDim.x;
   const T* rt = rtab<T>(L);
   const T* tt = ttab<T>(L);
-  const T s2 = s2of<T>(B, slot);
-  const size_t base = size_t(p) * L.nr * L.nt;
-  T ax = 0, ay = 0;
+  for (int w = blockIdx.x; w < nact * bpp; w += gridDim.x) {
+    const int k = w / bpp;
+    const int cidx = (w - k * bpp) * blockDim.x + threadIdx.x;
+    if (cidx >= nc) continue;
+    const int p = B.act[k];
+    const int slot = B.slot ? B.slot[p] : p;
+    const int J = cidx / C.nr, I = cidx - J * C.nr;
+    const T s2 = s2of<T>(B, slot);
+    const size_t base = size_t(p) * L.nr * L.nt;
+    T ax = 0, ay = 0;
 #pragma unroll
-  for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 2; ++b)
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      const int i = 2 * I + a, j = 2 * J + b;
-      const V r = defect<T>(L, rt, tt, s2, e + base, f + base, i, j);
-      const T wgt = RTAB(rt, RT_RW, i + 1) * TTAB(tt, TT_RW, j + 1);
-      ax += wgt * r.x;
-      ay += wgt * r.y;
-    }
-  fc[size_t(p) * C.nr * C.nt + cidx] = vmk<V, T>(ax, ay);
+      for (int a = 0; a < 2; ++a) {
+        const int i = 2 * I + a, j = 2 * J + b;
+        const V r = defect<T>(L, rt, tt, s2, e + base, f + base, i, j);
+        const T wgt = RTAB(rt, RT_RW, i + 1) * TTAB(tt, TT_RW, j + 1);
+        ax += wgt * r.x;
+        ay += wgt * r.y;
+      }
+    fc[size_t(p) * nc + cidx] = vmk<V, T>(ax, ay);
+  }
 }
 
 template <typename T>
 void launch_restrict(const LevelDev& F, const LevelDev& C, const Batch& B, const vec2_t<T>* e,
                      const vec2_t<T>* f, vec2_t<T>* fc, cudaStream_t st) {
   const int n = C.nr * C.nt;
-  dim3 grid((n + 255) / 256, B.max_planes);
-  k_restrict<T><<<grid, 256, 0, st>>>(F, C, B, e, f, fc);
+  k_restrict<T><<<work_grid(long((n + 255) / 256) * B.max_planes), 256, 0, st>>>(F, C, B, e, f, fc);
 }
 
 // ---------------------------------------------------------------------------
@@ -134,32 +152,35 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev L, LevelDev C, Batch B
                                                  vec2_t<T>* __restrict__ e,
                                                  const vec2_t<T>* __restrict__ ec) {
   typedef vec2_t<T> V;
-  int p, slot;
-  if (!plane_of(B, blockIdx.y, p, slot)) return;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= L.nr * L.nt) return;
-  const int j = idx / L.nr, i = idx - j * L.nr;
-  const int i1 = i + 1, j1 = j + 1;
-  const int I1 = (i1 & 1) ? (i1 + 1) / 2 - 1 : i1 / 2, J1 = (j1 & 1) ? (j1 + 1) / 2 - 1 : j1 / 2;
+  const int nact = *B.nact, n = L.nr * L.nt, bpp = (n + blockDim.x - 1) / blockDim.x;
   const T* rt = rtab<T>(L);
   const T* tt = ttab<T>(L);
-  const T p1 = RTAB(rt, RT_P1, i1), p2 = RTAB(rt, RT_P2, i1);
-  const T q1 = TTAB(tt, TT_P1, j1), q2 = TTAB(tt, TT_P2, j1);
-  const int m = B.mode[slot];
-  const V* ecp = ec + size_t(p) * C.nr * C.nt;
-  const V a = coarse_val<T>(C, ecp, I1, J1, m), b = coarse_val<T>(C, ecp, I1 + 1, J1, m);
-  const V c = coarse_val<T>(C, ecp, I1, J1 + 1, m), d = coarse_val<T>(C, ecp, I1 + 1, J1 + 1, m);
-  V& u = e[size_t(p) * L.nr * L.nt + idx];
-  u.x += p1 * q1 * a.x + p2 * q1 * b.x + p1 * q2 * c.x + p2 * q2 * d.x;
-  u.y += p1 * q1 * a.y + p2 * q1 * b.y + p1 * q2 * c.y + p2 * q2 * d.y;
+  for (int w = blockIdx.x; w < nact * bpp; w += gridDim.x) {
+    const int k = w / bpp;
+    const int idx = (w - k * bpp) * blockDim.x + threadIdx.x;
+    if (idx >= n) continue;
+    const int p = B.act[k];
+    const int slot = B.slot ? B.slot[p] : p;
+    const int j = idx / L.nr, i = idx - j * L.nr;
+    const int i1 = i + 1, j1 = j + 1;
+    const int I1 = (i1 & 1) ? (i1 + 1) / 2 - 1 : i1 / 2, J1 = (j1 & 1) ? (j1 + 1) / 2 - 1 : j1 / 2;
+    const T p1 = RTAB(rt, RT_P1, i1), p2 = RTAB(rt, RT_P2, i1);
+    const T q1 = TTAB(tt, TT_P1, j1), q2 = TTAB(tt, TT_P2, j1);
+    const int m = B.mode[slot];
+    const V* ecp = ec + size_t(p) * C.nr * C.nt;
+    const V a = coarse_val<T>(C, ecp, I1, J1, m), b = coarse_val<T>(C, ecp, I1 + 1, J1, m);
+    const V c = coarse_val<T>(C, ecp, I1, J1 + 1, m), d = coarse_val<T>(C, ecp, I1 + 1, J1 + 1, m);
+    V& u = e[size_t(p) * n + idx];
+    u.x += p1 * q1 * a.x + p2 * q1 * b.x + p1 * q2 * c.x + p2 * q2 * d.x;
+    u.y += p1 * q1 * a.y + p2 * q1 * b.y + p1 * q2 * c.y + p2 * q2 * d.y;
+  }
 }
 
 template <typename T>
 void launch_prolong(const LevelDev& F, const LevelDev& C, const Batch& B, vec2_t<T>* e,
                     const vec2_t<T>* ec, cudaStream_t st) {
   const int n = F.nr * F.nt;
-  dim3 grid((n + 255) / 256, B.max_planes);
-  k_prolong<T><<<grid, 256, 0, st>>>(F, C, B, e, ec);
+  k_prolong<T><<<work_grid(long((n + 255) / 256) * B.max_planes), 256, 0, st>>>(F, C, B, e, ec);
 }
 
 // ---------------------------------------------------------------------------
@@ -168,27 +189,31 @@ void launch_prolong(const LevelDev& F, const LevelDev& C, const Batch& B, vec2_t
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_update(int n, Batch B, double2* __restrict__ u, const vec2_t<T>* __restrict__ e) {
-  int p, slot;
-  if (!plane_of(B, blockIdx.y, p, slot)) return;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n) return;
-  const size_t o = size_t(p) * n + idx;
-  const vec2_t<T> v = e[o];
-  double2 w = u[o];
-  w.x += double(v.x);
-  w.y += double(v.y);
-  u[o] = w;
+  const int nact = *B.nact, bpp = (n + blockDim.x - 1) / blockDim.x;
+  for (int w = blockIdx.x; w < nact * bpp; w += gridDim.x) {
+    const int k = w / bpp;
+    const int idx = (w - k * bpp) * blockDim.x + threadIdx.x;
+    if (idx >= n) continue;
+    const size_t o = size_t(B.act[k]) * n + idx;
+    const vec2_t<T> v = e[o];
+    double2 x = u[o];
+    x.x += double(v.x);
+    x.y += double(v.y);
+    u[o] = x;
+  }
 }
 
 template <typename T>
 void launch_update(const LevelDev& L, const Batch& B, double2* u, const vec2_t<T>* e,
                    cudaStream_t st) {
   const int n = L.nr * L.nt;
-  dim3 grid((n + 255) / 256, B.max_planes);
-  k_update<T><<<grid, 256, 0, st>>>(n, B, u, e);
+  k_update<T><<<work_grid(long((n + 255) / 256) * B.max_planes), 256, 0, st>>>(n, B, u, e);
 }
 
-int residual_blocks(int nr, int nt) { return (nr * nt + 255) / 256; }
+int residual_blocks(int nr, int nt) {
+  work_grid(1);   // queries the SM count once, outside any stream capture
+  return (nr * nt + 255) / 256;
+}
 
 __device__ __forceinline__ double4 add4(double4 a, double4 b) {
   return make_double4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
@@ -219,84 +244,84 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const double2* __restrict__ f,
                                                   const double2* __restrict__ u,
                                                   vec2_t<T>* __restrict__ r, double4* part,
-                                                  double4* psum, int* cnt, RetireArgs ra) {
+                                                  double4* psum, int* cnt, int bpp, RetireArgs ra) {
   __shared__ double4 sh[8];
+  __shared__ float4 shf[8];
   __shared__ int last, glast;
   __shared__ int scan[256];
-  int p, slot;
-  if (!plane_of(B, blockIdx.y, p, slot)) return;
+  // nact is read once: the retiring block rewrites it only after every work
+  // item of this launch has been summed
+  const int nact = *B.nact;
   const int nr = L.nr, nt = L.nt, n = nr * nt;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const bool want_f = *ra.S.iter == 0;     // |f| is needed on the first iteration only
-  // the residual is FP64; its norm only drives the convergence test, so the
-  // volume-weighted squares are accumulated in FP32 within the block
-  float4 accf = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (idx < n) {
-    const int j = idx / nr, i = idx - j * nr;
-    const size_t base = size_t(p) * n;
-    const double s2 = B.s2d[slot];
-    const double2 rv = defect<double>(L, L.rd, L.td, s2, u + base, f + base, i, j);
-    const vec2_t<T> ro = vmk<vec2_t<T>, T>(T(rv.x), T(rv.y));
-    r[base + idx] = ro;
-    const float dv = L.rf[RT_V * (nr + 2) + i + 1] * L.tf[TT_V * (nt + 2) + j + 1];
-    const float rx = float(ro.x), ry = float(ro.y);
-    accf.x = dv * rx * rx;
-    accf.y = dv * ry * ry;
-    if (want_f) {
-      const double2 fv = f[base + idx];
-      const float fx = float(fv.x), fy = float(fv.y);
-      accf.z = dv * fx * fx;
-      accf.w = dv * fy * fy;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int w = blockIdx.x; w < nact * bpp; w += gridDim.x) {
+    const int k = w / bpp, bx = w - k * bpp;
+    const int p = B.act[k];
+    const int slot = B.slot ? B.slot[p] : p;
+    const int idx = bx * blockDim.x + threadIdx.x;
+    // the residual is FP64; its norm only drives the convergence test, so the
+    // volume-weighted squares are accumulated in FP32 within the block
+    float4 accf = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (idx < n) {
+      const int j = idx / nr, i = idx - j * nr;
+      const size_t base = size_t(p) * n;
+      const double s2 = B.s2d[slot];
+      const double2 rv = defect<double>(L, L.rd, L.td, s2, u + base, f + base, i, j);
+      const vec2_t<T> ro = vmk<vec2_t<T>, T>(T(rv.x), T(rv.y));
+      r[base + idx] = ro;
+      const float dv = L.rf[RT_V * (nr + 2) + i + 1] * L.tf[TT_V * (nt + 2) + j + 1];
+      const float rx = float(ro.x), ry = float(ro.y);
+      accf.x = dv * rx * rx;
+      accf.y = dv * ry * ry;
+      if (want_f) {
+        const double2 fv = f[base + idx];
+        const float fx = float(fv.x), fy = float(fv.y);
+        accf.z = dv * fx * fx;
+        accf.w = dv * fy * fy;
+      }
     }
-  }
-  double4 acc;
-  {
     for (int o = 16; o > 0; o >>= 1) {
       accf.x += __shfl_down_sync(0xffffffffu, accf.x, o);
       accf.y += __shfl_down_sync(0xffffffffu, accf.y, o);
       accf.z += __shfl_down_sync(0xffffffffu, accf.z, o);
       accf.w += __shfl_down_sync(0xffffffffu, accf.w, o);
     }
-    __shared__ float4 shf[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) shf[warp] = accf;
     __syncthreads();
-    acc = make_double4(0, 0, 0, 0);
-    if (threadIdx.x == 0)
-      for (int w = 0; w < int(blockDim.x >> 5); ++w)
-        acc = add4(acc, make_double4(shf[w].x, shf[w].y, shf[w].z, shf[w].w));
-  }
-  const double4 s = acc;
-  const int nblk = gridDim.x;
-  if (threadIdx.x == 0) {
-    part[size_t(p) * nblk + blockIdx.x] = s;
-    __threadfence();
-    last = (atomicAdd(&cnt[p], 1) == nblk - 1);
-  }
-  __syncthreads();
-  if (last) {
-    __threadfence();
-    double4 t = make_double4(0, 0, 0, 0);
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-      const double2* q2 = reinterpret_cast<const double2*>(&part[size_t(p) * nblk + b]);
-      const double2 qa = __ldcg(q2), qb = __ldcg(q2 + 1);
-      const double4 q = make_double4(qa.x, qa.y, qb.x, qb.y);
-      t = add4(t, q);
-    }
-    const double4 tot = block_sum4(t, sh);
     if (threadIdx.x == 0) {
-      psum[p] = tot;
-      cnt[p] = 0;
+      double4 acc = make_double4(0, 0, 0, 0);
+      for (int q = 0; q < int(blockDim.x >> 5); ++q)
+        acc = add4(acc, make_double4(shf[q].x, shf[q].y, shf[q].z, shf[q].w));
+      part[size_t(p) * bpp + bx] = acc;
       __threadfence();
-      glast = (atomicAdd(ra.gcnt, 1) == *B.nact - 1);
+      last = (atomicAdd(&cnt[p], 1) == bpp - 1);
     }
     __syncthreads();
-    if (glast) {   // every plane's sum is in: retire converged planes (App. B)
+    if (last) {
       __threadfence();
-      retire_block(const_cast<int*>(B.act), const_cast<int*>(B.nact), psum, ra.S, ra.tol,
-                   ra.max_cycles, ra.stagnation, ra.use_cond, ra.handle, scan);
-      if (threadIdx.x == 0) *ra.gcnt = 0;
+      double4 t = make_double4(0, 0, 0, 0);
+      for (int b = threadIdx.x; b < bpp; b += blockDim.x) {
+        const double2* q2 = reinterpret_cast<const double2*>(&part[size_t(p) * bpp + b]);
+        const double2 qa = __ldcg(q2), qb = __ldcg(q2 + 1);
+        t = add4(t, make_double4(qa.x, qa.y, qb.x, qb.y));
+      }
+      const double4 tot = block_sum4(t, sh);
+      if (threadIdx.x == 0) {
+        psum[p] = tot;
+        cnt[p] = 0;
+        __threadfence();
+        glast = (atomicAdd(ra.gcnt, 1) == nact - 1);
+      }
+      __syncthreads();
+      if (glast) {   // every plane's sum is in: retire converged planes (App. B)
+        __threadfence();
+        retire_block(const_cast<int*>(B.act), const_cast<int*>(B.nact), psum, ra.S, ra.tol,
+                     ra.max_cycles, ra.stagnation, ra.use_cond, ra.handle, scan);
+        if (threadIdx.x == 0) *ra.gcnt = 0;
+      }
     }
+    __syncthreads();   // shf / last / glast are reused by the next work item
   }
 }
 
@@ -304,8 +329,9 @@ template <typename T>
 void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
                      vec2_t<T>* r, double4* part, double4* psum, int* cnt, const RetireArgs& ra,
                      cudaStream_t st) {
-  dim3 grid(residual_blocks(L.nr, L.nt), B.max_planes);
-  k_residual<T><<<grid, 256, 0, st>>>(L, B, f, u, r, part, psum, cnt, ra);
+  const int bpp = residual_blocks(L.nr, L.nt);
+  k_residual<T><<<work_grid(long(bpp) * B.max_planes), 256, 0, st>>>(L, B, f, u, r, part, psum,
+                                                                       cnt, bpp, ra);
 }
 
 // ---------------------------------------------------------------------------

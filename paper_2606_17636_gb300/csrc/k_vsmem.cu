@@ -12,6 +12,7 @@
 // single cells), so both the row-wise vector accesses of radial lines and the
 // column accesses of polar lines are free of bank conflicts.
 #include <cstdio>
+#include <type_traits>
 
 #include "lines.cuh"
 
@@ -29,7 +30,7 @@ __device__ __forceinline__ int vslot(const LevelDev& L, int j, int i) {
 }
 
 template <typename T, int CPL>
-__device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int n_sor,
+__device__ __noinline__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int n_sor,
                          int color) {
   typedef vec2_t<T> V;
   const int nr = L.nr, nt = L.nt;
@@ -61,7 +62,7 @@ __device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T 
 }
 
 template <typename T, int CPL>
-__device__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int n_sor,
+__device__ __noinline__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int n_sor,
                         int color) {
   typedef vec2_t<T> V;
   const int nr = L.nr, nt = L.nt;
@@ -119,7 +120,7 @@ __device__ void s_smooth(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T 
 }
 
 template <typename T>
-__device__ void s_restrict(const LevelDev& L, const LevelDev& C, const vec2_t<T>* e,
+__device__ __noinline__ void s_restrict(const LevelDev& L, const LevelDev& C, const vec2_t<T>* e,
                            const vec2_t<T>* f, vec2_t<T>* fc, T s2) {
   typedef vec2_t<T> V;
   const int nr = L.nr, nt = L.nt;
@@ -165,22 +166,36 @@ __device__ __forceinline__ vec2_t<T> s_cval(const LevelDev& C, const vec2_t<T>* 
   return V{fac * v.x, fac * v.y};
 }
 
+// e += P ec (bilinear, Sec. 3.1): one thread per coarse cell (I, J) updates
+// its four children (2I + a, 2J + b) from the 3 x 3 coarse neighbourhood;
+// child a uses coarse columns I - 1 + a, I + a, child b rows J - 1 + b, J + b.
 template <typename T>
-__device__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, const vec2_t<T>* ec, int m) {
+__device__ __noinline__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, const vec2_t<T>* ec, int m) {
   typedef vec2_t<T> V;
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
-  for (int idx = threadIdx.x; idx < L.nr * L.nt; idx += blockDim.x) {
-    const int j = idx / L.nr, i = idx - j * L.nr;
-    const int i1 = i + 1, j1 = j + 1;
-    const int I1 = (i1 & 1) ? (i1 + 1) / 2 - 1 : i1 / 2, J1 = (j1 & 1) ? (j1 + 1) / 2 - 1 : j1 / 2;
-    const T p1 = R_(RT_P1, i1), p2 = R_(RT_P2, i1), q1 = T_(TT_P1, j1), q2 = T_(TT_P2, j1);
-    const V a = s_cval<T>(C, ec, I1, J1, m), b = s_cval<T>(C, ec, I1 + 1, J1, m);
-    const V c = s_cval<T>(C, ec, I1, J1 + 1, m), d = s_cval<T>(C, ec, I1 + 1, J1 + 1, m);
-    V u = e[vslot(L, j, i)];
-    u.x += p1 * q1 * a.x + p2 * q1 * b.x + p1 * q2 * c.x + p2 * q2 * d.x;
-    u.y += p1 * q1 * a.y + p2 * q1 * b.y + p1 * q2 * c.y + p2 * q2 * d.y;
-    e[vslot(L, j, i)] = u;
+  for (int cidx = threadIdx.x; cidx < C.nr * C.nt; cidx += blockDim.x) {
+    const int J = cidx / C.nr, I = cidx - J * C.nr;
+    V cv[3][3];   // coarse (I - 1 + u, J - 1 + v), 1-based index I + u, J + v
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int u = 0; u < 3; ++u) cv[v][u] = s_cval<T>(C, ec, I + u, J + v, m);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int j = 2 * J + b;
+      const T q1 = T_(TT_P1, j + 1), q2 = T_(TT_P2, j + 1);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int i = 2 * I + a;
+        const T p1 = R_(RT_P1, i + 1), p2 = R_(RT_P2, i + 1);
+        const V A = cv[b][a], Bv = cv[b][a + 1], Cv = cv[b + 1][a], D = cv[b + 1][a + 1];
+        V u = e[vslot(L, j, i)];
+        u.x += p1 * q1 * A.x + p2 * q1 * Bv.x + p1 * q2 * Cv.x + p2 * q2 * D.x;
+        u.y += p1 * q1 * A.y + p2 * q1 * Bv.y + p1 * q2 * Cv.y + p2 * q2 * D.y;
+        e[vslot(L, j, i)] = u;
+      }
+    }
   }
   __syncthreads();
 }
@@ -204,33 +219,33 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
   // block-local copy of the level descriptors at them
   __shared__ LevelDev sL[8];
   {
-    // each table block starts one element past an even element offset, so
-    // the two entries of a cell pair are one aligned vector load
+    // one flat copy of this slot's packed tables (each level's block starts
+    // one element past an even element offset, so the two entries of a cell
+    // pair are one aligned vector load), then block-local level descriptors
     T* tb = reinterpret_cast<T*>(sm + a.tab_off);
-    int toff = 0;
-    for (int l = 0; l < K; ++l) {
-      const LevelDev& G = a.L[l];
-      const int NR = G.nr + 2, NT = G.nt + 2;
-      const T* grt = rt_<T>(G);
-      const T* gtt = tt_<T>(G);
-      const T* gor = omr_<T>(G) + size_t(slot) * G.nt;
-      const T* got = omt_<T>(G) + size_t(slot) * G.nr;
-      toff = (toff + 1) / 2 * 2 + 1;
-      T* srt = tb + toff;
-      T* stt = srt + RT_N * NR;
-      T* sor = stt + TT_N * NT;
-      T* sot = sor + G.nt;
-      for (int k = threadIdx.x; k < RT_N * NR; k += blockDim.x) srt[k] = grt[k];
-      for (int k = threadIdx.x; k < TT_N * NT; k += blockDim.x) stt[k] = gtt[k];
-      for (int k = threadIdx.x; k < G.nt; k += blockDim.x) sor[k] = gor[k];
-      for (int k = threadIdx.x; k < G.nr; k += blockDim.x) sot[k] = got[k];
-      if (threadIdx.x == 0) {
+    {
+      typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type W4;
+      constexpr int per = int(sizeof(W4) / sizeof(T));
+      const W4* src = reinterpret_cast<const W4*>(static_cast<const T*>(a.tabs) + size_t(slot) * a.tab_stride);
+      W4* dst = reinterpret_cast<W4*>(tb);
+      for (int k = threadIdx.x; k < a.tab_stride / per; k += blockDim.x) dst[k] = src[k];
+    }
+    if (threadIdx.x == 0) {
+      int toff = 0;
+      for (int l = 0; l < K; ++l) {
+        const LevelDev& G = a.L[l];
+        const int NR = G.nr + 2, NT = G.nt + 2;
+        toff = (toff + 1) / 2 * 2 + 1;
+        T* srt = tb + toff;
+        T* stt = srt + RT_N * NR;
+        T* sor = stt + TT_N * NT;
+        T* sot = sor + G.nt;
         LevelDev d = G;
         if constexpr (sizeof(T) == 8) { d.rd = srt; d.td = stt; d.omr_d = sor; d.omt_d = sot; }
         else { d.rf = srt; d.tf = stt; d.omr_f = sor; d.omt_f = sot; }
         sL[l] = d;
+        toff += RT_N * NR + TT_N * NT + G.nt + G.nr;
       }
-      toff += RT_N * NR + TT_N * NT + G.nt + G.nr;
     }
   }
   // this mode's coarsest-level block factors (when they fit)

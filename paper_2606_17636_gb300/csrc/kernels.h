@@ -69,6 +69,8 @@ struct VSmemArgs {
   int dbl_off, blk_off;  // byte offsets in shared memory: FP64 solve scratch, staged factors
   int nu1, nu2, n_sor;
   int tab_off;           // shared-memory offset (complex elements) of the staged tables
+  const void* tabs;      // per-slot packed tables (T), tab_stride elements per slot
+  int tab_stride;
   size_t smem_bytes;
 };
 template <typename T>

@@ -128,10 +128,39 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
       off += size_t(d.nr) * d.nt;
     }
     vs.tab_off = int(off);
+    // per-slot packed copy of the fused levels' tables and this slot's omega
+    // rows, laid out exactly as the kernel's shared-memory copy: per level,
+    // at the next odd element offset, RT_N x (nr+2) radial and TT_N x (nt+2)
+    // polar entries, then nt r-line and nr polar-line omegas
     size_t tab = 0;
+    std::vector<size_t> lvl_off(vs.nlev);
     for (int k = 0; k < vs.nlev; ++k) {
       const LevelDev& d = lv[first + k];
-      tab += size_t(RT_N) * (d.nr + 2) + size_t(TT_N) * (d.nt + 2) + d.nr + d.nt + 2;
+      tab = (tab + 1) / 2 * 2 + 1;
+      lvl_off[k] = tab;
+      tab += size_t(RT_N) * (d.nr + 2) + size_t(TT_N) * (d.nt + 2) + d.nr + d.nt;
+    }
+    tab = (tab + 3) / 4 * 4;
+    vs.tab_stride = int(tab);
+    {
+      const size_t S = modes.size();
+      std::vector<double> pk(S * tab, 0.0);
+      for (size_t q = 0; q < S; ++q)
+        for (int k = 0; k < vs.nlev; ++k) {
+          const LevelHost& h = H.lv[first + k];
+          const int nr = lv[first + k].nr, nt = lv[first + k].nt;
+          double* o = pk.data() + q * tab + lvl_off[k];
+          std::copy(h.rtab.begin(), h.rtab.end(), o);
+          o += size_t(RT_N) * (nr + 2);
+          std::copy(h.ttab.begin(), h.ttab.end(), o);
+          o += size_t(TT_N) * (nt + 2);
+          std::copy(h.om_r.begin() + q * nt, h.om_r.begin() + (q + 1) * nt, o);
+          o += nt;
+          std::copy(h.om_t.begin() + q * nr, h.om_t.begin() + (q + 1) * nr, o);
+        }
+      if (opt.precision) vs.tabs = upload(A, to_f(pk));
+      else vs.tabs = upload(A, pk);
+      if (!vs.tabs) { err = "out of device memory"; return false; }
     }
     size_t sbytes = (off * vb + tab * (vb / 2) + 15) / 16 * 16;
     vs.dbl_off = int(sbytes);
