@@ -98,10 +98,27 @@ def ghost_values(plane, values):
     return g
 
 
+def solve_mode(plane, m, f_m, gt_m):
+    """Steps 3-6 of Sec. 5.1 for one azimuthal mode: f_m (n_r, n_t) complex
+    right-hand side 4 pi G rho^m, gt_m the mode's DGF table [t, s].  Returns
+    (psi^m, sigma^m, theta^m, phi^m)."""
+    nr, nt = plane.n_r, plane.n_t
+    lu = spla.splu(operator.matrix(plane, m).tocsc())
+    b = operator.to_vec(f_m)
+    x = lu.solve(np.ascontiguousarray(b.real)) + 1j * lu.solve(np.ascontiguousarray(b.imag))
+    psi = operator.from_vec(x, nr, nt)                  # step 3
+    sigma = screening_mass(plane, psi)                  # step 4
+    theta = gt_m @ sigma                                # step 5
+    g = ghost_values(plane, -theta)
+    b2 = operator.to_vec(f_m - operator.ghost_rhs(plane, g))
+    x = lu.solve(np.ascontiguousarray(b2.real)) + 1j * lu.solve(np.ascontiguousarray(b2.imag))
+    return psi, sigma, theta, operator.from_vec(x, nr, nt)   # step 6
+
+
 def solve(plane, rho, gt, return_parts=False):
     """Seven-step solve (Sec. 5.1).  rho: (n_r, n_t, n_phi) FP64 at the cell
     centres; gt: DGF table [m, t, s].  Returns phi (n_r, n_t, n_phi)."""
-    nr, nt, N = plane.n_r, plane.n_t, plane.n_phi
+    N = plane.n_phi
     M = N // 2 + 1
     rho_hat = dft.forward(rho)                          # step 2
     f = 4.0 * np.pi * plane.G * rho_hat                 # (n_r, n_t, M)
@@ -110,16 +127,7 @@ def solve(plane, rho, gt, return_parts=False):
     sigma = np.zeros((len(boundary_points(plane)), M), dtype=complex)
     theta = np.zeros_like(sigma)
     for m in range(M):
-        lu = spla.splu(operator.matrix(plane, m).tocsc())
-        b = operator.to_vec(f[:, :, m])
-        x = lu.solve(np.ascontiguousarray(b.real)) + 1j * lu.solve(np.ascontiguousarray(b.imag))
-        psi[:, :, m] = operator.from_vec(x, nr, nt)     # step 3
-        sigma[:, m] = screening_mass(plane, psi[:, :, m])           # step 4
-        theta[:, m] = gt[m] @ sigma[:, m]                           # step 5
-        g = ghost_values(plane, -theta[:, m])
-        b2 = operator.to_vec(f[:, :, m] - operator.ghost_rhs(plane, g))
-        x = lu.solve(np.ascontiguousarray(b2.real)) + 1j * lu.solve(np.ascontiguousarray(b2.imag))
-        phi_hat[:, :, m] = operator.from_vec(x, nr, nt)  # step 6
+        psi[:, :, m], sigma[:, m], theta[:, m], phi_hat[:, :, m] = solve_mode(plane, m, f[:, :, m], gt[m])
     phi = dft.inverse(phi_hat, N)                        # step 7
     if return_parts:
         return phi, dict(rho_hat=rho_hat, f=f, psi=psi, sigma=sigma, theta=theta,
