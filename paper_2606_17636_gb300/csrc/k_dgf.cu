@@ -45,6 +45,11 @@ __global__ void __launch_bounds__(256) k_green(GreenArgs a) {
 void launch_green(const GreenArgs& a, cudaStream_t st) {
   if (a.npairs == 0) return;
   const long blocks = (a.npairs + 7) / 8;
+  static bool attr = false;
+  if (!attr) {   // 8 warps x N doubles: 64 KB at the largest N = 1024
+    cudaFuncSetAttribute(k_green, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 1024 * int(sizeof(double)));
+    attr = true;
+  }
   k_green<<<unsigned(blocks), 256, 8 * a.N * sizeof(double), st>>>(a);
 }
 

@@ -32,6 +32,25 @@ struct Corr {          // fused prolongation source (ec == nullptr: none)
 };
 
 // Radial pass, both colours: a block owns W lines [j0, j0+W), W = 8 / mult.
+// Every line it reads is first staged in shared memory with asynchronous
+// copies (all loads in flight at once): e lines j0-1 .. j0+W+1 (zero beyond
+// the plane, or all zero for a zero initial guess) and f lines j0 .. j0+W.
+template <typename T>
+__device__ __forceinline__ void stage_lines(vec2_t<T>* dst, const vec2_t<T>* plane, int j_first,
+                                            int nlines, int nr, int nt, bool zero) {
+  typedef vec2_t<T> V;
+  constexpr int per = 16 / int(sizeof(V));   // complex values per 16-byte chunk
+  const int chunks = nr / per;                // nr is a multiple of 2
+  for (int idx = threadIdx.x; idx < nlines * chunks; idx += blockDim.x) {
+    const int q = idx / chunks, c = idx - q * chunks, j = j_first + q;
+    const bool valid = !zero && j >= 0 && j < nt;
+    const V* src = plane + (valid ? size_t(j) * nr + c * per : 0);
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst + size_t(q) * nr + c * per));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 16 : 0) : "memory");
+  }
+}
+
 template <typename T, int CPL>
 __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_t<T>* __restrict__ ein,
                                                 vec2_t<T>* __restrict__ eout,
@@ -39,7 +58,6 @@ __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_
                                                 int n_sor, Corr corr) {
   typedef vec2_t<T> V;
   extern __shared__ __align__(16) unsigned char sraw[];
-  V* s0 = reinterpret_cast<V*>(sraw);   // up to 5 colour-0 lines (own + 1 recomputed)
   const int nact = *B.nact;
   const int mult = spread(int(gridDim.x), nact);
   const int per = int(gridDim.x) * mult;
@@ -52,38 +70,39 @@ __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_
   const int slot = B.slot ? B.slot[p] : p;
   const int m = B.mode[slot];
   const int nr = L.nr, nt = L.nt;
+  V* se = reinterpret_cast<V*>(sraw);   // e lines j0-1 .. j0+W+1 (line j at se + (j - j0 + 1) nr)
+  V* sf = se + size_t(W + 3) * nr;       // f lines j0 .. j0+W
+  V* s0 = sf + size_t(W + 1) * nr;       // relaxed colour-0 lines j0, j0+2, .., j0+W
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t base = size_t(p) * nr * nt;
+  stage_lines<T>(se, ein + base, j0 - 1, W + 3, nr, nt, zero_init != 0);
+  stage_lines<T>(sf, f + base, j0, W + 1, nr, nt, false);
+  cp_async_wait_all();
+  __syncthreads();
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
+  if (corr.ec) {   // fused prolongation: add the coarse correction to the staged e lines
+    const V* ec = static_cast<const V*>(corr.ec) + size_t(p) * corr.C.nr * corr.C.nt;
+    for (int idx = threadIdx.x; idx < (W + 3) * nr; idx += blockDim.x) {
+      const int q = idx / nr, i = idx - q * nr, j = j0 - 1 + q;
+      if (j < 0 || j >= nt) continue;
+      const V d = prolong_at<T>(L, rt, tt, corr.C, ec, i, j, m);
+      se[idx].x += d.x;
+      se[idx].y += d.y;
+    }
+    __syncthreads();
+  }
   const T s2 = s2_<T>(B, slot);
   const T* om = omr_<T>(L) + size_t(slot) * nt;
-  const V* ei = ein + base;
-  const V* fi = f + base;
-  const V* ec = corr.ec ? static_cast<const V*>(corr.ec) + size_t(p) * corr.C.nr * corr.C.nt : nullptr;
-  // line j of e_in (+ coarse correction), or zero
-  auto load = [&](V (&x)[CPL], int j) {
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) x[c] = z2<V>();
-    if (zero_init || j < 0 || j >= nt) return;
-    ld_line<V, CPL>(x, ei + size_t(j) * nr, lane, nr);
-    if (ec && (CPL > 1 || lane < nr)) {
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        const V d = prolong_at<T>(L, rt, tt, corr.C, ec, lcell<CPL>(lane, c), j, m);
-        x[c].x += d.x;
-        x[c].y += d.y;
-      }
-    }
-  };
+  auto eline = [&](int j) { return se + size_t(j - j0 + 1) * nr; };
   if (warp <= W / 2) {            // colour 0: lines j0, j0+2, .., j0+W
     const int j = j0 + 2 * warp;
     if (j < nt) {
       V ev[CPL], g[CPL], un[CPL], us[CPL];
-      load(ev, j);
-      load(un, j + 1);
-      load(us, j - 1);
-      ld_line<V, CPL>(g, fi + size_t(j) * nr, lane, nr);
+      ld_line<V, CPL>(ev, eline(j), lane, nr);
+      ld_line<V, CPL>(un, eline(j + 1), lane, nr);
+      ld_line<V, CPL>(us, eline(j - 1), lane, nr);
+      ld_line<V, CPL>(g, sf + size_t(j - j0) * nr, lane, nr);
       relax_r<T, CPL>(L, rt, tt, s2, om[j], j, g, un, us, n_sor, ev);
       st_line<V, CPL>(s0 + warp * nr, ev, lane, nr);
     }
@@ -93,8 +112,8 @@ __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_
     const int j = j0 + 1 + 2 * warp;
     if (j < nt) {
       V ev[CPL], g[CPL], un[CPL], us[CPL];
-      load(ev, j);
-      ld_line<V, CPL>(g, fi + size_t(j) * nr, lane, nr);
+      ld_line<V, CPL>(ev, eline(j), lane, nr);
+      ld_line<V, CPL>(g, sf + size_t(j - j0) * nr, lane, nr);
       ld_line<V, CPL>(us, s0 + warp * nr, lane, nr);
       if (j + 1 < nt) {
         ld_line<V, CPL>(un, s0 + (warp + 1) * nr, lane, nr);
@@ -151,9 +170,11 @@ __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_
     const int j = idx / TC, cc = idx - j * TC, i = i0 - 1 + cc;
     const bool in = i >= 0 && i < nr;
     const int o = tslot<CPL>(j, cc, SW);
-    se[o] = in ? ein[base + size_t(j) * nr + i] : z2<V>();
-    sf[o] = in ? f[base + size_t(j) * nr + i] : z2<V>();
+    const size_t g = base + size_t(j) * nr + (in ? i : 0);
+    cp_async_v(se + o, ein + g, in);
+    cp_async_v(sf + o, f + g, in);
   }
+  cp_async_wait_all();
   __syncthreads();
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
@@ -202,9 +223,14 @@ static int tile_w(int nr, int nt, size_t vb) {
 template <typename T, int CPL>
 static void rpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
                    const vec2_t<T>* f, bool zi, int n_sor, const Corr& corr, cudaStream_t st) {
+  const size_t sm = size_t(11 + 9 + 5) * L.nr * sizeof(vec2_t<T>);   // W = 8: e, f, colour-0 lines
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_rpass2<T, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
   dim3 grid((L.nt + 7) / 8, B.max_planes);
-  k_rpass2<T, CPL><<<grid, 256, 5 * L.nr * sizeof(vec2_t<T>), st>>>(L, B, ein, eout, f, zi ? 1 : 0,
-                                                                    n_sor, corr);
+  k_rpass2<T, CPL><<<grid, 256, sm, st>>>(L, B, ein, eout, f, zi ? 1 : 0, n_sor, corr);
 }
 
 template <typename T, int CPL>

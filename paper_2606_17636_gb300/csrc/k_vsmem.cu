@@ -30,7 +30,7 @@ __device__ __forceinline__ int vslot(const LevelDev& L, int j, int i) {
 }
 
 template <typename T, int CPL>
-__device__ __noinline__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int n_sor,
+__device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int n_sor,
                          int color) {
   typedef vec2_t<T> V;
   const int nr = L.nr, nt = L.nt;
@@ -62,7 +62,7 @@ __device__ __noinline__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec
 }
 
 template <typename T, int CPL>
-__device__ __noinline__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int n_sor,
+__device__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int n_sor,
                         int color) {
   typedef vec2_t<T> V;
   const int nr = L.nr, nt = L.nt;
@@ -120,7 +120,7 @@ __device__ void s_smooth(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T 
 }
 
 template <typename T>
-__device__ __noinline__ void s_restrict(const LevelDev& L, const LevelDev& C, const vec2_t<T>* e,
+__device__ void s_restrict(const LevelDev& L, const LevelDev& C, const vec2_t<T>* e,
                            const vec2_t<T>* f, vec2_t<T>* fc, T s2) {
   typedef vec2_t<T> V;
   const int nr = L.nr, nt = L.nt;
@@ -170,7 +170,7 @@ __device__ __forceinline__ vec2_t<T> s_cval(const LevelDev& C, const vec2_t<T>* 
 // its four children (2I + a, 2J + b) from the 3 x 3 coarse neighbourhood;
 // child a uses coarse columns I - 1 + a, I + a, child b rows J - 1 + b, J + b.
 template <typename T>
-__device__ __noinline__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, const vec2_t<T>* ec, int m) {
+__device__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, const vec2_t<T>* ec, int m) {
   typedef vec2_t<T> V;
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
@@ -333,10 +333,11 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     const int ncr = Lc.nr;
     // g lanes per row; nc is a power of two >= 16, so g * nc is a whole
     // number of warps and every warp below it takes part in the shuffles
+    // (g > 1 only when g * nc fits in one pass of the block)
     int g = 1;
     while (g < 32 && g * 2 * nc <= int(blockDim.x)) g *= 2;   // uses all threads when nc >= 32
-    if (int(threadIdx.x) < g * nc) {
-      const int row = threadIdx.x / g, sub = threadIdx.x & (g - 1);
+    for (int t = threadIdx.x; t < g * nc; t += blockDim.x) {
+      const int row = t / g, sub = t & (g - 1);
       double sx = 0.0, sy = 0.0;
       for (int k = sub; k < nc; k += g) {
         const double c = A[size_t(row) * nc + k];
@@ -360,11 +361,12 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     ge[size_t(p) * n0 + k] = sm[a.off_e[0] + vslot(a.L[0], k / nr0, k % nr0)];
 }
 
-// FP32 planes: 1024 threads (64 registers each); FP64 planes: 512 threads.
+// 512 threads (up to 128 registers each, no spills); each warp takes every
+// 16th line of a colour.
 template <typename T>
 void launch_vsmem(const VSmemArgs& a, const Batch& B, const vec2_t<T>* gf, vec2_t<T>* ge,
                   cudaStream_t st) {
-  constexpr int NTH = sizeof(T) == 4 ? 1024 : 512;
+  constexpr int NTH = 512;
   static bool attr = false;
   if (!attr) {   // opt in to the largest dynamic size the kernel's static usage leaves
     cudaFuncAttributes fa;

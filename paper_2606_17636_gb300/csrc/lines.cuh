@@ -37,6 +37,10 @@ template <> __device__ __forceinline__ float s2_<float>(const Batch& B, int slot
 
 template <typename V> __device__ __forceinline__ V z2() { V v; v.x = 0; v.y = 0; return v; }
 
+// Correctly rounded reciprocal (the same value as 1 / x).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 template <typename V> __device__ __forceinline__ V shup(V v) {
   v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
   v.y = __shfl_up_sync(0xffffffffu, v.y, 1);
@@ -51,6 +55,21 @@ template <typename V> __device__ __forceinline__ V shidx(V v, int src) {
   v.x = __shfl_sync(0xffffffffu, v.x, src);
   v.y = __shfl_sync(0xffffffffu, v.y, src);
   return v;
+}
+
+// Asynchronous global -> shared copy of one complex value (zero-filled when
+// !valid; src must still be a valid address), and the wait for all of them.
+template <typename V>
+__device__ __forceinline__ void cp_async_v(V* dst, const V* src, bool valid) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  const int n = valid ? int(sizeof(V)) : 0;
+  if constexpr (sizeof(V) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // Cell index held in register slot c of `lane`.
@@ -223,7 +242,7 @@ __device__ __forceinline__ void relax_r(const LevelDev& L, const T* rt, const T*
     ld_tab<T, CPL>(dr, rt + RT_DR * NR, lane, nr);
     ld_tab<T, CPL>(q, rt + RT_Q * NR, lane, nr);
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) id[c] = on ? T(1) / (dr[c] + P[c] * dtj - s2 * q[c] * Tj) : T(0);
+    for (int c = 0; c < CPL; ++c) id[c] = on ? rcp_rn(dr[c] + P[c] * dtj - s2 * q[c] * Tj) : T(0);
   }
   ld_tab<T, CPL>(up, rt + RT_AE * NR, lane, nr);
   ld_tab<T, CPL>(dn, rt + RT_AW * NR, lane, nr);
@@ -253,7 +272,7 @@ __device__ __forceinline__ void relax_t(const LevelDev& L, const T* rt, const T*
     ld_tab<T, CPL>(dt, tt + TT_DT * NT, lane, nt);
     ld_tab<T, CPL>(tj, tt + TT_T * NT, lane, nt);
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) id[c] = on ? T(1) / (dr + P * dt[c] - s2 * Qi * tj[c]) : T(0);
+    for (int c = 0; c < CPL; ++c) id[c] = on ? rcp_rn(dr + P * dt[c] - s2 * Qi * tj[c]) : T(0);
   }
   ld_tab<T, CPL>(up, tt + TT_AN * NT, lane, nt);
   ld_tab<T, CPL>(dn, tt + TT_AS * NT, lane, nt);
