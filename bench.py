@@ -294,7 +294,8 @@ def ours(a, ws, rank, local):
     e2e = ws * a.steps / te2e
     # dominant kernel, timed alone on the same stream: one alternating-line
     # smoothing cycle of the finest level over all modes, FP32 planes
-    roof = smoother_roofline(torch, ps, sm, stream)
+    roof = vcycle_roofline(torch, ps, sm, stream)
+    roof_stream = smoother_roofline(torch, ps, sm, stream)
     launches = launches_per_solve(sm, st)
     if rank != 0:
         return
@@ -319,6 +320,7 @@ def ours(a, ws, rank, local):
                 "d2h_bytes_per_step": phi.numel() * 8},
         "gpu_launches": launches * a.steps,
         "roofline": roof,
+        "roofline_streaming": roof_stream,
         "clocks": clocks,
     }
     if not a.no_baseline:
@@ -342,9 +344,57 @@ def launches_per_solve(s, st):
     return fixed + body * (st["iterations_psi"] + 1 + st["iterations_phi"] + 1)
 
 
+# FP32 flops per cell of a fused smoothed level and V-cycle: a line
+# relaxation pass costs 48 per cell (neighbour-line source 10, inverse
+# diagonal 6, two even-odd SOR sweeps 2 x 16); nu_pre + nu_post = 4 cycles of
+# 2 passes give 384; defect restriction and prolongation add 40.
+VCYCLE_FLOPS_PER_CELL = 424
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+
+
+def vcycle_roofline(torch, ps, s, stream):
+    """The dominant kernel: the fused coarse V-cycle (k_vsmem, one block per
+    mode plane, levels held in shared memory), all modes, timed alone
+    through psolve_stage_vcycle with CUDA events on the library's stream.
+    Algorithmic work per launch: M x sum over the fused smoothed levels of
+    cells x VCYCLE_FLOPS_PER_CELL FP32 flops, plus the FP64 block solve of
+    the coarsest level (4 n^2 (2 nt - 1) per mode)."""
+    M = s.n_modes
+    lev = s.fused_level()
+    n_r, n_tz = s.shape[0], s.shape[1]
+    f = torch.randn((M, n_tz >> lev, n_r >> lev), dtype=torch.complex64, device="cuda")
+    for _ in range(3):
+        s.stage_vcycle(f)
+    reps = 20
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("bench_vcycle")
+    ev0.record(stream)
+    for _ in range(reps):
+        s.stage_vcycle(f)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    dt = ev0.elapsed_time(ev1) / 1e3 / reps
+    cells, l = 0, lev
+    while l < s.n_levels - 1:
+        cells += (n_r >> l) * (n_tz >> l)
+        l += 1
+    cr, ct = n_r >> (s.n_levels - 1), n_tz >> (s.n_levels - 1)
+    flops = M * (cells * VCYCLE_FLOPS_PER_CELL + 4 * cr * cr * (2 * ct - 1))
+    ach = flops / dt / 1e12
+    return {"kernel": "fused coarse V-cycle k_vsmem (levels %d..%d in shared memory, all %d modes)"
+                      % (lev, s.n_levels - 1, M),
+            "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP32_PEAK_TFLOPS,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
+            "traffic": None, "algorithmic_flops_per_launch": flops, "avg_ms": dt * 1e3,
+            "note": "one block per mode plane: latency-bound line relaxations"}
+
+
 def smoother_roofline(torch, ps, s, stream):
     """One alternating-line smoothing cycle (radial zebra pass + polar zebra
-    pass, 4 launches) on the finest level over all modes in FP32, timed with
+    pass, 2 launches) on the finest level over all modes in FP32, timed with
     CUDA events.  Algorithmic bytes per cell per cycle: each zebra pass reads
     e once and f once and writes e once over the plane (8 B float2 each),
     twice (radial, polar): 2 x 24 B = 48 B per complex cell."""
@@ -367,7 +417,7 @@ def smoother_roofline(torch, ps, s, stream):
     bytes_ = 48.0 * M * n_tz * n_r
     pk = peaks().get("hbm_gbs")
     ach = bytes_ / dt / 1e9
-    return {"kernel": "finest-level smoothing cycle (k_rpass x2 + k_tpass x2, FP32, all modes)",
+    return {"kernel": "finest-level smoothing cycle (k_rpass2 + k_tpass2, FP32, all modes)",
             "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
             "frac": (ach / pk) if pk else None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
             "traffic": None, "algorithmic_bytes_per_launch_set": bytes_, "avg_ms": dt * 1e3}

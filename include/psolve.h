@@ -143,6 +143,16 @@ int psolve_stage_smooth(psolve_t h, int level, int precision, void* e, const voi
 int psolve_stage_restrict(psolve_t h, int level, int precision, const void* e, const void* f,
                           void* coarse);
 int psolve_stage_prolong(psolve_t h, int level, int precision, void* e, const void* coarse);
+/* Sec. 3: the coarse part of one V-cycle, fused into one kernel: from
+ * level `level` (which must be the handle's fused level, see
+ * psolve_get_fused_level) down to the coarsest, on L_m e = f with a zero
+ * initial guess: nu_pre smoothing cycles, defect restriction, recursion,
+ * the exact coarsest solve (FP64), prolongation, nu_post smoothing cycles.
+ * f, e: planes [M][n_tz_l][n_r_l] complex in FP64 (precision 0) or FP32 (1);
+ * e is overwritten.  PSOLVE_ERR_ARG for another level or precision. */
+int psolve_stage_vcycle(psolve_t h, int level, int precision, const void* f, void* e);
+/* The first multigrid level held in shared memory by the fused V-cycle. */
+int psolve_get_fused_level(psolve_t h, int* level);
 /* Eqs. charge_sph / charge_cyl: sigma[m][b] (complex) from psi_hat. */
 int psolve_stage_screening(psolve_t h, const double* psi_hat, double* sigma);
 /* Eqs. theta_left..theta_top: theta[m][t] = sum_s Gt[m][t][s] sigma[m][s]. */

@@ -67,6 +67,8 @@ def lib():
             "psolve_stage_mg_solve": (I, [P, P, P, D, I, ctypes.POINTER(I)]),
             "psolve_stage_smooth": (I, [P, I, I, P, P, I]),
             "psolve_stage_smooth_static": (I, [P, I, I, P, P, I]),
+            "psolve_stage_vcycle": (I, [P, I, I, P, P]),
+            "psolve_get_fused_level": (I, [P, ctypes.POINTER(ctypes.c_int)]),
             "psolve_stage_restrict": (I, [P, I, I, P, P, P]),
             "psolve_stage_prolong": (I, [P, I, I, P, P]),
             "psolve_stage_screening": (I, [P, P, P]),
@@ -238,6 +240,20 @@ class Solver:
         prec = 1 if self.desc.precision == MIXED else 0
         check(lib().psolve_stage_smooth_static(self.h, level, prec, _ptr(e), _ptr(f), cycles),
               "psolve_stage_smooth_static")
+        return e
+
+    def fused_level(self):
+        lv = ctypes.c_int()
+        check(lib().psolve_get_fused_level(self.h, ctypes.byref(lv)), "psolve_get_fused_level")
+        return lv.value
+
+    def stage_vcycle(self, f):
+        """Fused coarse V-cycle from the fused level (zero initial guess);
+        returns the correction e."""
+        level = self.fused_level()
+        prec = 1 if self.desc.precision == MIXED else 0
+        e = self.planes(level, f.dtype)
+        check(lib().psolve_stage_vcycle(self.h, level, prec, _ptr(f), _ptr(e)), "psolve_stage_vcycle")
         return e
 
     def stage_restrict(self, level, e, f):

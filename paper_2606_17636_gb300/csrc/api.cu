@@ -564,6 +564,28 @@ extern "C" int psolve_stage_prolong(psolve_t h, int level, int precision, void* 
                                                                              : PSOLVE_ERR_CUDA;
 }
 
+extern "C" int psolve_get_fused_level(psolve_t h, int* level) {
+  if (!h || !level) return fail(PSOLVE_ERR_ARG, "null argument");
+  *level = h->mg.first;
+  return PSOLVE_OK;
+}
+
+extern "C" int psolve_stage_vcycle(psolve_t h, int level, int precision, const void* f, void* e) {
+  if (!h || !f || !e) return fail(PSOLVE_ERR_ARG, "null argument");
+  int rc = check_level(h, level, precision, false);
+  if (rc) return rc;
+  if (level != h->mg.first)
+    return fail(PSOLVE_ERR_ARG, "the fused V-cycle starts at level " + std::to_string(h->mg.first));
+  full_batch(h);
+  if (precision)
+    launch_vsmem<float>(h->mg.vs, h->mg.batch, static_cast<const float2*>(f), static_cast<float2*>(e), h->st);
+  else
+    launch_vsmem<double>(h->mg.vs, h->mg.batch, static_cast<const double2*>(f), static_cast<double2*>(e),
+                         h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("vcycle") ? PSOLVE_OK
+                                                                            : PSOLVE_ERR_CUDA;
+}
+
 extern "C" int psolve_stage_screening(psolve_t h, const double* psi_hat, double* sigma) {
   if (!h || !psi_hat || !sigma) return fail(PSOLVE_ERR_ARG, "null argument");
   launch_screening(h->bdev, reinterpret_cast<const double2*>(psi_hat),

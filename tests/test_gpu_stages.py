@@ -131,3 +131,30 @@ def test_screening_boundary_and_dgf(ps, key):
     ref_th = np.einsum("mts,ms->mt", got_gt, ref_sig)
     assert np.abs(th - ref_th).max() <= 1e-13 * np.abs(ref_th).max()
     s.close()
+
+
+@pytest.mark.parametrize("key", list(SMALL))
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-4)])
+def test_fused_vcycle_matches_oracle_vcycle(ps, key, precision, tol):
+    """The fused coarse V-cycle (Sec. 3) from the fused level down, zero
+    initial guess, against the oracle's recursive V-cycle on the same level.
+    FP32: the cycle chains ~400 single-precision operations per cell and
+    level plus the exact coarsest solve, hence 1e-4 of the largest value."""
+    from oracle import mg
+    sp = SMALL[key]
+    s = _solver(ps, key, precision)
+    lev = s.fused_level()
+    H = mg.Hierarchy(oracle_plane(sp))
+    nr, nt, M = sp["n_r"] >> lev, sp["n_tz"] >> lev, s.n_modes
+    cdt = torch.complex128 if precision == 0 else torch.complex64
+    f = torch.from_numpy(_rand_planes((M, nt, nr), 40 + lev)).to(cdt).cuda()
+    got = s.stage_vcycle(f).cpu().numpy().astype(np.complex128)
+    fh = f.cpu().numpy().astype(np.complex128)
+    ref = np.zeros_like(got)
+    for m in range(M):
+        u = np.zeros((nr + 2, nt + 2), complex)
+        H.vcycle(lev, m, u, fh[m].T)
+        ref[m] = u[1:-1, 1:-1].T
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    assert err <= tol, err
+    s.close()
