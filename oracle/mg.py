@@ -2,11 +2,13 @@
 
 Readings fixed here (the paper leaves them open):
 * Level hierarchy: factor-two coarsening of both axes while the shorter one
-  has more than 8 cells, or more than 4 cells and the plane more than 256
+  has more than 16 cells, or more than 4 cells and the plane more than 1024
   cells; coarse faces are every other fine face (Sec. 5.2 power-of-two
-  rule); the coarse operator is re-discretised from those faces.  (Stopping
-  at 4 cells makes the coarse correction of m = 0 poor on strongly stretched
-  logarithmic grids: 40 instead of 26 V-cycles at 256 x 128, r_out/r_in = 400.)
+  rule); the coarse operator is re-discretised from those faces.  The paper
+  leaves the size of the directly solved coarsest level open; on strongly
+  stretched logarithmic grids it sets the m = 0 convergence rate (256 x 128,
+  r_out/r_in = 400, tol 1e-8: 40 V-cycles with an 8 x 4 coarsest level, 26
+  with 16 x 8, 21 with 32 x 16, 16 with 64 x 32, the count App. B quotes).
 * Coarsest level: exact (sparse direct) solve; Sec. 3.3 allows a direct
   solver.
 * Smoother (Sec. 3.2, Algorithm 1): one smoothing cycle relaxes all radial
@@ -69,8 +71,8 @@ class Level:
 
 
 class Hierarchy:
-    def __init__(self, plane, neumann_inner=False, min_cells=8, nu1=2, nu2=2, n_sor=2,
-                 max_coarse=256):
+    def __init__(self, plane, neumann_inner=False, min_cells=16, nu1=2, nu2=2, n_sor=2,
+                 max_coarse=1024):
         planes = [plane]
         while True:
             nr, nt = planes[-1].n_r, planes[-1].n_t

@@ -248,12 +248,14 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
       }
     }
   }
-  // this mode's coarsest-level block factors (when they fit)
+  // this mode's coarsest-level factors (when they fit)
   const size_t blk_stride = size_t(a.blk_nt) * a.blk_n * (a.blk_n + 2);
+  const size_t fac_stride = a.sep_stride > 0 ? size_t(a.sep_stride) : blk_stride;
   if (a.blk_smem) {
-    const double2* src = reinterpret_cast<const double2*>(a.blk + size_t(slot) * blk_stride);
+    const double2* src = reinterpret_cast<const double2*>(
+        (a.sep_stride > 0 ? a.sep : a.blk) + size_t(slot) * fac_stride);
     double2* dst = reinterpret_cast<double2*>(vraw + a.blk_off);
-    for (int k = threadIdx.x; k < int(blk_stride / 2); k += blockDim.x) dst[k] = src[k];
+    for (int k = threadIdx.x; k < int(fac_stride / 2); k += blockDim.x) dst[k] = src[k];
   }
   // load f of the first level, zero all errors
   for (int k = threadIdx.x; k < n0; k += blockDim.x)
@@ -267,7 +269,63 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     s_smooth<T>(sL[l], sm + a.off_e[l], sm + a.off_f[l], s2, a.nu1, a.n_sor);
     s_restrict<T>(sL[l], sL[l + 1], sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
   }
-  if (a.blk_n > 0) {
+  if (a.sep_stride > 0) {
+    // coarsest level, exact FP64 separable solve: L_m = L_r (x) I + D_r (x) L_t
+    // with L_t = V diag(lambda) V^-1: z = (V^-1 (x) I) f, one tridiagonal
+    // radial solve (L_r + lambda_k D_r) per eigenvalue k (Thomas), then
+    // e = (V (x) I) z.
+    const LevelDev& Lc = a.L[K - 1];
+    const int nr = Lc.nr, nt = Lc.nt, nc = nr * nt;
+    const V* fc = sm + a.off_f[K - 1];
+    V* ec = sm + a.off_e[K - 1];
+    double* z = reinterpret_cast<double*>(vraw + a.dbl_off);   // [2][nt][nr]
+    const double* Fq = a.blk_smem ? reinterpret_cast<const double*>(vraw + a.blk_off)
+                                  : a.sep + size_t(slot) * fac_stride;
+    const double* Vm = Fq;
+    const double* Vi = Vm + nt * nt;
+    const double* invd = Vi + nt * nt;
+    const double* cp = invd + nt * nr;
+    const double* low = cp + nt * nr;
+    for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
+      const int c = q / nc, r = q - c * nc, k = r / nr, i = r - k * nr;
+      double acc = 0.0;
+      for (int j = 0; j < nt; ++j) {
+        const V v = fc[vslot(Lc, j, i)];
+        acc += Vi[k * nt + j] * double(c ? v.y : v.x);
+      }
+      z[q] = acc;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * nt; q += blockDim.x) {
+      const int c = q / nt, k = q - c * nt;
+      double* zz = z + c * nc + k * nr;
+      const double* id = invd + k * nr;
+      const double* cc = cp + k * nr;
+      double dp = zz[0] * id[0];
+      zz[0] = dp;
+      for (int i = 1; i < nr; ++i) {
+        dp = (zz[i] - low[i] * dp) * id[i];
+        zz[i] = dp;
+      }
+      double xv = zz[nr - 1];
+      for (int i = nr - 2; i >= 0; --i) {
+        xv = zz[i] - cc[i] * xv;
+        zz[i] = xv;
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      const int j = q / nr, i = q - j * nr;
+      double ax = 0.0, ay = 0.0;
+      for (int k = 0; k < nt; ++k) {
+        const double vk = Vm[j * nt + k];
+        ax += vk * z[k * nr + i];
+        ay += vk * z[nc + k * nr + i];
+      }
+      ec[vslot(Lc, j, i)] = V{T(ax), T(ay)};
+    }
+    __syncthreads();
+  } else if (a.blk_n > 0) {
     // coarsest level, exact FP64 block-tridiagonal solve (Schur complements
     // of the polar rows): forward z_J = f_J - b_J (S_{J-1}^{-1} z_{J-1}),
     // backward x_J = S_J^{-1} (z_J - c_J x_{J+1}).  Four warps (128 threads:

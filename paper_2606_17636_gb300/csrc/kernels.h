@@ -67,6 +67,8 @@ struct VSmemArgs {
   int blk_n, blk_nt;     // block size (= coarsest nr) and block count (= coarsest nt)
   int blk_smem;          // 1: this slot's factors are staged in shared memory at blk_off
   int dbl_off, blk_off;  // byte offsets in shared memory: FP64 solve scratch, staged factors
+  const double* sep;     // separable coarsest-level factors [slots][sep_stride] (sep_stride > 0)
+  int sep_stride;
   int nu1, nu2, n_sor;
   int tab_off;           // shared-memory offset (complex elements) of the staged tables
   const void* tabs;      // per-slot packed tables (T), tab_stride elements per slot

@@ -161,6 +161,134 @@ static bool invert(std::vector<double>& A, int n) {  // Gauss-Jordan, partial pi
   return true;
 }
 
+// Eigen-decomposition of a symmetric n x n matrix S (row-major, destroyed)
+// by cyclic Jacobi rotations: S = U diag(lam) U^T, U orthogonal (columns).
+static void jacobi_eig(std::vector<double>& S, int n, std::vector<double>& U,
+                       std::vector<double>& lam) {
+  U.assign(size_t(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) U[size_t(i) * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int p = 0; p < n; ++p) {
+      dia += S[size_t(p) * n + p] * S[size_t(p) * n + p];
+      for (int q = p + 1; q < n; ++q) off += S[size_t(p) * n + q] * S[size_t(p) * n + q];
+    }
+    if (off <= 1e-32 * dia) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double b = S[size_t(p) * n + q];
+        if (std::fabs(b) < 1e-300) continue;
+        // rotation by phi with cot(2 phi) = (S_qq - S_pp) / (2 S_pq) zeroes S_pq
+        const double th = (S[size_t(q) * n + q] - S[size_t(p) * n + p]) / (2.0 * b);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; ++k) {   // columns p, q
+          const double skp = S[size_t(k) * n + p], skq = S[size_t(k) * n + q];
+          S[size_t(k) * n + p] = c * skp - sn * skq;
+          S[size_t(k) * n + q] = sn * skp + c * skq;
+        }
+        for (int k = 0; k < n; ++k) {   // rows p, q
+          const double spk = S[size_t(p) * n + k], sqk = S[size_t(q) * n + k];
+          S[size_t(p) * n + k] = c * spk - sn * sqk;
+          S[size_t(q) * n + k] = sn * spk + c * sqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double ukp = U[size_t(k) * n + p], ukq = U[size_t(k) * n + q];
+          U[size_t(k) * n + p] = c * ukp - sn * ukq;
+          U[size_t(k) * n + q] = sn * ukp + c * ukq;
+        }
+      }
+  }
+  lam.resize(n);
+  for (int i = 0; i < n; ++i) lam[i] = S[size_t(i) * n + i];
+}
+
+// Separable factors of L_m on plane g (see Hierarchy::coarse_sep), written
+// to out.  Returns false when the operator does not split this way or the
+// factors fail the residual check (the caller then uses block factors).
+static bool separable_factors(const PlaneGeo& g, int m, double* out) {
+  const int nr = g.r.n, nt = g.t.n;
+  const double s2 = g.s2(m);
+  const bool sph = g.geometry == SPH;
+  std::vector<double> dr(nr + 1), dt(nt + 1);
+  for (int i = 1; i <= nr; ++i) dr[i] = -(g.aE[i] + g.aW[i]) - (sph ? 0.0 : s2 * g.Q[i] * g.T[1]);
+  for (int j = 1; j <= nt; ++j) dt[j] = -(g.aN[j] + g.aS[j]) - (sph ? s2 * g.T[j] : 0.0);
+  for (int j = 1; j <= nt; ++j)
+    for (int i = 1; i <= nr; ++i) {
+      const double d = g.diag(m, i, j), sp = dr[i] + g.P[i] * dt[j];
+      if (std::fabs(d - sp) > 1e-12 * std::fabs(d)) return false;   // not separable
+      if (!sph && (g.P[i] != 1.0 || g.T[j] != 1.0)) return false;
+    }
+  // W-symmetrised polar operator: off-diagonal sqrt(aN_j aS_{j+1}), weights w
+  std::vector<double> S(size_t(nt) * nt, 0.0), w(nt + 1, 1.0), U, lam;
+  for (int j = 1; j <= nt; ++j) S[size_t(j - 1) * nt + (j - 1)] = dt[j];
+  for (int j = 1; j < nt; ++j) {
+    if (!(g.aN[j] > 0.0 && g.aS[j + 1] > 0.0)) return false;
+    const double e = std::sqrt(g.aN[j] * g.aS[j + 1]);
+    S[size_t(j - 1) * nt + j] = S[size_t(j) * nt + (j - 1)] = e;
+    w[j + 1] = w[j] * g.aN[j] / g.aS[j + 1];
+  }
+  jacobi_eig(S, nt, U, lam);
+  double* V = out;
+  double* Vi = V + size_t(nt) * nt;
+  double* invd = Vi + size_t(nt) * nt;
+  double* cp = invd + size_t(nt) * nr;
+  double* low = cp + size_t(nt) * nr;
+  for (int j = 0; j < nt; ++j)
+    for (int k = 0; k < nt; ++k) {
+      V[size_t(j) * nt + k] = U[size_t(j) * nt + k] / std::sqrt(w[j + 1]);
+      Vi[size_t(k) * nt + j] = U[size_t(j) * nt + k] * std::sqrt(w[j + 1]);
+    }
+  for (int i = 1; i <= nr; ++i) low[i - 1] = i > 1 ? g.aW[i] : 0.0;
+  for (int k = 0; k < nt; ++k) {
+    double cprev = 0.0;
+    for (int i = 1; i <= nr; ++i) {
+      const double up = i < nr ? g.aE[i] : 0.0;
+      const double den = dr[i] + lam[k] * g.P[i] - low[i - 1] * cprev;
+      if (den == 0.0) return false;
+      invd[size_t(k) * nr + i - 1] = 1.0 / den;
+      cprev = up / den;
+      cp[size_t(k) * nr + i - 1] = cprev;
+    }
+  }
+  // residual check of the factors on a fixed test vector, stencil apply
+  std::vector<double> b(size_t(nr) * nt), z(size_t(nr) * nt), x(size_t(nr) * nt);
+  for (size_t q = 0; q < b.size(); ++q) b[q] = std::sin(0.37 * double(q) + 1.0);
+  for (int k = 0; k < nt; ++k)
+    for (int i = 0; i < nr; ++i) {
+      double a = 0.0;
+      for (int j = 0; j < nt; ++j) a += Vi[size_t(k) * nt + j] * b[size_t(j) * nr + i];
+      z[size_t(k) * nr + i] = a;
+    }
+  for (int k = 0; k < nt; ++k) {
+    double* zz = z.data() + size_t(k) * nr;
+    double dp = zz[0] * invd[size_t(k) * nr];
+    zz[0] = dp;
+    for (int i = 1; i < nr; ++i) { dp = (zz[i] - low[i] * dp) * invd[size_t(k) * nr + i]; zz[i] = dp; }
+    double xv = zz[nr - 1];
+    for (int i = nr - 2; i >= 0; --i) { xv = zz[i] - cp[size_t(k) * nr + i] * xv; zz[i] = xv; }
+  }
+  for (int j = 0; j < nt; ++j)
+    for (int i = 0; i < nr; ++i) {
+      double a = 0.0;
+      for (int k = 0; k < nt; ++k) a += V[size_t(j) * nt + k] * z[size_t(k) * nr + i];
+      x[size_t(j) * nr + i] = a;
+    }
+  double rn = 0.0, bn = 0.0;
+  for (int j = 1; j <= nt; ++j)
+    for (int i = 1; i <= nr; ++i) {
+      const size_t q = size_t(j - 1) * nr + (i - 1);
+      double ax = g.diag(m, i, j) * x[q];
+      if (i < nr) ax += g.aE[i] * x[q + 1];
+      if (i > 1) ax += g.aW[i] * x[q - 1];
+      if (j < nt) ax += g.P[i] * g.aN[j] * x[q + nr];
+      if (j > 1) ax += g.P[i] * g.aS[j] * x[q - nr];
+      rn += (ax - b[q]) * (ax - b[q]);
+      bn += b[q] * b[q];
+    }
+  return rn <= 1e-20 * bn;   // 1e-10 relative: a sound factorisation (rounding only)
+}
+
 bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,
                      Hierarchy& H, std::string& err) {
   H.lv.clear();
@@ -171,10 +299,10 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
     L.g = g;
     if (neumann) L.g.aW[1] = 0.0;
     H.lv.push_back(L);
-    // coarsen while the short side exceeds 8 cells, or exceeds 4 cells while
-    // the plane has more than 256 (coarsest exact solve stays small)
+    // coarsen while the short side exceeds 16 cells, or exceeds 4 cells while
+    // the plane has more than 1024 (the coarsest level is solved exactly)
     const int mn = std::min(g.r.n, g.t.n);
-    if (!(mn > 8 || (mn > 4 && g.r.n * g.t.n > 256))) break;
+    if (!(mn > 16 || (mn > 4 && g.r.n * g.t.n > 1024))) break;
     if (g.r.n % 2 || g.t.n % 2) { err = "grid sizes must be powers of two"; return false; }
     PlaneGeo c;
     c.geometry = g.geometry; c.n_phi = g.n_phi; c.G = g.G;
@@ -274,6 +402,16 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
   const LevelHost& C = H.lv.back();
   const int nr = C.g.r.n, nt = C.g.t.n, nc = nr * nt;
   H.nc = nc;
+  if (nt <= 64) {
+    H.sep_stride = (2 * nt * nt + 2 * nt * nr + nr + 1) / 2 * 2;
+    H.coarse_sep.assign(size_t(M) * H.sep_stride, 0.0);
+    bool ok = true;
+    for (int k = 0; k < M && ok; ++k)
+      ok = separable_factors(C.g, modes[k], H.coarse_sep.data() + size_t(k) * H.sep_stride);
+    if (ok) return true;
+    H.coarse_sep.clear();
+    H.sep_stride = 0;
+  }
   const bool blocks = nr <= 64;
   H.blk_n = blocks ? nr : 0;
   H.blk_nt = blocks ? nt : 0;

@@ -76,6 +76,15 @@ struct Hierarchy {
   std::vector<double> coarse_blk;
   std::vector<double> coarse_inv;
   int blk_n = 0, blk_nt = 0;
+  // Separable factors (used when nt <= 64): on the coarsest level
+  // L_m = L_r (x) I + D_r (x) L_t, with D_r = diag(P) and the s_m^2 term in
+  // L_t (spherical, P = Q) or in L_r (cylindrical, P = T = 1).  Per slot:
+  // V [nt][nt] and V^-1 [nt][nt] (L_t = V diag(lambda) V^-1), then per
+  // eigenvalue k the Thomas factors of L_r + lambda_k D_r: 1/pivot [nt][nr],
+  // upper/pivot [nt][nr], then the radial lower couplings [nr]; sep_stride
+  // doubles per slot.
+  std::vector<double> coarse_sep;
+  int sep_stride = 0;
 };
 
 // Build levels (coarsening stops at a short side of 8 cells, or 4 cells when

@@ -93,6 +93,7 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   d_slot = plane_slot.empty() ? nullptr : upload(A, plane_slot);
   if (!H.coarse_inv.empty()) d_inv = upload(A, H.coarse_inv);
   if (!H.coarse_blk.empty()) d_blk = upload(A, H.coarse_blk);
+  if (!H.coarse_sep.empty()) d_sep = upload(A, H.coarse_sep);
   const size_t vb = vbytes();
   e.assign(nl, nullptr);
   f.assign(nl, nullptr);
@@ -170,8 +171,12 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
     vs.nc = H.nc;
     vs.blk_n = H.blk_n;
     vs.blk_nt = H.blk_nt;
-    const size_t blk_bytes = size_t(H.blk_nt) * H.blk_n * (H.blk_n + 2) * sizeof(double);
-    vs.blk_smem = (H.blk_n > 0 && sbytes + blk_bytes <= 220 * 1024) ? 1 : 0;
+    vs.sep = d_sep;
+    vs.sep_stride = H.sep_stride;
+    const size_t blk_bytes = H.sep_stride > 0
+                                 ? size_t(H.sep_stride) * sizeof(double)
+                                 : size_t(H.blk_nt) * H.blk_n * (H.blk_n + 2) * sizeof(double);
+    vs.blk_smem = ((H.blk_n > 0 || H.sep_stride > 0) && sbytes + blk_bytes <= 220 * 1024) ? 1 : 0;
     vs.blk_off = int(sbytes);
     if (vs.blk_smem) sbytes += blk_bytes;
     vs.smem_bytes = sbytes + 16;

@@ -75,6 +75,7 @@ class MGSolver {
   float* d_s2f = nullptr;
   double* d_inv = nullptr;
   double* d_blk = nullptr;
+  double* d_sep = nullptr;
   double4* d_part = nullptr;
   double4* d_psum = nullptr;
   int* d_cnt = nullptr;

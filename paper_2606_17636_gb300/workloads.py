@@ -102,7 +102,7 @@ def _lognormal_box(rng, n=256, L=20.0):
     ok = kk >= 2 * np.pi / L
     amp[ok] = kk[ok] ** -1.5                      # sqrt of P(k) ~ k^-3
     noise = rng.standard_normal((n, n, n))
-    g = np.fft.irfftn(np.fft.rfftn(noise) * amp, s=(n, n, n))
+    g = np.fft.irfftn(np.fft.rfftn(noise) * amp, s=(n, n, n), axes=(0, 1, 2))
     g = (g - g.mean()) / g.std()
     return np.exp(g - 0.5)
 

@@ -65,6 +65,9 @@ def test_smooth_restrict_prolong(ps, key, precision, tol, level):
         H.smooth(level, m, u, f.cpu().numpy()[m].T.astype(complex), 1)
         ref[m] = u[1:-1, 1:-1].T
     assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    if level + 1 >= len(H.levels):   # the coarsest level has no transfers
+        s.close()
+        return
     # defect restriction; the defect cancels terms of size |L e|, so the
     # rounding bound scales with the restricted |f| + |L e|
     from oracle import operator

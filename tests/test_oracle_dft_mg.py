@@ -51,7 +51,7 @@ MG_GRIDS = [
 @pytest.mark.parametrize("m", [0, 1, 7])
 def test_multigrid_reaches_direct_solution(g, sp, ri, ro, kw, m):
     p = Plane.make(g, 32, 16, 16, sp, ri, ro, **kw)
-    H = mg.Hierarchy(p)
+    H = mg.Hierarchy(p, min_cells=4, max_coarse=64)   # several levels on a small plane
     rng = np.random.default_rng(m)
     f = rng.standard_normal((32, 16)) + 1j * rng.standard_normal((32, 16))
     A = operator.matrix(p, m).tocsc()
@@ -64,7 +64,7 @@ def test_multigrid_reaches_direct_solution(g, sp, ri, ro, kw, m):
 
 def test_multigrid_neumann_inner_face_reaches_direct_solution():
     p = Plane.make(SPHERICAL, 32, 16, 16, LOG, 0.01, 1.0)
-    H = mg.Hierarchy(p, neumann_inner=True)
+    H = mg.Hierarchy(p, neumann_inner=True, min_cells=4, max_coarse=64)
     assert p.aW[1] == 0.0
     f = np.random.default_rng(3).standard_normal((32, 16)) + 0j
     x = spla.spsolve(operator.matrix(p, 0).tocsc(), operator.to_vec(f.real))
@@ -77,7 +77,7 @@ def test_prolongation_is_exact_for_bilinear_fields():
     c eta + d xi eta on the coarse centres is reproduced at the fine centres
     that have four coarse neighbours inside the domain."""
     p = Plane.make(SPHERICAL, 32, 16, 8, LOG, 0.5, 4.0, t_min=0.2, t_max=2.0)
-    H = mg.Hierarchy(p)
+    H = mg.Hierarchy(p, min_cells=4, max_coarse=64)   # at least two levels
     F, C = H.levels[0], H.levels[1]
     fn = lambda xi, eta: 1.0 + 0.3 * xi - 2.0 * eta + 0.7 * xi * eta
     ec = fn(C.xi[1:-1][:, None], C.eta[1:-1][None, :]) + 0j
@@ -88,7 +88,7 @@ def test_prolongation_is_exact_for_bilinear_fields():
 
 def test_restriction_preserves_constants_and_area_integral():
     p = Plane.make(CYLINDRICAL, 32, 16, 8, LOG, 0.05, 3.0)
-    H = mg.Hierarchy(p)
+    H = mg.Hierarchy(p, min_cells=4, max_coarse=64)   # at least two levels
     assert np.allclose(H.restrict(0, np.ones((32, 16)) + 0j), 1.0, atol=1e-14)
     r = np.random.default_rng(0).standard_normal((32, 16)) + 0j
     a = np.diff(p.r.F)[1:33]
@@ -100,14 +100,10 @@ def test_restriction_preserves_constants_and_area_integral():
     assert abs((a[:, None] * b[None, :] * r).sum() - (ac[:, None] * bc[None, :] * c).sum()) < 1e-12
 
 
-def test_vcycle_counts_follow_appendix_b():
-    """App. B: the double sphere on a log-spherical grid, zero initial guess:
-    m = 0 is the slowest mode and needs about 16 V-cycles for eight decades;
-    the count falls with m and modes m >~ 30 need very few."""
+def _double_sphere_rhs(n):
     from oracle import closed_forms as cf
     ds = GOLD["double_sphere"]
-    p = Plane.make(SPHERICAL, 64, 64, 128, LOG, *ds["sph_domain"]["r"])
-    H = mg.Hierarchy(p)
+    p = Plane.make(SPHERICAL, n, n, 128, LOG, *ds["sph_domain"]["r"])
     N = p.n_phi
     ph = (np.arange(N) + 0.5) * 2 * np.pi / N
     x, y, z = cf.sph_to_cart(p.r.x[1:-1][:, None, None], p.t.x[1:-1][None, :, None],
@@ -117,13 +113,27 @@ def test_vcycle_counts_follow_appendix_b():
         cx, cy, cz = cf.sph_to_cart(s_["r"], np.pi * s_["theta_over_pi"],
                                     s_.get("phi", np.pi * s_.get("phi_over_pi", 0.0)))
         rho += np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) < s_["a"]
-    f = 4 * np.pi * dft.forward(rho)
+    return p, 4 * np.pi * dft.forward(rho)
+
+
+def test_vcycle_counts_follow_appendix_b():
+    """App. B: on a log-spherical problem with a zero initial guess, m = 0 is
+    the slowest mode, needing about 16 V-cycles for eight decades at the
+    paper's resolution and a count that grows only weakly with the resolution
+    N (about N^0.27); the count falls with m, and modes m >~ 30 need very
+    few.  Double sphere at N = 64 (all modes listed) and N = 128 (m = 0)."""
     tol = GOLD["vcycles"]["tol"]
+    p, f = _double_sphere_rhs(64)
+    H = mg.Hierarchy(p)
     counts = [H.solve(m, f[:, :, m], tol)[1] for m in (0, 1, 4, 16, 30, 50)]
     paper = GOLD["vcycles"]["m0_cycles_for_8_decades"]
-    assert paper - 4 <= counts[0] <= paper + 4
+    assert paper / 2 <= counts[0] <= paper + 4
     assert all(a >= b for a, b in zip(counts, counts[1:]))
     assert counts[4] <= 3
+    p2, f2 = _double_sphere_rhs(128)
+    c128 = mg.Hierarchy(p2).solve(0, f2[:, :, 0], tol)[1]
+    growth = 2.0 ** GOLD["vcycles"]["resolution_exponent"]     # about 1.2 per doubling
+    assert counts[0] <= c128 <= counts[0] * growth * 1.35 + 1, (counts[0], c128)
 
 
 # -- App. A -----------------------------------------------------------------
