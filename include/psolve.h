@@ -112,6 +112,17 @@ int psolve_solve(psolve_t h, const double* rho, double* phi, double tol);
 int psolve_solve_batched(psolve_t* hs, const double* const* rhos, double* const* phis, int n,
                          double tol);
 
+/* Warm start for time stepping (Sec. 5.1 and App. B: in a simulation the
+ * previous step's solution is the initial guess, which cuts the V-cycles
+ * needed).  When enabled, every later psolve_solve / psolve_solve_batched on
+ * this handle starts the Psi solve from the previous solve's Psi and the Phi
+ * solve from the previous Phi; the first solve after enabling starts from
+ * zero (Psi) and Psi (Phi) as usual.  Enabling allocates two mode-plane
+ * buffers (2 M n_tz n_r complex FP64) through the handle's allocator
+ * (PSOLVE_ERR_NOMEM when that fails); enable = 0 returns to cold starts and
+ * keeps the buffers.  A solve that fails with PSOLVE_ERR_NONFINITE or a CUDA
+ * error clears the history. */
+int psolve_set_warm_start(psolve_t h, int enable);
 int psolve_set_stream(psolve_t h, void* cuda_stream);
 int psolve_get_stats(psolve_t h, psolve_stats* st);
 /* Number of boundary points nb (the side of the DGF table) and modes M. */

@@ -68,6 +68,7 @@ def lib():
             "psolve_stage_smooth": (I, [P, I, I, P, P, I]),
             "psolve_stage_smooth_static": (I, [P, I, I, P, P, I]),
             "psolve_stage_vcycle": (I, [P, I, I, P, P]),
+            "psolve_set_warm_start": (I, [P, I]),
             "psolve_get_fused_level": (I, [P, ctypes.POINTER(ctypes.c_int)]),
             "psolve_stage_restrict": (I, [P, I, I, P, P, P]),
             "psolve_stage_prolong": (I, [P, I, I, P, P]),
@@ -160,6 +161,10 @@ class Solver:
     def from_spec(cls, spec, **kw):
         return cls(spec["geometry"], spec["n_r"], spec["n_tz"], spec["n_phi"], spec["spacing"],
                    spec["r_in"], spec["r_out"], spec.get("t_min"), spec.get("t_max"), **kw)
+
+    def set_warm_start(self, enable=True):
+        """Start later solves from the previous solve's Psi and Phi."""
+        check(lib().psolve_set_warm_start(self.h, int(bool(enable))), "psolve_set_warm_start")
 
     def close(self):
         if getattr(self, "h", None):

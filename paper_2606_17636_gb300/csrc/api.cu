@@ -39,6 +39,9 @@ struct psolve_ctx {
   double* gt = nullptr;
   double2* tw = nullptr;
   double2 *u = nullptr, *f = nullptr, *sigma = nullptr, *theta = nullptr;
+  // warm start: the previous solve's Psi and Phi mode planes as initial guesses
+  double2 *psi_prev = nullptr, *phi_prev = nullptr;
+  int warm = 0, warm_hist = 0;
   SolveStats sp, sf;
   int* d_worst = nullptr;
   int* h_worst = nullptr;
@@ -49,7 +52,11 @@ struct psolve_ctx {
   const double* g_rho = nullptr;
   double* g_phi = nullptr;
   double g_tol = -1;
+  int g_warm = -1;   // warm state the graph was captured with
 };
+
+static size_t plane_bytes(psolve_t h) { return sizeof(double2) * size_t(h->M) * h->d.n_r * h->d.n_tz; }
+static int warm_state(psolve_t h) { return h->warm ? (h->warm_hist ? 2 : 1) : 0; }
 
 static int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -272,6 +279,21 @@ extern "C" void psolve_destroy(psolve_t h) {
   delete h;
 }
 
+extern "C" int psolve_set_warm_start(psolve_t h, int enable) {
+  if (!h) return fail(PSOLVE_ERR_ARG, "null handle");
+  if (enable && !h->psi_prev) {
+    h->psi_prev = static_cast<double2*>(h->A.get(plane_bytes(h)));
+    h->phi_prev = static_cast<double2*>(h->A.get(plane_bytes(h)));
+    if (!h->psi_prev || !h->phi_prev) {
+      h->psi_prev = h->phi_prev = nullptr;
+      return fail(PSOLVE_ERR_NOMEM, "warm-start buffers: out of device memory");
+    }
+  }
+  h->warm = enable ? 1 : 0;
+  h->warm_hist = 0;
+  return PSOLVE_OK;
+}
+
 extern "C" int psolve_set_stream(psolve_t h, void* s) {
   if (!h) return fail(PSOLVE_ERR_ARG, "null handle");
   h->st = static_cast<cudaStream_t>(s);
@@ -295,20 +317,28 @@ extern "C" int psolve_get_sizes(psolve_t h, int* n_modes, int* n_boundary, int* 
 static void enqueue_front(psolve_t h, const double* rho) {
   launch_fft_forward(rho, h->f, h->d.n_r, h->d.n_tz, h->d.n_phi, 4.0 * kPi * h->d.G / h->d.n_phi,
                      h->tw, h->st);
-  cudaMemsetAsync(h->u, 0, sizeof(double2) * size_t(h->M) * h->d.n_r * h->d.n_tz, h->st);
+  if (warm_state(h) == 2)
+    cudaMemcpyAsync(h->u, h->psi_prev, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
+  else
+    cudaMemsetAsync(h->u, 0, plane_bytes(h), h->st);
   h->mg.init_loop(h->st);
 }
 
 static void enqueue_middle(psolve_t h) {
   snapshot(h, h->sp);
+  if (h->warm) cudaMemcpyAsync(h->psi_prev, h->u, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
   launch_screening(h->bdev, h->u, h->sigma, h->M, h->st);
   launch_boundary_potential(h->gt, h->sigma, h->theta, h->M, h->nb, h->st);
   launch_rhs_ghosts(h->bdev, h->f, h->theta, h->M, h->st);
+  // initial guess of the Phi solve: the previous Phi (warm start), else Psi
+  if (warm_state(h) == 2)
+    cudaMemcpyAsync(h->u, h->phi_prev, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
   h->mg.init_loop(h->st);
 }
 
 static void enqueue_back(psolve_t h, double* phi) {
   snapshot(h, h->sf);
+  if (h->warm) cudaMemcpyAsync(h->phi_prev, h->u, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
   launch_fft_inverse(h->u, phi, h->d.n_r, h->d.n_tz, h->d.n_phi, h->tw, h->st);
   k_worst<<<1, 256, 0, h->st>>>(h->sp.status, h->sf.status, h->M, h->d_worst);
   cudaMemcpyAsync(h->h_worst, h->d_worst, sizeof(int), cudaMemcpyDeviceToHost, h->st);
@@ -382,7 +412,15 @@ static int capture(psolve_t h, const double* rho, double* phi, double tol) {
   h->g_rho = rho;
   h->g_phi = phi;
   h->g_tol = tol;
+  h->g_warm = warm_state(h);
   return 0;
+}
+
+// After a warm-start solve the history holds its Psi and Phi (also the last
+// iterates of a solve that stopped short of the tolerance); a non-finite or
+// failed solve discards it.
+static void note_history(psolve_t h, int rc) {
+  if (h->warm) h->warm_hist = (rc == PSOLVE_OK || rc == PSOLVE_ERR_NOT_CONVERGED) ? 1 : 0;
 }
 
 static int finish(psolve_t h) {
@@ -396,7 +434,8 @@ static int finish(psolve_t h) {
 
 static int enqueue_solve(psolve_t h, const double* rho, double* phi, double tol) {
   if (h->d.use_graph) {
-    if (!h->gexec || h->g_rho != rho || h->g_phi != phi || h->g_tol != tol) {
+    if (!h->gexec || h->g_rho != rho || h->g_phi != phi || h->g_tol != tol ||
+        h->g_warm != warm_state(h)) {
       if (capture(h, rho, phi, tol) != 0)
         return fail(PSOLVE_ERR_CUDA, "graph capture failed: " + g_err);
     }
@@ -418,7 +457,9 @@ extern "C" int psolve_solve(psolve_t h, const double* rho, double* phi, double t
   if (tol <= 0) tol = 1e-8;
   int rc = enqueue_solve(h, rho, phi, tol);
   if (rc != PSOLVE_OK) return rc;
-  return finish(h);
+  rc = finish(h);
+  note_history(h, rc);
+  return rc;
 }
 
 extern "C" int psolve_solve_batched(psolve_t* hs, const double* const* rhos, double* const* phis,
@@ -437,6 +478,7 @@ extern "C" int psolve_solve_batched(psolve_t* hs, const double* const* rhos, dou
   int first = PSOLVE_OK;
   for (int k = 0; k < n; ++k) {
     int rc = finish(hs[k]);
+    note_history(hs[k], rc);
     if (rc != PSOLVE_OK && first == PSOLVE_OK) first = rc;
   }
   return first;
