@@ -387,8 +387,8 @@ def vcycle_roofline(torch, ps, s, stream):
     mode plane, levels held in shared memory), all modes, timed alone
     through psolve_stage_vcycle with CUDA events on the library's stream.
     Algorithmic work per launch: M x sum over the fused smoothed levels of
-    cells x VCYCLE_FLOPS_PER_CELL FP32 flops, plus the FP64 block solve of
-    the coarsest level (4 n^2 (2 nt - 1) per mode)."""
+    cells x VCYCLE_FLOPS_PER_CELL FP32 flops, plus the FP64 separable solve
+    of the coarsest level (8 n_r n_t^2 + 10 n_r n_t per mode)."""
     M = s.n_modes
     lev = s.fused_level()
     n_r, n_tz = s.shape[0], s.shape[1]
@@ -411,7 +411,9 @@ def vcycle_roofline(torch, ps, s, stream):
         cells += (n_r >> l) * (n_tz >> l)
         l += 1
     cr, ct = n_r >> (s.n_levels - 1), n_tz >> (s.n_levels - 1)
-    flops = M * (cells * VCYCLE_FLOPS_PER_CELL + 4 * cr * cr * (2 * ct - 1))
+    # separable coarsest solve: two FP64 transforms along theta (2 components)
+    # and n_theta Thomas solves along r
+    flops = M * (cells * VCYCLE_FLOPS_PER_CELL + 8 * cr * ct * ct + 10 * cr * ct)
     ach = flops / dt / 1e12
     return {"kernel": "fused coarse V-cycle k_vsmem (levels %d..%d in shared memory, all %d modes)"
                       % (lev, s.n_levels - 1, M),

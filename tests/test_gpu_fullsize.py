@@ -89,6 +89,12 @@ def test_mixed_full_size_matches_oracle_on_sampled_modes(ps, full):
         e10 = _real_space_share(p, out[ps.MIXED, 1e-10][1][:, :, m] - ref[m], m, N)
         assert e10 <= 1e-7 * norm, (m, e10 / norm)
     # the two precisions agree on the whole field at equal tolerance
+    wv = p.volume_weights()[:, :, None]
     d = out[ps.MIXED, 1e-8][0] - out[ps.FP64, 1e-8][0]
-    dn = float(np.sqrt((p.volume_weights()[:, :, None] * d ** 2).sum()))
+    dn = float(np.sqrt((wv * d ** 2).sum()))
     assert dn <= 1e-9 * norm, dn / norm
+    # whole-field error of the mixed path at tol 1e-8 against the FP64 path
+    # at tol 1e-11 (itself within 1e-10 of the oracle on every sampled mode)
+    ref64, _ = _solve(ps, w, ps.FP64, 1e-11)
+    e = float(np.sqrt((wv * (out[ps.MIXED, 1e-8][0] - ref64) ** 2).sum()))
+    assert e <= 1e-7 * float(np.sqrt((wv * ref64 ** 2).sum())), e
