@@ -321,6 +321,7 @@ static void enqueue_front(psolve_t h, const double* rho) {
     cudaMemcpyAsync(h->u, h->psi_prev, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
   else
     cudaMemsetAsync(h->u, 0, plane_bytes(h), h->st);
+  h->mg.zero_guess = warm_state(h) == 2 ? 0 : 1;   // the Psi loop is enqueued next
   h->mg.init_loop(h->st);
 }
 
@@ -333,6 +334,7 @@ static void enqueue_middle(psolve_t h) {
   // initial guess of the Phi solve: the previous Phi (warm start), else Psi
   if (warm_state(h) == 2)
     cudaMemcpyAsync(h->u, h->phi_prev, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
+  h->mg.zero_guess = 0;   // the Phi loop starts from Psi or the previous Phi
   h->mg.init_loop(h->st);
 }
 
@@ -544,6 +546,7 @@ extern "C" int psolve_stage_mg_solve(psolve_t h, const double* f_hat, double* u_
   if (tol <= 0) tol = 1e-8;
   const size_t bytes = sizeof(double2) * size_t(h->M) * h->d.n_r * h->d.n_tz;
   if (!warm) cudaMemsetAsync(u_hat, 0, bytes, h->st);
+  h->mg.zero_guess = warm ? 0 : 1;
   std::string err;
   if (h->mg.eager_solve(reinterpret_cast<const double2*>(f_hat), reinterpret_cast<double2*>(u_hat),
                         tol, h->st, err) != 0)

@@ -240,11 +240,31 @@ __device__ void retire_block(int* act, int* nact, const double4* __restrict__ ps
                              double tol, int max_cycles, int stagnation, int use_cond,
                              unsigned long long handle, int* scan);
 
+// FP64 defect at (i, j) from the per-cell products (one FP64 operation for
+// the mode's diagonal, five per component for the stencil).
+__device__ __forceinline__ double2 defect_tab(const LevelDev& L, const double* __restrict__ ct,
+                                              int n, double s2, const double2* __restrict__ e,
+                                              const double2* __restrict__ f, int i, int j) {
+  const int nr = L.nr, nt = L.nt, idx = j * nr + i;
+  const double2 c = e[idx];
+  const double2 E = (i + 1 < nr) ? e[idx + 1] : make_double2(0.0, 0.0);
+  const double2 W = (i > 0) ? e[idx - 1] : make_double2(0.0, 0.0);
+  const double2 N = (j + 1 < nt) ? e[idx + nr] : make_double2(0.0, 0.0);
+  const double2 S = (j > 0) ? e[idx - nr] : make_double2(0.0, 0.0);
+  const double aE = RTAB(L.rd, RT_AE, i + 1), aW = RTAB(L.rd, RT_AW, i + 1);
+  const double aN = ct[idx], aS = ct[n + idx];
+  const double d = fma(-s2, ct[3 * n + idx], ct[2 * n + idx]);
+  const double2 fv = f[idx];
+  return make_double2(fv.x - (aE * E.x + aW * W.x + aN * N.x + aS * S.x + d * c.x),
+                      fv.y - (aE * E.y + aW * W.y + aN * N.y + aS * S.y + d * c.y));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const double2* __restrict__ f,
                                                   const double2* __restrict__ u,
                                                   vec2_t<T>* __restrict__ r, double4* part,
-                                                  double4* psum, int* cnt, int bpp, RetireArgs ra) {
+                                                  double4* psum, int* cnt, int bpp, RetireArgs ra,
+                                                  const double* __restrict__ ctab) {
   __shared__ double4 sh[8];
   __shared__ float4 shf[8];
   __shared__ int last, glast;
@@ -254,6 +274,8 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
   const int nact = *B.nact;
   const int nr = L.nr, nt = L.nt, n = nr * nt;
   const bool want_f = *ra.S.iter == 0;     // |f| is needed on the first iteration only
+  // from a zero initial guess the first defect is f itself (no stencil)
+  const bool r_is_f = want_f && ra.zero_guess;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int w = blockIdx.x; w < nact * bpp; w += gridDim.x) {
     const int k = w / bpp, bx = w - k * bpp;
@@ -267,7 +289,7 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
       const int j = idx / nr, i = idx - j * nr;
       const size_t base = size_t(p) * n;
       const double s2 = B.s2d[slot];
-      const double2 rv = defect<double>(L, L.rd, L.td, s2, u + base, f + base, i, j);
+      const double2 rv = r_is_f ? f[base + idx] : defect_tab(L, ctab, n, s2, u + base, f + base, i, j);
       const vec2_t<T> ro = vmk<vec2_t<T>, T>(T(rv.x), T(rv.y));
       r[base + idx] = ro;
       const float dv = L.rf[RT_V * (nr + 2) + i + 1] * L.tf[TT_V * (nt + 2) + j + 1];
@@ -328,10 +350,10 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
 template <typename T>
 void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
                      vec2_t<T>* r, double4* part, double4* psum, int* cnt, const RetireArgs& ra,
-                     cudaStream_t st) {
+                     cudaStream_t st, const double* ctab) {
   const int bpp = residual_blocks(L.nr, L.nt);
   k_residual<T><<<work_grid(long(bpp) * B.max_planes), 256, 0, st>>>(L, B, f, u, r, part, psum,
-                                                                       cnt, bpp, ra);
+                                                                       cnt, bpp, ra, ctab);
 }
 
 // ---------------------------------------------------------------------------
@@ -436,7 +458,7 @@ void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t 
                                  cudaStream_t);                                                  \
   template void launch_residual<T>(const LevelDev&, const Batch&, const double2*,               \
                                    const double2*, vec2_t<T>*, double4*, double4*, int*,        \
-                                   const RetireArgs&, cudaStream_t);
+                                   const RetireArgs&, cudaStream_t, const double*);
 INST(float)
 INST(double)
 

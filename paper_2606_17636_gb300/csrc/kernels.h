@@ -110,6 +110,7 @@ struct RetireArgs {
   int max_cycles, stagnation, use_cond;
   unsigned long long handle;   // graph conditional (use_cond)
   int* gcnt;                   // completion counter, zero between launches
+  int zero_guess;              // u is zero on the first iteration: r = f there
 };
 
 // r = f - L u (FP64), stored as T2, and the volume-weighted norms per plane
@@ -118,10 +119,12 @@ struct RetireArgs {
 // plane to finish then applies the App. B criterion to every active plane,
 // counts cycles, sets the status, compacts the active list and sets the
 // continue flag (and the graph conditional).
+// ctab: the level's per-cell FP64 products [4][nt][nr] (P aN, P aS,
+// DR + P DT, Q T), the same for every mode.
 template <typename T>
 void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
                      vec2_t<T>* r, double4* part, double4* psum, int* cnt, const RetireArgs& ra,
-                     cudaStream_t st);
+                     cudaStream_t st, const double* ctab);
 int residual_blocks(int nr, int nt);
 
 void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t st);

@@ -4,6 +4,7 @@
 #include "solver.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -91,6 +92,23 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   d_s2f = upload(A, to_f(s2));
   d_mode = upload(A, modes);
   d_slot = plane_slot.empty() ? nullptr : upload(A, plane_slot);
+  {   // level-0 per-cell products for the FP64 residual (mode independent)
+    const LevelHost& h0 = H.lv[0];
+    const int nr = lv[0].nr, nt = lv[0].nt, NR = nr + 2, NT = nt + 2;
+    const size_t n = size_t(nr) * nt;
+    std::vector<double> ct(4 * n);
+    for (int j = 0; j < nt; ++j)
+      for (int i = 0; i < nr; ++i) {
+        const size_t q = size_t(j) * nr + i;
+        const double P = h0.rtab[RT_P * NR + i + 1];
+        ct[q] = P * h0.ttab[TT_AN * NT + j + 1];
+        ct[n + q] = P * h0.ttab[TT_AS * NT + j + 1];
+        ct[2 * n + q] = std::fma(P, h0.ttab[TT_DT * NT + j + 1], h0.rtab[RT_DR * NR + i + 1]);
+        ct[3 * n + q] = h0.rtab[RT_Q * NR + i + 1] * h0.ttab[TT_T * NT + j + 1];
+      }
+    d_ctab = upload(A, ct);
+    if (!d_ctab) { err = "out of device memory"; return false; }
+  }
   if (!H.coarse_inv.empty()) d_inv = upload(A, H.coarse_inv);
   if (!H.coarse_blk.empty()) d_blk = upload(A, H.coarse_blk);
   if (!H.coarse_sep.empty()) d_sep = upload(A, H.coarse_sep);
@@ -261,10 +279,11 @@ void MGSolver::residual(const double2* ff, const double2* u, double tol, cudaStr
   ra.use_cond = use_cond;
   ra.handle = cond;
   ra.gcnt = d_gcnt;
+  ra.zero_guess = zero_guess;
   if (opt.precision)
-    launch_residual<float>(lv[0], batch, ff, u, (float2*)f[0], d_part, d_psum, d_cnt, ra, st);
+    launch_residual<float>(lv[0], batch, ff, u, (float2*)f[0], d_part, d_psum, d_cnt, ra, st, d_ctab);
   else
-    launch_residual<double>(lv[0], batch, ff, u, (double2*)f[0], d_part, d_psum, d_cnt, ra, st);
+    launch_residual<double>(lv[0], batch, ff, u, (double2*)f[0], d_part, d_psum, d_cnt, ra, st, d_ctab);
 }
 
 // One V-cycle on the error equation L e_0 = f_0 (f_0 = FP64 residual in the

@@ -58,6 +58,7 @@ class MGSolver {
   std::vector<void*> e, f;
   void* tmp = nullptr;             // ping-pong buffer of the global-memory smoother
   int first = 0;                   // first level handled by the shared-memory kernel
+  int zero_guess = 0;              // the next solve starts from u = 0 (set by the caller)
   VSmemArgs vs{};
   // stage helpers on explicit buffers
   void smooth(int level, void* e, const void* f, int cycles, bool zero_init, cudaStream_t st,
@@ -76,6 +77,7 @@ class MGSolver {
   double* d_inv = nullptr;
   double* d_blk = nullptr;
   double* d_sep = nullptr;
+  double* d_ctab = nullptr;   // level-0 per-cell FP64 products [4][nt][nr]
   double4* d_part = nullptr;
   double4* d_psum = nullptr;
   int* d_cnt = nullptr;
