@@ -38,6 +38,10 @@ __device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T 
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
   const T* om = omr_<T>(L);
+  // the same for every radial line of the level: loaded once (FP32; the
+  // FP64 kernel reloads them per line to stay within its registers)
+  RLineTabs<T, CPL> tabs;
+  if constexpr (sizeof(T) == 4) ld_rtabs<T, CPL>(tabs, L, rt);
   for (int line = warp; 2 * line + color < nt; line += nw) {
     const int j = 2 * line + color;
     const int sj = vswz(L, j);
@@ -56,7 +60,8 @@ __device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T 
 #pragma unroll
       for (int c = 0; c < CPL; ++c) us[c] = z2<V>();
     }
-    relax_r<T, CPL>(L, rt, tt, s2, om[j], j, g, un, us, n_sor, ev);
+    if constexpr (sizeof(T) == 4) relax_r<T, CPL>(L, tabs, tt, s2, om[j], j, g, un, us, n_sor, ev);
+    else relax_r<T, CPL>(L, rt, tt, s2, om[j], j, g, un, us, n_sor, ev);
     st_line_swz<V, CPL>(e + j * nr, sj, ev, lane, nr);
   }
 }
@@ -71,6 +76,8 @@ __device__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s
   const T* tt = tt_<T>(L);
   const T* om = omt_<T>(L);
   const bool on = CPL > 1 || lane < nt;
+  TLineTabs<T, CPL> tabs;   // the same for every polar line of the level (FP32: loaded once)
+  if constexpr (sizeof(T) == 4) ld_ttabs<T, CPL>(tabs, L, tt);
   for (int col = warp; 2 * col + color < nr; col += nw) {
     const int i = 2 * col + color;
     V ev[CPL], g[CPL], ue[CPL], uw[CPL];
@@ -85,7 +92,8 @@ __device__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s
         if (i + 1 < nr) ue[c] = e[row + ((i + 1) ^ s)];
       }
     }
-    relax_t<T, CPL>(L, rt, tt, s2, om[i], i, g, ue, uw, n_sor, ev);
+    if constexpr (sizeof(T) == 4) relax_t<T, CPL>(L, rt, tabs, s2, om[i], i, g, ue, uw, n_sor, ev);
+    else relax_t<T, CPL>(L, rt, tt, s2, om[i], i, g, ue, uw, n_sor, ev);
     if (on) {
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {

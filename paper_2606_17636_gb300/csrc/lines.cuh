@@ -216,9 +216,60 @@ __device__ __forceinline__ void sor_line(vec2_t<T> (&ev)[CPL], const vec2_t<T> (
   }
 }
 
+// Coefficients of the lane's cells that every radial line of a level shares
+// (they depend on the radial index only), and likewise for polar lines.
+template <typename T, int CPL>
+struct RLineTabs {
+  T P[CPL], dr[CPL], q[CPL], up[CPL], dn[CPL];
+};
+template <typename T, int CPL>
+struct TLineTabs {
+  T dt[CPL], tj[CPL], an[CPL], as[CPL];
+};
+
+template <typename T, int CPL>
+__device__ __forceinline__ void ld_rtabs(RLineTabs<T, CPL>& a, const LevelDev& L, const T* rt) {
+  const int lane = threadIdx.x & 31, nr = L.nr, NR = nr + 2;
+  ld_tab<T, CPL>(a.P, rt + RT_P * NR, lane, nr);
+  ld_tab<T, CPL>(a.dr, rt + RT_DR * NR, lane, nr);
+  ld_tab<T, CPL>(a.q, rt + RT_Q * NR, lane, nr);
+  ld_tab<T, CPL>(a.up, rt + RT_AE * NR, lane, nr);
+  ld_tab<T, CPL>(a.dn, rt + RT_AW * NR, lane, nr);
+}
+template <typename T, int CPL>
+__device__ __forceinline__ void ld_ttabs(TLineTabs<T, CPL>& a, const LevelDev& L, const T* tt) {
+  const int lane = threadIdx.x & 31, nt = L.nt, NT = nt + 2;
+  ld_tab<T, CPL>(a.dt, tt + TT_DT * NT, lane, nt);
+  ld_tab<T, CPL>(a.tj, tt + TT_T * NT, lane, nt);
+  ld_tab<T, CPL>(a.an, tt + TT_AN * NT, lane, nt);
+  ld_tab<T, CPL>(a.as, tt + TT_AS * NT, lane, nt);
+}
+
 // Radial line j: g = source values of the lane's cells (clobbered), un / us =
 // lines j+1 / j-1 (zero beyond the plane), ev = own line on entry, relaxed
-// line on exit.
+// line on exit; a = the level's radial-line coefficients of the lane's cells.
+template <typename T, int CPL>
+__device__ __forceinline__ void relax_r(const LevelDev& L, const RLineTabs<T, CPL>& a, const T* tt,
+                                        T s2, T w, int j, vec2_t<T> (&g)[CPL],
+                                        const vec2_t<T> (&un)[CPL], const vec2_t<T> (&us)[CPL],
+                                        int n_sor, vec2_t<T> (&ev)[CPL]) {
+  const int lane = threadIdx.x & 31, nr = L.nr, NT = L.nt + 2;
+  const T aN = tt[TT_AN * NT + j + 1], aS = tt[TT_AS * NT + j + 1];
+  const T Tj = tt[TT_T * NT + j + 1], dtj = tt[TT_DT * NT + j + 1];
+  const bool on = CPL > 1 || lane < nr;
+  T id[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    g[c].x = g[c].x - a.P[c] * (aN * un[c].x + aS * us[c].x);
+    g[c].y = g[c].y - a.P[c] * (aN * un[c].y + aS * us[c].y);
+    id[c] = on ? rcp_rn(a.dr[c] + a.P[c] * dtj - s2 * a.q[c] * Tj) : T(0);
+  }
+  sor_line<T, CPL>(ev, g, a.up, a.dn, id, w, nr, n_sor);
+}
+
+// Same, loading the coefficients from the level's table as it uses them (for
+// kernels without registers to keep them): neighbour lines first (they die
+// there), then the diagonal, then the along-line couplings.
 template <typename T, int CPL>
 __device__ __forceinline__ void relax_r(const LevelDev& L, const T* rt, const T* tt, T s2, T w,
                                         int j, vec2_t<T> (&g)[CPL], const vec2_t<T> (&un)[CPL],
@@ -228,8 +279,6 @@ __device__ __forceinline__ void relax_r(const LevelDev& L, const T* rt, const T*
   const T aN = tt[TT_AN * NT + j + 1], aS = tt[TT_AS * NT + j + 1];
   const T Tj = tt[TT_T * NT + j + 1], dtj = tt[TT_DT * NT + j + 1];
   const bool on = CPL > 1 || lane < nr;
-  // neighbour lines first (they die here), then the diagonal, then the
-  // along-line couplings: keeps the live register set small
   T P[CPL], up[CPL], dn[CPL], id[CPL];
   ld_tab<T, CPL>(P, rt + RT_P * NR, lane, nr);
 #pragma unroll
@@ -251,7 +300,30 @@ __device__ __forceinline__ void relax_r(const LevelDev& L, const T* rt, const T*
 
 // Polar / vertical line i: g = source values of the lane's cells (clobbered),
 // ue / uw = columns i+1 / i-1 (zero beyond the plane), ev = own column on
-// entry, relaxed column on exit.
+// entry, relaxed column on exit; a = the level's polar-line coefficients of
+// the lane's cells.
+template <typename T, int CPL>
+__device__ __forceinline__ void relax_t(const LevelDev& L, const T* rt, const TLineTabs<T, CPL>& a,
+                                        T s2, T w, int i, vec2_t<T> (&g)[CPL],
+                                        const vec2_t<T> (&ue)[CPL], const vec2_t<T> (&uw)[CPL],
+                                        int n_sor, vec2_t<T> (&ev)[CPL]) {
+  const int lane = threadIdx.x & 31, nt = L.nt, NR = L.nr + 2;
+  const T P = rt[RT_P * NR + i + 1], aE = rt[RT_AE * NR + i + 1], aW = rt[RT_AW * NR + i + 1];
+  const T dr = rt[RT_DR * NR + i + 1], Qi = rt[RT_Q * NR + i + 1];
+  const bool on = CPL > 1 || lane < nt;
+  T up[CPL], dn[CPL], id[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    g[c].x = g[c].x - aE * ue[c].x - aW * uw[c].x;
+    g[c].y = g[c].y - aE * ue[c].y - aW * uw[c].y;
+    id[c] = on ? rcp_rn(dr + P * a.dt[c] - s2 * Qi * a.tj[c]) : T(0);
+    up[c] = P * a.an[c];
+    dn[c] = P * a.as[c];
+  }
+  sor_line<T, CPL>(ev, g, up, dn, id, w, nt, n_sor);
+}
+
+// Same, loading the coefficients as it uses them.
 template <typename T, int CPL>
 __device__ __forceinline__ void relax_t(const LevelDev& L, const T* rt, const T* tt, T s2, T w,
                                         int i, vec2_t<T> (&g)[CPL], const vec2_t<T> (&ue)[CPL],
