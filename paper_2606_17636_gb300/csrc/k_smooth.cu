@@ -41,8 +41,8 @@ __device__ __forceinline__ void stage_lines(vec2_t<T>* dst, const vec2_t<T>* pla
   typedef vec2_t<T> V;
   constexpr int per = 16 / int(sizeof(V));   // complex values per 16-byte chunk
   const int chunks = nr / per;                // nr is a multiple of 2
-  for (int idx = threadIdx.x; idx < nlines * chunks; idx += blockDim.x) {
-    const int q = idx / chunks, c = idx - q * chunks, j = j_first + q;
+  for (RowWalk w(threadIdx.x, blockDim.x, chunks); w.j < nlines; w.next()) {
+    const int q = w.j, c = w.c, j = j_first + q;
     const bool valid = !zero && j >= 0 && j < nt;
     const V* src = plane + (valid ? size_t(j) * nr + c * per : 0);
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst + size_t(q) * nr + c * per));
@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_
   V* se = reinterpret_cast<V*>(sraw);   // [nt][SW], column cc <-> i0 - 1 + cc
   V* sf = se + size_t(nt) * SW;          // same layout for f
   const size_t base = size_t(p) * nr * nt;
-  for (int idx = threadIdx.x; idx < nt * TC; idx += blockDim.x) {
-    const int j = idx / TC, cc = idx - j * TC, i = i0 - 1 + cc;
+  for (RowWalk w(threadIdx.x, blockDim.x, TC); w.j < nt; w.next()) {
+    const int j = w.j, cc = w.c, i = i0 - 1 + cc;
     const bool in = i >= 0 && i < nr;
     const int o = tslot<CPL>(j, cc, SW);
     const size_t g = base + size_t(j) * nr + (in ? i : 0);
@@ -208,10 +208,8 @@ __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_
     }
     __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < nt * TW; idx += blockDim.x) {
-    const int j = idx / TW, cc = idx - j * TW;
-    eout[base + size_t(j) * nr + i0 + cc] = se[tslot<CPL>(j, cc + 1, SW)];
-  }
+  for (RowWalk w(threadIdx.x, blockDim.x, TW); w.j < nt; w.next())
+    eout[base + size_t(w.j) * nr + i0 + w.c] = se[tslot<CPL>(w.j, w.c + 1, SW)];
 }
 
 static int tile_w(int nr, int nt, size_t vb) {

@@ -134,8 +134,8 @@ __device__ void s_restrict(const LevelDev& L, const LevelDev& C, const vec2_t<T>
   const int nr = L.nr, nt = L.nt;
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
-  for (int cidx = threadIdx.x; cidx < C.nr * C.nt; cidx += blockDim.x) {
-    const int J = cidx / C.nr, I = cidx - J * C.nr;
+  for (RowWalk w(threadIdx.x, blockDim.x, C.nr); w.j < C.nt; w.next()) {
+    const int J = w.j, I = w.c;
     T ax = 0, ay = 0;
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) {
@@ -182,8 +182,8 @@ __device__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, co
   typedef vec2_t<T> V;
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
-  for (int cidx = threadIdx.x; cidx < C.nr * C.nt; cidx += blockDim.x) {
-    const int J = cidx / C.nr, I = cidx - J * C.nr;
+  for (RowWalk w(threadIdx.x, blockDim.x, C.nr); w.j < C.nt; w.next()) {
+    const int J = w.j, I = w.c;
     V cv[3][3];   // coarse (I - 1 + u, J - 1 + v), 1-based index I + u, J + v
 #pragma unroll
     for (int v = 0; v < 3; ++v)
@@ -266,8 +266,11 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     for (int k = threadIdx.x; k < int(fac_stride / 2); k += blockDim.x) dst[k] = src[k];
   }
   // load f of the first level, zero all errors
-  for (int k = threadIdx.x; k < n0; k += blockDim.x)
-    sm[a.off_f[0] + vslot(a.L[0], k / nr0, k % nr0)] = gf[size_t(p) * n0 + k];
+  {
+    RowWalk w(threadIdx.x, blockDim.x, nr0);
+    for (int k = threadIdx.x; k < n0; k += blockDim.x, w.next())
+      sm[a.off_f[0] + vslot(a.L[0], w.j, w.c)] = gf[size_t(p) * n0 + k];
+  }
   for (int l = 0; l < K; ++l) {
     const int n = a.L[l].nr * a.L[l].nt;
     for (int k = threadIdx.x; k < n; k += blockDim.x) sm[a.off_e[l] + k] = V{0, 0};
@@ -423,8 +426,11 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     s_prolong<T>(sL[l], sL[l + 1], sm + a.off_e[l], sm + a.off_e[l + 1], m);
     s_smooth<T>(sL[l], sm + a.off_e[l], sm + a.off_f[l], s2, a.nu2, a.n_sor);
   }
-  for (int k = threadIdx.x; k < n0; k += blockDim.x)
-    ge[size_t(p) * n0 + k] = sm[a.off_e[0] + vslot(a.L[0], k / nr0, k % nr0)];
+  {
+    RowWalk w(threadIdx.x, blockDim.x, nr0);
+    for (int k = threadIdx.x; k < n0; k += blockDim.x, w.next())
+      ge[size_t(p) * n0 + k] = sm[a.off_e[0] + vslot(a.L[0], w.j, w.c)];
+  }
 }
 
 // 512 threads (up to 128 registers each, no spills); each warp takes every

@@ -73,6 +73,20 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Cell index held in register slot c of `lane`.
+// Walks the (row, column) pairs of a row-major n-column array in steps of
+// `step` flat elements from flat index `start`: one division at set-up, then
+// an add and a conditional subtract per step (0 <= c < n throughout).
+struct RowWalk {
+  int j, c, dj, dc, n;
+  __device__ __forceinline__ RowWalk(int start, int step, int n_) : n(n_) {
+    j = start / n; c = start - j * n; dj = step / n; dc = step - dj * n;
+  }
+  __device__ __forceinline__ void next() {
+    c += dc; j += dj;
+    if (c >= n) { c -= n; ++j; }
+  }
+};
+
 template <int CPL> __device__ __forceinline__ int lcell(int lane, int c) {
   if constexpr (CPL == 1) return lane;
   else return 2 * lane + 64 * (c >> 1) + (c & 1);
