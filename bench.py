@@ -39,6 +39,8 @@ def args_():
     a.add_argument("--warmup", type=int, default=3)
     a.add_argument("--impl", default="ours", choices=["ours", "reference"])
     a.add_argument("--no-baseline", action="store_true")
+    a.add_argument("--no-tune", action="store_true",
+                   help="keep the default smoothing schedule and tile shapes (skip psolve_autotune)")
     a.add_argument("--eager", action="store_true",
                    help="host-driven loop instead of the captured graph (for per-kernel profiling)")
     return a.parse_args()
@@ -256,6 +258,11 @@ def ours(a, ws, rank, local):
     phi = torch.empty_like(rho)
     sm = ps.Solver.from_spec(spec, precision=ps.MIXED, use_graph=not a.eager)
     sd = ps.Solver.from_spec(spec, precision=ps.FP64, use_graph=not a.eager)
+    # schedules and tile shapes picked by the library's autotuner on this
+    # input (untimed setup, like the plan itself)
+    tune = None
+    if not a.no_tune:
+        tune = {"mixed": sm.autotune(rho, tol=TOL, phi=phi), "fp64": sd.autotune(rho, tol=TOL, phi=phi)}
     for _ in range(max(3, a.warmup)):
         sm.solve(rho, phi, tol=TOL)
     torch.cuda.synchronize()
@@ -300,6 +307,8 @@ def ours(a, ws, rank, local):
     nk = a.steps + 3
     rhos = [rho * (1.0 + (0.02 * k / nk) * pert) for k in range(nk)]
     sw = ps.Solver.from_spec(spec, precision=ps.MIXED, use_graph=not a.eager)
+    if not a.no_tune:
+        sw.autotune(rho, tol=TOL, phi=phi)   # the mixed handle's choice, from the process cache
     sw.set_warm_start(True)
     for k in range(3):
         sw.solve(rhos[k], phi, tol=TOL)
@@ -339,6 +348,9 @@ def ours(a, ws, rank, local):
         "fp64_gpu": {"value": fp64_value, "unit": "solves/s", "ms_per_step": 1e3 * t64 / k64,
                      "speedup_mixed_vs_fp64": value / fp64_value},
         "mixed_vs_fp64_rel_l2": diff,
+        "schedule": {"mixed": sm.schedule(), "fp64": sd.schedule(),
+                     "autotune": {k: {"ms": v["ms"], "candidates": v["candidates"]} for k, v in tune.items()}
+                     if tune else None},
         "solver": {"iterations_psi": st["iterations_psi"], "iterations_phi": st["iterations_phi"],
                    "rel_residual_psi": st["rel_residual_psi"], "rel_residual_phi": st["rel_residual_phi"],
                    "sum_mode_cycles_psi": sum(st["cycles_psi"]), "sum_mode_cycles_phi": sum(st["cycles_phi"]),
@@ -364,21 +376,25 @@ def ours(a, ws, rank, local):
 
 
 def launches_per_solve(s, st):
-    """Kernel launches of one solve: fixed ones plus the per-iteration body
-    of each multigrid loop (residual, retirement, V-cycle, update)."""
-    d = s.desc
-    nl = s.n_levels
-    nu1, nu2 = d.nu_pre or 2, d.nu_post or 2
-    body = 2 + (nl - 1) * (4 * nu1 + 1 + 1 + 4 * nu2) + 1 + 1
+    """Kernel launches of one solve: fixed ones plus the body of each
+    multigrid loop, run once per residual evaluation (iterations + 1): the
+    residual/retirement kernel; on every level below the fused one nu_pre
+    smoothing cycles of two passes (radial, polar), a restriction, later a
+    prolongation and nu_post cycles; the fused V-cycle; the update."""
+    sc = s.schedule()
+    first = s.fused_level()
+    body = 1 + first * (2 * sc["nu_pre"] + 1 + 1 + 2 * sc["nu_post"]) + 1 + 1
     fixed = 1 + 1 + 3 + 1 + 1 + 1           # fft, init x2, screening/boundary/ghosts, ifft, status
     return fixed + body * (st["iterations_psi"] + 1 + st["iterations_phi"] + 1)
 
 
 # FP32 flops per cell of a fused smoothed level and V-cycle: a line
-# relaxation pass costs 48 per cell (neighbour-line source 10, inverse
-# diagonal 6, two even-odd SOR sweeps 2 x 16); nu_pre + nu_post = 4 cycles of
-# 2 passes give 384; defect restriction and prolongation add 40.
-VCYCLE_FLOPS_PER_CELL = 424
+# relaxation pass costs 16 + 16 n_sor per cell (neighbour-line source 10,
+# inverse diagonal 6, each even-odd SOR sweep 16); nu_pre + nu_post cycles of
+# 2 passes each; defect restriction and prolongation add 40 (424 for the
+# default schedule nu = (2, 2), n_sor = 2).
+def vcycle_flops_per_cell(sched):
+    return (sched["nu_pre"] + sched["nu_post"]) * 2 * (16 + 16 * sched["n_sor"]) + 40
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 
 
@@ -387,7 +403,7 @@ def vcycle_roofline(torch, ps, s, stream):
     mode plane, levels held in shared memory), all modes, timed alone
     through psolve_stage_vcycle with CUDA events on the library's stream.
     Algorithmic work per launch: M x sum over the fused smoothed levels of
-    cells x VCYCLE_FLOPS_PER_CELL FP32 flops, plus the FP64 separable solve
+    cells x vcycle_flops_per_cell(schedule) FP32 flops, plus the FP64 separable solve
     of the coarsest level (8 n_r n_t^2 + 10 n_r n_t per mode)."""
     M = s.n_modes
     lev = s.fused_level()
@@ -413,7 +429,7 @@ def vcycle_roofline(torch, ps, s, stream):
     cr, ct = n_r >> (s.n_levels - 1), n_tz >> (s.n_levels - 1)
     # separable coarsest solve: two FP64 transforms along theta (2 components)
     # and n_theta Thomas solves along r
-    flops = M * (cells * VCYCLE_FLOPS_PER_CELL + 8 * cr * ct * ct + 10 * cr * ct)
+    flops = M * (cells * vcycle_flops_per_cell(s.schedule()) + 8 * cr * ct * ct + 10 * cr * ct)
     ach = flops / dt / 1e12
     return {"kernel": "fused coarse V-cycle k_vsmem (levels %d..%d in shared memory, all %d modes)"
                       % (lev, s.n_levels - 1, M),

@@ -124,6 +124,55 @@ int psolve_solve_batched(psolve_t* hs, const double* const* rhos, double* const*
  * error clears the history. */
 int psolve_set_warm_start(psolve_t h, int enable);
 int psolve_set_stream(psolve_t h, void* cuda_stream);
+
+/* Smoothing schedule and tile shapes of a handle.  Sec. 3.2 leaves the
+ * schedule open (a small number of smoothing cycles per level, typically two
+ * or three, and a few SOR sweeps per line); it changes the convergence rate,
+ * not the converged answer.  The tile shapes of the level-wide smoothing
+ * passes change only how lines are grouped into thread blocks: every tile
+ * shape gives bitwise the same result. */
+typedef struct {
+  int nu_pre, nu_post; /* smoothing cycles before / after coarse correction, 1..8 */
+  int n_sor;           /* SOR sweeps per line relaxation, 1..8                    */
+  int lines_r;         /* radial lines per block: 4 or 8                          */
+  int cols_t;          /* polar columns per block: 8, 16 or 32; 0 = widest that
+                          fits (32, or fewer where n_r or 160 KB of shared memory
+                          per block is the limit)                                 */
+  double ms;           /* psolve_autotune: median solve time of the choice, ms    */
+  int candidates;      /* psolve_autotune: candidates timed (0: from a cache)      */
+  int cached;          /* psolve_autotune: 1 when the choice came from a cache     */
+} psolve_schedule;
+
+/* The handle's current schedule (ms, candidates, cached = 0). */
+int psolve_get_schedule(psolve_t h, psolve_schedule* s);
+/* Install a schedule for later solves (a captured solve is captured again).
+ * PSOLVE_ERR_ARG, with the handle unchanged, when a field is out of range. */
+int psolve_set_schedule(psolve_t h, const psolve_schedule* s);
+
+/* Autotuner: picks the smoothing schedule and tile shapes of this handle by
+ * timing solves of rho (device pointer, layout as psolve_solve) to tolerance
+ * tol on the handle's stream, and installs the fastest.
+ *   Stage 1, schedules: nu_post <= nu_pre <= 3, n_sor <= 3 (18 candidates,
+ *     the handle's current schedule first).  Schedules with more post- than
+ *     pre-smoothing are not tried: they leave a smoother final residual, whose
+ *     error at the same tolerance is larger.
+ *   Stage 2, tile shapes: lines_r in {4, 8} x cols_t in {8, 16, 32} with the
+ *     stage-1 schedule (shapes that reduce to the same launch are timed once).
+ * Each candidate runs one untimed solve (graph capture, caches), then three
+ * timed solves (CUDA events on the handle's stream); its time is their
+ * median.  Candidates whose solve fails are skipped.  Warm start is
+ * suspended while tuning (the history is kept).  phi (device, caller-owned)
+ * receives the last solve's potential.
+ * Choices are cached per process by the key (geometry, sizes, spacing,
+ * extents, precision): a later call with the same key installs the cached
+ * choice without timing.  When the environment variable PSOLVE_TUNE_CACHE
+ * names a file, it is read on a process-cache miss (text, one line per key:
+ * key nu_pre nu_post n_sor lines_r cols_t ms; the last line of a key wins)
+ * and every new choice is appended to it.
+ * out (may be NULL) receives the choice.  Returns PSOLVE_OK, or the error of
+ * the solve with the handle's current schedule, which then stays installed. */
+int psolve_autotune(psolve_t h, const double* rho, double* phi, double tol,
+                    psolve_schedule* out);
 int psolve_get_stats(psolve_t h, psolve_stats* st);
 /* Number of boundary points nb (the side of the DGF table) and modes M. */
 int psolve_get_sizes(psolve_t h, int* n_modes, int* n_boundary, int* n_levels);

@@ -43,6 +43,15 @@ class Stats(ctypes.Structure):
                 ("status", ctypes.POINTER(ctypes.c_int))]
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("n_sor", ctypes.c_int),
+                ("lines_r", ctypes.c_int), ("cols_t", ctypes.c_int), ("ms", ctypes.c_double),
+                ("candidates", ctypes.c_int), ("cached", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def lib():
     """The loaded library; raises when it has not been built."""
     global _lib
@@ -75,6 +84,9 @@ def lib():
             "psolve_stage_screening": (I, [P, P, P]),
             "psolve_stage_boundary": (I, [P, P, P]),
             "psolve_get_dgf": (I, [P, P]),
+            "psolve_get_schedule": (I, [P, ctypes.POINTER(Schedule)]),
+            "psolve_set_schedule": (I, [P, ctypes.POINTER(Schedule)]),
+            "psolve_autotune": (I, [P, P, P, D, ctypes.POINTER(Schedule)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -161,6 +173,28 @@ class Solver:
     def from_spec(cls, spec, **kw):
         return cls(spec["geometry"], spec["n_r"], spec["n_tz"], spec["n_phi"], spec["spacing"],
                    spec["r_in"], spec["r_out"], spec.get("t_min"), spec.get("t_max"), **kw)
+
+    def schedule(self):
+        """The smoothing schedule and tile shapes later solves use."""
+        s = Schedule()
+        check(lib().psolve_get_schedule(self.h, ctypes.byref(s)), "psolve_get_schedule")
+        return s.as_dict()
+
+    def set_schedule(self, nu_pre, nu_post, n_sor, lines_r=8, cols_t=0):
+        s = Schedule(nu_pre=nu_pre, nu_post=nu_post, n_sor=n_sor, lines_r=lines_r, cols_t=cols_t)
+        check(lib().psolve_set_schedule(self.h, ctypes.byref(s)), "psolve_set_schedule")
+
+    def autotune(self, rho, tol=1e-8, phi=None):
+        """Time candidate schedules and tile shapes on rho and keep the
+        fastest (psolve_autotune); returns the choice."""
+        torch = self.torch
+        self._need(rho, self.shape, torch.float64)
+        if phi is None:
+            phi = torch.empty_like(rho)
+        s = Schedule()
+        check(lib().psolve_autotune(self.h, _ptr(rho), _ptr(phi), float(tol), ctypes.byref(s)),
+              "psolve_autotune")
+        return s.as_dict()
 
     def set_warm_start(self, enable=True):
         """Start later solves from the previous solve's Psi and Phi."""

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -486,6 +487,206 @@ extern "C" int psolve_solve_batched(psolve_t* hs, const double* const* rhos, dou
   return first;
 }
 
+// ---- smoothing schedule and autotuner ---------------------------------------
+
+extern "C" int psolve_get_schedule(psolve_t h, psolve_schedule* s) {
+  if (!h || !s) return fail(PSOLVE_ERR_ARG, "null argument");
+  const MGOptions& o = h->mg.opt;
+  *s = psolve_schedule{};
+  s->nu_pre = o.nu1;
+  s->nu_post = o.nu2;
+  s->n_sor = o.n_sor;
+  s->lines_r = o.tiles.lines_r;
+  s->cols_t = o.tiles.cols_t;
+  return PSOLVE_OK;
+}
+
+static bool schedule_ok(const psolve_schedule& s, std::string& why) {
+  if (s.nu_pre < 1 || s.nu_pre > 8 || s.nu_post < 1 || s.nu_post > 8) why = "nu_pre and nu_post must be 1..8";
+  else if (s.n_sor < 1 || s.n_sor > 8) why = "n_sor must be 1..8";
+  else if (s.lines_r != 4 && s.lines_r != 8) why = "lines_r must be 4 or 8";
+  else if (s.cols_t != 0 && s.cols_t != 8 && s.cols_t != 16 && s.cols_t != 32) why = "cols_t must be 0, 8, 16 or 32";
+  else return true;
+  return false;
+}
+
+static void install_schedule(psolve_t h, const psolve_schedule& s) {
+  Tiles t;
+  t.lines_r = s.lines_r;
+  t.cols_t = s.cols_t;
+  h->mg.set_schedule(s.nu_pre, s.nu_post, s.n_sor, t);
+  h->d.nu_pre = s.nu_pre;
+  h->d.nu_post = s.nu_post;
+  h->d.n_sor = s.n_sor;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+}
+
+extern "C" int psolve_set_schedule(psolve_t h, const psolve_schedule* s) {
+  if (!h || !s) return fail(PSOLVE_ERR_ARG, "null argument");
+  std::string why;
+  if (!schedule_ok(*s, why)) return fail(PSOLVE_ERR_ARG, "psolve_set_schedule: " + why);
+  install_schedule(h, *s);
+  return PSOLVE_OK;
+}
+
+static std::mutex g_tune_mu;
+static std::vector<std::pair<std::string, psolve_schedule>> g_tune;   // process cache
+
+static std::string tune_key(const psolve_desc& d) {
+  char b[320];
+  std::snprintf(b, sizeof b, "g%d:nr%d:nt%d:np%d:sp%d:r%.17g:%.17g:t%.17g:%.17g:p%d", d.geometry,
+                d.n_r, d.n_tz, d.n_phi, d.spacing, d.r_in, d.r_out, d.t_min, d.t_max, d.precision);
+  return b;
+}
+
+static const psolve_schedule* tune_find(const std::string& key) {
+  for (auto it = g_tune.rbegin(); it != g_tune.rend(); ++it)
+    if (it->first == key) return &it->second;
+  return nullptr;
+}
+
+// The last valid line of `key` in the cache file, if any.
+static bool tune_file_read(const char* path, const std::string& key, psolve_schedule& out) {
+  FILE* fp = std::fopen(path, "r");
+  if (!fp) return false;
+  bool found = false;
+  char line[512], k[384];
+  while (std::fgets(line, sizeof line, fp)) {
+    psolve_schedule s{};
+    if (std::sscanf(line, "%383s %d %d %d %d %d %lf", k, &s.nu_pre, &s.nu_post, &s.n_sor, &s.lines_r,
+                    &s.cols_t, &s.ms) != 7)
+      continue;
+    std::string why;
+    if (key == k && schedule_ok(s, why)) {
+      out = s;
+      found = true;
+    }
+  }
+  std::fclose(fp);
+  return found;
+}
+
+static void tune_file_append(const char* path, const std::string& key, const psolve_schedule& s) {
+  FILE* fp = std::fopen(path, "a");
+  if (!fp) return;
+  std::fprintf(fp, "%s %d %d %d %d %d %.4f\n", key.c_str(), s.nu_pre, s.nu_post, s.n_sor, s.lines_r,
+               s.cols_t, s.ms);
+  std::fclose(fp);
+}
+
+// Median of three timed solves after one untimed solve; PSOLVE_OK or the
+// failing solve's code.
+static int time_solves(psolve_t h, const double* rho, double* phi, double tol, cudaEvent_t e0,
+                       cudaEvent_t e1, double& ms) {
+  int rc = enqueue_solve(h, rho, phi, tol);
+  if (rc == PSOLVE_OK) rc = finish(h);
+  if (rc != PSOLVE_OK) return rc;
+  float t[3];
+  for (int k = 0; k < 3; ++k) {
+    cudaEventRecord(e0, h->st);
+    rc = enqueue_solve(h, rho, phi, tol);
+    cudaEventRecord(e1, h->st);
+    if (rc == PSOLVE_OK) rc = finish(h);
+    if (rc != PSOLVE_OK) return rc;
+    if (cudaEventElapsedTime(&t[k], e0, e1) != cudaSuccess) return fail(PSOLVE_ERR_CUDA, "autotune timing");
+  }
+  const float lo = std::fmin(t[0], std::fmin(t[1], t[2])), hi = std::fmax(t[0], std::fmax(t[1], t[2]));
+  ms = double(t[0] + t[1] + t[2] - lo - hi);
+  return PSOLVE_OK;
+}
+
+extern "C" int psolve_autotune(psolve_t h, const double* rho, double* phi, double tol,
+                               psolve_schedule* out) {
+  if (!h || !rho || !phi) return fail(PSOLVE_ERR_ARG, "null argument");
+  if (rho == phi) return fail(PSOLVE_ERR_ARG, "phi must not alias rho");
+  if (tol <= 0) tol = 1e-8;
+  const std::string key = tune_key(h->d);
+  const char* path = std::getenv("PSOLVE_TUNE_CACHE");
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  psolve_schedule best{};
+  const psolve_schedule* hit = tune_find(key);
+  if (hit || (path && *path && tune_file_read(path, key, best))) {
+    if (hit) best = *hit;
+    else g_tune.emplace_back(key, best);
+    install_schedule(h, best);
+    best.candidates = 0;
+    best.cached = 1;
+    if (out) *out = best;
+    return PSOLVE_OK;
+  }
+  psolve_schedule cur{};
+  psolve_get_schedule(h, &cur);
+  const int warm = h->warm;
+  h->warm = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // stage 1: schedules, the current one first
+  std::vector<psolve_schedule> cand{cur};
+  for (int a = 1; a <= 3; ++a)
+    for (int b = 1; b <= a; ++b)
+      for (int c = 1; c <= 3; ++c) {
+        psolve_schedule s = cur;
+        s.nu_pre = a;
+        s.nu_post = b;
+        s.n_sor = c;
+        if (a != cur.nu_pre || b != cur.nu_post || c != cur.n_sor) cand.push_back(s);
+      }
+  int n_timed = 0, rc0 = PSOLVE_OK;
+  best = cur;
+  best.ms = -1;
+  for (size_t k = 0; k < cand.size(); ++k) {
+    double ms = 0;
+    install_schedule(h, cand[k]);
+    const int rc = time_solves(h, rho, phi, tol, e0, e1, ms);
+    if (k == 0) rc0 = rc;
+    if (rc != PSOLVE_OK) {
+      if (k == 0) break;   // the current schedule fails: keep it and report
+      continue;
+    }
+    ++n_timed;
+    if (best.ms < 0 || ms < best.ms) { best = cand[k]; best.ms = ms; }
+  }
+  if (rc0 == PSOLVE_OK) {
+    // stage 2: tile shapes with the chosen schedule (distinct launches only)
+    const size_t vb = h->d.precision ? 8 : 16;
+    std::vector<int> widths;
+    for (int want : {8, 16, 32}) {
+      const int w = smooth_tile_cols(h->d.n_r, h->d.n_tz, vb, want);
+      bool seen = false;
+      for (int x : widths) seen = seen || x == w;
+      if (!seen) widths.push_back(w);
+    }
+    const int cur_w = smooth_tile_cols(h->d.n_r, h->d.n_tz, vb, best.cols_t);
+    for (int lines : {8, 4})
+      for (int w : widths) {
+        if (lines == best.lines_r && w == cur_w) continue;   // timed in stage 1
+        psolve_schedule s = best;
+        s.lines_r = lines;
+        s.cols_t = w;
+        double ms = 0;
+        install_schedule(h, s);
+        if (time_solves(h, rho, phi, tol, e0, e1, ms) != PSOLVE_OK) continue;
+        ++n_timed;
+        if (ms < best.ms) { best = s; best.ms = ms; }
+      }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->warm = warm;
+  if (rc0 != PSOLVE_OK) {
+    install_schedule(h, cur);
+    return rc0;
+  }
+  install_schedule(h, best);
+  best.candidates = n_timed;
+  best.cached = 0;
+  g_tune.emplace_back(key, best);
+  if (path && *path) tune_file_append(path, key, best);
+  if (out) *out = best;
+  return PSOLVE_OK;
+}
+
 extern "C" int psolve_get_stats(psolve_t h, psolve_stats* s) {
   if (!h || !s) return fail(PSOLVE_ERR_ARG, "null argument");
   cudaStreamSynchronize(h->st);
@@ -733,11 +934,11 @@ extern "C" int psolve_stage_smooth_static(psolve_t h, int level, int precision, 
   if (precision)
     launch_smooth<float>(L, B, static_cast<float2*>(e), static_cast<const float2*>(f),
                          reinterpret_cast<float2*>(base + list_bytes), cycles, h->mg.opt.n_sor,
-                         false, nullptr, nullptr, h->st);
+                         false, nullptr, nullptr, h->mg.opt.tiles, h->st);
   else
     launch_smooth<double>(L, B, static_cast<double2*>(e), static_cast<const double2*>(f),
                           reinterpret_cast<double2*>(base + list_bytes), cycles, h->mg.opt.n_sor,
-                          false, nullptr, nullptr, h->st);
+                          false, nullptr, nullptr, h->mg.opt.tiles, h->st);
   return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("smooth_static") ? PSOLVE_OK
                                                                                    : PSOLVE_ERR_CUDA;
 }

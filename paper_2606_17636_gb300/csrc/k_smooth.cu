@@ -7,10 +7,13 @@
 // giving exactly the values the two-launch ordering produces.  A smoothing
 // cycle is a radial pass e -> tmp followed by a polar pass tmp -> e.
 //
-// Re-tiling: grids are sized for all planes with the widest tiles; when only
-// a few planes are active the blocks are spread over them with narrower
-// tiles (up to 4x more blocks per plane), so a lone slow mode still uses
-// many SMs.  The first post-smoothing radial pass of a level can add the
+// Tile shapes: a radial block owns Wmax = 8 or 4 lines (one warp per line),
+// a polar block TWmax columns (8, 16 or 32; at most 160 KB of staged tile);
+// both are options the autotuner may change.  Re-tiling: grids are sized for
+// all planes with the widest tiles; when only a few planes are active the
+// blocks are spread over them with narrower tiles (up to 4x more blocks per
+// plane, at least two lines or columns per block so that a block's first
+// line or column keeps colour 0), so a lone slow mode still uses many SMs.  The first post-smoothing radial pass of a level can add the
 // bilinear coarse correction to every value it loads (prolongation fused).
 #include <cstdio>
 
@@ -18,11 +21,12 @@
 
 namespace ps {
 
-// Blocks per plane for the active count: base * mult, mult in {1, 2, 4}.
-__device__ __forceinline__ int spread(int base, int nact) {
+// Blocks per plane for the active count: base * mult, mult in {1, 2, 4},
+// mult <= cap.
+__device__ __forceinline__ int spread(int base, int nact, int cap) {
   const int G = int(gridDim.x * gridDim.y);
   int mult = 1;
-  while (mult < 4 && nact * base * mult * 2 <= G) mult *= 2;
+  while (mult < 4 && mult < cap && nact * base * mult * 2 <= G) mult *= 2;
   return mult;
 }
 
@@ -31,7 +35,8 @@ struct Corr {          // fused prolongation source (ec == nullptr: none)
   const void* ec;
 };
 
-// Radial pass, both colours: a block owns W lines [j0, j0+W), W = 8 / mult.
+// Radial pass, both colours: a block of 32 Wmax threads owns W lines
+// [j0, j0+W), W = Wmax / mult.
 // Every line it reads is first staged in shared memory with asynchronous
 // copies (all loads in flight at once): e lines j0-1 .. j0+W+1 (zero beyond
 // the plane, or all zero for a zero initial guess) and f lines j0 .. j0+W.
@@ -55,16 +60,16 @@ template <typename T, int CPL>
 __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_t<T>* __restrict__ ein,
                                                 vec2_t<T>* __restrict__ eout,
                                                 const vec2_t<T>* __restrict__ f, int zero_init,
-                                                int n_sor, Corr corr) {
+                                                int n_sor, Corr corr, int Wmax) {
   typedef vec2_t<T> V;
   extern __shared__ __align__(16) unsigned char sraw[];
   const int nact = *B.nact;
-  const int mult = spread(int(gridDim.x), nact);
+  const int mult = spread(int(gridDim.x), nact, Wmax / 2);
   const int per = int(gridDim.x) * mult;
   const int b = int(blockIdx.y * gridDim.x + blockIdx.x);
   const int k = b / per;
   if (k >= nact) return;
-  const int W = 8 / mult;
+  const int W = Wmax / mult;
   const int j0 = (b - k * per) * W;
   const int p = B.act[k];
   const int slot = B.slot ? B.slot[p] : p;
@@ -124,8 +129,8 @@ __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_
       relax_r<T, CPL>(L, rt, tt, s2, om[j], j, g, un, us, n_sor, ev);
       st_line<V, CPL>(eout + base + size_t(j) * nr, ev, lane, nr);
     }
-  } else if (warp >= 4 && warp < 4 + W / 2) {   // store the block's colour-0 lines
-    const int q = warp - 4, j = j0 + 2 * q;
+  } else if (warp < W) {          // store the block's colour-0 lines
+    const int q = warp - W / 2, j = j0 + 2 * q;
     if (j < nt) {
       V ev[CPL];
       ld_line<V, CPL>(ev, s0 + q * nr, lane, nr);
@@ -152,7 +157,7 @@ __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_
   typedef vec2_t<T> V;
   extern __shared__ __align__(16) unsigned char sraw[];
   const int nact = *B.nact;
-  const int mult = TWmax >= 8 ? spread(int(gridDim.x), nact) : 1;
+  const int mult = spread(int(gridDim.x), nact, TWmax / 2);
   const int per = int(gridDim.x) * mult;
   const int b = int(blockIdx.y * gridDim.x + blockIdx.x);
   const int kp = b / per;
@@ -212,29 +217,36 @@ __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_
     eout[base + size_t(w.j) * nr + i0 + w.c] = se[tslot<CPL>(w.j, w.c + 1, SW)];
 }
 
-static int tile_w(int nr, int nt, size_t vb) {
-  int tw = nr < 32 ? nr : 32;
+// Polar tile width: the requested width (0: 32), at most n_r, halved until
+// the staged tile (e and f, n_t x (TW + 5) each) fits in 160 KB.
+static int tile_w(int nr, int nt, size_t vb, int want) {
+  int tw = want > 0 ? want : 32;
+  if (tw > nr) tw = nr;
   while (tw > 2 && size_t(nt) * 2 * (tw + 5) * vb > 160 * 1024) tw /= 2;
   return tw;
 }
 
+int smooth_tile_cols(int nr, int nt, size_t vb, int want) { return tile_w(nr, nt, vb, want); }
+
 template <typename T, int CPL>
 static void rpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                   const vec2_t<T>* f, bool zi, int n_sor, const Corr& corr, cudaStream_t st) {
-  const size_t sm = size_t(11 + 9 + 5) * L.nr * sizeof(vec2_t<T>);   // W = 8: e, f, colour-0 lines
+                   const vec2_t<T>* f, bool zi, int n_sor, const Corr& corr, int Wmax,
+                   cudaStream_t st) {
+  // e lines (W + 3), f lines (W + 1) and relaxed colour-0 lines (W / 2 + 1)
+  const size_t sm = size_t(Wmax + 3 + Wmax + 1 + Wmax / 2 + 1) * L.nr * sizeof(vec2_t<T>);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_rpass2<T, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  dim3 grid((L.nt + 7) / 8, B.max_planes);
-  k_rpass2<T, CPL><<<grid, 256, sm, st>>>(L, B, ein, eout, f, zi ? 1 : 0, n_sor, corr);
+  dim3 grid((L.nt + Wmax - 1) / Wmax, B.max_planes);
+  k_rpass2<T, CPL><<<grid, 32 * Wmax, sm, st>>>(L, B, ein, eout, f, zi ? 1 : 0, n_sor, corr, Wmax);
 }
 
 template <typename T, int CPL>
 static void tpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                   const vec2_t<T>* f, int n_sor, cudaStream_t st) {
-  const int TW = tile_w(L.nr, L.nt, sizeof(vec2_t<T>));
+                   const vec2_t<T>* f, int n_sor, int cols, cudaStream_t st) {
+  const int TW = tile_w(L.nr, L.nt, sizeof(vec2_t<T>), cols);
   const size_t sm = size_t(L.nt) * 2 * (TW + 5) * sizeof(vec2_t<T>);
   static bool attr = false;
   if (!attr) {
@@ -247,28 +259,29 @@ static void tpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2
 
 template <typename T>
 static void rpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                       const vec2_t<T>* f, bool zi, int n_sor, const Corr& corr, cudaStream_t st) {
+                       const vec2_t<T>* f, bool zi, int n_sor, const Corr& corr, int Wmax,
+                       cudaStream_t st) {
   switch (L.nr <= 32 ? 1 : L.nr / 32) {
-    case 1: rpass2<T, 1>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
-    case 2: rpass2<T, 2>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
-    case 4: rpass2<T, 4>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
-    case 8: rpass2<T, 8>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
-    case 16: rpass2<T, 16>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
-    case 32: rpass2<T, 32>(L, B, ein, eout, f, zi, n_sor, corr, st); break;
+    case 1: rpass2<T, 1>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
+    case 2: rpass2<T, 2>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
+    case 4: rpass2<T, 4>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
+    case 8: rpass2<T, 8>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
+    case 16: rpass2<T, 16>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
+    case 32: rpass2<T, 32>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
     default: std::fprintf(stderr, "psolve: radial size %d unsupported\n", L.nr);
   }
 }
 
 template <typename T>
 static void tpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                       const vec2_t<T>* f, int n_sor, cudaStream_t st) {
+                       const vec2_t<T>* f, int n_sor, int cols, cudaStream_t st) {
   switch (L.nt <= 32 ? 1 : L.nt / 32) {
-    case 1: tpass2<T, 1>(L, B, ein, eout, f, n_sor, st); break;
-    case 2: tpass2<T, 2>(L, B, ein, eout, f, n_sor, st); break;
-    case 4: tpass2<T, 4>(L, B, ein, eout, f, n_sor, st); break;
-    case 8: tpass2<T, 8>(L, B, ein, eout, f, n_sor, st); break;
-    case 16: tpass2<T, 16>(L, B, ein, eout, f, n_sor, st); break;
-    case 32: tpass2<T, 32>(L, B, ein, eout, f, n_sor, st); break;
+    case 1: tpass2<T, 1>(L, B, ein, eout, f, n_sor, cols, st); break;
+    case 2: tpass2<T, 2>(L, B, ein, eout, f, n_sor, cols, st); break;
+    case 4: tpass2<T, 4>(L, B, ein, eout, f, n_sor, cols, st); break;
+    case 8: tpass2<T, 8>(L, B, ein, eout, f, n_sor, cols, st); break;
+    case 16: tpass2<T, 16>(L, B, ein, eout, f, n_sor, cols, st); break;
+    case 32: tpass2<T, 32>(L, B, ein, eout, f, n_sor, cols, st); break;
     default: std::fprintf(stderr, "psolve: polar size %d unsupported\n", L.nt);
   }
 }
@@ -276,22 +289,24 @@ static void tpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, 
 template <typename T>
 void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
                    vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, const LevelDev* C,
-                   const vec2_t<T>* ec, cudaStream_t st) {
+                   const vec2_t<T>* ec, Tiles tiles, cudaStream_t st) {
+  const int Wmax = tiles.lines_r == 4 ? 4 : 8;
   for (int c = 0; c < cycles; ++c) {
     Corr corr{};
     if (c == 0 && ec) {
       corr.C = *C;
       corr.ec = ec;
     }
-    rpass2_any<T>(L, B, e, tmp, f, zero_init && c == 0, n_sor, corr, st);
-    tpass2_any<T>(L, B, tmp, e, f, n_sor, st);
+    rpass2_any<T>(L, B, e, tmp, f, zero_init && c == 0, n_sor, corr, Wmax, st);
+    tpass2_any<T>(L, B, tmp, e, f, n_sor, tiles.cols_t, st);
   }
 }
 
 template void launch_smooth<float>(const LevelDev&, const Batch&, float2*, const float2*, float2*,
-                                   int, int, bool, const LevelDev*, const float2*, cudaStream_t);
+                                   int, int, bool, const LevelDev*, const float2*, Tiles,
+                                   cudaStream_t);
 template void launch_smooth<double>(const LevelDev&, const Batch&, double2*, const double2*,
-                                    double2*, int, int, bool, const LevelDev*, const double2*,
+                                    double2*, int, int, bool, const LevelDev*, const double2*, Tiles,
                                     cudaStream_t);
 
 }  // namespace ps

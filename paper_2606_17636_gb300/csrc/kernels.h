@@ -47,6 +47,17 @@ void launch_fft_inverse(const double2* fh, double* phi, int nr, int nt, int N,
                         const double2* tw, cudaStream_t st);
 
 // ---- multigrid (k_mg.cu), T = float or double ---------------------------------
+// Tile shapes of the level-wide smoothing passes: radial lines per block
+// (8 or 4) and polar columns per block (8, 16 or 32; 0 = the widest that
+// fits).  They change only how lines are grouped into blocks: every tile
+// shape gives bitwise the same result.
+struct Tiles {
+  int lines_r = 8;
+  int cols_t = 0;
+};
+// Polar columns per block that the polar pass uses for a level of nr x nt
+// cells of vb bytes each when `want` are requested (0: the widest).
+int smooth_tile_cols(int nr, int nt, size_t vb, int want);
 // `cycles` alternating-line smoothing cycles (k_smooth.cu); tmp is a
 // scratch buffer of the level's size (ping-pong between the two passes).
 // When ec != nullptr the first radial pass adds the bilinear correction
@@ -54,7 +65,7 @@ void launch_fft_inverse(const double2* fh, double* phi, int nr, int nt, int N,
 template <typename T>
 void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
                    vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, const LevelDev* C,
-                   const vec2_t<T>* ec, cudaStream_t st);
+                   const vec2_t<T>* ec, Tiles tiles, cudaStream_t st);
 
 // Lower part of a V-cycle in shared memory, one block per plane (k_vsmem.cu).
 struct VSmemArgs {

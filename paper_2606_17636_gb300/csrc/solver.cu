@@ -246,10 +246,10 @@ void MGSolver::smooth(int l, void* ee, const void* ff, int cycles, bool zi, cuda
   const LevelDev* C = ec ? &lv[l + 1] : nullptr;
   if (opt.precision)
     launch_smooth<float>(lv[l], batch, (float2*)ee, (const float2*)ff, (float2*)tmp, cycles,
-                         opt.n_sor, zi, C, (const float2*)ec, st);
+                         opt.n_sor, zi, C, (const float2*)ec, opt.tiles, st);
   else
     launch_smooth<double>(lv[l], batch, (double2*)ee, (const double2*)ff, (double2*)tmp, cycles,
-                          opt.n_sor, zi, C, (const double2*)ec, st);
+                          opt.n_sor, zi, C, (const double2*)ec, opt.tiles, st);
 }
 void MGSolver::restrict_(int l, const void* ee, const void* ff, void* fc, cudaStream_t st) {
   if (opt.precision)
@@ -302,6 +302,13 @@ void MGSolver::vcycle(cudaStream_t st) {
     prolong(l, e[l], e[l + 1], st);
     if (opt.nu2 > 0) smooth(l, e[l], f[l], opt.nu2, false, st);
   }
+}
+
+void MGSolver::set_schedule(int nu1, int nu2, int n_sor, Tiles tiles) {
+  opt.nu1 = vs.nu1 = nu1;
+  opt.nu2 = vs.nu2 = nu2;
+  opt.n_sor = vs.n_sor = n_sor;
+  opt.tiles = tiles;
 }
 
 void MGSolver::init_loop(cudaStream_t st) { launch_init_active(d_act, d_nact, max_planes, S, st); }

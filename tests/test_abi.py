@@ -62,3 +62,41 @@ def test_static_entry_point_rejects_bad_arguments_without_a_gpu(libpath):
     L = ps.lib()
     assert L.psolve_stage_smooth_static(None, 0, 0, None, None, 1) == ps.ERR_ARG
     assert "null" in ps.last_error()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of psolve_desc, psolve_stats and psolve_schedule
+    have the C layout (sizes and field offsets, from gcc on the header)."""
+    import shutil
+    import subprocess
+    import paper_2606_17636_gb300 as ps
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    mirrors = {"psolve_desc": ps.Desc, "psolve_stats": ps.Stats, "psolve_schedule": ps.Schedule}
+    lines = ['#include <stdio.h>', '#include "psolve.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for cname, py in mirrors.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
+
+
+def test_schedule_entry_points_reject_null_arguments(libpath):
+    import paper_2606_17636_gb300 as ps
+    L = ps.lib()
+    s = ps.Schedule(nu_pre=2, nu_post=2, n_sor=2, lines_r=8)
+    assert L.psolve_set_schedule(None, ctypes.byref(s)) == ps.ERR_ARG
+    assert L.psolve_get_schedule(None, ctypes.byref(s)) == ps.ERR_ARG
+    assert L.psolve_autotune(None, None, None, 1e-8, None) == ps.ERR_ARG
+    assert "null" in ps.last_error()
