@@ -276,9 +276,13 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     for (int k = threadIdx.x; k < n; k += blockDim.x) sm[a.off_e[l] + k] = V{0, 0};
   }
   __syncthreads();
+  // Each phase works on register copies of the level descriptors: read
+  // through sL, every shared-memory store of a phase could alias them and
+  // force the descriptor fields to be loaded again.
   for (int l = 0; l < K - 1; ++l) {
-    s_smooth<T>(sL[l], sm + a.off_e[l], sm + a.off_f[l], s2, a.nu1, a.n_sor);
-    s_restrict<T>(sL[l], sL[l + 1], sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
+    const LevelDev Lf = sL[l], Lq = sL[l + 1];
+    s_smooth<T>(Lf, sm + a.off_e[l], sm + a.off_f[l], s2, a.nu1, a.n_sor);
+    s_restrict<T>(Lf, Lq, sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
   }
   if (a.sep_stride > 0) {
     // coarsest level, exact FP64 separable solve: L_m = L_r (x) I + D_r (x) L_t
@@ -296,31 +300,48 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     const double* Vi = Vm + nt * nt;
     const double* invd = Vi + nt * nt;
     const double* cp = invd + nt * nr;
-    const double* low = cp + nt * nr;
-    for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
-      const int c = q / nc, r = q - c * nc, k = r / nr, i = r - k * nr;
-      double acc = 0.0;
-      for (int j = 0; j < nt; ++j) {
-        const V v = fc[vslot(Lc, j, i)];
-        acc += Vi[k * nt + j] * double(c ? v.y : v.x);
-      }
-      z[q] = acc;
+    const double* lid = cp + nt * nr;
+    // f in FP64, converted once (each value feeds nt products; the
+    // conversion itself runs on the FP64 pipe)
+    double* fd = z + 2 * nc;   // [2][nt][nr]
+    for (RowWalk w(threadIdx.x, blockDim.x, nr); w.j < nt; w.next()) {
+      const V v = fc[vslot(Lc, w.j, w.c)];
+      fd[w.j * nr + w.c] = double(v.x);
+      fd[nc + w.j * nr + w.c] = double(v.y);
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < 2 * nt; q += blockDim.x) {
+    // z = (1/pivot) .* ((V^-1 (x) I) f): the transform with the forward
+    // sweep's first scaling folded in
+    for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
+      const int c = q / nc, r = q - c * nc, k = r / nr, i = r - k * nr;
+      const double* fcol = fd + c * nc + i;
+      double acc = 0.0;
+      for (int j = 0; j < nt; ++j) acc += Vi[k * nt + j] * fcol[j * nr];
+      z[q] = acc * invd[k * nr + i];
+    }
+    __syncthreads();
+    // Thomas per (component, eigenvalue), one FMA per step each way:
+    // dp_i = z_i - lid_i dp_{i-1}, then x_i = dp_i - cp_i x_{i+1}.  The 2 nt
+    // independent systems run on the block's first four warps, eight lanes
+    // each (one warp per scheduler: the FP64 pipe is narrow).
+    for (int q = ((threadIdx.x >> 5) < 4 && (threadIdx.x & 31) < 8)
+                     ? (threadIdx.x >> 5) * 8 + (threadIdx.x & 31)
+                     : 2 * nt;
+         q < 2 * nt; q += 32) {
       const int c = q / nt, k = q - c * nt;
-      double* zz = z + c * nc + k * nr;
-      const double* id = invd + k * nr;
-      const double* cc = cp + k * nr;
-      double dp = zz[0] * id[0];
-      zz[0] = dp;
+      double* __restrict__ zz = z + c * nc + k * nr;
+      const double* __restrict__ lk = lid + k * nr;
+      const double* __restrict__ ck = cp + k * nr;
+      double dp = zz[0];
+#pragma unroll 4
       for (int i = 1; i < nr; ++i) {
-        dp = (zz[i] - low[i] * dp) * id[i];
+        dp = fma(-lk[i], dp, zz[i]);
         zz[i] = dp;
       }
-      double xv = zz[nr - 1];
+      double xv = dp;
+#pragma unroll 4
       for (int i = nr - 2; i >= 0; --i) {
-        xv = zz[i] - cc[i] * xv;
+        xv = fma(-ck[i], xv, zz[i]);
         zz[i] = xv;
       }
     }
@@ -423,8 +444,9 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     __syncthreads();
   }
   for (int l = K - 2; l >= 0; --l) {
-    s_prolong<T>(sL[l], sL[l + 1], sm + a.off_e[l], sm + a.off_e[l + 1], m);
-    s_smooth<T>(sL[l], sm + a.off_e[l], sm + a.off_f[l], s2, a.nu2, a.n_sor);
+    const LevelDev Lf = sL[l], Lq = sL[l + 1];
+    s_prolong<T>(Lf, Lq, sm + a.off_e[l], sm + a.off_e[l + 1], m);
+    s_smooth<T>(Lf, sm + a.off_e[l], sm + a.off_f[l], s2, a.nu2, a.n_sor);
   }
   {
     RowWalk w(threadIdx.x, blockDim.x, nr0);

@@ -37,9 +37,12 @@ template <> __device__ __forceinline__ float s2_<float>(const Batch& B, int slot
 
 template <typename V> __device__ __forceinline__ V z2() { V v; v.x = 0; v.y = 0; return v; }
 
-// Correctly rounded reciprocal (the same value as 1 / x).
-__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+// Inverse diagonal of a line relaxation.  FP32 (the smoother of the FP32
+// V-cycle, a preconditioner inside FP64 refinement): the hardware
+// approximation __fdividef (within 2 ulp for the diagonal's range); FP64:
+// correctly rounded, the same value as 1 / x.
+__device__ __forceinline__ float rcp_diag(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_diag(double x) { return __drcp_rn(x); }
 
 template <typename V> __device__ __forceinline__ V shup(V v) {
   v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
@@ -276,7 +279,7 @@ __device__ __forceinline__ void relax_r(const LevelDev& L, const RLineTabs<T, CP
   for (int c = 0; c < CPL; ++c) {
     g[c].x = g[c].x - a.P[c] * (aN * un[c].x + aS * us[c].x);
     g[c].y = g[c].y - a.P[c] * (aN * un[c].y + aS * us[c].y);
-    id[c] = on ? rcp_rn(a.dr[c] + a.P[c] * dtj - s2 * a.q[c] * Tj) : T(0);
+    id[c] = on ? rcp_diag(a.dr[c] + a.P[c] * dtj - s2 * a.q[c] * Tj) : T(0);
   }
   sor_line<T, CPL>(ev, g, a.up, a.dn, id, w, nr, n_sor);
 }
@@ -305,7 +308,7 @@ __device__ __forceinline__ void relax_r(const LevelDev& L, const T* rt, const T*
     ld_tab<T, CPL>(dr, rt + RT_DR * NR, lane, nr);
     ld_tab<T, CPL>(q, rt + RT_Q * NR, lane, nr);
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) id[c] = on ? rcp_rn(dr[c] + P[c] * dtj - s2 * q[c] * Tj) : T(0);
+    for (int c = 0; c < CPL; ++c) id[c] = on ? rcp_diag(dr[c] + P[c] * dtj - s2 * q[c] * Tj) : T(0);
   }
   ld_tab<T, CPL>(up, rt + RT_AE * NR, lane, nr);
   ld_tab<T, CPL>(dn, rt + RT_AW * NR, lane, nr);
@@ -330,7 +333,7 @@ __device__ __forceinline__ void relax_t(const LevelDev& L, const T* rt, const TL
   for (int c = 0; c < CPL; ++c) {
     g[c].x = g[c].x - aE * ue[c].x - aW * uw[c].x;
     g[c].y = g[c].y - aE * ue[c].y - aW * uw[c].y;
-    id[c] = on ? rcp_rn(dr + P * a.dt[c] - s2 * Qi * a.tj[c]) : T(0);
+    id[c] = on ? rcp_diag(dr + P * a.dt[c] - s2 * Qi * a.tj[c]) : T(0);
     up[c] = P * a.an[c];
     dn[c] = P * a.as[c];
   }
@@ -358,7 +361,7 @@ __device__ __forceinline__ void relax_t(const LevelDev& L, const T* rt, const T*
     ld_tab<T, CPL>(dt, tt + TT_DT * NT, lane, nt);
     ld_tab<T, CPL>(tj, tt + TT_T * NT, lane, nt);
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) id[c] = on ? rcp_rn(dr + P * dt[c] - s2 * Qi * tj[c]) : T(0);
+    for (int c = 0; c < CPL; ++c) id[c] = on ? rcp_diag(dr + P * dt[c] - s2 * Qi * tj[c]) : T(0);
   }
   ld_tab<T, CPL>(up, tt + TT_AN * NT, lane, nt);
   ld_tab<T, CPL>(dn, tt + TT_AS * NT, lane, nt);

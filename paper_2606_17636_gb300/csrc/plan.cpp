@@ -233,7 +233,8 @@ static bool separable_factors(const PlaneGeo& g, int m, double* out) {
   double* Vi = V + size_t(nt) * nt;
   double* invd = Vi + size_t(nt) * nt;
   double* cp = invd + size_t(nt) * nr;
-  double* low = cp + size_t(nt) * nr;
+  double* lid = cp + size_t(nt) * nr;
+  std::vector<double> low(nr);
   for (int j = 0; j < nt; ++j)
     for (int k = 0; k < nt; ++k) {
       V[size_t(j) * nt + k] = U[size_t(j) * nt + k] / std::sqrt(w[j + 1]);
@@ -249,22 +250,23 @@ static bool separable_factors(const PlaneGeo& g, int m, double* out) {
       invd[size_t(k) * nr + i - 1] = 1.0 / den;
       cprev = up / den;
       cp[size_t(k) * nr + i - 1] = cprev;
+      lid[size_t(k) * nr + i - 1] = low[i - 1] / den;
     }
   }
   // residual check of the factors on a fixed test vector, stencil apply
   std::vector<double> b(size_t(nr) * nt), z(size_t(nr) * nt), x(size_t(nr) * nt);
   for (size_t q = 0; q < b.size(); ++q) b[q] = std::sin(0.37 * double(q) + 1.0);
+  // the kernel's form: z' = invd .* (V^-1 f), then dp_i = z'_i - lid_i dp_{i-1}
   for (int k = 0; k < nt; ++k)
     for (int i = 0; i < nr; ++i) {
       double a = 0.0;
       for (int j = 0; j < nt; ++j) a += Vi[size_t(k) * nt + j] * b[size_t(j) * nr + i];
-      z[size_t(k) * nr + i] = a;
+      z[size_t(k) * nr + i] = a * invd[size_t(k) * nr + i];
     }
   for (int k = 0; k < nt; ++k) {
     double* zz = z.data() + size_t(k) * nr;
-    double dp = zz[0] * invd[size_t(k) * nr];
-    zz[0] = dp;
-    for (int i = 1; i < nr; ++i) { dp = (zz[i] - low[i] * dp) * invd[size_t(k) * nr + i]; zz[i] = dp; }
+    double dp = zz[0];
+    for (int i = 1; i < nr; ++i) { dp = zz[i] - lid[size_t(k) * nr + i] * dp; zz[i] = dp; }
     double xv = zz[nr - 1];
     for (int i = nr - 2; i >= 0; --i) { xv = zz[i] - cp[size_t(k) * nr + i] * xv; zz[i] = xv; }
   }
@@ -403,7 +405,7 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
   const int nr = C.g.r.n, nt = C.g.t.n, nc = nr * nt;
   H.nc = nc;
   if (nt <= 64) {
-    H.sep_stride = (2 * nt * nt + 2 * nt * nr + nr + 1) / 2 * 2;
+    H.sep_stride = (2 * nt * nt + 3 * nt * nr + 1) / 2 * 2;
     H.coarse_sep.assign(size_t(M) * H.sep_stride, 0.0);
     bool ok = true;
     for (int k = 0; k < M && ok; ++k)

@@ -81,8 +81,9 @@ struct Hierarchy {
   // L_t (spherical, P = Q) or in L_r (cylindrical, P = T = 1).  Per slot:
   // V [nt][nt] and V^-1 [nt][nt] (L_t = V diag(lambda) V^-1), then per
   // eigenvalue k the Thomas factors of L_r + lambda_k D_r: 1/pivot [nt][nr],
-  // upper/pivot [nt][nr], then the radial lower couplings [nr]; sep_stride
-  // doubles per slot.
+  // upper/pivot [nt][nr] and lower/pivot [nt][nr] (the forward sweep is then
+  // one FMA per cell: dp_i = z_i/pivot_i - (lower_i/pivot_i) dp_{i-1});
+  // sep_stride doubles per slot.
   std::vector<double> coarse_sep;
   int sep_stride = 0;
 };
