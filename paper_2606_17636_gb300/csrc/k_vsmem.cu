@@ -296,27 +296,43 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     double* z = reinterpret_cast<double*>(vraw + a.dbl_off);   // [2][nt][nr]
     const double* Fq = a.blk_smem ? reinterpret_cast<const double*>(vraw + a.blk_off)
                                   : a.sep + size_t(slot) * fac_stride;
-    const double* Vm = Fq;
-    const double* Vi = Vm + nt * nt;
-    const double* invd = Vi + nt * nt;
+    // mirror-symmetric layout (sep_sym): V rows j < h = nt/2, V^-1 columns
+    // j < h; eigenvectors k < h even, k >= h odd
+    const int h = nt / 2, vr = a.sep_sym ? h : nt;
+    const double* Vm = Fq;                  // [vr][nt]
+    const double* Vi = Vm + vr * nt;        // [nt][vr]
+    const double* invd = Vi + nt * vr;
     const double* cp = invd + nt * nr;
     const double* lid = cp + nt * nr;
-    // f in FP64, converted once (each value feeds nt products; the
-    // conversion itself runs on the FP64 pipe)
+    // f in FP64, converted once (each value feeds several products; the
+    // conversion itself runs on the FP64 pipe); mirror-symmetric: rows j < h
+    // hold f_j + f_{nt-1-j} and rows h + j hold f_j - f_{nt-1-j}
     double* fd = z + 2 * nc;   // [2][nt][nr]
-    for (RowWalk w(threadIdx.x, blockDim.x, nr); w.j < nt; w.next()) {
-      const V v = fc[vslot(Lc, w.j, w.c)];
-      fd[w.j * nr + w.c] = double(v.x);
-      fd[nc + w.j * nr + w.c] = double(v.y);
+    if (a.sep_sym) {
+      for (RowWalk w(threadIdx.x, blockDim.x, nr); w.j < h; w.next()) {
+        const V u = fc[vslot(Lc, w.j, w.c)], v = fc[vslot(Lc, nt - 1 - w.j, w.c)];
+        const double ux = u.x, uy = u.y, vx = v.x, vy = v.y;
+        fd[w.j * nr + w.c] = ux + vx;
+        fd[(h + w.j) * nr + w.c] = ux - vx;
+        fd[nc + w.j * nr + w.c] = uy + vy;
+        fd[nc + (h + w.j) * nr + w.c] = uy - vy;
+      }
+    } else {
+      for (RowWalk w(threadIdx.x, blockDim.x, nr); w.j < nt; w.next()) {
+        const V v = fc[vslot(Lc, w.j, w.c)];
+        fd[w.j * nr + w.c] = double(v.x);
+        fd[nc + w.j * nr + w.c] = double(v.y);
+      }
     }
     __syncthreads();
     // z = (1/pivot) .* ((V^-1 (x) I) f): the transform with the forward
-    // sweep's first scaling folded in
+    // sweep's first scaling folded in (mirror-symmetric: even eigenvectors
+    // take the sums, odd ones the differences, over j < h)
     for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
       const int c = q / nc, r = q - c * nc, k = r / nr, i = r - k * nr;
-      const double* fcol = fd + c * nc + i;
+      const double* fcol = fd + c * nc + (a.sep_sym && k >= h ? h * nr : 0) + i;
       double acc = 0.0;
-      for (int j = 0; j < nt; ++j) acc += Vi[k * nt + j] * fcol[j * nr];
+      for (int j = 0; j < vr; ++j) acc += Vi[k * vr + j] * fcol[j * nr];
       z[q] = acc * invd[k * nr + i];
     }
     __syncthreads();
@@ -346,15 +362,34 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
       }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
-      const int j = q / nr, i = q - j * nr;
-      double ax = 0.0, ay = 0.0;
-      for (int k = 0; k < nt; ++k) {
-        const double vk = Vm[j * nt + k];
-        ax += vk * z[k * nr + i];
-        ay += vk * z[nc + k * nr + i];
+    if (a.sep_sym) {   // e_j = E + O, e_{nt-1-j} = E - O (even, odd eigenvector parts)
+      for (int q = threadIdx.x; q < h * nr; q += blockDim.x) {
+        const int j = q / nr, i = q - j * nr;
+        double ex = 0.0, ey = 0.0, ox = 0.0, oy = 0.0;
+        for (int k = 0; k < h; ++k) {
+          const double vk = Vm[j * nt + k];
+          ex += vk * z[k * nr + i];
+          ey += vk * z[nc + k * nr + i];
+        }
+        for (int k = h; k < nt; ++k) {
+          const double vk = Vm[j * nt + k];
+          ox += vk * z[k * nr + i];
+          oy += vk * z[nc + k * nr + i];
+        }
+        ec[vslot(Lc, j, i)] = V{T(ex + ox), T(ey + oy)};
+        ec[vslot(Lc, nt - 1 - j, i)] = V{T(ex - ox), T(ey - oy)};
       }
-      ec[vslot(Lc, j, i)] = V{T(ax), T(ay)};
+    } else {
+      for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+        const int j = q / nr, i = q - j * nr;
+        double ax = 0.0, ay = 0.0;
+        for (int k = 0; k < nt; ++k) {
+          const double vk = Vm[j * nt + k];
+          ax += vk * z[k * nr + i];
+          ay += vk * z[nc + k * nr + i];
+        }
+        ec[vslot(Lc, j, i)] = V{T(ax), T(ay)};
+      }
     }
     __syncthreads();
   } else if (a.blk_n > 0) {

@@ -80,6 +80,7 @@ struct VSmemArgs {
   int dbl_off, blk_off;  // byte offsets in shared memory: FP64 solve scratch, staged factors
   const double* sep;     // separable coarsest-level factors [slots][sep_stride] (sep_stride > 0)
   int sep_stride;
+  int sep_sym;           // mirror-symmetric separable layout (see Hierarchy::sep_sym)
   int nu1, nu2, n_sor;
   int tab_off;           // shared-memory offset (complex elements) of the staged tables
   const void* tabs;      // per-slot packed tables (T), tab_stride elements per slot

@@ -203,11 +203,26 @@ static void jacobi_eig(std::vector<double>& S, int n, std::vector<double>& U,
   for (int i = 0; i < n; ++i) lam[i] = S[size_t(i) * n + i];
 }
 
+// Mirror symmetry j <-> n-1-j of the symmetrised polar operator S and its
+// weights w (relative 1e-13).
+static bool mirror_symmetric(const std::vector<double>& S, const std::vector<double>& w, int n) {
+  auto near = [](double x, double y) { return std::fabs(x - y) <= 1e-13 * std::fmax(std::fabs(x), std::fabs(y)); };
+  if (n % 2) return false;
+  for (int j = 0; j < n; ++j) {
+    if (!near(S[size_t(j) * n + j], S[size_t(n - 1 - j) * n + (n - 1 - j)])) return false;
+    if (!near(w[j + 1], w[n - j])) return false;
+    if (j + 1 < n && !near(S[size_t(j) * n + j + 1], S[size_t(n - 2 - j) * n + (n - 1 - j)])) return false;
+  }
+  return true;
+}
+
 // Separable factors of L_m on plane g (see Hierarchy::coarse_sep), written
-// to out.  Returns false when the operator does not split this way or the
-// factors fail the residual check (the caller then uses block factors).
-static bool separable_factors(const PlaneGeo& g, int m, double* out) {
-  const int nr = g.r.n, nt = g.t.n;
+// to out; sym selects the mirror-symmetric layout (the polar eigenvectors
+// taken in the even / odd subspaces).  Returns false when the operator does
+// not split this way (or is not mirror-symmetric, for sym) or the factors
+// fail the residual check.
+static bool separable_factors(const PlaneGeo& g, int m, double* out, bool sym) {
+  const int nr = g.r.n, nt = g.t.n, h = nt / 2;
   const double s2 = g.s2(m);
   const bool sph = g.geometry == SPH;
   std::vector<double> dr(nr + 1), dt(nt + 1);
@@ -228,17 +243,46 @@ static bool separable_factors(const PlaneGeo& g, int m, double* out) {
     S[size_t(j - 1) * nt + j] = S[size_t(j) * nt + (j - 1)] = e;
     w[j + 1] = w[j] * g.aN[j] / g.aS[j + 1];
   }
-  jacobi_eig(S, nt, U, lam);
+  if (sym) {
+    // even / odd subspaces, basis (delta_j +- delta_{n-1-j}) / sqrt 2, j < h:
+    // the top-left block of S with the middle coupling added (even) or
+    // subtracted (odd); eigenvectors k < h even, k >= h odd
+    if (!mirror_symmetric(S, w, nt)) return false;
+    const double emid = S[size_t(h - 1) * nt + h];
+    U.assign(size_t(nt) * nt, 0.0);
+    lam.assign(nt, 0.0);
+    for (int par = 0; par < 2; ++par) {
+      std::vector<double> Sh(size_t(h) * h), Uh, lh;
+      for (int x = 0; x < h; ++x)
+        for (int y = 0; y < h; ++y) Sh[size_t(x) * h + y] = S[size_t(x) * nt + y];
+      Sh[size_t(h - 1) * h + (h - 1)] += par ? -emid : emid;
+      jacobi_eig(Sh, h, Uh, lh);
+      for (int kk = 0; kk < h; ++kk) {
+        const int k = par * h + kk;
+        lam[k] = lh[kk];
+        for (int j = 0; j < h; ++j) {
+          const double v = Uh[size_t(j) * h + kk] * std::sqrt(0.5);
+          U[size_t(j) * nt + k] = v;
+          U[size_t(nt - 1 - j) * nt + k] = par ? -v : v;
+        }
+      }
+    }
+  } else {
+    jacobi_eig(S, nt, U, lam);
+  }
+  // general layout: V [nt][nt], V^-1 [nt][nt]; mirror-symmetric layout: the
+  // rows j < h of V [h][nt] and the columns j < h of V^-1 [nt][h]
+  const int vr = sym ? h : nt;
   double* V = out;
-  double* Vi = V + size_t(nt) * nt;
-  double* invd = Vi + size_t(nt) * nt;
+  double* Vi = V + size_t(vr) * nt;
+  double* invd = Vi + size_t(nt) * vr;
   double* cp = invd + size_t(nt) * nr;
   double* lid = cp + size_t(nt) * nr;
   std::vector<double> low(nr);
-  for (int j = 0; j < nt; ++j)
+  for (int j = 0; j < vr; ++j)
     for (int k = 0; k < nt; ++k) {
       V[size_t(j) * nt + k] = U[size_t(j) * nt + k] / std::sqrt(w[j + 1]);
-      Vi[size_t(k) * nt + j] = U[size_t(j) * nt + k] * std::sqrt(w[j + 1]);
+      Vi[size_t(k) * vr + j] = U[size_t(j) * nt + k] * std::sqrt(w[j + 1]);
     }
   for (int i = 1; i <= nr; ++i) low[i - 1] = i > 1 ? g.aW[i] : 0.0;
   for (int k = 0; k < nt; ++k) {
@@ -253,14 +297,27 @@ static bool separable_factors(const PlaneGeo& g, int m, double* out) {
       lid[size_t(k) * nr + i - 1] = low[i - 1] / den;
     }
   }
-  // residual check of the factors on a fixed test vector, stencil apply
-  std::vector<double> b(size_t(nr) * nt), z(size_t(nr) * nt), x(size_t(nr) * nt);
+  // residual check of the factors on a fixed test vector, in the kernel's
+  // form: z' = invd .* (V^-1 f), dp_i = z'_i - lid_i dp_{i-1}, back
+  // substitution, x = V z (mirror-symmetric: sums and differences of the
+  // mirrored rows in, even and odd parts out)
+  std::vector<double> b(size_t(nr) * nt), z(size_t(nr) * nt), x(size_t(nr) * nt), fs(size_t(nr) * nt);
   for (size_t q = 0; q < b.size(); ++q) b[q] = std::sin(0.37 * double(q) + 1.0);
-  // the kernel's form: z' = invd .* (V^-1 f), then dp_i = z'_i - lid_i dp_{i-1}
+  if (sym) {
+    for (int j = 0; j < h; ++j)
+      for (int i = 0; i < nr; ++i) {
+        const double u = b[size_t(j) * nr + i], v = b[size_t(nt - 1 - j) * nr + i];
+        fs[size_t(j) * nr + i] = u + v;
+        fs[size_t(h + j) * nr + i] = u - v;
+      }
+  } else {
+    fs = b;
+  }
   for (int k = 0; k < nt; ++k)
     for (int i = 0; i < nr; ++i) {
+      const double* src = fs.data() + (sym && k >= h ? size_t(h) * nr : 0) + i;
       double a = 0.0;
-      for (int j = 0; j < nt; ++j) a += Vi[size_t(k) * nt + j] * b[size_t(j) * nr + i];
+      for (int j = 0; j < vr; ++j) a += Vi[size_t(k) * vr + j] * src[size_t(j) * nr];
       z[size_t(k) * nr + i] = a * invd[size_t(k) * nr + i];
     }
   for (int k = 0; k < nt; ++k) {
@@ -270,11 +327,15 @@ static bool separable_factors(const PlaneGeo& g, int m, double* out) {
     double xv = zz[nr - 1];
     for (int i = nr - 2; i >= 0; --i) { xv = zz[i] - cp[size_t(k) * nr + i] * xv; zz[i] = xv; }
   }
-  for (int j = 0; j < nt; ++j)
+  for (int j = 0; j < vr; ++j)
     for (int i = 0; i < nr; ++i) {
-      double a = 0.0;
-      for (int k = 0; k < nt; ++k) a += V[size_t(j) * nt + k] * z[size_t(k) * nr + i];
-      x[size_t(j) * nr + i] = a;
+      double ev = 0.0, od = 0.0;
+      for (int k = 0; k < nt; ++k) {
+        const double t = V[size_t(j) * nt + k] * z[size_t(k) * nr + i];
+        if (sym && k >= h) od += t; else ev += t;
+      }
+      x[size_t(j) * nr + i] = ev + od;
+      if (sym) x[size_t(nt - 1 - j) * nr + i] = ev - od;
     }
   double rn = 0.0, bn = 0.0;
   for (int j = 1; j <= nt; ++j)
@@ -405,14 +466,22 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
   const int nr = C.g.r.n, nt = C.g.t.n, nc = nr * nt;
   H.nc = nc;
   if (nt <= 64) {
-    H.sep_stride = (2 * nt * nt + 3 * nt * nr + 1) / 2 * 2;
-    H.coarse_sep.assign(size_t(M) * H.sep_stride, 0.0);
-    bool ok = true;
-    for (int k = 0; k < M && ok; ++k)
-      ok = separable_factors(C.g, modes[k], H.coarse_sep.data() + size_t(k) * H.sep_stride);
-    if (ok) return true;
+    // the mirror-symmetric layout first (half the transform work), else general
+    for (int sym = 1; sym >= 0; --sym) {
+      if (sym && nt % 2) continue;
+      H.sep_stride = ((sym ? 1 : 2) * nt * nt + 3 * nt * nr + 1) / 2 * 2;
+      H.coarse_sep.assign(size_t(M) * H.sep_stride, 0.0);
+      bool ok = true;
+      for (int k = 0; k < M && ok; ++k)
+        ok = separable_factors(C.g, modes[k], H.coarse_sep.data() + size_t(k) * H.sep_stride, sym != 0);
+      if (ok) {
+        H.sep_sym = sym;
+        return true;
+      }
+    }
     H.coarse_sep.clear();
     H.sep_stride = 0;
+    H.sep_sym = 0;
   }
   const bool blocks = nr <= 64;
   H.blk_n = blocks ? nr : 0;

@@ -83,9 +83,13 @@ struct Hierarchy {
   // eigenvalue k the Thomas factors of L_r + lambda_k D_r: 1/pivot [nt][nr],
   // upper/pivot [nt][nr] and lower/pivot [nt][nr] (the forward sweep is then
   // one FMA per cell: dp_i = z_i/pivot_i - (lower_i/pivot_i) dp_{i-1});
-  // sep_stride doubles per slot.
+  // sep_stride doubles per slot.  sep_sym = 1: the polar operator is
+  // mirror-symmetric (j <-> nt-1-j), eigenvectors k < nt/2 are even and
+  // k >= nt/2 odd, and only the rows j < nt/2 of V ([nt/2][nt]) and the
+  // columns j < nt/2 of V^-1 ([nt][nt/2]) are stored.
   std::vector<double> coarse_sep;
   int sep_stride = 0;
+  int sep_sym = 0;
 };
 
 // Build levels (coarsening stops at a short side of 8 cells, or 4 cells when

@@ -191,6 +191,7 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
     vs.blk_nt = H.blk_nt;
     vs.sep = d_sep;
     vs.sep_stride = H.sep_stride;
+    vs.sep_sym = H.sep_sym;
     const size_t blk_bytes = H.sep_stride > 0
                                  ? size_t(H.sep_stride) * sizeof(double)
                                  : size_t(H.blk_nt) * H.blk_n * (H.blk_n + 2) * sizeof(double);

@@ -31,6 +31,11 @@ SMALL = {
     "cyl_cavity": workloads.spec(workloads.CYLINDRICAL, 32, 64, 8, workloads.UNIFORM, 0.2, 1.0),
     "sph_partial": workloads.spec(workloads.SPHERICAL, 32, 32, 8, workloads.UNIFORM, 1.0, 2.0,
                                   0.25 * np.pi, 0.75 * np.pi),
+    # a polar range off the equator: the polar operator is not mirror-symmetric,
+    # so the coarsest solve takes the general separable layout (the others the
+    # mirror-symmetric one)
+    "sph_offcentre": workloads.spec(workloads.SPHERICAL, 32, 32, 8, workloads.UNIFORM, 1.0, 2.0,
+                                    0.3 * np.pi, 0.65 * np.pi),
 }
 
 
