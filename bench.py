@@ -393,6 +393,14 @@ def launches_per_solve(s, st):
 # inverse diagonal 6, each even-odd SOR sweep 16); nu_pre + nu_post cycles of
 # 2 passes each; defect restriction and prolongation add 40 (424 for the
 # default schedule nu = (2, 2), n_sor = 2).
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu captures summarised in profiles/k_vsmem_256x128x256.md and
+# profiles/k_rpass2_k_tpass2_256x128x256.md (workload 3, all 129 modes).
+# They hold for the kernels as captured; a changed kernel needs a new capture.
+VSMEM_TRAFFIC_BYTES = 12150016
+SMOOTH_CYCLE_TRAFFIC_BYTES = 74273792 + 75833088   # k_rpass2 + k_tpass2
+
+
 def vcycle_flops_per_cell(sched):
     return (sched["nu_pre"] + sched["nu_post"]) * 2 * (16 + 16 * sched["n_sor"]) + 40
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
@@ -436,7 +444,8 @@ def vcycle_roofline(torch, ps, s, stream):
             "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": ach / FP32_PEAK_TFLOPS,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
-            "traffic": None, "algorithmic_flops_per_launch": flops, "avg_ms": dt * 1e3,
+            "traffic": VSMEM_TRAFFIC_BYTES if M == 129 and (n_r, n_tz) == (256, 128) else None,
+            "traffic_unit": "bytes per launch (ncu)", "algorithmic_flops_per_launch": flops, "avg_ms": dt * 1e3,
             "note": "one block per mode plane: latency-bound line relaxations"}
 
 
@@ -468,7 +477,9 @@ def smoother_roofline(torch, ps, s, stream):
     return {"kernel": "finest-level smoothing cycle (k_rpass2 + k_tpass2, FP32, all modes)",
             "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
             "frac": (ach / pk) if pk else None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-            "traffic": None, "algorithmic_bytes_per_launch_set": bytes_, "avg_ms": dt * 1e3}
+            "traffic": SMOOTH_CYCLE_TRAFFIC_BYTES if M == 129 and (n_r, n_tz) == (256, 128) else None,
+            "traffic_unit": "bytes per cycle (ncu, two launches)",
+            "algorithmic_bytes_per_launch_set": bytes_, "avg_ms": dt * 1e3}
 
 
 def main():
