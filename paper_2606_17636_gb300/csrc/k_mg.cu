@@ -215,11 +215,11 @@ int residual_blocks(int nr, int nt) {
   return (nr * nt + 255) / 256;
 }
 
-__device__ __forceinline__ double4 add4(double4 a, double4 b) {
-  return make_double4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+__device__ __forceinline__ Sum4 add4(Sum4 a, Sum4 b) {
+  return sum4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
 
-__device__ double4 block_sum4(double4 v, double4* sh) {
+__device__ Sum4 block_sum4(Sum4 v, Sum4* sh) {
   for (int o = 16; o > 0; o >>= 1) {
     v.x += __shfl_down_sync(0xffffffffu, v.x, o);
     v.y += __shfl_down_sync(0xffffffffu, v.y, o);
@@ -230,13 +230,13 @@ __device__ double4 block_sum4(double4 v, double4* sh) {
   __syncthreads();
   if (lane == 0) sh[warp] = v;
   __syncthreads();
-  double4 s = make_double4(0, 0, 0, 0);
+  Sum4 s = sum4(0, 0, 0, 0);
   if (threadIdx.x == 0)
     for (int w = 0; w < int(blockDim.x >> 5); ++w) s = add4(s, sh[w]);
   return s;
 }
 
-__device__ void retire_block(int* act, int* nact, const double4* __restrict__ psum, RetireState S,
+__device__ void retire_block(int* act, int* nact, const Sum4* __restrict__ psum, RetireState S,
                              double tol, int max_cycles, int stagnation, int use_cond,
                              unsigned long long handle, int* scan);
 
@@ -262,10 +262,10 @@ __device__ __forceinline__ double2 defect_tab(const LevelDev& L, const double* _
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const double2* __restrict__ f,
                                                   const double2* __restrict__ u,
-                                                  vec2_t<T>* __restrict__ r, double4* part,
-                                                  double4* psum, int* cnt, int bpp, RetireArgs ra,
+                                                  vec2_t<T>* __restrict__ r, Sum4* part,
+                                                  Sum4* psum, int* cnt, int bpp, RetireArgs ra,
                                                   const double* __restrict__ ctab) {
-  __shared__ double4 sh[8];
+  __shared__ Sum4 sh[8];
   __shared__ float4 shf[8];
   __shared__ int last, glast;
   __shared__ int scan[256];
@@ -312,9 +312,9 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
     if (lane == 0) shf[warp] = accf;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double4 acc = make_double4(0, 0, 0, 0);
+      Sum4 acc = sum4(0, 0, 0, 0);
       for (int q = 0; q < int(blockDim.x >> 5); ++q)
-        acc = add4(acc, make_double4(shf[q].x, shf[q].y, shf[q].z, shf[q].w));
+        acc = add4(acc, sum4(shf[q].x, shf[q].y, shf[q].z, shf[q].w));
       part[size_t(p) * bpp + bx] = acc;
       __threadfence();
       last = (atomicAdd(&cnt[p], 1) == bpp - 1);
@@ -322,13 +322,13 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
     __syncthreads();
     if (last) {
       __threadfence();
-      double4 t = make_double4(0, 0, 0, 0);
+      Sum4 t = sum4(0, 0, 0, 0);
       for (int b = threadIdx.x; b < bpp; b += blockDim.x) {
         const double2* q2 = reinterpret_cast<const double2*>(&part[size_t(p) * bpp + b]);
         const double2 qa = __ldcg(q2), qb = __ldcg(q2 + 1);
-        t = add4(t, make_double4(qa.x, qa.y, qb.x, qb.y));
+        t = add4(t, sum4(qa.x, qa.y, qb.x, qb.y));
       }
-      const double4 tot = block_sum4(t, sh);
+      const Sum4 tot = block_sum4(t, sh);
       if (threadIdx.x == 0) {
         psum[p] = tot;
         cnt[p] = 0;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
 
 template <typename T>
 void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
-                     vec2_t<T>* r, double4* part, double4* psum, int* cnt, const RetireArgs& ra,
+                     vec2_t<T>* r, Sum4* part, Sum4* psum, int* cnt, const RetireArgs& ra,
                      cudaStream_t st, const double* ctab) {
   const int bpp = residual_blocks(L.nr, L.nt);
   k_residual<T><<<work_grid(long(bpp) * B.max_planes), 256, 0, st>>>(L, B, f, u, r, part, psum,
@@ -360,7 +360,7 @@ void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const 
 // Retirement (App. B criterion, per mode and component) and compaction.
 // ---------------------------------------------------------------------------
 
-__device__ void retire_block(int* act, int* nact, const double4* __restrict__ psum, RetireState S,
+__device__ void retire_block(int* act, int* nact, const Sum4* __restrict__ psum, RetireState S,
                              double tol, int max_cycles, int stagnation, int use_cond,
                              unsigned long long handle, int* scan) {
   __shared__ double smax[32];
@@ -372,7 +372,7 @@ __device__ void retire_block(int* act, int* nact, const double4* __restrict__ ps
     double mx = 0.0;
     for (int k = tid; k < n; k += blockDim.x) {
       const int p = act[k];
-      const double4 s = psum[p];
+      const Sum4 s = psum[p];
       S.nf2[p] = make_double2(s.z, s.w);
       mx = fmax(mx, fmax(s.z, s.w));
     }
@@ -395,7 +395,7 @@ __device__ void retire_block(int* act, int* nact, const double4* __restrict__ ps
     int keep = 0, p = -1;
     if (k < n) {
       p = act[k];
-      const double4 s = psum[p];
+      const Sum4 s = psum[p];
       const double2 nf = S.nf2[p];
       const double2 prev = S.nr2[p];
       const double tre = tol2 * fmax(nf.x, floor2), tim = tol2 * fmax(nf.y, floor2);
@@ -457,7 +457,7 @@ void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t 
   template void launch_update<T>(const LevelDev&, const Batch&, double2*, const vec2_t<T>*,     \
                                  cudaStream_t);                                                  \
   template void launch_residual<T>(const LevelDev&, const Batch&, const double2*,               \
-                                   const double2*, vec2_t<T>*, double4*, double4*, int*,        \
+                                   const double2*, vec2_t<T>*, Sum4*, Sum4*, int*,        \
                                    const RetireArgs&, cudaStream_t, const double*);
 INST(float)
 INST(double)

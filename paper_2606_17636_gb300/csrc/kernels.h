@@ -12,6 +12,15 @@ template <> struct Vec2<double> { typedef double2 type; };
 template <typename T> using vec2_t = typename Vec2<T>::type;
 
 // Device view of one multigrid level.
+// Four FP64 partial sums (|r|^2 and |f|^2 of both components of a plane),
+// 16-byte aligned like CUDA's vector types.
+struct __align__(16) Sum4 {
+  double x, y, z, w;
+};
+__host__ __device__ __forceinline__ Sum4 sum4(double x, double y, double z, double w) {
+  return Sum4{x, y, z, w};
+}
+
 struct LevelDev {
   int nr, nt;
   const double* rd;   // RT_N x (nr+2) radial tables
@@ -135,7 +144,7 @@ struct RetireArgs {
 // DR + P DT, Q T), the same for every mode.
 template <typename T>
 void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
-                     vec2_t<T>* r, double4* part, double4* psum, int* cnt, const RetireArgs& ra,
+                     vec2_t<T>* r, Sum4* part, Sum4* psum, int* cnt, const RetireArgs& ra,
                      cudaStream_t st, const double* ctab);
 int residual_blocks(int nr, int nt);
 

@@ -207,8 +207,8 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   const int nblk = residual_blocks(lv[0].nr, lv[0].nt);
   d_act = static_cast<int*>(A.get(sizeof(int) * mp));
   d_nact = static_cast<int*>(A.get(sizeof(int)));
-  d_part = static_cast<double4*>(A.get(sizeof(double4) * size_t(mp) * nblk));
-  d_psum = static_cast<double4*>(A.get(sizeof(double4) * mp));
+  d_part = static_cast<Sum4*>(A.get(sizeof(Sum4) * size_t(mp) * nblk));
+  d_psum = static_cast<Sum4*>(A.get(sizeof(Sum4) * mp));
   d_cnt = static_cast<int*>(A.get(sizeof(int) * mp));
   d_cycles = static_cast<int*>(A.get(sizeof(int) * mp));
   d_status = static_cast<int*>(A.get(sizeof(int) * mp));

@@ -82,8 +82,8 @@ class MGSolver {
   double* d_blk = nullptr;
   double* d_sep = nullptr;
   double* d_ctab = nullptr;   // level-0 per-cell FP64 products [4][nt][nr]
-  double4* d_part = nullptr;
-  double4* d_psum = nullptr;
+  Sum4* d_part = nullptr;
+  Sum4* d_psum = nullptr;
   int* d_cnt = nullptr;
   int* d_gcnt = nullptr;
   double* d_fmax2 = nullptr;
