@@ -277,30 +277,39 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
   // from a zero initial guess the first defect is f itself (no stencil)
   const bool r_is_f = want_f && ra.zero_guess;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int w = blockIdx.x; w < nact * bpp; w += gridDim.x) {
-    const int k = w / bpp, bx = w - k * bpp;
+  // Work items of cpt x 256 cells: with many planes active the per-item
+  // reduction, fence and arrival count are paid once per 1024 cells; with few
+  // planes every item is 256 cells, spreading a plane's FP64 work over more
+  // SMs.  bpp (the caller's) is the item count for cpt = 1.
+  const int cpt = nact >= 16 ? 4 : 1;
+  const int ipp = (bpp + cpt - 1) / cpt;   // items per plane
+  for (int w = blockIdx.x; w < nact * ipp; w += gridDim.x) {
+    const int k = w / ipp, bx = w - k * ipp;
     const int p = B.act[k];
     const int slot = B.slot ? B.slot[p] : p;
-    const int idx = bx * blockDim.x + threadIdx.x;
     // the residual is FP64; its norm only drives the convergence test, so the
     // volume-weighted squares are accumulated in FP32 within the block
     float4 accf = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (idx < n) {
-      const int j = idx / nr, i = idx - j * nr;
-      const size_t base = size_t(p) * n;
-      const double s2 = B.s2d[slot];
-      const double2 rv = r_is_f ? f[base + idx] : defect_tab(L, ctab, n, s2, u + base, f + base, i, j);
-      const vec2_t<T> ro = vmk<vec2_t<T>, T>(T(rv.x), T(rv.y));
-      r[base + idx] = ro;
-      const float dv = L.rf[RT_V * (nr + 2) + i + 1] * L.tf[TT_V * (nt + 2) + j + 1];
-      const float rx = float(ro.x), ry = float(ro.y);
-      accf.x = dv * rx * rx;
-      accf.y = dv * ry * ry;
-      if (want_f) {
-        const double2 fv = f[base + idx];
-        const float fx = float(fv.x), fy = float(fv.y);
-        accf.z = dv * fx * fx;
-        accf.w = dv * fy * fy;
+#pragma unroll 4
+    for (int c = 0; c < cpt; ++c) {
+      const int idx = (bx * cpt + c) * blockDim.x + threadIdx.x;
+      if (idx < n) {
+        const int j = idx / nr, i = idx - j * nr;
+        const size_t base = size_t(p) * n;
+        const double s2 = B.s2d[slot];
+        const double2 rv = r_is_f ? f[base + idx] : defect_tab(L, ctab, n, s2, u + base, f + base, i, j);
+        const vec2_t<T> ro = vmk<vec2_t<T>, T>(T(rv.x), T(rv.y));
+        r[base + idx] = ro;
+        const float dv = L.rf[RT_V * (nr + 2) + i + 1] * L.tf[TT_V * (nt + 2) + j + 1];
+        const float rx = float(ro.x), ry = float(ro.y);
+        accf.x += dv * rx * rx;
+        accf.y += dv * ry * ry;
+        if (want_f) {
+          const double2 fv = f[base + idx];
+          const float fx = float(fv.x), fy = float(fv.y);
+          accf.z += dv * fx * fx;
+          accf.w += dv * fy * fy;
+        }
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -317,13 +326,13 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
         acc = add4(acc, sum4(shf[q].x, shf[q].y, shf[q].z, shf[q].w));
       part[size_t(p) * bpp + bx] = acc;
       __threadfence();
-      last = (atomicAdd(&cnt[p], 1) == bpp - 1);
+      last = (atomicAdd(&cnt[p], 1) == ipp - 1);
     }
     __syncthreads();
     if (last) {
       __threadfence();
       Sum4 t = sum4(0, 0, 0, 0);
-      for (int b = threadIdx.x; b < bpp; b += blockDim.x) {
+      for (int b = threadIdx.x; b < ipp; b += blockDim.x) {
         const double2* q2 = reinterpret_cast<const double2*>(&part[size_t(p) * bpp + b]);
         const double2 qa = __ldcg(q2), qb = __ldcg(q2 + 1);
         t = add4(t, sum4(qa.x, qa.y, qb.x, qb.y));
