@@ -138,12 +138,15 @@ typedef struct {
   int cols_t;          /* polar columns per block: 8, 16 or 32; 0 = widest that
                           fits (32, or fewer where n_r or 160 KB of shared memory
                           per block is the limit)                                 */
+  int nu_pre_fused, nu_post_fused; /* smoothing cycles on the levels of the fused
+                          shared-memory V-cycle, 0..8; 0 = nu_pre / nu_post       */
   double ms;           /* psolve_autotune: median solve time of the choice, ms    */
   int candidates;      /* psolve_autotune: candidates timed (0: from a cache)      */
   int cached;          /* psolve_autotune: 1 when the choice came from a cache     */
 } psolve_schedule;
 
-/* The handle's current schedule (ms, candidates, cached = 0). */
+/* The handle's current schedule (ms, candidates, cached = 0; the fused-level
+ * counts 0 when they equal nu_pre / nu_post). */
 int psolve_get_schedule(psolve_t h, psolve_schedule* s);
 /* Install a schedule for later solves (a captured solve is captured again).
  * PSOLVE_ERR_ARG, with the handle unchanged, when a field is out of range. */
@@ -158,6 +161,9 @@ int psolve_set_schedule(psolve_t h, const psolve_schedule* s);
  *     error at the same tolerance is larger.
  *   Stage 2, tile shapes: lines_r in {4, 8} x cols_t in {8, 16, 32} with the
  *     stage-1 schedule (shapes that reduce to the same launch are timed once).
+ *   Stage 3, the fused levels' own smoothing counts: nu_post_fused <=
+ *     nu_pre_fused <= 3 with the stage-1 and stage-2 choices (5 candidates
+ *     besides the stage-1 counts).
  * Each candidate runs one untimed solve (graph capture, caches), then three
  * timed solves (CUDA events on the handle's stream); its time is their
  * median.  Candidates whose solve fails are skipped.  Warm start is
@@ -167,7 +173,8 @@ int psolve_set_schedule(psolve_t h, const psolve_schedule* s);
  * extents, precision): a later call with the same key installs the cached
  * choice without timing.  When the environment variable PSOLVE_TUNE_CACHE
  * names a file, it is read on a process-cache miss (text, one line per key:
- * key nu_pre nu_post n_sor lines_r cols_t ms; the last line of a key wins)
+ * key nu_pre nu_post n_sor lines_r cols_t nu_pre_fused nu_post_fused ms; the
+ * last line of a key wins)
  * and every new choice is appended to it.
  * out (may be NULL) receives the choice.  Returns PSOLVE_OK, or the error of
  * the solve with the handle's current schedule, which then stays installed. */

@@ -45,7 +45,8 @@ class Stats(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("n_sor", ctypes.c_int),
-                ("lines_r", ctypes.c_int), ("cols_t", ctypes.c_int), ("ms", ctypes.c_double),
+                ("lines_r", ctypes.c_int), ("cols_t", ctypes.c_int), ("nu_pre_fused", ctypes.c_int),
+                ("nu_post_fused", ctypes.c_int), ("ms", ctypes.c_double),
                 ("candidates", ctypes.c_int), ("cached", ctypes.c_int)]
 
     def as_dict(self):
@@ -180,8 +181,9 @@ class Solver:
         check(lib().psolve_get_schedule(self.h, ctypes.byref(s)), "psolve_get_schedule")
         return s.as_dict()
 
-    def set_schedule(self, nu_pre, nu_post, n_sor, lines_r=8, cols_t=0):
-        s = Schedule(nu_pre=nu_pre, nu_post=nu_post, n_sor=n_sor, lines_r=lines_r, cols_t=cols_t)
+    def set_schedule(self, nu_pre, nu_post, n_sor, lines_r=8, cols_t=0, nu_pre_fused=0, nu_post_fused=0):
+        s = Schedule(nu_pre=nu_pre, nu_post=nu_post, n_sor=n_sor, lines_r=lines_r, cols_t=cols_t,
+                     nu_pre_fused=nu_pre_fused, nu_post_fused=nu_post_fused)
         check(lib().psolve_set_schedule(self.h, ctypes.byref(s)), "psolve_set_schedule")
 
     def autotune(self, rho, tol=1e-8, phi=None):

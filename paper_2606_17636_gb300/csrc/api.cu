@@ -498,6 +498,8 @@ extern "C" int psolve_get_schedule(psolve_t h, psolve_schedule* s) {
   s->n_sor = o.n_sor;
   s->lines_r = o.tiles.lines_r;
   s->cols_t = o.tiles.cols_t;
+  s->nu_pre_fused = o.nu1f;
+  s->nu_post_fused = o.nu2f;
   return PSOLVE_OK;
 }
 
@@ -506,6 +508,8 @@ static bool schedule_ok(const psolve_schedule& s, std::string& why) {
   else if (s.n_sor < 1 || s.n_sor > 8) why = "n_sor must be 1..8";
   else if (s.lines_r != 4 && s.lines_r != 8) why = "lines_r must be 4 or 8";
   else if (s.cols_t != 0 && s.cols_t != 8 && s.cols_t != 16 && s.cols_t != 32) why = "cols_t must be 0, 8, 16 or 32";
+  else if (s.nu_pre_fused < 0 || s.nu_pre_fused > 8 || s.nu_post_fused < 0 || s.nu_post_fused > 8)
+    why = "nu_pre_fused and nu_post_fused must be 0..8";
   else return true;
   return false;
 }
@@ -514,7 +518,7 @@ static void install_schedule(psolve_t h, const psolve_schedule& s) {
   Tiles t;
   t.lines_r = s.lines_r;
   t.cols_t = s.cols_t;
-  h->mg.set_schedule(s.nu_pre, s.nu_post, s.n_sor, t);
+  h->mg.set_schedule(s.nu_pre, s.nu_post, s.n_sor, t, s.nu_pre_fused, s.nu_post_fused);
   h->d.nu_pre = s.nu_pre;
   h->d.nu_post = s.nu_post;
   h->d.n_sor = s.n_sor;
@@ -553,8 +557,8 @@ static bool tune_file_read(const char* path, const std::string& key, psolve_sche
   char line[512], k[384];
   while (std::fgets(line, sizeof line, fp)) {
     psolve_schedule s{};
-    if (std::sscanf(line, "%383s %d %d %d %d %d %lf", k, &s.nu_pre, &s.nu_post, &s.n_sor, &s.lines_r,
-                    &s.cols_t, &s.ms) != 7)
+    if (std::sscanf(line, "%383s %d %d %d %d %d %d %d %lf", k, &s.nu_pre, &s.nu_post, &s.n_sor,
+                    &s.lines_r, &s.cols_t, &s.nu_pre_fused, &s.nu_post_fused, &s.ms) != 9)
       continue;
     std::string why;
     if (key == k && schedule_ok(s, why)) {
@@ -569,8 +573,8 @@ static bool tune_file_read(const char* path, const std::string& key, psolve_sche
 static void tune_file_append(const char* path, const std::string& key, const psolve_schedule& s) {
   FILE* fp = std::fopen(path, "a");
   if (!fp) return;
-  std::fprintf(fp, "%s %d %d %d %d %d %.4f\n", key.c_str(), s.nu_pre, s.nu_post, s.n_sor, s.lines_r,
-               s.cols_t, s.ms);
+  std::fprintf(fp, "%s %d %d %d %d %d %d %d %.4f\n", key.c_str(), s.nu_pre, s.nu_post, s.n_sor,
+               s.lines_r, s.cols_t, s.nu_pre_fused, s.nu_post_fused, s.ms);
   std::fclose(fp);
 }
 
@@ -630,6 +634,7 @@ extern "C" int psolve_autotune(psolve_t h, const double* rho, double* phi, doubl
         s.nu_pre = a;
         s.nu_post = b;
         s.n_sor = c;
+        s.nu_pre_fused = s.nu_post_fused = 0;
         if (a != cur.nu_pre || b != cur.nu_post || c != cur.n_sor) cand.push_back(s);
       }
   int n_timed = 0, rc0 = PSOLVE_OK;
@@ -670,6 +675,24 @@ extern "C" int psolve_autotune(psolve_t h, const double* rho, double* phi, doubl
         ++n_timed;
         if (ms < best.ms) { best = s; best.ms = ms; }
       }
+    // stage 3: the fused levels' own smoothing counts
+    if (h->mg.vs.nlev > 1) {   // the fused kernel smooths at least one level
+      const int a0 = best.nu_pre_fused > 0 ? best.nu_pre_fused : best.nu_pre;
+      const int b0 = best.nu_post_fused > 0 ? best.nu_post_fused : best.nu_post;
+      const psolve_schedule base = best;
+      for (int a = 1; a <= 3; ++a)
+        for (int b = 1; b <= a; ++b) {
+          if (a == a0 && b == b0) continue;
+          psolve_schedule s = base;
+          s.nu_pre_fused = a;
+          s.nu_post_fused = b;
+          double ms = 0;
+          install_schedule(h, s);
+          if (time_solves(h, rho, phi, tol, e0, e1, ms) != PSOLVE_OK) continue;
+          ++n_timed;
+          if (ms < best.ms) { best = s; best.ms = ms; }
+        }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -418,18 +418,25 @@ __device__ void retire_block(int* act, int* nact, const Sum4* __restrict__ psum,
       S.status[p] = st;
       keep = (st == ST_ACTIVE);
     }
+    // compaction: rank within the warp from a ballot, warp offsets from an
+    // exclusive prefix over the block's warps
+    const int lane = tid & 31, wid = tid >> 5, nw = int(blockDim.x >> 5);
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) scan[wid] = __popc(bal);
     __syncthreads();
-    scan[tid] = keep;
-    __syncthreads();
-    for (int o = 1; o < int(blockDim.x); o <<= 1) {
-      const int v = (tid >= o) ? scan[tid - o] : 0;
-      __syncthreads();
-      scan[tid] += v;
-      __syncthreads();
+    if (tid == 0) {
+      int acc = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int c = scan[w];
+        scan[w] = acc;
+        acc += c;
+      }
+      scan[nw] = acc;
     }
-    if (keep) act[base_out + scan[tid] - 1] = p;
     __syncthreads();
-    if (tid == 0) base_out += scan[blockDim.x - 1];
+    if (keep) act[base_out + scan[wid] + __popc(bal & ((1u << lane) - 1u))] = p;
+    __syncthreads();
+    if (tid == 0) base_out += scan[nw];
     __syncthreads();
   }
   if (tid == 0) {

@@ -305,9 +305,13 @@ void MGSolver::vcycle(cudaStream_t st) {
   }
 }
 
-void MGSolver::set_schedule(int nu1, int nu2, int n_sor, Tiles tiles) {
-  opt.nu1 = vs.nu1 = nu1;
-  opt.nu2 = vs.nu2 = nu2;
+void MGSolver::set_schedule(int nu1, int nu2, int n_sor, Tiles tiles, int nu1f, int nu2f) {
+  opt.nu1 = nu1;
+  opt.nu2 = nu2;
+  opt.nu1f = nu1f;
+  opt.nu2f = nu2f;
+  vs.nu1 = nu1f > 0 ? nu1f : nu1;
+  vs.nu2 = nu2f > 0 ? nu2f : nu2;
   opt.n_sor = vs.n_sor = n_sor;
   opt.tiles = tiles;
 }

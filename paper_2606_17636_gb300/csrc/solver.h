@@ -21,6 +21,7 @@ struct Arena {
 struct MGOptions {
   int precision = 1;   // 0 FP64, 1 mixed (FP32 V-cycles inside FP64 refinement)
   int nu1 = 2, nu2 = 2, n_sor = 2;
+  int nu1f = 0, nu2f = 0;   // smoothing cycles of the fused (shared-memory) levels; 0: nu1 / nu2
   Tiles tiles;         // tile shapes of the level-wide smoothing passes
   int max_cycles = 100;
   int stagnation = 0;  // retire planes whose residual stops falling
@@ -44,7 +45,7 @@ class MGSolver {
   void vcycle(cudaStream_t st);
   // Change the smoothing schedule and tile shapes of later V-cycles (a
   // captured solve must be captured again).
-  void set_schedule(int nu1, int nu2, int n_sor, Tiles tiles);
+  void set_schedule(int nu1, int nu2, int n_sor, Tiles tiles, int nu1f, int nu2f);
   // results (device arrays, per plane)
   int* d_cycles = nullptr;
   int* d_status = nullptr;

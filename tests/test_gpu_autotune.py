@@ -19,6 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KEYS = ("nu_pre", "nu_post", "n_sor", "lines_r", "cols_t", "nu_pre_fused", "nu_post_fused")
 
 
 @pytest.fixture(scope="module")
@@ -69,12 +70,17 @@ def test_schedule_changes_cycles_not_the_answer(ps):
     s = ps.Solver.from_spec(sp, precision=ps.FP64)
     ref = s.solve(rho, tol=1e-11)[0].clone()
     counts = {}
-    for nu1, nu2, ns in [(1, 1, 1), (3, 3, 3)]:
-        s.set_schedule(nu1, nu2, ns)
+    cases = {"light": dict(nu_pre=1, nu_post=1, n_sor=1), "heavy": dict(nu_pre=3, nu_post=3, n_sor=3),
+             "light fused levels": dict(nu_pre=2, nu_post=2, n_sor=2, nu_pre_fused=1, nu_post_fused=1),
+             "heavy fused levels": dict(nu_pre=2, nu_post=2, n_sor=2, nu_pre_fused=3, nu_post_fused=3)}
+    for name, kw in cases.items():
+        s.set_schedule(**kw)
+        assert {k: s.schedule()[k] for k in kw} == kw
         phi = s.solve(rho, tol=1e-11)[0]
-        counts[(nu1, nu2, ns)] = s.stats()["iterations_psi"]
-        assert _rel(phi, ref) <= 1e-9
-    assert counts[(1, 1, 1)] > counts[(3, 3, 3)]
+        counts[name] = s.stats()["iterations_psi"]
+        assert _rel(phi, ref) <= 1e-9, name
+    assert counts["light"] > counts["heavy"]
+    assert counts["light fused levels"] >= counts["heavy fused levels"]
     s.close()
 
 
@@ -84,7 +90,8 @@ def test_set_schedule_rejects_out_of_range_fields(ps):
     before = s.schedule()
     for bad in [dict(nu_pre=0, nu_post=2, n_sor=2), dict(nu_pre=2, nu_post=9, n_sor=2),
                 dict(nu_pre=2, nu_post=2, n_sor=0), dict(nu_pre=2, nu_post=2, n_sor=2, lines_r=6),
-                dict(nu_pre=2, nu_post=2, n_sor=2, cols_t=12)]:
+                dict(nu_pre=2, nu_post=2, n_sor=2, cols_t=12),
+                dict(nu_pre=2, nu_post=2, n_sor=2, nu_pre_fused=9), dict(nu_pre=2, nu_post=2, n_sor=2, nu_post_fused=-1)]:
         with pytest.raises(ps.PSolveError) as e:
             s.set_schedule(**bad)
         assert e.value.code == ps.ERR_ARG
@@ -104,8 +111,9 @@ def test_autotune_picks_a_candidate_and_keeps_the_answer(ps):
     assert ch["cached"] == 0 and ch["candidates"] >= 18 and ch["ms"] > 0
     assert 1 <= ch["nu_post"] <= ch["nu_pre"] <= 3 and 1 <= ch["n_sor"] <= 3
     assert ch["lines_r"] in (4, 8) and ch["cols_t"] in (0, 8, 16, 32)
+    assert 0 <= ch["nu_post_fused"] <= 3 and 0 <= ch["nu_pre_fused"] <= 3
     now = s.schedule()
-    assert all(now[k] == ch[k] for k in ("nu_pre", "nu_post", "n_sor", "lines_r", "cols_t"))
+    assert all(now[k] == ch[k] for k in KEYS)
     phi = s.solve(rho, tol=1e-8)[0]
     st = s.stats()
     assert st["rel_residual_psi"] <= 1e-8 and st["rel_residual_phi"] <= 1e-8
@@ -115,7 +123,7 @@ def test_autotune_picks_a_candidate_and_keeps_the_answer(ps):
     s2 = ps.Solver.from_spec(sp, precision=ps.MIXED)
     ch2 = s2.autotune(rho, tol=1e-8)
     assert ch2["cached"] == 1 and ch2["candidates"] == 0
-    assert all(ch2[k] == ch[k] for k in ("nu_pre", "nu_post", "n_sor", "lines_r", "cols_t"))
+    assert all(ch2[k] == ch[k] for k in KEYS)
     s.close()
     s2.close()
 
@@ -132,9 +140,9 @@ def test_autotune_file_cache(ps, tmp_path, monkeypatch):
     lines = path.read_text().splitlines()
     assert len(lines) == 1
     f = lines[0].split()
-    assert [int(x) for x in f[1:6]] == [ch["nu_pre"], ch["nu_post"], ch["n_sor"], ch["lines_r"], ch["cols_t"]]
+    assert [int(x) for x in f[1:8]] == [ch[k] for k in KEYS]
     # another process reads the file: rewrite the entry and check it is used
-    path.write_text("%s 3 1 1 4 8 1.0\n" % f[0])
+    path.write_text("%s 3 1 1 4 8 2 1 1.0\n" % f[0])
     code = ("import json, sys, torch; sys.path.insert(0, %r)\n"
             "import paper_2606_17636_gb300 as ps\n"
             "s = ps.Solver.from_spec(json.loads(%r), precision=ps.MIXED)\n"
@@ -145,4 +153,4 @@ def test_autotune_file_cache(ps, tmp_path, monkeypatch):
     assert out.returncode == 0, out.stderr[-2000:]
     got = json.loads(out.stdout.strip().splitlines()[-1])
     assert got["cached"] == 1 and got["candidates"] == 0
-    assert [got[k] for k in ("nu_pre", "nu_post", "n_sor", "lines_r", "cols_t")] == [3, 1, 1, 4, 8]
+    assert [got[k] for k in KEYS] == [3, 1, 1, 4, 8, 2, 1]
