@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
       constexpr int per = int(sizeof(W4) / sizeof(T));
       const W4* src = reinterpret_cast<const W4*>(static_cast<const T*>(a.tabs) + size_t(slot) * a.tab_stride);
       W4* dst = reinterpret_cast<W4*>(tb);
-      for (int k = threadIdx.x; k < a.tab_stride / per; k += blockDim.x) dst[k] = src[k];
+      for (int k = threadIdx.x; k < a.tab_stride / per; k += blockDim.x) cp_async_v(dst + k, src + k, true);
     }
     if (threadIdx.x == 0) {
       int toff = 0;
@@ -263,18 +263,20 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     const double2* src = reinterpret_cast<const double2*>(
         (a.sep_stride > 0 ? a.sep : a.blk) + size_t(slot) * fac_stride);
     double2* dst = reinterpret_cast<double2*>(vraw + a.blk_off);
-    for (int k = threadIdx.x; k < int(fac_stride / 2); k += blockDim.x) dst[k] = src[k];
+    for (int k = threadIdx.x; k < int(fac_stride / 2); k += blockDim.x) cp_async_v(dst + k, src + k, true);
   }
-  // load f of the first level, zero all errors
+  // stage f of the first level, zero all errors
   {
     RowWalk w(threadIdx.x, blockDim.x, nr0);
     for (int k = threadIdx.x; k < n0; k += blockDim.x, w.next())
-      sm[a.off_f[0] + vslot(a.L[0], w.j, w.c)] = gf[size_t(p) * n0 + k];
+      cp_async_v(sm + a.off_f[0] + vslot(a.L[0], w.j, w.c), gf + size_t(p) * n0 + k, true);
   }
   for (int l = 0; l < K; ++l) {
     const int n = a.L[l].nr * a.L[l].nt;
     for (int k = threadIdx.x; k < n; k += blockDim.x) sm[a.off_e[l] + k] = V{0, 0};
   }
+  // tables, factors and f arrive by asynchronous copies, all in flight at once
+  cp_async_wait_all();
   __syncthreads();
   // Each phase works on register copies of the level descriptors: read
   // through sL, every shared-memory store of a phase could alias them and

@@ -154,3 +154,20 @@ def test_autotune_file_cache(ps, tmp_path, monkeypatch):
     got = json.loads(out.stdout.strip().splitlines()[-1])
     assert got["cached"] == 1 and got["candidates"] == 0
     assert [got[k] for k in KEYS] == [3, 1, 1, 4, 8, 2, 1]
+
+
+def test_autotune_reports_a_failing_solve_and_keeps_the_schedule(ps):
+    """A handle whose solves cannot converge (two V-cycles at most): the
+    tuner returns the solve's error and leaves the handle's schedule as it
+    was.  FP64 on this grid is a key no other test tunes, so the process
+    cache cannot answer."""
+    sp = _wide_level_specs()["cyl_cavity"]
+    rho = torch.from_numpy(clumps(sp, 45)).cuda()
+    s = ps.Solver.from_spec(sp, precision=ps.FP64, max_cycles=2)
+    s.set_schedule(2, 1, 2, lines_r=8, cols_t=32)
+    before = s.schedule()
+    with pytest.raises(ps.PSolveError) as e:
+        s.autotune(rho, tol=1e-10)
+    assert e.value.code == ps.ERR_NOT_CONVERGED
+    assert s.schedule() == before
+    s.close()
