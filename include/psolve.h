@@ -100,6 +100,26 @@ int psolve_create(psolve_t* out, int geometry, int n_r, int n_theta_or_z, int n_
 /* Same with every option; fields left zero take their defaults. */
 int psolve_create_ex(psolve_t* out, const psolve_desc* d);
 
+/* The multigrid plan psolve_create_ex would build for d, computed on the
+ * host only (no device memory, no kernels: usable without a GPU).  Levels
+ * halve both sides while the short side exceeds 16, or exceeds 4 with more
+ * than 1024 cells (Sec. 3; the paper leaves the coarsest size open); the
+ * coarsest level is solved exactly in FP64 (Sec. 3.3 allows a direct
+ * solver) in one of four forms, reported in `coarsest`. */
+enum { PSOLVE_COARSE_SEPARABLE_MIRROR = 0, /* separable, mirror-symmetric polar operator */
+       PSOLVE_COARSE_SEPARABLE = 1,        /* separable, general polar operator          */
+       PSOLVE_COARSE_BLOCK = 2,            /* block-tridiagonal (Schur complements)      */
+       PSOLVE_COARSE_DENSE = 3 };          /* dense inverse                              */
+typedef struct {
+  int n_modes;                 /* M = n_phi / 2 + 1                                 */
+  int n_levels;                /* multigrid levels, finest first (at most 16)       */
+  int level_n_r[16], level_n_tz[16];
+  int coarsest;                /* PSOLVE_COARSE_*                                   */
+  int coarse_doubles_per_mode; /* FP64 values of the coarsest-level factors per mode */
+} psolve_plan;
+/* PSOLVE_ERR_ARG (with a message) for an invalid descriptor, as psolve_create_ex. */
+int psolve_plan_inspect(const psolve_desc* d, psolve_plan* out);
+
 /* Solve (Sec. 5.1 steps 2-7): rho [n_r][n_tz][n_phi] -> phi (same layout),
  * device pointers, phi must not alias rho.  tol is the relative residual of
  * each mode's Helmholtz problem in the volume-weighted L2 norm (App. B),

@@ -53,6 +53,33 @@ class Schedule(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Plan(ctypes.Structure):
+    _fields_ = [("n_modes", ctypes.c_int), ("n_levels", ctypes.c_int),
+                ("level_n_r", ctypes.c_int * 16), ("level_n_tz", ctypes.c_int * 16),
+                ("coarsest", ctypes.c_int), ("coarse_doubles_per_mode", ctypes.c_int)]
+
+
+COARSE_FORMS = {0: "separable, mirror-symmetric", 1: "separable", 2: "block-tridiagonal", 3: "dense"}
+
+
+def plan_inspect(spec, precision=1):
+    """The multigrid plan of a problem spec (psolve_plan_inspect: host only,
+    no GPU needed): levels (n_r, n_tz), finest first, and the coarsest-level
+    solve's form and factor size per mode."""
+    d = Desc()
+    d.geometry, d.n_r, d.n_tz, d.n_phi, d.spacing = (spec["geometry"], spec["n_r"], spec["n_tz"],
+                                                     spec["n_phi"], spec["spacing"])
+    d.r_in, d.r_out = spec["r_in"], spec["r_out"]
+    d.t_min = spec.get("t_min") or 0.0
+    d.t_max = spec.get("t_max") or 0.0
+    d.precision = precision
+    p = Plan()
+    check(lib().psolve_plan_inspect(ctypes.byref(d), ctypes.byref(p)), "psolve_plan_inspect")
+    return {"n_modes": p.n_modes,
+            "levels": [(p.level_n_r[l], p.level_n_tz[l]) for l in range(p.n_levels)],
+            "coarsest": COARSE_FORMS[p.coarsest], "coarse_doubles_per_mode": p.coarse_doubles_per_mode}
+
+
 def lib():
     """The loaded library; raises when it has not been built."""
     global _lib
@@ -88,6 +115,7 @@ def lib():
             "psolve_get_schedule": (I, [P, ctypes.POINTER(Schedule)]),
             "psolve_set_schedule": (I, [P, ctypes.POINTER(Schedule)]),
             "psolve_autotune": (I, [P, P, P, D, ctypes.POINTER(Schedule)]),
+            "psolve_plan_inspect": (I, [ctypes.POINTER(Desc), ctypes.POINTER(Plan)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

@@ -103,11 +103,9 @@ static void snapshot(psolve_ctx* h, SolveStats& s) {
   cudaMemcpyAsync(s.iter, h->mg.d_iter, sizeof(int), cudaMemcpyDeviceToDevice, h->st);
 }
 
-static int create_impl(psolve_t* out, const psolve_desc* din) {
-  auto t0 = std::chrono::steady_clock::now();
-  if (!out || !din) return fail(PSOLVE_ERR_ARG, "null argument");
-  *out = nullptr;
-  psolve_desc d = *din;
+// Checks a descriptor and fills its defaults (PSOLVE_OK or PSOLVE_ERR_ARG).
+static int prepare_desc(const psolve_desc& din, psolve_desc& d) {
+  d = din;
   if (d.geometry != PSOLVE_SPHERICAL && d.geometry != PSOLVE_CYLINDRICAL)
     return fail(PSOLVE_ERR_ARG, "geometry must be PSOLVE_SPHERICAL or PSOLVE_CYLINDRICAL");
   if (!pow2(d.n_r) || !pow2(d.n_tz) || d.n_r < 8 || d.n_tz < 8 || d.n_r > 1024 || d.n_tz > 1024)
@@ -134,21 +132,35 @@ static int create_impl(psolve_t* out, const psolve_desc* din) {
   if (d.n_sor <= 0) d.n_sor = 2;
   if (d.precision != PSOLVE_FP64 && d.precision != PSOLVE_MIXED)
     return fail(PSOLVE_ERR_ARG, "precision must be PSOLVE_FP64 or PSOLVE_MIXED");
+  return PSOLVE_OK;
+}
+
+// The finest plane's geometry of a prepared descriptor (host arithmetic only).
+static void make_geo(const psolve_desc& d, PlaneGeo& g, Law& rlaw, Law& tlaw) {
+  const int geo = d.geometry == PSOLVE_SPHERICAL ? SPH : CYL;
+  rlaw = Law{d.r_in, d.r_out, d.n_r, d.spacing == PSOLVE_LOG ? LOGS : UNI};
+  tlaw = Law{d.t_min, d.t_max, d.n_tz, UNI};
+  g.geometry = geo;
+  g.n_phi = d.n_phi;
+  g.G = d.G;
+  g.r = axis_from_law(geo == SPH ? 0 : 1, rlaw, 1, d.n_r);
+  g.t = axis_from_law(geo == SPH ? 2 : 3, tlaw, 1, d.n_tz);
+  g.build();
+}
+
+static int create_impl(psolve_t* out, const psolve_desc* din) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!out || !din) return fail(PSOLVE_ERR_ARG, "null argument");
+  *out = nullptr;
+  psolve_desc d;
+  if (const int rc = prepare_desc(*din, d)) return rc;
 
   std::unique_ptr<psolve_ctx> h(new psolve_ctx());
   h->d = d;
   h->A.alloc_fn = d.alloc_fn;
   h->A.free_fn = d.free_fn;
   h->A.user = d.alloc_user;
-  const int geo = d.geometry == PSOLVE_SPHERICAL ? SPH : CYL;
-  h->rlaw = Law{d.r_in, d.r_out, d.n_r, d.spacing == PSOLVE_LOG ? LOGS : UNI};
-  h->tlaw = Law{d.t_min, d.t_max, d.n_tz, UNI};
-  h->g.geometry = geo;
-  h->g.n_phi = d.n_phi;
-  h->g.G = d.G;
-  h->g.r = axis_from_law(geo == SPH ? 0 : 1, h->rlaw, 1, d.n_r);
-  h->g.t = axis_from_law(geo == SPH ? 2 : 3, h->tlaw, 1, d.n_tz);
-  h->g.build();
+  make_geo(d, h->g, h->rlaw, h->tlaw);
   h->M = d.n_phi / 2 + 1;
   const int M = h->M;
   const size_t plane = size_t(d.n_r) * d.n_tz;
@@ -252,6 +264,43 @@ static int create_impl(psolve_t* out, const psolve_desc* din) {
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = h.release();
   return PSOLVE_OK;
+}
+
+extern "C" int psolve_plan_inspect(const psolve_desc* din, psolve_plan* out) {
+  if (!din || !out) return fail(PSOLVE_ERR_ARG, "null argument");
+  psolve_desc d;
+  if (const int rc = prepare_desc(*din, d)) return rc;
+  try {
+    PlaneGeo g;
+    Law rl, tl;
+    make_geo(d, g, rl, tl);
+    const int M = d.n_phi / 2 + 1;
+    std::vector<int> modes(M);
+    for (int m = 0; m < M; ++m) modes[m] = m;
+    Hierarchy H;
+    std::string err;
+    if (!build_hierarchy(g, false, modes, H, err)) return fail(PSOLVE_ERR_ARG, "multigrid plan: " + err);
+    *out = psolve_plan{};
+    out->n_modes = M;
+    out->n_levels = int(H.lv.size());
+    for (int l = 0; l < out->n_levels && l < 16; ++l) {
+      out->level_n_r[l] = H.lv[l].g.r.n;
+      out->level_n_tz[l] = H.lv[l].g.t.n;
+    }
+    if (H.sep_stride > 0) {
+      out->coarsest = H.sep_sym ? PSOLVE_COARSE_SEPARABLE_MIRROR : PSOLVE_COARSE_SEPARABLE;
+      out->coarse_doubles_per_mode = H.sep_stride;
+    } else if (H.blk_n > 0) {
+      out->coarsest = PSOLVE_COARSE_BLOCK;
+      out->coarse_doubles_per_mode = H.blk_nt * H.blk_n * (H.blk_n + 2);
+    } else {
+      out->coarsest = PSOLVE_COARSE_DENSE;
+      out->coarse_doubles_per_mode = H.nc * H.nc;
+    }
+    return PSOLVE_OK;
+  } catch (const std::exception& e) {
+    return fail(PSOLVE_ERR_NOMEM, std::string("plan: ") + e.what());
+  }
 }
 
 extern "C" int psolve_create_ex(psolve_t* out, const psolve_desc* d) {

@@ -72,7 +72,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     import paper_2606_17636_gb300 as ps
     if not shutil.which("gcc"):
         pytest.skip("gcc not available")
-    mirrors = {"psolve_desc": ps.Desc, "psolve_stats": ps.Stats, "psolve_schedule": ps.Schedule}
+    mirrors = {"psolve_desc": ps.Desc, "psolve_stats": ps.Stats, "psolve_schedule": ps.Schedule,
+               "psolve_plan": ps.Plan}
     lines = ['#include <stdio.h>', '#include "psolve.h"', "int main(void) {"]
     for cname, py in mirrors.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))

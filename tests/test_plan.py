@@ -1,0 +1,87 @@
+"""The multigrid plan (psolve_plan_inspect), computed on the host with no
+GPU: the coarsening rule, the form of the exact coarsest solve (Sec. 3.3
+allows a direct solver) and its factor sizes, and argument checks."""
+import numpy as np
+import pytest
+
+from paper_2606_17636_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def ps():
+    import os
+    import paper_2606_17636_gb300 as m
+    if not os.path.exists(m.LIB_PATH):
+        from paper_2606_17636_gb300 import build
+        build.build()
+    return m
+
+
+def _coarsen(nr, nt):
+    """The coarsening reading: halve both sides while the short side exceeds
+    16, or exceeds 4 with more than 1024 cells."""
+    out = [(nr, nt)]
+    while True:
+        mn = min(nr, nt)
+        if not (mn > 16 or (mn > 4 and nr * nt > 1024)):
+            return out
+        nr, nt = nr // 2, nt // 2
+        out.append((nr, nt))
+
+
+def test_benchmark_grid_plan(ps):
+    p = ps.plan_inspect(wl.spec(wl.SPHERICAL, 256, 128, 256, wl.LOG, 0.05, 20.0))
+    assert p["n_modes"] == 129
+    assert p["levels"] == [(256, 128), (128, 64), (64, 32), (32, 16)]
+    # full theta range: the polar operator is mirror-symmetric about the equator
+    assert p["coarsest"] == "separable, mirror-symmetric"
+    nr, nt = p["levels"][-1]
+    # half of V and of V^-1 (nt^2 in all), three Thomas factor tables nt x nr
+    assert p["coarse_doubles_per_mode"] == nt * nt + 3 * nt * nr
+
+
+@pytest.mark.parametrize("nr,nt", [(8, 8), (16, 8), (32, 32), (64, 16), (128, 8), (256, 16), (8, 128),
+                                   (512, 256), (1024, 64), (64, 1024)])
+def test_levels_follow_the_coarsening_rule(ps, nr, nt):
+    p = ps.plan_inspect(wl.spec(wl.CYLINDRICAL, nr, nt, 8, wl.UNIFORM, 0.2, 1.0))
+    assert p["levels"] == _coarsen(nr, nt)
+
+
+def test_off_centre_polar_range_takes_the_general_separable_form(ps):
+    p = ps.plan_inspect(wl.spec(wl.SPHERICAL, 32, 32, 8, wl.UNIFORM, 1.0, 2.0, 0.3 * np.pi, 0.65 * np.pi))
+    assert p["coarsest"] == "separable"
+    nr, nt = p["levels"][-1]
+    assert p["coarse_doubles_per_mode"] == (2 * nt * nt + 3 * nt * nr + 1) // 2 * 2
+
+
+@pytest.mark.parametrize("sp", [
+    wl.spec(wl.SPHERICAL, 64, 32, 16, wl.LOG, 0.1, 10.0),                          # full theta
+    wl.spec(wl.SPHERICAL, 32, 32, 8, wl.UNIFORM, 1.0, 2.0, 0.25 * np.pi, 0.75 * np.pi),  # centred range
+    wl.spec(wl.CYLINDRICAL, 32, 64, 8, wl.UNIFORM, 0.2, 1.0, -0.3, 0.5),          # uniform z, any range
+])
+def test_mirror_symmetric_polar_operators(ps, sp):
+    assert ps.plan_inspect(sp)["coarsest"] == "separable, mirror-symmetric"
+
+
+def test_many_polar_cells_on_the_coarsest_level_take_block_factors(ps):
+    # 8 x 128 is not coarsened (short side 8, 1024 cells); 128 polar cells
+    # exceed the separable form's 64, so the polar rows become 8 x 8 blocks
+    p = ps.plan_inspect(wl.spec(wl.CYLINDRICAL, 8, 128, 8, wl.UNIFORM, 0.2, 1.0))
+    assert p["levels"] == [(8, 128)]
+    assert p["coarsest"] == "block-tridiagonal"
+    assert p["coarse_doubles_per_mode"] == 128 * 8 * (8 + 2)
+
+
+@pytest.mark.parametrize("bad,word", [
+    (dict(n_r=24), "power"),
+    (dict(spacing=wl.LOG, r_in=0.0), "r_in"),
+    (dict(n_r=512, n_tz=8), "16"),
+    (dict(t_min=-0.5, t_max=1.0), "theta"),
+])
+def test_invalid_descriptors_are_rejected(ps, bad, word):
+    sp = dict(wl.spec(wl.SPHERICAL, 32, 32, 8, wl.UNIFORM, 0.5, 2.0))
+    sp.update(bad)
+    with pytest.raises(ps.PSolveError) as e:
+        ps.plan_inspect(sp)
+    assert e.value.code == ps.ERR_ARG
+    assert word in str(e.value)
