@@ -1006,11 +1006,11 @@ extern "C" int psolve_stage_smooth_static(psolve_t h, int level, int precision, 
   if (precision)
     launch_smooth<float>(L, B, static_cast<float2*>(e), static_cast<const float2*>(f),
                          reinterpret_cast<float2*>(base + list_bytes), cycles, h->mg.opt.n_sor,
-                         false, nullptr, nullptr, h->mg.opt.tiles, h->st);
+                         false, h->mg.opt.tiles, h->st);
   else
     launch_smooth<double>(L, B, static_cast<double2*>(e), static_cast<const double2*>(f),
                           reinterpret_cast<double2*>(base + list_bytes), cycles, h->mg.opt.n_sor,
-                          false, nullptr, nullptr, h->mg.opt.tiles, h->st);
+                          false, h->mg.opt.tiles, h->st);
   return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("smooth_static") ? PSOLVE_OK
                                                                                    : PSOLVE_ERR_CUDA;
 }

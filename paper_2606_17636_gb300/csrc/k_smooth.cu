@@ -13,8 +13,7 @@
 // all planes with the widest tiles; when only a few planes are active the
 // blocks are spread over them with narrower tiles (up to 4x more blocks per
 // plane, at least two lines or columns per block so that a block's first
-// line or column keeps colour 0), so a lone slow mode still uses many SMs.  The first post-smoothing radial pass of a level can add the
-// bilinear coarse correction to every value it loads (prolongation fused).
+// line or column keeps colour 0), so a lone slow mode still uses many SMs.
 #include <cstdio>
 
 #include "lines.cuh"
@@ -30,10 +29,6 @@ __device__ __forceinline__ int spread(int base, int nact, int cap) {
   return mult;
 }
 
-struct Corr {          // fused prolongation source (ec == nullptr: none)
-  LevelDev C;
-  const void* ec;
-};
 
 // Radial pass, both colours: a block of 32 Wmax threads owns W lines
 // [j0, j0+W), W = Wmax / mult.
@@ -60,7 +55,7 @@ template <typename T, int CPL>
 __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_t<T>* __restrict__ ein,
                                                 vec2_t<T>* __restrict__ eout,
                                                 const vec2_t<T>* __restrict__ f, int zero_init,
-                                                int n_sor, Corr corr, int Wmax) {
+                                                int n_sor, int Wmax) {
   typedef vec2_t<T> V;
   extern __shared__ __align__(16) unsigned char sraw[];
   const int nact = *B.nact;
@@ -73,7 +68,6 @@ __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_
   const int j0 = (b - k * per) * W;
   const int p = B.act[k];
   const int slot = B.slot ? B.slot[p] : p;
-  const int m = B.mode[slot];
   const int nr = L.nr, nt = L.nt;
   V* se = reinterpret_cast<V*>(sraw);   // e lines j0-1 .. j0+W+1 (line j at se + (j - j0 + 1) nr)
   V* sf = se + size_t(W + 3) * nr;       // f lines j0 .. j0+W
@@ -86,17 +80,6 @@ __global__ void __launch_bounds__(256) k_rpass2(LevelDev L, Batch B, const vec2_
   __syncthreads();
   const T* rt = rt_<T>(L);
   const T* tt = tt_<T>(L);
-  if (corr.ec) {   // fused prolongation: add the coarse correction to the staged e lines
-    const V* ec = static_cast<const V*>(corr.ec) + size_t(p) * corr.C.nr * corr.C.nt;
-    for (int idx = threadIdx.x; idx < (W + 3) * nr; idx += blockDim.x) {
-      const int q = idx / nr, i = idx - q * nr, j = j0 - 1 + q;
-      if (j < 0 || j >= nt) continue;
-      const V d = prolong_at<T>(L, rt, tt, corr.C, ec, i, j, m);
-      se[idx].x += d.x;
-      se[idx].y += d.y;
-    }
-    __syncthreads();
-  }
   const T s2 = s2_<T>(B, slot);
   const T* om = omr_<T>(L) + size_t(slot) * nt;
   auto eline = [&](int j) { return se + size_t(j - j0 + 1) * nr; };
@@ -230,7 +213,7 @@ int smooth_tile_cols(int nr, int nt, size_t vb, int want) { return tile_w(nr, nt
 
 template <typename T, int CPL>
 static void rpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                   const vec2_t<T>* f, bool zi, int n_sor, const Corr& corr, int Wmax,
+                   const vec2_t<T>* f, bool zi, int n_sor, int Wmax,
                    cudaStream_t st) {
   // e lines (W + 3), f lines (W + 1) and relaxed colour-0 lines (W / 2 + 1)
   const size_t sm = size_t(Wmax + 3 + Wmax + 1 + Wmax / 2 + 1) * L.nr * sizeof(vec2_t<T>);
@@ -240,7 +223,7 @@ static void rpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2
     attr = true;
   }
   dim3 grid((L.nt + Wmax - 1) / Wmax, B.max_planes);
-  k_rpass2<T, CPL><<<grid, 32 * Wmax, sm, st>>>(L, B, ein, eout, f, zi ? 1 : 0, n_sor, corr, Wmax);
+  k_rpass2<T, CPL><<<grid, 32 * Wmax, sm, st>>>(L, B, ein, eout, f, zi ? 1 : 0, n_sor, Wmax);
 }
 
 template <typename T, int CPL>
@@ -259,15 +242,15 @@ static void tpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2
 
 template <typename T>
 static void rpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                       const vec2_t<T>* f, bool zi, int n_sor, const Corr& corr, int Wmax,
+                       const vec2_t<T>* f, bool zi, int n_sor, int Wmax,
                        cudaStream_t st) {
   switch (L.nr <= 32 ? 1 : L.nr / 32) {
-    case 1: rpass2<T, 1>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
-    case 2: rpass2<T, 2>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
-    case 4: rpass2<T, 4>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
-    case 8: rpass2<T, 8>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
-    case 16: rpass2<T, 16>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
-    case 32: rpass2<T, 32>(L, B, ein, eout, f, zi, n_sor, corr, Wmax, st); break;
+    case 1: rpass2<T, 1>(L, B, ein, eout, f, zi, n_sor, Wmax, st); break;
+    case 2: rpass2<T, 2>(L, B, ein, eout, f, zi, n_sor, Wmax, st); break;
+    case 4: rpass2<T, 4>(L, B, ein, eout, f, zi, n_sor, Wmax, st); break;
+    case 8: rpass2<T, 8>(L, B, ein, eout, f, zi, n_sor, Wmax, st); break;
+    case 16: rpass2<T, 16>(L, B, ein, eout, f, zi, n_sor, Wmax, st); break;
+    case 32: rpass2<T, 32>(L, B, ein, eout, f, zi, n_sor, Wmax, st); break;
     default: std::fprintf(stderr, "psolve: radial size %d unsupported\n", L.nr);
   }
 }
@@ -288,25 +271,18 @@ static void tpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, 
 
 template <typename T>
 void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
-                   vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, const LevelDev* C,
-                   const vec2_t<T>* ec, Tiles tiles, cudaStream_t st) {
+                   vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, Tiles tiles,
+                   cudaStream_t st) {
   const int Wmax = tiles.lines_r == 4 ? 4 : 8;
   for (int c = 0; c < cycles; ++c) {
-    Corr corr{};
-    if (c == 0 && ec) {
-      corr.C = *C;
-      corr.ec = ec;
-    }
-    rpass2_any<T>(L, B, e, tmp, f, zero_init && c == 0, n_sor, corr, Wmax, st);
+    rpass2_any<T>(L, B, e, tmp, f, zero_init && c == 0, n_sor, Wmax, st);
     tpass2_any<T>(L, B, tmp, e, f, n_sor, tiles.cols_t, st);
   }
 }
 
 template void launch_smooth<float>(const LevelDev&, const Batch&, float2*, const float2*, float2*,
-                                   int, int, bool, const LevelDev*, const float2*, Tiles,
-                                   cudaStream_t);
+                                   int, int, bool, Tiles, cudaStream_t);
 template void launch_smooth<double>(const LevelDev&, const Batch&, double2*, const double2*,
-                                    double2*, int, int, bool, const LevelDev*, const double2*, Tiles,
-                                    cudaStream_t);
+                                    double2*, int, int, bool, Tiles, cudaStream_t);
 
 }  // namespace ps

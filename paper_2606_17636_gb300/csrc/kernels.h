@@ -69,12 +69,10 @@ struct Tiles {
 int smooth_tile_cols(int nr, int nt, size_t vb, int want);
 // `cycles` alternating-line smoothing cycles (k_smooth.cu); tmp is a
 // scratch buffer of the level's size (ping-pong between the two passes).
-// When ec != nullptr the first radial pass adds the bilinear correction
-// from the coarser level C (prolongation fused into post-smoothing).
 template <typename T>
 void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
-                   vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, const LevelDev* C,
-                   const vec2_t<T>* ec, Tiles tiles, cudaStream_t st);
+                   vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, Tiles tiles,
+                   cudaStream_t st);
 
 // Lower part of a V-cycle in shared memory, one block per plane (k_vsmem.cu).
 struct VSmemArgs {

@@ -373,40 +373,4 @@ __device__ __forceinline__ void relax_t(const LevelDev& L, const T* rt, const T*
   sor_line<T, CPL>(ev, g, up, dn, id, w, nt, n_sor);
 }
 
-// Bilinear coarse correction (Sec. 3.1, Eq. prolongation_sph) at fine cell
-// (i, j): coarse level C of plane p, parity sign of mode m at poles / axis.
-template <typename T>
-__device__ __forceinline__ vec2_t<T> coarse_at(const LevelDev& C, const vec2_t<T>* __restrict__ ec,
-                                               int I, int J, int m) {
-  typedef vec2_t<T> V;
-  T fac = T(1);
-  const T sgn = (m & 1) ? T(-1) : T(1);
-  int Ic = I, Jc = J;
-  if (I == 0) { if (C.gL == GH_ZERO) return z2<V>(); Ic = 1; if (C.gL == GH_PARITY) fac *= sgn; }
-  if (I == C.nr + 1) { if (C.gR == GH_ZERO) return z2<V>(); Ic = C.nr; if (C.gR == GH_PARITY) fac *= sgn; }
-  if (J == 0) { if (C.gB == GH_ZERO) return z2<V>(); Jc = 1; if (C.gB == GH_PARITY) fac *= sgn; }
-  if (J == C.nt + 1) { if (C.gT == GH_ZERO) return z2<V>(); Jc = C.nt; if (C.gT == GH_PARITY) fac *= sgn; }
-  V v = ec[size_t(Jc - 1) * C.nr + (Ic - 1)];
-  v.x *= fac;
-  v.y *= fac;
-  return v;
-}
-
-template <typename T>
-__device__ __forceinline__ vec2_t<T> prolong_at(const LevelDev& L, const T* rt, const T* tt,
-                                                const LevelDev& C, const vec2_t<T>* __restrict__ ec,
-                                                int i, int j, int m) {
-  typedef vec2_t<T> V;
-  const int i1 = i + 1, j1 = j + 1, NR = L.nr + 2, NT = L.nt + 2;
-  const int I1 = (i1 & 1) ? (i1 + 1) / 2 - 1 : i1 / 2, J1 = (j1 & 1) ? (j1 + 1) / 2 - 1 : j1 / 2;
-  const T p1 = rt[RT_P1 * NR + i1], p2 = rt[RT_P2 * NR + i1];
-  const T q1 = tt[TT_P1 * NT + j1], q2 = tt[TT_P2 * NT + j1];
-  const V a = coarse_at<T>(C, ec, I1, J1, m), b = coarse_at<T>(C, ec, I1 + 1, J1, m);
-  const V c = coarse_at<T>(C, ec, I1, J1 + 1, m), d = coarse_at<T>(C, ec, I1 + 1, J1 + 1, m);
-  V r;
-  r.x = p1 * q1 * a.x + p2 * q1 * b.x + p1 * q2 * c.x + p2 * q2 * d.x;
-  r.y = p1 * q1 * a.y + p2 * q1 * b.y + p1 * q2 * c.y + p2 * q2 * d.y;
-  return r;
-}
-
 }  // namespace ps

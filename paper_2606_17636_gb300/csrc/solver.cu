@@ -242,15 +242,13 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
 }
 
 // ---- typed dispatch -----------------------------------------------------------
-void MGSolver::smooth(int l, void* ee, const void* ff, int cycles, bool zi, cudaStream_t st,
-                      const void* ec) {
-  const LevelDev* C = ec ? &lv[l + 1] : nullptr;
+void MGSolver::smooth(int l, void* ee, const void* ff, int cycles, bool zi, cudaStream_t st) {
   if (opt.precision)
     launch_smooth<float>(lv[l], batch, (float2*)ee, (const float2*)ff, (float2*)tmp, cycles,
-                         opt.n_sor, zi, C, (const float2*)ec, opt.tiles, st);
+                         opt.n_sor, zi, opt.tiles, st);
   else
     launch_smooth<double>(lv[l], batch, (double2*)ee, (const double2*)ff, (double2*)tmp, cycles,
-                          opt.n_sor, zi, C, (const double2*)ec, opt.tiles, st);
+                          opt.n_sor, zi, opt.tiles, st);
 }
 void MGSolver::restrict_(int l, const void* ee, const void* ff, void* fc, cudaStream_t st) {
   if (opt.precision)

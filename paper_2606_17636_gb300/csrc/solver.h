@@ -66,8 +66,7 @@ class MGSolver {
   int zero_guess = 0;              // the next solve starts from u = 0 (set by the caller)
   VSmemArgs vs{};
   // stage helpers on explicit buffers
-  void smooth(int level, void* e, const void* f, int cycles, bool zero_init, cudaStream_t st,
-              const void* ec = nullptr);
+  void smooth(int level, void* e, const void* f, int cycles, bool zero_init, cudaStream_t st);
   void restrict_(int level, const void* e, const void* f, void* fc, cudaStream_t st);
   void prolong(int level, void* e, const void* ec, cudaStream_t st);
   void fused(cudaStream_t st);   // levels first .. coarsest in shared memory
