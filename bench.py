@@ -416,10 +416,9 @@ def launches_per_solve(s, st):
 # 2 passes each; defect restriction and prolongation add 40 (424 for the
 # default schedule nu = (2, 2), n_sor = 2).
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu capture summarised in profiles/k_vsmem_256x128x256.md (workload 3,
-# all 129 modes).  They hold for the kernel as captured; a changed kernel
-# needs a new capture.  The smoothing passes changed after theirs
-# (profiles/k_rpass2_k_tpass2_256x128x256.md), so their traffic is not
+# the ncu --set full capture of k_vsmem on workload 3 (all 129 modes).  They
+# hold for the kernel as captured; a changed kernel needs a new capture.  The
+# smoothing passes changed after their capture, so their traffic is not
 # reported.
 VSMEM_TRAFFIC_BYTES = 12149760
 SMOOTH_CYCLE_TRAFFIC_BYTES = None
