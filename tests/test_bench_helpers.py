@@ -1,0 +1,62 @@
+"""The bench's own arithmetic, checked on the CPU: the volume weights of its
+accuracy figure, the FP32 work per cell it divides by for the fused
+V-cycle's roofline, and its count of kernel launches per solve."""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import SMALL, oracle_plane
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("key", list(SMALL))
+def test_cell_volumes_are_the_oracles_volume_weights(bench, key):
+    a = bench.cell_volumes(SMALL[key])
+    b = oracle_plane(SMALL[key]).volume_weights()
+    ratio = a / b
+    # the same weights up to the constant azimuthal factor
+    assert np.allclose(ratio, ratio.flat[0], rtol=1e-12, atol=0)
+
+
+def test_vcycle_flops_per_cell(bench):
+    base = dict(nu_pre=2, nu_post=2, n_sor=2, nu_pre_fused=0, nu_post_fused=0)
+    # two passes per cycle, (16 + 16 N_SOR) per pass, 40 for the transfers
+    assert bench.vcycle_flops_per_cell(base) == 4 * 2 * 48 + 40 == 424
+    assert bench.vcycle_flops_per_cell(dict(base, n_sor=1)) == 4 * 2 * 32 + 40
+    # the fused levels' own counts replace the level-wide ones
+    assert bench.vcycle_flops_per_cell(dict(base, nu_pre_fused=3, nu_post_fused=3)) == 6 * 2 * 48 + 40
+
+
+class _FakeSolver:
+    def __init__(self, sched, first):
+        self._s, self._f = sched, first
+
+    def schedule(self):
+        return self._s
+
+    def fused_level(self):
+        return self._f
+
+
+def test_launches_per_solve_counts_the_loop_body(bench):
+    """One iteration at the benchmark's shape (fused from level 1, nu = (2, 2)):
+    residual, 2 x 2 smoothing passes, restriction, fused V-cycle,
+    prolongation, 2 x 2 passes, update = 13 launches; a solve adds 8 fixed
+    launches and runs each loop body once per residual evaluation."""
+    s = _FakeSolver(dict(nu_pre=2, nu_post=2, n_sor=1), 1)
+    st = {"iterations_psi": 21, "iterations_phi": 16}
+    assert bench.launches_per_solve(s, st) == 8 + 13 * (22 + 17)
+    s = _FakeSolver(dict(nu_pre=3, nu_post=1, n_sor=2), 2)
+    # two level-wide levels: each 2 x 3 + 1 + 1 + 2 x 1 = 10 launches
+    assert bench.launches_per_solve(s, st) == 8 + (1 + 2 * 10 + 1 + 1) * (22 + 17)
