@@ -175,14 +175,15 @@ int psolve_set_schedule(psolve_t h, const psolve_schedule* s);
 /* Autotuner: picks the smoothing schedule and tile shapes of this handle by
  * timing solves of rho (device pointer, layout as psolve_solve) to tolerance
  * tol on the handle's stream, and installs the fastest.
- *   Stage 1, schedules: nu_post <= nu_pre <= 3, n_sor <= 3 (18 candidates,
- *     the handle's current schedule first).  Schedules with more post- than
+ *   Stage 1, schedules: nu_post <= nu_pre <= 3, n_sor <= 3 (18 schedules,
+ *     after the handle's current one when that lies outside them).  Schedules with more post- than
  *     pre-smoothing are not tried: they leave a smoother final residual, whose
  *     error at the same tolerance is larger.
  *   Stage 2, tile shapes: lines_r in {4, 8} x cols_t in {8, 16, 32} with the
  *     stage-1 schedule (shapes that reduce to the same launch are timed once).
- *   Stage 3, the fused levels' own smoothing counts: nu_post_fused <=
- *     nu_pre_fused <= 3 with the stage-1 and stage-2 choices (5 candidates
+ *   Stage 3, when the fused shared-memory V-cycle smooths at least one
+ *     level: that kernel's own smoothing counts, nu_post_fused <=
+ *     nu_pre_fused <= 3, with the stage-1 and stage-2 choices (5 candidates
  *     besides the stage-1 counts).
  * Each candidate runs one untimed solve (graph capture, caches), then three
  * timed solves (CUDA events on the handle's stream); its time is their
@@ -192,10 +193,9 @@ int psolve_set_schedule(psolve_t h, const psolve_schedule* s);
  * Choices are cached per process by the key (geometry, sizes, spacing,
  * extents, precision): a later call with the same key installs the cached
  * choice without timing.  When the environment variable PSOLVE_TUNE_CACHE
- * names a file, it is read on a process-cache miss (text, one line per key:
- * key nu_pre nu_post n_sor lines_r cols_t nu_pre_fused nu_post_fused ms; the
- * last line of a key wins)
- * and every new choice is appended to it.
+ * names a file, it is read on a process-cache miss and every new choice is
+ * appended to it (text, one line per key: key nu_pre nu_post n_sor lines_r
+ * cols_t nu_pre_fused nu_post_fused ms; the last line of a key wins).
  * out (may be NULL) receives the choice.  Returns PSOLVE_OK, or the error of
  * the solve with the handle's current schedule, which then stays installed. */
 int psolve_autotune(psolve_t h, const double* rho, double* phi, double tol,
