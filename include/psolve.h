@@ -116,6 +116,9 @@ typedef struct {
   int level_n_r[16], level_n_tz[16];
   int coarsest;                /* PSOLVE_COARSE_*                                   */
   int coarse_doubles_per_mode; /* FP64 values of the coarsest-level factors per mode */
+  double coarse_check;         /* separable forms: the largest relative residual, over
+                                  the modes, of the factors applied to a fixed test
+                                  vector (rounding level when sound); else -1     */
 } psolve_plan;
 /* PSOLVE_ERR_ARG (with a message) for an invalid descriptor, as psolve_create_ex. */
 int psolve_plan_inspect(const psolve_desc* d, psolve_plan* out);

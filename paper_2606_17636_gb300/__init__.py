@@ -56,7 +56,8 @@ class Schedule(ctypes.Structure):
 class Plan(ctypes.Structure):
     _fields_ = [("n_modes", ctypes.c_int), ("n_levels", ctypes.c_int),
                 ("level_n_r", ctypes.c_int * 16), ("level_n_tz", ctypes.c_int * 16),
-                ("coarsest", ctypes.c_int), ("coarse_doubles_per_mode", ctypes.c_int)]
+                ("coarsest", ctypes.c_int), ("coarse_doubles_per_mode", ctypes.c_int),
+                ("coarse_check", ctypes.c_double)]
 
 
 COARSE_FORMS = {0: "separable, mirror-symmetric", 1: "separable", 2: "block-tridiagonal", 3: "dense"}
@@ -77,7 +78,8 @@ def plan_inspect(spec, precision=1):
     check(lib().psolve_plan_inspect(ctypes.byref(d), ctypes.byref(p)), "psolve_plan_inspect")
     return {"n_modes": p.n_modes,
             "levels": [(p.level_n_r[l], p.level_n_tz[l]) for l in range(p.n_levels)],
-            "coarsest": COARSE_FORMS[p.coarsest], "coarse_doubles_per_mode": p.coarse_doubles_per_mode}
+            "coarsest": COARSE_FORMS[p.coarsest], "coarse_doubles_per_mode": p.coarse_doubles_per_mode,
+            "coarse_check": p.coarse_check}
 
 
 def lib():

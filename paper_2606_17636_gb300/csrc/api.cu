@@ -290,12 +290,15 @@ extern "C" int psolve_plan_inspect(const psolve_desc* din, psolve_plan* out) {
     if (H.sep_stride > 0) {
       out->coarsest = H.sep_sym ? PSOLVE_COARSE_SEPARABLE_MIRROR : PSOLVE_COARSE_SEPARABLE;
       out->coarse_doubles_per_mode = H.sep_stride;
+      out->coarse_check = H.sep_check;
     } else if (H.blk_n > 0) {
       out->coarsest = PSOLVE_COARSE_BLOCK;
       out->coarse_doubles_per_mode = H.blk_nt * H.blk_n * (H.blk_n + 2);
+      out->coarse_check = -1.0;
     } else {
       out->coarsest = PSOLVE_COARSE_DENSE;
       out->coarse_doubles_per_mode = H.nc * H.nc;
+      out->coarse_check = -1.0;
     }
     return PSOLVE_OK;
   } catch (const std::exception& e) {

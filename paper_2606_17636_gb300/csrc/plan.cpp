@@ -220,8 +220,8 @@ static bool mirror_symmetric(const std::vector<double>& S, const std::vector<dou
 // to out; sym selects the mirror-symmetric layout (the polar eigenvectors
 // taken in the even / odd subspaces).  Returns false when the operator does
 // not split this way (or is not mirror-symmetric, for sym) or the factors
-// fail the residual check.
-static bool separable_factors(const PlaneGeo& g, int m, double* out, bool sym) {
+// fail the residual check; *resid receives the check's relative residual.
+static bool separable_factors(const PlaneGeo& g, int m, double* out, bool sym, double* resid) {
   const int nr = g.r.n, nt = g.t.n, h = nt / 2;
   const double s2 = g.s2(m);
   const bool sph = g.geometry == SPH;
@@ -349,6 +349,7 @@ static bool separable_factors(const PlaneGeo& g, int m, double* out, bool sym) {
       rn += (ax - b[q]) * (ax - b[q]);
       bn += b[q] * b[q];
     }
+  *resid = std::sqrt(rn / bn);
   return rn <= 1e-20 * bn;   // 1e-10 relative: a sound factorisation (rounding only)
 }
 
@@ -472,10 +473,16 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
       H.sep_stride = ((sym ? 1 : 2) * nt * nt + 3 * nt * nr + 1) / 2 * 2;
       H.coarse_sep.assign(size_t(M) * H.sep_stride, 0.0);
       bool ok = true;
-      for (int k = 0; k < M && ok; ++k)
-        ok = separable_factors(C.g, modes[k], H.coarse_sep.data() + size_t(k) * H.sep_stride, sym != 0);
+      double worst = 0.0;
+      for (int k = 0; k < M && ok; ++k) {
+        double res = 0.0;
+        ok = separable_factors(C.g, modes[k], H.coarse_sep.data() + size_t(k) * H.sep_stride, sym != 0,
+                               &res);
+        worst = std::fmax(worst, res);
+      }
       if (ok) {
         H.sep_sym = sym;
+        H.sep_check = worst;
         return true;
       }
     }

@@ -90,6 +90,7 @@ struct Hierarchy {
   std::vector<double> coarse_sep;
   int sep_stride = 0;
   int sep_sym = 0;
+  double sep_check = -1.0;   // largest relative residual of the factors' check over the modes
 };
 
 // Build levels (coarsening stops at a short side of 8 cells, or 4 cells when

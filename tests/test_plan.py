@@ -85,3 +85,28 @@ def test_invalid_descriptors_are_rejected(ps, bad, word):
         ps.plan_inspect(sp)
     assert e.value.code == ps.ERR_ARG
     assert word in str(e.value)
+
+
+@pytest.mark.parametrize("sp,bound", [
+    # full theta: the poles make the polar weights span a wide range, and the
+    # factors' residual sits near 1e-12 in either separable form
+    (wl.spec(wl.SPHERICAL, 256, 128, 16, wl.LOG, 0.05, 20.0), 1e-11),
+    (wl.spec(wl.SPHERICAL, 128, 64, 16, wl.LOG, 0.1, 10.0), 1e-12),
+    # away from the poles both forms reach rounding level
+    (wl.spec(wl.SPHERICAL, 256, 128, 16, wl.LOG, 0.05, 20.0, 0.3 * np.pi, 0.7 * np.pi), 1e-13),
+    (wl.spec(wl.SPHERICAL, 32, 32, 8, wl.UNIFORM, 1.0, 2.0, 0.3 * np.pi, 0.65 * np.pi), 1e-13),
+    (wl.spec(wl.CYLINDRICAL, 64, 64, 16, wl.UNIFORM, 0.0, 1.0), 1e-13),
+    (wl.spec(wl.CYLINDRICAL, 512, 256, 16, wl.UNIFORM, 0.2, 4.0, -1.0, 1.0), 1e-13),
+])
+def test_coarsest_factors_solve_the_coarsest_operator(ps, sp, bound):
+    """The separable factors applied to a fixed vector, in the kernel's order
+    of operations, against the coarsest operator applied to the result: the
+    largest relative residual over all modes."""
+    p = ps.plan_inspect(sp)
+    assert p["coarsest"].startswith("separable")
+    assert 0.0 <= p["coarse_check"] <= bound, p
+
+
+def test_block_factors_report_no_separable_check(ps):
+    p = ps.plan_inspect(wl.spec(wl.CYLINDRICAL, 8, 128, 8, wl.UNIFORM, 0.2, 1.0))
+    assert p["coarsest"] == "block-tridiagonal" and p["coarse_check"] == -1.0
