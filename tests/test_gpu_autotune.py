@@ -10,7 +10,6 @@ import os
 import subprocess
 import sys
 
-import numpy as np
 import pytest
 
 from gpu_helpers import clumps
@@ -64,7 +63,6 @@ def test_tile_shapes_give_bitwise_equal_solves(ps, key, precision):
 
 
 def test_schedule_changes_cycles_not_the_answer(ps):
-    from paper_2606_17636_gb300 import workloads as wl
     sp = _wide_level_specs()["sph_log"]
     rho = torch.from_numpy(clumps(sp, 42)).cuda()
     s = ps.Solver.from_spec(sp, precision=ps.FP64)
