@@ -60,3 +60,14 @@ def test_launches_per_solve_counts_the_loop_body(bench):
     s = _FakeSolver(dict(nu_pre=3, nu_post=1, n_sor=2), 2)
     # two level-wide levels: each 2 x 3 + 1 + 1 + 2 x 1 = 10 launches
     assert bench.launches_per_solve(s, st) == 8 + (1 + 2 * 10 + 1 + 1) * (22 + 17)
+
+
+def test_oracle_timings_runs_the_full_oracle_solve(bench):
+    """The CPU baseline times whole oracle solves (every mode, real DGF
+    tables) in a spawned pool and in one process."""
+    from gpu_helpers import clumps
+    sp = SMALL["cyl_cavity"]
+    tm = bench.oracle_timings(clumps(sp, 1), sp, warmup=1, steps=2, procs=2, single_thread_repeats=1)
+    assert tm["procs"] == 2 and tm["dgf_setup_s"] > 0
+    assert len(tm["solve_s"]) == 2 and all(t > 0 for t in tm["solve_s"])
+    assert len(tm["solve_1thread_s"]) == 1 and tm["solve_1thread_s"][0] > 0
