@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpsolve.so")
-SOURCES = ["plan.cpp", "k_fft.cu", "k_mg.cu", "k_smooth.cu", "k_vsmem.cu", "k_bc.cu", "k_dgf.cu",
+SOURCES = ["plan.cpp", "k_fft.cu", "k_mg.cu", "k_smooth.cu", "k_vsmem.cu", "k_bc.cu", "k_dgf.cu", "k_tail.cu",
            "dgf_host.cu", "solver.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

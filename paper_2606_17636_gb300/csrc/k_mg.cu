@@ -238,7 +238,7 @@ __device__ Sum4 block_sum4(Sum4 v, Sum4* sh) {
 
 __device__ void retire_block(int* act, int* nact, const Sum4* __restrict__ psum, RetireState S,
                              double tol, int max_cycles, int stagnation, int use_cond,
-                             unsigned long long handle, int* scan);
+                             unsigned long long handle, int* scan, int tail_planes);
 
 // FP64 defect at (i, j) from the per-cell products (one FP64 operation for
 // the mode's diagonal, five per component for the stencil).
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
       if (glast) {   // every plane's sum is in: retire converged planes (App. B)
         __threadfence();
         retire_block(const_cast<int*>(B.act), const_cast<int*>(B.nact), psum, ra.S, ra.tol,
-                     ra.max_cycles, ra.stagnation, ra.use_cond, ra.handle, scan);
+                     ra.max_cycles, ra.stagnation, ra.use_cond, ra.handle, scan, ra.tail_planes);
         if (threadIdx.x == 0) *ra.gcnt = 0;
       }
     }
@@ -371,7 +371,7 @@ void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const 
 
 __device__ void retire_block(int* act, int* nact, const Sum4* __restrict__ psum, RetireState S,
                              double tol, int max_cycles, int stagnation, int use_cond,
-                             unsigned long long handle, int* scan) {
+                             unsigned long long handle, int* scan, int tail_planes) {
   __shared__ double smax[32];
   __shared__ int base_out;
   const int n = *nact;
@@ -440,10 +440,13 @@ __device__ void retire_block(int* act, int* nact, const Sum4* __restrict__ psum,
     __syncthreads();
   }
   if (tid == 0) {
+    // continue flag: 0 done, 1 another batched iteration, 2 this iteration's
+    // V-cycle and update, then the tail kernel finishes the remaining planes
+    const int cont = base_out == 0 ? 0 : (base_out > tail_planes ? 1 : 2);
     *nact = base_out;
     *S.iter = iter + 1;
-    *S.cont = base_out > 0 ? 1 : 0;
-    if (use_cond) cudaGraphSetConditional(handle, base_out > 0 ? 1u : 0u);
+    *S.cont = cont;
+    if (use_cond) cudaGraphSetConditional(handle, cont == 1 ? 1u : 0u);
   }
 }
 

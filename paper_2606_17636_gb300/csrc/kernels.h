@@ -130,6 +130,7 @@ struct RetireArgs {
   unsigned long long handle;   // graph conditional (use_cond)
   int* gcnt;                   // completion counter, zero between launches
   int zero_guess;              // u is zero on the first iteration: r = f there
+  int tail_planes;             // hand over to the tail kernel once at most this many remain (0: never)
 };
 
 // r = f - L u (FP64), stored as T2, and the volume-weighted norms per plane
@@ -147,6 +148,45 @@ void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const 
 int residual_blocks(int nr, int nt);
 
 void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t st);
+
+// ---- cluster-resident tail iterations (k_tail.cu) ------------------------------
+// One level of the tail kernel's per-CTA layout: each CTA of a cluster owns
+// `s` consecutive rows of the level (rows rank * s ..), keeps them in shared
+// memory (eo), plus two buffers of the 2h rows around them owned by its
+// neighbours (eh0 / eh1, alternating between smoothing steps) and the
+// right-hand side of its rows and their halo (fo, rows -h .. s + h - 1).
+// Offsets in complex FP32 elements.
+struct TailLevel {
+  LevelDev L;        // global tables, ghost rules
+  int s;             // rows per CTA
+  int eo, eh0, eh1, fo;
+  int tab;           // offset (floats) of this level's tables in a slot's packed block
+  int nu1, nu2;      // smoothing cycles before / after the coarse correction
+};
+struct TailArgs {
+  int nlev, C, h, n_sor;    // levels, CTAs per cluster, halo rows, SOR sweeps per line
+  TailLevel lv[8];
+  const float* tabs;        // per-slot packed FP32 tables of every level
+  int tab_stride;           // floats per slot
+  int tab_off, g_off, z_off, zl_off, u_off, part_off;   // shared-memory byte offsets
+  size_t smem_bytes;
+  const double* ctab;       // level-0 per-cell FP64 products [4][nt][nr]
+  const double* sep;        // separable coarsest-level factors per slot
+  int sep_stride, sep_sym;
+  double tol;
+  int max_cycles, stagnation;
+  int* titer;               // scratch: max iteration count over the clusters
+  int* tdone;               // scratch: clusters finished
+};
+// Finishes the active planes B.act[0..*B.nact) (at most `clusters`) with one
+// cluster of a.C CTAs per plane, iterating residual -> V-cycle -> update on
+// chip until each plane meets the App. B criterion (FP32 V-cycles, FP64
+// residual and update: the mixed path).
+void launch_tail(const TailArgs& a, const Batch& B, const RetireState& S, const double2* f,
+                 double2* u, int clusters, cudaStream_t st);
+// Clusters of a.C CTAs with a.smem_bytes each that can be resident at once
+// (0 when the configuration cannot launch).
+int tail_max_clusters(const TailArgs& a);
 
 // ---- boundary treatment (k_bc.cu) ---------------------------------------------
 struct BDev {

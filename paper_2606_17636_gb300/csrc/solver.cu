@@ -236,6 +236,40 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   S.iter = d_iter;
   S.cont = d_cont;
   S.fmax2 = d_fmax2;
+  if (opt.precision) {
+    // per-slot packed FP32 tables of every level for the cluster-resident
+    // tail: per level, at the next odd element offset, RT_N x (nr+2) radial
+    // and TT_N x (nt+2) polar entries, then nt r-line and nr polar-line
+    // omegas of the slot
+    size_t tab = 0;
+    std::vector<size_t> off(nl);
+    for (int l = 0; l < nl && l < 8; ++l) {
+      tab = (tab + 1) / 2 * 2 + 1;
+      off[l] = tab;
+      tab += size_t(RT_N) * (lv[l].nr + 2) + size_t(TT_N) * (lv[l].nt + 2) + lv[l].nr + lv[l].nt;
+    }
+    tab = (tab + 3) / 4 * 4;
+    const size_t S_ = modes.size();
+    std::vector<float> pk(S_ * tab, 0.f);
+    for (size_t q = 0; q < S_; ++q)
+      for (int l = 0; l < nl && l < 8; ++l) {
+        const LevelHost& hl = H.lv[l];
+        const int nr = lv[l].nr, nt = lv[l].nt;
+        float* o = pk.data() + q * tab + off[l];
+        o = std::copy(hl.rtab.begin(), hl.rtab.end(), o);
+        o = std::copy(hl.ttab.begin(), hl.ttab.end(), o);
+        o = std::copy(hl.om_r.begin() + q * nt, hl.om_r.begin() + (q + 1) * nt, o);
+        std::copy(hl.om_t.begin() + q * nr, hl.om_t.begin() + (q + 1) * nr, o);
+      }
+    d_tail_tabs = upload(A, pk);
+    tl.tab_stride = int(tab);
+    for (int l = 0; l < nl && l < 8; ++l) tl.lv[l].tab = int(off[l]);
+    tl.titer = static_cast<int*>(A.get(2 * sizeof(int)));
+    tl.tdone = tl.titer ? tl.titer + 1 : nullptr;
+    if (!d_tail_tabs || !tl.titer) { err = "out of device memory"; return false; }
+    cudaMemset(tl.titer, 0, 2 * sizeof(int));
+    prepare_tail();
+  }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { err = std::string("multigrid setup: ") + cudaGetErrorString(e); return false; }
   return true;
@@ -279,6 +313,7 @@ void MGSolver::residual(const double2* ff, const double2* u, double tol, cudaStr
   ra.handle = cond;
   ra.gcnt = d_gcnt;
   ra.zero_guess = zero_guess;
+  ra.tail_planes = tail_planes;
   if (opt.precision)
     launch_residual<float>(lv[0], batch, ff, u, (float2*)f[0], d_part, d_psum, d_cnt, ra, st, d_ctab);
   else
@@ -312,6 +347,83 @@ void MGSolver::set_schedule(int nu1, int nu2, int n_sor, Tiles tiles, int nu1f, 
   vs.nu2 = nu2f > 0 ? nu2f : nu2;
   opt.n_sor = vs.n_sor = n_sor;
   opt.tiles = tiles;
+  prepare_tail();
+}
+
+// Layout of the cluster-resident tail for the current schedule.  Needs the
+// mixed path, a separable coarsest level, a cluster size C (16, or the
+// coarsest level's polar cell count when smaller) that divides every level
+// into slabs of an even number of rows (one row or more on the coarsest
+// level), radial lines of at most 256 cells, polar segments (own rows plus
+// h = 2 n_sor halo rows each side) of at most 24 cells, and a shared-memory
+// layout within the SM's 227 KB.
+bool MGSolver::prepare_tail() {
+  tail_planes = 0;
+  if (!opt.precision || tail_cap == 0 || !d_tail_tabs || H.sep_stride <= 0) return false;
+  const int nl = int(lv.size());
+  if (nl < 2 || nl > 8) return false;
+  const int h = 2 * opt.n_sor;
+  const int ntc = lv[nl - 1].nt, nrc = lv[nl - 1].nr;
+  int C = 16;
+  while (C > ntc) C /= 2;
+  if (C < 2 || ntc % C) return false;
+  TailArgs t = tl;
+  t.nlev = nl;
+  t.C = C;
+  t.h = h;
+  t.n_sor = opt.n_sor;
+  size_t off = 0;   // complex FP32 elements
+  for (int l = 0; l < nl; ++l) {
+    const int nr = lv[l].nr, nt = lv[l].nt, s = nt / C;
+    if (nt % C || s < 1 || nr > 256 || (nr & 1)) return false;
+    if (l < nl - 1 && (s < 2 || (s & 1) || s + 2 * h > 24)) return false;
+    TailLevel& q = t.lv[l];
+    q.L = lv[l];
+    q.s = s;
+    q.eo = int(off); off += size_t(s) * nr;
+    q.eh0 = int(off); off += size_t(2 * h) * nr;
+    q.eh1 = int(off); off += size_t(2 * h) * nr;
+    q.fo = int(off); off += size_t(s + 2 * h) * nr;
+    const bool fused = l >= first;
+    q.nu1 = fused ? vs.nu1 : opt.nu1;
+    q.nu2 = fused ? vs.nu2 : opt.nu2;
+  }
+  t.g_off = int(off * sizeof(float2));
+  off += size_t(ntc) * nrc;
+  size_t bytes = (off * sizeof(float2) + 15) / 16 * 16;
+  t.z_off = int(bytes);
+  bytes += size_t(ntc) * nrc * sizeof(double2);
+  t.zl_off = int(bytes);
+  bytes += size_t(ntc / C) * nrc * sizeof(double2);
+  t.u_off = int(bytes);
+  bytes += size_t(lv[0].nt / C + 2) * lv[0].nr * sizeof(double2);
+  t.part_off = int(bytes);
+  bytes += size_t(C) * 32;
+  t.tab_off = int(bytes);
+  bytes += size_t(t.tab_stride) * sizeof(float);
+  bytes = (bytes + 15) / 16 * 16;
+  t.smem_bytes = bytes;
+  if (bytes > 200 * 1024) return false;   // leaves the kernel's static shared memory room
+  t.ctab = d_ctab;
+  t.sep = d_sep;
+  t.sep_stride = H.sep_stride;
+  t.sep_sym = H.sep_sym;
+  t.tabs = d_tail_tabs;
+  const int fit = tail_max_clusters(t);
+  if (fit < 1) return false;
+  tl = t;
+  tail_planes = std::min(std::min(fit, 8), max_planes);
+  if (tail_cap > 0) tail_planes = std::min(tail_planes, tail_cap);
+  return true;
+}
+
+void MGSolver::tail(const double2* ff, double2* u, double tol, cudaStream_t st) {
+  if (tail_planes <= 0) return;
+  TailArgs t = tl;
+  t.tol = tol;
+  t.max_cycles = opt.max_cycles;
+  t.stagnation = opt.stagnation;
+  launch_tail(t, batch, S, ff, u, tail_planes, st);
 }
 
 void MGSolver::init_loop(cudaStream_t st) { launch_init_active(d_act, d_nact, max_planes, S, st); }
@@ -344,6 +456,10 @@ int MGSolver::eager_solve(const double2* ff, double2* u, double tol, cudaStream_
       launch_update<float>(lv[0], batch, u, (const float2*)e[0], st);
     else
       launch_update<double>(lv[0], batch, u, (const double2*)e[0], st);
+    if (*h_cont == 2) {   // at most tail_planes remain: the tail kernel finishes them
+      tail(ff, u, tol, st);
+      return 0;
+    }
   }
   return 0;
 }

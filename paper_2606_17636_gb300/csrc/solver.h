@@ -88,6 +88,14 @@ class MGSolver {
   int* d_gcnt = nullptr;
   double* d_fmax2 = nullptr;
   RetireState S{};
+  // cluster-resident tail (k_tail.cu): the last tail_planes active planes
+  // (0: disabled) are finished by one launch, one cluster per plane
+  TailArgs tl{};
+  float* d_tail_tabs = nullptr;   // per-slot packed FP32 tables of every level
+  int tail_planes = 0;
+  int tail_cap = -1;              // -1: as many as can be resident; 0: off; n: at most n
+  bool prepare_tail();            // layout for the current schedule; false when unsupported
+  void tail(const double2* f, double2* u, double tol, cudaStream_t st);
   int precision_of_buffers = 1;
   size_t vbytes() const { return opt.precision ? sizeof(float2) : sizeof(double2); }
 };
