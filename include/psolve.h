@@ -146,7 +146,31 @@ int psolve_solve_batched(psolve_t* hs, const double* const* rhos, double* const*
  * keeps the buffers.  A solve that fails with PSOLVE_ERR_NONFINITE or a CUDA
  * error clears the history. */
 int psolve_set_warm_start(psolve_t h, int enable);
+/* Bind the handle to a CUDA stream (cudaStream_t passed as void*; NULL: the
+ * legacy default stream, the initial binding).  Every later call of the
+ * handle enqueues its work there; a captured solve is captured again on the
+ * next solve.  The caller keeps the stream alive while the handle uses it.
+ * Returns PSOLVE_OK or PSOLVE_ERR_ARG (null handle). */
 int psolve_set_stream(psolve_t h, void* cuda_stream);
+
+/* Cluster-resident tail of each multigrid solve (App. B: the low modes, m = 0
+ * above all, need many more V-cycles than the rest, so a solve ends with
+ * iterations on one or a few mode planes).  Once at most P planes remain
+ * active, one kernel launch finishes them: each plane gets a cluster of C
+ * CTAs (one per SM) holding its whole multigrid hierarchy in distributed
+ * shared memory, iterating FP64 residual -> FP32 V-cycle (Sec. 3) -> FP64
+ * update on the device until the plane meets the App. B criterion.  The
+ * results are those of the batched iteration up to rounding.  Used by the
+ * mixed path when the plan allows (separable coarsest level, radial lines of
+ * at most 256 cells, the cluster's shared memory holds the plane); P is the
+ * number of clusters that fit on the GPU, at most 8.
+ * psolve_set_tail: max_planes -1 (default) uses that P, 0 disables the tail
+ * kernel, n > 0 caps P at n; a captured solve is captured again.
+ * psolve_get_tail: *planes = P in use (0: not used), *cluster_ctas = C.
+ * Both return PSOLVE_OK, or PSOLVE_ERR_ARG for a null handle or
+ * max_planes < -1. */
+int psolve_set_tail(psolve_t h, int max_planes);
+int psolve_get_tail(psolve_t h, int* planes, int* cluster_ctas);
 
 /* Smoothing schedule and tile shapes of a handle.  Sec. 3.2 leaves the
  * schedule open (a small number of smoothing cycles per level, typically two
@@ -214,6 +238,29 @@ void psolve_destroy(psolve_t h);
 /* Sec. 2.2: rho_hat[m][j][i] = (4 pi G / n_phi) sum_k rho[i][j][k] e^{-2 pi i m k / n_phi},
  * i.e. the right-hand side 4 pi G rho^m of the mode equations. */
 int psolve_stage_forward(psolve_t h, const double* rho, double* f_hat);
+/* The same transforms on a radial slab of n_rows consecutive radial rows
+ * (1 <= n_rows <= n_r; the transform along phi does not depend on the
+ * radius): rho_rows [n_rows][n_tz][n_phi] -> f_hat_rows [M][n_tz][n_rows]
+ * complex, and back (phi_hat_rows [M][n_tz][n_rows] -> phi_rows
+ * [n_rows][n_tz][n_phi]).  The building blocks of a mode-sharded solve over
+ * several GPUs: each rank transforms its slab, an all-to-all exchange moves
+ * every mode's planes to the rank that owns the mode (psolve_solve_modes),
+ * and the reverse exchange returns the potential's modes for the inverse
+ * transform of each slab. */
+int psolve_stage_forward_rows(psolve_t h, const double* rho_rows, int n_rows, double* f_hat_rows);
+int psolve_stage_inverse_rows(psolve_t h, const double* phi_hat_rows, int n_rows, double* phi_rows);
+/* Sec. 5.1 steps 3-6 (both Helmholtz solves, the screening mass and the
+ * boundary convolution) for the n azimuthal modes listed in modes_host
+ * (host array of distinct mode numbers 0 <= m < M, any order):
+ * f_hat [n][n_tz][n_r] complex FP64 holds 4 pi G rho^m of those modes in
+ * list order (device), phi_hat (device, same layout) receives Phi^m.  The
+ * modes solve independently of each other (Sec. 2.2), so the result of a
+ * mode equals that of a whole-problem solve.  Runs eagerly on the handle's
+ * stream without warm start; the statistics describe this call (unlisted
+ * modes: zero cycles).  Returns as psolve_solve, PSOLVE_ERR_ARG for a bad
+ * list. */
+int psolve_solve_modes(psolve_t h, const int* modes_host, int n, const double* f_hat,
+                       double* phi_hat, double tol);
 /* Sec. 2.2, Eq. Hermitian_symmetry: phi[i][j][k] = Re sum over all n_phi modes
  * with the upper half rebuilt as conjugates; imaginary parts of m = 0 and
  * m = n_phi/2 ignored. */
@@ -266,14 +313,19 @@ int psolve_get_dgf(psolve_t h, double* dst);
  * device pointers owned by the caller).  The step's working memory (an
  * active-plane list and one ping-pong copy of the level's planes, 256-byte
  * aligned) is taken from the static array; the handle supplies only its
- * read-only tables, so the call does not touch a solve in flight on the same
- * handle.
+ * read-only tables and writes none of its workspaces.  The call runs in
+ * order on the handle's stream and returns once that stream is idle, so it
+ * waits behind any work already enqueued there; it must not be called while
+ * that stream is being captured.
  *   Size limit: round_up_256(4 (M + 1)) + M n_tz_l n_r_l (16 for precision 0,
  *   8 for precision 1) bytes must not exceed PSOLVE_STATIC_SCRATCH_BYTES;
  *   larger levels return PSOLVE_ERR_ARG with a message naming the need.
- *   First call per device: looks up the array's device address with that
- *   device current (the handle's device must be current); make this first
- *   call before any stream capture begins.
+ *   Device: the device current at the handle's creation must be current
+ *   (PSOLVE_ERR_ARG otherwise).  The first call on a device looks up the
+ *   array's device address with that device current and keeps it for the
+ *   life of the process (the address assumes the device's primary context
+ *   lives until exit: no cudaDeviceReset in between); make this first call
+ *   before any stream capture begins.
  *   Sharing: all calls on a device use the same array, which keeps the last
  *   call's contents; each call rewrites what it reads.  Calls whose work
  *   overlaps on one GPU (other streams, threads or handles) race.

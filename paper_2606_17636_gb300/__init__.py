@@ -103,11 +103,16 @@ def lib():
             "psolve_destroy": (V, [P]),
             "psolve_stage_forward": (I, [P, P, P]),
             "psolve_stage_inverse": (I, [P, P, P]),
+            "psolve_stage_forward_rows": (I, [P, P, I, P]),
+            "psolve_stage_inverse_rows": (I, [P, P, I, P]),
+            "psolve_solve_modes": (I, [P, ctypes.POINTER(I), I, P, P, D]),
             "psolve_stage_mg_solve": (I, [P, P, P, D, I, ctypes.POINTER(I)]),
             "psolve_stage_smooth": (I, [P, I, I, P, P, I]),
             "psolve_stage_smooth_static": (I, [P, I, I, P, P, I]),
             "psolve_stage_vcycle": (I, [P, I, I, P, P]),
             "psolve_set_warm_start": (I, [P, I]),
+            "psolve_set_tail": (I, [P, I]),
+            "psolve_get_tail": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
             "psolve_get_fused_level": (I, [P, ctypes.POINTER(ctypes.c_int)]),
             "psolve_stage_restrict": (I, [P, I, I, P, P, P]),
             "psolve_stage_prolong": (I, [P, I, I, P, P]),
@@ -232,6 +237,16 @@ class Solver:
         """Start later solves from the previous solve's Psi and Phi."""
         check(lib().psolve_set_warm_start(self.h, int(bool(enable))), "psolve_set_warm_start")
 
+    def set_tail(self, max_planes=-1):
+        """Cluster-resident tail: -1 as many planes as fit, 0 off, n at most n."""
+        check(lib().psolve_set_tail(self.h, int(max_planes)), "psolve_set_tail")
+
+    def tail(self):
+        """(planes the tail kernel takes over, CTAs per cluster); (0, 0) when unused."""
+        p, c = ctypes.c_int(), ctypes.c_int()
+        check(lib().psolve_get_tail(self.h, ctypes.byref(p), ctypes.byref(c)), "psolve_get_tail")
+        return p.value, c.value
+
     def close(self):
         if getattr(self, "h", None):
             lib().psolve_destroy(self.h)
@@ -291,6 +306,38 @@ class Solver:
         phi = self.torch.empty(self.shape, dtype=self.torch.float64, device="cuda")
         check(lib().psolve_stage_inverse(self.h, _ptr(phi_hat), _ptr(phi)), "psolve_stage_inverse")
         return phi
+
+    def stage_forward_rows(self, rho_rows):
+        """Transform a radial slab [rows][n_tz][n_phi] -> [M][n_tz][rows] complex."""
+        torch = self.torch
+        rows = rho_rows.shape[0]
+        self._need(rho_rows, (rows, self.shape[1], self.shape[2]), torch.float64)
+        f = torch.empty((self.n_modes, self.shape[1], rows), dtype=torch.complex128, device="cuda")
+        check(lib().psolve_stage_forward_rows(self.h, _ptr(rho_rows), rows, _ptr(f)),
+              "psolve_stage_forward_rows")
+        return f
+
+    def stage_inverse_rows(self, phi_hat_rows):
+        torch = self.torch
+        rows = phi_hat_rows.shape[2]
+        self._need(phi_hat_rows, (self.n_modes, self.shape[1], rows), torch.complex128)
+        phi = torch.empty((rows, self.shape[1], self.shape[2]), dtype=torch.float64, device="cuda")
+        check(lib().psolve_stage_inverse_rows(self.h, _ptr(phi_hat_rows), rows, _ptr(phi)),
+              "psolve_stage_inverse_rows")
+        return phi
+
+    def solve_modes(self, modes, f_hat, tol=1e-8, raise_on_error=True):
+        """Steps 3-6 of Sec. 5.1 for the listed modes: f_hat [n][n_tz][n_r]
+        complex (list order) -> (phi_hat of the same layout, return code)."""
+        torch = self.torch
+        n = len(modes)
+        self._need(f_hat, (n, self.shape[1], self.shape[0]), torch.complex128)
+        phi = torch.empty_like(f_hat)
+        arr = (ctypes.c_int * max(n, 1))(*[int(m) for m in modes])
+        rc = lib().psolve_solve_modes(self.h, arr, n, _ptr(f_hat), _ptr(phi), float(tol))
+        if raise_on_error:
+            check(rc, "psolve_solve_modes")
+        return phi, rc
 
     def stage_mg_solve(self, f_hat, tol=1e-8, u0=None):
         u = self.planes() if u0 is None else u0.clone()

@@ -47,6 +47,7 @@ struct psolve_ctx {
   int* d_worst = nullptr;
   int* h_worst = nullptr;
   cudaStream_t st = 0;
+  int device = 0;     // the device current at create: the handle's memory lives there
   double setup_ms = 0;
   // captured solve
   cudaGraphExec_t gexec = nullptr;
@@ -157,6 +158,7 @@ static int create_impl(psolve_t* out, const psolve_desc* din) {
 
   std::unique_ptr<psolve_ctx> h(new psolve_ctx());
   h->d = d;
+  cudaGetDevice(&h->device);
   h->A.alloc_fn = d.alloc_fn;
   h->A.free_fn = d.free_fn;
   h->A.user = d.alloc_user;
@@ -354,6 +356,22 @@ extern "C" int psolve_set_stream(psolve_t h, void* s) {
   return PSOLVE_OK;
 }
 
+extern "C" int psolve_set_tail(psolve_t h, int max_planes) {
+  if (!h) return fail(PSOLVE_ERR_ARG, "null handle");
+  if (max_planes < -1) return fail(PSOLVE_ERR_ARG, "max_planes must be -1, 0 or positive");
+  h->mg.tail_cap = max_planes;
+  h->mg.prepare_tail();
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  return cuda_ok("set_tail") ? PSOLVE_OK : PSOLVE_ERR_CUDA;
+}
+
+extern "C" int psolve_get_tail(psolve_t h, int* planes, int* cluster_ctas) {
+  if (!h) return fail(PSOLVE_ERR_ARG, "null handle");
+  if (planes) *planes = h->mg.tail_planes;
+  if (cluster_ctas) *cluster_ctas = h->mg.tail_planes > 0 ? h->mg.tl.C : 0;
+  return PSOLVE_OK;
+}
+
 extern "C" const char* psolve_last_error(void) { return g_err.c_str(); }
 
 extern "C" int psolve_get_sizes(psolve_t h, int* n_modes, int* n_boundary, int* n_levels) {
@@ -426,6 +444,7 @@ static int add_while(psolve_t h, cudaGraph_t graph, double tol, cudaStream_t bod
   h->mg.loop_body(h->f, h->u, tol, body_st, 1, cond);
   cudaGraph_t out;
   if (cudaStreamEndCapture(body_st, &out) != cudaSuccess) return -1;
+  h->mg.tail(h->f, h->u, tol, h->st);   // planes the loop handed over (none: returns at once)
   return 0;
 }
 
@@ -808,6 +827,68 @@ extern "C" int psolve_stage_forward(psolve_t h, const double* rho, double* f_hat
                                                                              : PSOLVE_ERR_CUDA;
 }
 
+extern "C" int psolve_stage_forward_rows(psolve_t h, const double* rho_rows, int n_rows,
+                                         double* f_hat_rows) {
+  if (!h || !rho_rows || !f_hat_rows) return fail(PSOLVE_ERR_ARG, "null argument");
+  if (n_rows < 1 || n_rows > h->d.n_r) return fail(PSOLVE_ERR_ARG, "n_rows must lie in 1..n_r");
+  launch_fft_forward(rho_rows, reinterpret_cast<double2*>(f_hat_rows), n_rows, h->d.n_tz, h->d.n_phi,
+                     4.0 * kPi * h->d.G / h->d.n_phi, h->tw, h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("forward_rows") ? PSOLVE_OK
+                                                                                  : PSOLVE_ERR_CUDA;
+}
+
+extern "C" int psolve_stage_inverse_rows(psolve_t h, const double* phi_hat_rows, int n_rows,
+                                         double* phi_rows) {
+  if (!h || !phi_hat_rows || !phi_rows) return fail(PSOLVE_ERR_ARG, "null argument");
+  if (n_rows < 1 || n_rows > h->d.n_r) return fail(PSOLVE_ERR_ARG, "n_rows must lie in 1..n_r");
+  launch_fft_inverse(reinterpret_cast<const double2*>(phi_hat_rows), phi_rows, n_rows, h->d.n_tz,
+                     h->d.n_phi, h->tw, h->st);
+  return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("inverse_rows") ? PSOLVE_OK
+                                                                                  : PSOLVE_ERR_CUDA;
+}
+
+extern "C" int psolve_solve_modes(psolve_t h, const int* modes_host, int n, const double* f_hat,
+                                  double* phi_hat, double tol) {
+  if (!h || (n > 0 && (!modes_host || !f_hat || !phi_hat))) return fail(PSOLVE_ERR_ARG, "null argument");
+  if (n < 0 || n > h->M) return fail(PSOLVE_ERR_ARG, "n must lie in 0..n_modes");
+  if (n > 0 && f_hat == phi_hat) return fail(PSOLVE_ERR_ARG, "phi_hat must not alias f_hat");
+  std::vector<char> seen(h->M, 0);
+  for (int k = 0; k < n; ++k) {
+    const int m = modes_host[k];
+    if (m < 0 || m >= h->M || seen[m]) return fail(PSOLVE_ERR_ARG, "modes must be distinct and in 0..n_modes-1");
+    seen[m] = 1;
+  }
+  if (tol <= 0) tol = 1e-8;
+  const size_t plane = size_t(h->d.n_r) * h->d.n_tz;
+  const int warm = h->warm;
+  h->warm = 0;   // the history belongs to whole-problem solves
+  // the listed modes' right-hand sides in their planes, zero elsewhere: a
+  // zero plane meets the criterion at its first residual and retires
+  cudaMemsetAsync(h->f, 0, plane_bytes(h), h->st);
+  for (int k = 0; k < n; ++k)
+    cudaMemcpyAsync(h->f + size_t(modes_host[k]) * plane, reinterpret_cast<const double2*>(f_hat) + k * plane,
+                    plane * sizeof(double2), cudaMemcpyDeviceToDevice, h->st);
+  cudaMemsetAsync(h->u, 0, plane_bytes(h), h->st);
+  h->mg.zero_guess = 1;
+  h->mg.init_loop(h->st);
+  std::string err;
+  int rc = PSOLVE_OK;
+  if (h->mg.eager_solve(h->f, h->u, tol, h->st, err) != 0) rc = fail(PSOLVE_ERR_CUDA, err);
+  if (rc == PSOLVE_OK) {
+    enqueue_middle(h);
+    if (h->mg.eager_solve(h->f, h->u, tol, h->st, err) != 0) rc = fail(PSOLVE_ERR_CUDA, err);
+  }
+  h->warm = warm;
+  if (rc != PSOLVE_OK) return rc;
+  snapshot(h, h->sf);
+  for (int k = 0; k < n; ++k)
+    cudaMemcpyAsync(reinterpret_cast<double2*>(phi_hat) + k * plane, h->u + size_t(modes_host[k]) * plane,
+                    plane * sizeof(double2), cudaMemcpyDeviceToDevice, h->st);
+  k_worst<<<1, 256, 0, h->st>>>(h->sp.status, h->sf.status, h->M, h->d_worst);
+  cudaMemcpyAsync(h->h_worst, h->d_worst, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+  return finish(h);
+}
+
 extern "C" int psolve_stage_inverse(psolve_t h, const double* phi_hat, double* phi) {
   if (!h || !phi_hat || !phi) return fail(PSOLVE_ERR_ARG, "null argument");
   launch_fft_inverse(reinterpret_cast<const double2*>(phi_hat), phi, h->d.n_r, h->d.n_tz,
@@ -954,10 +1035,13 @@ void* g_scratch_dev[kMaxDevices] = {};   // device address of g_static_scratch, 
 
 // In host code g_static_scratch names a host-side stand-in; the device
 // address is looked up once per device, with that device current.
-int static_scratch(void** out) {
+int static_scratch(int handle_device, void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(PSOLVE_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != handle_device)
+    return fail(PSOLVE_ERR_ARG, "the handle's device (" + std::to_string(handle_device) +
+                                    ") must be current, not device " + std::to_string(dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(PSOLVE_ERR_ARG, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_dev[dev]) {
@@ -996,7 +1080,7 @@ extern "C" int psolve_stage_smooth_static(psolve_t h, int level, int precision, 
                     std::to_string(size_t(PSOLVE_STATIC_SCRATCH_BYTES)) +
                     " bytes; use psolve_stage_smooth");
   unsigned char* base = nullptr;
-  rc = static_scratch(reinterpret_cast<void**>(&base));
+  rc = static_scratch(h->device, reinterpret_cast<void**>(&base));
   if (rc) return rc;
   int* act = reinterpret_cast<int*>(base);
   // The active list is rewritten on every call (the array holds the last

@@ -13,9 +13,6 @@ from gpu_helpers import SMALL
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# the smoothing stage tests' tolerances (max error relative to max |value|)
-TOL = {0: 1e-12, 1: 2e-5}
-
 
 @pytest.fixture(scope="module")
 def ps():
@@ -35,9 +32,10 @@ def _ptr(t):
 
 
 def _compare(got, ref, precision):
-    err = (got - ref).abs().max().item()
-    scale = ref.abs().max().item()
-    assert err <= TOL[precision] * scale, (err, scale)
+    """The static entry point runs the same kernels with the same grid,
+    active list and tile shapes as psolve_stage_smooth: the results are
+    bitwise equal (a stale or overlapping scratch plane would show)."""
+    assert torch.equal(got, ref), (got - ref).abs().max().item()
 
 
 @pytest.mark.parametrize("key,precision", [("sph_log", 0), ("sph_log", 1), ("cyl_axis", 1),
@@ -90,4 +88,28 @@ def test_static_smooth_rejects_levels_above_the_static_limit(ps):
         assert L.psolve_stage_smooth_static(s.h, 1, 0, _ptr(got), _ptr(f1), 2) == ps.OK, ps.last_error()
         assert L.psolve_stage_smooth(s.h, 1, 0, _ptr(ref), _ptr(f1), 2) == ps.OK, ps.last_error()
         _compare(got, ref, 0)
+    s.close()
+
+
+def test_static_smooth_allocates_no_device_memory(ps):
+    """After a first call (which looks up the static array's address), further
+    calls at different levels and cycle counts leave the device's free memory
+    unchanged: the step's scratch is the static array, nothing is allocated."""
+    L = ps.lib()
+    sp = SMALL["sph_log"]
+    s = ps.Solver.from_spec(sp, precision=1, use_graph=False)
+    M = s.n_modes
+    bufs = []
+    for level, seed in ((0, 21), (1, 22)):
+        shape = (M, sp["n_tz"] >> level, sp["n_r"] >> level)
+        bufs.append((level, _planes(shape, 1, seed), _planes(shape, 1, seed + 1)))
+    level, e, f = bufs[0]
+    assert L.psolve_stage_smooth_static(s.h, level, 1, _ptr(e), _ptr(f), 1) == ps.OK, ps.last_error()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for cycles in (1, 3, 2):
+        for level, e, f in bufs:
+            assert L.psolve_stage_smooth_static(s.h, level, 1, _ptr(e), _ptr(f), cycles) == ps.OK, ps.last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     s.close()
