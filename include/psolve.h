@@ -119,6 +119,10 @@ typedef struct {
   double coarse_check;         /* separable forms: the largest relative residual, over
                                   the modes, of the factors applied to a fixed test
                                   vector (rounding level when sound); else -1     */
+  int tail_cluster_ctas;       /* mixed path with the descriptor's n_sor: CTAs per
+                                  cluster of the cluster-resident tail (see
+                                  psolve_set_tail); 0 when the plan does not allow it */
+  int tail_smem_bytes;         /* its shared memory per CTA (0 when not allowed)      */
 } psolve_plan;
 /* PSOLVE_ERR_ARG (with a message) for an invalid descriptor, as psolve_create_ex. */
 int psolve_plan_inspect(const psolve_desc* d, psolve_plan* out);
@@ -134,6 +138,29 @@ int psolve_solve(psolve_t h, const double* rho, double* phi, double tol);
  * each handle's own stream; the same return convention, first error wins. */
 int psolve_solve_batched(psolve_t* hs, const double* const* rhos, double* const* phis, int n,
                          double tol);
+
+/* Many independent problems in ONE captured CUDA graph (a serving-style
+ * batch; the paper solves one problem at a time).  psolve_batch_create
+ * captures, for n distinct handles (of any sizes and kinds) with their
+ * device buffers rhos[k] -> phis[k] and tolerance tol, each problem's whole
+ * solve (Sec. 5.1 steps 2-7) on its own branch of one graph, so independent
+ * problems overlap on the GPU; a completion event follows each problem.
+ * The graph keeps the buffers, the tolerance, the handles' schedules and
+ * warm-start state as captured: create a new batch after changing any of
+ * them.  While a batch exists its handles must not run other work at the
+ * same time (the batch uses their workspaces).
+ * psolve_batch_run launches the graph on `stream` (cudaStream_t as void*,
+ * NULL: the legacy default stream), waits for it, and returns the first
+ * non-OK status in handle order (as psolve_solve); latency_ms (n floats, may
+ * be NULL) receives each problem's completion time from the launch, in ms.
+ * psolve_batch_destroy waits for the device and frees the graph (NULL-safe);
+ * the handles stay valid.  Errors: PSOLVE_ERR_ARG (null argument, n < 1, a
+ * handle twice, phi aliasing rho), PSOLVE_ERR_CUDA (capture or launch). */
+typedef struct psolve_batch_ctx* psolve_batch_t;
+int psolve_batch_create(psolve_batch_t* out, psolve_t* hs, const double* const* rhos,
+                        double* const* phis, int n, double tol);
+int psolve_batch_run(psolve_batch_t b, void* stream, float* latency_ms);
+void psolve_batch_destroy(psolve_batch_t b);
 
 /* Warm start for time stepping (Sec. 5.1 and App. B: in a simulation the
  * previous step's solution is the initial guess, which cuts the V-cycles

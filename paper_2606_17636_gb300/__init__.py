@@ -57,13 +57,14 @@ class Plan(ctypes.Structure):
     _fields_ = [("n_modes", ctypes.c_int), ("n_levels", ctypes.c_int),
                 ("level_n_r", ctypes.c_int * 16), ("level_n_tz", ctypes.c_int * 16),
                 ("coarsest", ctypes.c_int), ("coarse_doubles_per_mode", ctypes.c_int),
-                ("coarse_check", ctypes.c_double)]
+                ("coarse_check", ctypes.c_double), ("tail_cluster_ctas", ctypes.c_int),
+                ("tail_smem_bytes", ctypes.c_int)]
 
 
 COARSE_FORMS = {0: "separable, mirror-symmetric", 1: "separable", 2: "block-tridiagonal", 3: "dense"}
 
 
-def plan_inspect(spec, precision=1):
+def plan_inspect(spec, precision=1, n_sor=0):
     """The multigrid plan of a problem spec (psolve_plan_inspect: host only,
     no GPU needed): levels (n_r, n_tz), finest first, and the coarsest-level
     solve's form and factor size per mode."""
@@ -74,12 +75,14 @@ def plan_inspect(spec, precision=1):
     d.t_min = spec.get("t_min") or 0.0
     d.t_max = spec.get("t_max") or 0.0
     d.precision = precision
+    d.n_sor = n_sor
     p = Plan()
     check(lib().psolve_plan_inspect(ctypes.byref(d), ctypes.byref(p)), "psolve_plan_inspect")
     return {"n_modes": p.n_modes,
             "levels": [(p.level_n_r[l], p.level_n_tz[l]) for l in range(p.n_levels)],
             "coarsest": COARSE_FORMS[p.coarsest], "coarse_doubles_per_mode": p.coarse_doubles_per_mode,
-            "coarse_check": p.coarse_check}
+            "coarse_check": p.coarse_check, "tail_cluster_ctas": p.tail_cluster_ctas,
+            "tail_smem_bytes": p.tail_smem_bytes}
 
 
 def lib():
@@ -123,6 +126,9 @@ def lib():
             "psolve_set_schedule": (I, [P, ctypes.POINTER(Schedule)]),
             "psolve_autotune": (I, [P, P, P, D, ctypes.POINTER(Schedule)]),
             "psolve_plan_inspect": (I, [ctypes.POINTER(Desc), ctypes.POINTER(Plan)]),
+            "psolve_batch_create": (I, [ctypes.POINTER(P), P, P, P, I, D]),
+            "psolve_batch_run": (I, [P, P, ctypes.POINTER(ctypes.c_float)]),
+            "psolve_batch_destroy": (V, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -403,3 +409,44 @@ class Solver:
                              dtype=self.torch.float64, device="cuda")
         check(lib().psolve_get_dgf(self.h, _ptr(g)), "psolve_get_dgf")
         return g
+
+
+class Batch:
+    """Independent problems solved by one captured graph (psolve_batch_*):
+    solvers[k] maps rhos[k] to phis[k] (device tensors kept alive here)."""
+
+    def __init__(self, solvers, rhos, phis, tol=1e-8):
+        import torch
+        self.torch = torch
+        n = len(solvers)
+        for s, r, p in zip(solvers, rhos, phis):
+            s._need(r, s.shape, torch.float64)
+            s._need(p, s.shape, torch.float64)
+        self.solvers, self.rhos, self.phis = list(solvers), list(rhos), list(phis)
+        H = (ctypes.c_void_p * n)(*[s.h.value for s in solvers])
+        R = (ctypes.c_void_p * n)(*[r.data_ptr() for r in rhos])
+        Q = (ctypes.c_void_p * n)(*[p.data_ptr() for p in phis])
+        b = ctypes.c_void_p()
+        check(lib().psolve_batch_create(ctypes.byref(b), H, R, Q, n, float(tol)), "psolve_batch_create")
+        self.b = b
+        self.n = n
+
+    def run(self, raise_on_error=True):
+        """Launch on torch's current stream and wait; returns (code, per-problem
+        completion times in ms from the launch)."""
+        lat = (ctypes.c_float * self.n)()
+        rc = lib().psolve_batch_run(self.b, ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream), lat)
+        if raise_on_error:
+            check(rc, "psolve_batch_run")
+        return rc, list(lat)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().psolve_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -302,6 +302,14 @@ extern "C" int psolve_plan_inspect(const psolve_desc* din, psolve_plan* out) {
       out->coarse_doubles_per_mode = H.nc * H.nc;
       out->coarse_check = -1.0;
     }
+    if (d.precision == PSOLVE_MIXED) {
+      std::vector<int> nr(out->n_levels), nt(out->n_levels);
+      for (int l = 0; l < out->n_levels; ++l) { nr[l] = H.lv[l].g.r.n; nt[l] = H.lv[l].g.t.n; }
+      TailArgs t{};
+      const size_t bytes = tail_layout(nr, nt, d.n_sor, H.sep_stride > 0, t);
+      out->tail_cluster_ctas = bytes ? t.C : 0;
+      out->tail_smem_bytes = int(bytes);
+    }
     return PSOLVE_OK;
   } catch (const std::exception& e) {
     return fail(PSOLVE_ERR_NOMEM, std::string("plan: ") + e.what());
@@ -556,6 +564,125 @@ extern "C" int psolve_solve_batched(psolve_t* hs, const double* const* rhos, dou
     if (rc != PSOLVE_OK && first == PSOLVE_OK) first = rc;
   }
   return first;
+}
+
+// ---- many problems in one captured graph -----------------------------------
+
+struct psolve_batch_ctx {
+  std::vector<psolve_t> hs;
+  std::vector<cudaStream_t> branch;   // capture branches, one per problem
+  std::vector<cudaEvent_t> done;      // recorded by the graph when a problem's potential is written
+  cudaEvent_t start = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static void batch_release(psolve_batch_ctx* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaStream_t s : b->branch) if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->done) if (e) cudaEventDestroy(e);
+  if (b->start) cudaEventDestroy(b->start);
+  delete b;
+}
+
+extern "C" int psolve_batch_create(psolve_batch_t* out, psolve_t* hs, const double* const* rhos,
+                                   double* const* phis, int n, double tol) {
+  if (!out || !hs || !rhos || !phis || n < 1) return fail(PSOLVE_ERR_ARG, "null argument or n < 1");
+  *out = nullptr;
+  if (tol <= 0) tol = 1e-8;
+  for (int k = 0; k < n; ++k) {
+    if (!hs[k] || !rhos[k] || !phis[k] || rhos[k] == phis[k]) return fail(PSOLVE_ERR_ARG, "invalid batch entry");
+    for (int q = 0; q < k; ++q)
+      if (hs[q] == hs[k]) return fail(PSOLVE_ERR_ARG, "a handle appears twice in the batch");
+  }
+  psolve_batch_ctx* b = new psolve_batch_ctx();
+  b->hs.assign(hs, hs + n);
+  b->branch.assign(n, nullptr);
+  b->done.assign(n, nullptr);
+  cudaStream_t root = nullptr, body = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join(n, nullptr);
+  int rc = 0;
+  if (cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&b->start) != cudaSuccess)
+    rc = -1;
+  for (int k = 0; k < n && !rc; ++k)
+    if (cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&b->done[k]) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming) != cudaSuccess)
+      rc = -1;
+  cudaGraph_t graph = nullptr;
+  if (!rc && cudaGraphCreate(&graph, 0) != cudaSuccess) rc = -1;
+  if (!rc && cudaStreamBeginCaptureToGraph(root, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+                 cudaSuccess)
+    rc = -1;
+  if (!rc) {
+    cudaEventRecord(fork, root);
+    // each problem's whole solve on its own branch: independent problems
+    // overlap on the GPU; a completion event per problem
+    for (int k = 0; k < n && !rc; ++k) {
+      psolve_t h = hs[k];
+      const cudaStream_t saved = h->st;
+      h->st = b->branch[k];
+      cudaStreamWaitEvent(h->st, fork, 0);
+      enqueue_front(h, rhos[k]);
+      rc = add_while(h, graph, tol, body);
+      if (!rc) {
+        enqueue_middle(h);
+        rc = add_while(h, graph, tol, body);
+      }
+      if (!rc) {
+        enqueue_back(h, phis[k]);
+        cudaEventRecordWithFlags(b->done[k], h->st, cudaEventRecordExternal);
+        cudaEventRecord(join[k], h->st);
+        cudaStreamWaitEvent(root, join[k], 0);
+      }
+      h->st = saved;
+    }
+    cudaGraph_t g2;
+    if (cudaStreamEndCapture(root, &g2) != cudaSuccess) rc = -1;
+  }
+  if (!rc && cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) rc = -1;
+  if (graph) cudaGraphDestroy(graph);
+  if (body) cudaStreamDestroy(body);
+  if (root) cudaStreamDestroy(root);
+  if (fork) cudaEventDestroy(fork);
+  for (cudaEvent_t e : join) if (e) cudaEventDestroy(e);
+  const cudaError_t le = cudaGetLastError();
+  if (rc || le != cudaSuccess) {
+    batch_release(b);
+    return fail(PSOLVE_ERR_CUDA, std::string("batch capture failed: ") + cudaGetErrorString(le));
+  }
+  *out = b;
+  return PSOLVE_OK;
+}
+
+extern "C" int psolve_batch_run(psolve_batch_t b, void* stream, float* latency_ms) {
+  if (!b) return fail(PSOLVE_ERR_ARG, "null batch");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEventRecord(b->start, st);
+  if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return fail(PSOLVE_ERR_CUDA, "batch graph launch");
+  if (cudaStreamSynchronize(st) != cudaSuccess || !cuda_ok("batch run"))
+    return fail(PSOLVE_ERR_CUDA, g_err.empty() ? "batch run failed" : g_err);
+  int first = PSOLVE_OK;
+  for (size_t k = 0; k < b->hs.size(); ++k) {
+    psolve_t h = b->hs[k];
+    int rc = PSOLVE_OK;
+    if (*h->h_worst == -5) rc = fail(PSOLVE_ERR_NONFINITE, "non-finite residual norm");
+    else if (*h->h_worst == -4) rc = fail(PSOLVE_ERR_NOT_CONVERGED, "a mode did not reach the tolerance");
+    note_history(h, rc);
+    if (rc != PSOLVE_OK && first == PSOLVE_OK) first = rc;
+    if (latency_ms && cudaEventElapsedTime(&latency_ms[k], b->start, b->done[k]) != cudaSuccess)
+      return fail(PSOLVE_ERR_CUDA, "batch latency");
+  }
+  return first;
+}
+
+extern "C" void psolve_batch_destroy(psolve_batch_t b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  batch_release(b);
 }
 
 // ---- smoothing schedule and autotuner ---------------------------------------

@@ -15,15 +15,26 @@
 // of the (r, theta) / (R, z) plane.  Radial lines lie inside one CTA.  A
 // polar line crosses all CTAs; each CTA relaxes the segment of it that
 // covers its own rows plus h = 2 n_sor rows of its neighbours on each side
-// (halo rows, copied in).  n_sor even-odd SOR sweeps move information at
-// most 2 n_sor cells along the line, so the values the CTA keeps -- its own
-// rows -- are exactly those of a relaxation of the whole line.  After every
-// colour step each CTA writes its boundary rows into its neighbours' halo
-// buffers (distributed shared memory stores) and the cluster synchronises
-// once; the halo buffers alternate between steps, so a CTA still reading its
-// halo never sees a neighbour's newer rows.  Prolongation is computed by each
-// CTA for its halo rows too (it holds the coarse rows they need), so the
-// halo stays current without an exchange.
+// (halo rows).  n_sor even-odd SOR sweeps move information at most 2 n_sor
+// cells along the line, so the values the CTA keeps -- its own rows -- are
+// exactly those of a relaxation of the whole line.  A level's error lives in
+// the CTA's own rows and two buffers of halo rows used in turn: a step reads
+// halo buffer b and updates the own rows, then writes its boundary rows into
+// the neighbours' halo buffer b^1 (distributed shared memory stores), and the
+// cluster synchronises once; a CTA still reading buffer b never sees a
+// neighbour's newer rows.  The two
+// radial colours share one step: a CTA recomputes the neighbour's first
+// colour-0 row that its own last colour-1 row needs.  Prolongation is
+// computed by each CTA for its halo rows too (it holds the coarse rows they
+// need), so the halo stays current without an exchange.
+//
+// Row storage: cell (j, i) of a level sits at column i ^ sw(j) of its row,
+// with sw(j) = (j / 2) mod min(8, n_r / 2).  The 8 lanes that relax a polar
+// segment (two rows each) then read 8 distinct 8-byte slots, and the four
+// columns of a warp pass are chosen so that two of them fall in each half
+// of a 16-column block: a column load takes the minimum two wavefronts.  A
+// radial line still reads whole 16-byte pairs (the line helpers swap a pair
+// for odd sw).
 //
 // The arithmetic of every cell is that of the level-wide and shared-memory
 // kernels (the same line-relaxation helpers, restriction, prolongation,
@@ -50,211 +61,264 @@ struct __align__(16) D4 {
 
 __device__ __forceinline__ V vz() { return make_float2(0.f, 0.f); }
 
-// Row r (relative to the CTA's first row, -h <= r < s + h) of a level's error.
-__device__ __forceinline__ V* erow(unsigned char* sm, const TailLevel& t, int h, int cur, int r) {
-  V* b = reinterpret_cast<V*>(sm);
-  const int nr = t.L.nr;
-  if (r < 0) return b + (cur ? t.eh1 : t.eh0) + (r + h) * nr;
-  if (r >= t.s) return b + (cur ? t.eh1 : t.eh0) + (h + r - t.s) * nr;
-  return b + t.eo + r * nr;
+// Row r (relative to the CTA's first row, -h <= r < s + h) of a row block
+// (the right-hand side, rows -h .. s + h - 1 contiguous).
+__device__ __forceinline__ V* rowp(unsigned char* sm, int off, int nr, int h, int r) {
+  return reinterpret_cast<V*>(sm) + off + (r + h) * nr;
 }
-__device__ __forceinline__ V* frow(unsigned char* sm, const TailLevel& t, int h, int r) {
-  return reinterpret_cast<V*>(sm) + t.fo + (r + h) * t.L.nr;
-}
-
-// Copies the CTA's own rows (row r at src + r nr, r < s) into the halo slots
-// of every CTA of the cluster whose halo (h rows on each side) covers them.
-// Target rank + d receives rows r >= d s - h at its top slot r - d s + h
-// (top slots at top_off); target rank - d receives rows r < h - (d - 1) s at
-// its bottom slot r + (d - 1) s (bottom slots at bot_off).
-__device__ void push_halo(cg::cluster_group& cl, unsigned char* sm, const V* src, int s, int nr,
-                          int h, int top_off, int bot_off, int rank, int C) {
-  const int chunks = nr >> 1;   // two cells per 16-byte store
+// Row r of a level's error seen with halo buffer b.
+__device__ __forceinline__ V* erow(unsigned char* sm, const TailLevel& t, int h, int b, int r) {
   V* base = reinterpret_cast<V*>(sm);
-  for (int d = 1; (d - 1) * s < h; ++d) {
-    for (int side = 0; side < 2; ++side) {
-      const int tgt = side ? rank - d : rank + d;
-      if (tgt < 0 || tgt >= C) continue;
-      const int r0 = side ? 0 : max(0, d * s - h);
-      const int r1 = side ? min(s, h - (d - 1) * s) : s;
-      if (r1 <= r0) continue;
-      V* tb = cl.map_shared_rank(base, tgt);
-      const int n = (r1 - r0) * chunks;
-      for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-        const int q = idx / chunks, c = idx - q * chunks, rr = r0 + q;
-        const int slot = side ? bot_off + (rr + (d - 1) * s) * nr : top_off + (rr - d * s + h) * nr;
-        *reinterpret_cast<float4*>(tb + slot + 2 * c) = *reinterpret_cast<const float4*>(src + rr * nr + 2 * c);
-      }
-    }
+  const int nr = t.L.nr;
+  if (r < 0) return base + t.eh[b] + (r + h) * nr;
+  if (r >= t.s) return base + t.eh[b] + (h + r - t.s) * nr;
+  return base + t.eo + r * nr;
+}
+// Column swizzle of global row j.
+__device__ __forceinline__ int tsw(int nr, int j) { return (j >> 1) & ((nr < 16 ? nr : 16) / 2 - 1); }
+
+// Copies the own rows [r0, r1) (row r at src + r nr) to CTA tgt, whose own
+// rows start delta rows after ours (our row r is its row r - delta): into its
+// right-hand-side block at dst (eblock = 0) or its error halo buffer at dst
+// (eblock = 1: rows above its own at slots 0..h-1, below at h..2h-1).
+__device__ void push_rows(cg::cluster_group& cl, unsigned char* sm, const V* src, int dst, int eblock,
+                          int s, int nr, int h, int r0, int r1, int tgt, int delta) {
+  if (r1 <= r0) return;
+  const int chunks = nr >> 1;   // two cells per 16-byte store
+  V* tb = cl.map_shared_rank(reinterpret_cast<V*>(sm), tgt);
+  const int n = (r1 - r0) * chunks;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int q = idx / chunks, c = idx - q * chunks, r = r0 + q, rt = r - delta;
+    const int slot = !eblock ? rt + h : (rt < 0 ? rt + h : h + rt - s);
+    *reinterpret_cast<float4*>(tb + dst + slot * nr + 2 * c) =
+        *reinterpret_cast<const float4*>(src + r * nr + 2 * c);
   }
 }
 
-// Radial lines of colour `color` among the CTA's own rows, one warp per line
-// (Sec. 3.2; the helpers of the level-wide pass).
+// The CTA's own rows into the halo rows of every CTA whose halo (h rows on
+// each side) covers them.
+__device__ void push_halo(cg::cluster_group& cl, unsigned char* sm, const V* src, int dst, int eblock,
+                          int s, int nr, int h, int rank, int C) {
+  for (int d = 1; (d - 1) * s < h; ++d) {
+    if (rank + d < C) push_rows(cl, sm, src, dst, eblock, s, nr, h, max(0, d * s - h), s, rank + d, d * s);
+    if (rank - d >= 0) push_rows(cl, sm, src, dst, eblock, s, nr, h, 0, min(s, h - (d - 1) * s), rank - d, -d * s);
+  }
+}
+
+// End of a smoothing step: the own rows into the neighbours' halo buffer b^1.
+__device__ void publish(cg::cluster_group& cl, unsigned char* sm, const TailLevel& t, int h, int b,
+                        int rank, int C) {
+  push_halo(cl, sm, reinterpret_cast<const V*>(sm) + t.eo, t.eh[b ^ 1], 1, t.s, t.L.nr, h, rank, C);
+}
+
+// One radial line (own row r, or the first row of the next CTA) relaxed in
+// place (Sec. 3.2; the helpers of the level-wide pass), halo buffer b.
 template <int CPL>
-__device__ void t_rlines(const LevelDev& L, unsigned char* sm, const TailLevel& t, int h, int cur,
-                         int j0, float s2, int n_sor, int color) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int nr = L.nr, nt = L.nt;
+__device__ __forceinline__ void t_rline(const LevelDev& L, const RLineTabs<float, CPL>& tabs,
+                                        unsigned char* sm, const TailLevel& t, int h, int b, int j0,
+                                        int r, float s2, int n_sor) {
+  const int lane = threadIdx.x & 31, nr = L.nr, nt = L.nt, j = j0 + r;
+  V ev[CPL], g[CPL], un[CPL], us[CPL];
+  V* row = erow(sm, t, h, b, r);
+  ld_line_swz<V, CPL>(ev, row, tsw(nr, j), lane, nr);
+  ld_line_swz<V, CPL>(g, rowp(sm, t.fo, nr, h, r), tsw(nr, j), lane, nr);
+  if (j + 1 < nt) {
+    ld_line_swz<V, CPL>(un, erow(sm, t, h, b, r + 1), tsw(nr, j + 1), lane, nr);
+  } else {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) un[c] = vz();
+  }
+  if (j > 0) {
+    ld_line_swz<V, CPL>(us, erow(sm, t, h, b, r - 1), tsw(nr, j - 1), lane, nr);
+  } else {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) us[c] = vz();
+  }
+  relax_r<float, CPL>(L, tabs, L.tf, s2, L.omr_f[j], j, g, un, us, n_sor, ev);
+  st_line_swz<V, CPL>(row, tsw(nr, j), ev, lane, nr);
+}
+
+// Both radial colours of the own rows, one warp per line: colour 0 (even
+// rows, and the next CTA's first row -- in the halo buffer -- which the own
+// last colour-1 row needs: its inputs are the own last row, the halo rows
+// and the halo right-hand side, so the value equals the neighbour's), then
+// colour 1.
+template <int CPL>
+__device__ void t_rpass(const LevelDev& L, unsigned char* sm, const TailLevel& t, int h, int b,
+                        int j0, float s2, int n_sor) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   RLineTabs<float, CPL> tabs;
   ld_rtabs<float, CPL>(tabs, L, L.rf);
-  for (int r = 2 * warp + color; r < t.s; r += 2 * nw) {
-    const int j = j0 + r;
-    V ev[CPL], g[CPL], un[CPL], us[CPL];
-    ld_line<V, CPL>(ev, erow(sm, t, h, cur, r), lane, nr);
-    ld_line<V, CPL>(g, frow(sm, t, h, r), lane, nr);
-    if (j + 1 < nt) {
-      ld_line<V, CPL>(un, erow(sm, t, h, cur, r + 1), lane, nr);
-    } else {
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) un[c] = vz();
-    }
-    if (j > 0) {
-      ld_line<V, CPL>(us, erow(sm, t, h, cur, r - 1), lane, nr);
-    } else {
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) us[c] = vz();
-    }
-    relax_r<float, CPL>(L, tabs, L.tf, s2, L.omr_f[j], j, g, un, us, n_sor, ev);
-    st_line<V, CPL>(erow(sm, t, h, cur, r), ev, lane, nr);
+  const int n0 = t.s / 2 + (j0 + t.s < L.nt ? 1 : 0);
+  for (int w = warp; w < n0; w += nw) t_rline<CPL>(L, tabs, sm, t, h, b, j0, 2 * w, s2, n_sor);
+  __syncthreads();
+  for (int w = warp; w < t.s / 2; w += nw) t_rline<CPL>(L, tabs, sm, t, h, b, j0, 2 * w + 1, s2, n_sor);
+}
+
+__device__ void t_rstep(const LevelDev& L, unsigned char* sm, const TailLevel& t, int h, int b,
+                        int j0, float s2, int n_sor) {
+  switch (L.nr <= 32 ? 1 : L.nr >> 5) {
+    case 1: t_rpass<1>(L, sm, t, h, b, j0, s2, n_sor); break;
+    case 2: t_rpass<2>(L, sm, t, h, b, j0, s2, n_sor); break;
+    case 4: t_rpass<4>(L, sm, t, h, b, j0, s2, n_sor); break;
+    default: t_rpass<8>(L, sm, t, h, b, j0, s2, n_sor); break;
   }
 }
 
-// Polar lines of colour `color`: one thread per column relaxes the segment
-// of rows [rlo, rhi) (own rows and up to h halo rows each side, clipped to
-// the plane) with the even-odd SOR sweeps of the line smoother, and keeps
-// the own rows.  LM >= rhi - rlo.
-template <int LM>
-__device__ void t_tcols(const LevelDev& L, unsigned char* sm, const TailLevel& t, int h, int cur,
+// Polar lines of colour `color`: LPC lanes relax one column's segment of
+// rows [rlo, rhi) (own rows and up to h halo rows each side, clipped to the
+// plane), each lane two consecutive rows (an even and an odd global row), with
+// the even-odd SOR sweeps of the line smoother: an even row's neighbours are
+// the lane's odd row and the previous lane's odd row (a shuffle), an odd
+// row's the lane's even row and the next lane's even row.  32 / LPC columns
+// per warp pass; the own rows are kept.  The segment starts at an even row
+// (h and the CTA's first row are even).
+template <int LPC>
+__device__ void t_tcols(const LevelDev& L, unsigned char* sm, const TailLevel& t, int h, int b,
                         int j0, float s2, int n_sor, int color) {
   const int nr = L.nr, nt = L.nt, NR = nr + 2, NT = nt + 2;
   const float* rt = L.rf;
   const float* tt = L.tf;
-  const int rlo = max(-h, -j0), rhi = min(t.s + h, nt - j0), n = rhi - rlo;
-  const int par0 = (j0 + rlo) & 1;
-  for (int col = threadIdx.x; 2 * col + color < nr; col += blockDim.x) {
-    const int i = 2 * col + color;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int per = 32 / LPC;
+  const int sub = lane / LPC, k = lane - sub * LPC;
+  const int rlo = max(-h, -j0), rhi = min(t.s + h, nt - j0);
+  // the lane's rows r0 (even global row) and r0 + 1, and their coefficients
+  const int r0 = rlo + 2 * k;
+  bool on[2];
+  int rr[2], sw[2];
+  float dtj[2], tj[2], anj[2], asj[2];
+  V* er[2];
+  const V* fr[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    on[c] = r0 + c < rhi;
+    rr[c] = on[c] ? r0 + c : rlo;
+    const int j = j0 + rr[c];
+    sw[c] = tsw(nr, j);
+    er[c] = erow(sm, t, h, b, rr[c]);
+    fr[c] = rowp(sm, t.fo, nr, h, rr[c]);
+    dtj[c] = tt[TT_DT * NT + j + 1];
+    tj[c] = tt[TT_T * NT + j + 1];
+    anj[c] = tt[TT_AN * NT + j + 1];
+    asj[c] = tt[TT_AS * NT + j + 1];
+  }
+  const bool first = k == 0;
+  const int ncol = nr >> 1;   // columns of this colour: a multiple of 8
+  // pass p takes, from the block of 8 columns u = p / (8 / per), offsets
+  // {0, 1, 4, 5} (+2 on odd passes) for four groups, {0, 4} (+0..3) for two
+  const int passes = ncol / per;
+  for (int p = warp; p < passes; p += nw) {   // the same trip count on every lane
+    const int u = p / (8 / per), v = p - u * (8 / per);
+    const int q = 8 * u + (per == 4 ? 2 * v + (sub & 1) + 4 * (sub >> 1) : v + 4 * sub);
+    const int i = 2 * q + color;
     const float P = rt[RT_P * NR + i + 1], aE = rt[RT_AE * NR + i + 1], aW = rt[RT_AW * NR + i + 1];
     const float dr = rt[RT_DR * NR + i + 1], Qi = rt[RT_Q * NR + i + 1];
     const float w = L.omt_f[i], w1 = 1.0f - w;
-    V x[LM], g[LM];
-    float up[LM], dn[LM], id[LM];
+    V x[2], g[2];
+    float up[2], dn[2], id[2];
 #pragma unroll
-    for (int k = 0; k < LM; ++k) {
-      x[k] = g[k] = vz();
-      up[k] = dn[k] = id[k] = 0.f;
-      if (k < n) {
-        const int r = rlo + k, jj = j0 + r + 1;
-        const V* er = erow(sm, t, h, cur, r);
-        x[k] = er[i];
-        const V ue = (i + 1 < nr) ? er[i + 1] : vz();
-        const V uw = (i > 0) ? er[i - 1] : vz();
-        const V fv = frow(sm, t, h, r)[i];
-        g[k].x = fv.x - aE * ue.x - aW * uw.x;
-        g[k].y = fv.y - aE * ue.y - aW * uw.y;
-        id[k] = rcp_diag(dr + P * tt[TT_DT * NT + jj] - s2 * Qi * tt[TT_T * NT + jj]);
-        up[k] = P * tt[TT_AN * NT + jj];
-        dn[k] = P * tt[TT_AS * NT + jj];
+    for (int c = 0; c < 2; ++c) {
+      x[c] = g[c] = vz();
+      up[c] = dn[c] = id[c] = 0.f;
+      if (on[c]) {
+        const V* e = er[c];
+        x[c] = e[i ^ sw[c]];
+        const V ue = (i + 1 < nr) ? e[(i + 1) ^ sw[c]] : vz();
+        const V uw = (i > 0) ? e[(i - 1) ^ sw[c]] : vz();
+        const V fv = fr[c][i ^ sw[c]];
+        g[c].x = fv.x - aE * ue.x - aW * uw.x;
+        g[c].y = fv.y - aE * ue.y - aW * uw.y;
+        id[c] = rcp_diag(dr + P * dtj[c] - s2 * Qi * tj[c]);
+        up[c] = P * anj[c];
+        dn[c] = P * asj[c];
       }
     }
     for (int it = 0; it < n_sor; ++it) {
-#pragma unroll
-      for (int par = 0; par < 2; ++par) {
-#pragma unroll
-        for (int k = 0; k < LM; ++k) {
-          if (k < n && ((k + par0) & 1) == par) {
-            const V em = k > 0 ? x[k > 0 ? k - 1 : 0] : vz();
-            const V ep = k + 1 < n ? x[k + 1 < LM ? k + 1 : k] : vz();
-            const float tx = (g[k].x - up[k] * ep.x - dn[k] * em.x) * id[k];
-            const float ty = (g[k].y - up[k] * ep.y - dn[k] * em.y) * id[k];
-            x[k].x = w1 * x[k].x + w * tx;
-            x[k].y = w1 * x[k].y + w * ty;
-          }
-        }
+      {   // even rows: below, the previous lane's odd row; above, the own odd row
+        V em = shup(x[1]);
+        if (first) em = vz();
+        const float tx = (g[0].x - up[0] * x[1].x - dn[0] * em.x) * id[0];
+        const float ty = (g[0].y - up[0] * x[1].y - dn[0] * em.y) * id[0];
+        x[0].x = w1 * x[0].x + w * tx;
+        x[0].y = w1 * x[0].y + w * ty;
+      }
+      {   // odd rows: below, the own even row; above, the next lane's even row
+        V ep = shdn(x[0]);
+        if (k == LPC - 1) ep = vz();
+        const float tx = (g[1].x - up[1] * ep.x - dn[1] * x[0].x) * id[1];
+        const float ty = (g[1].y - up[1] * ep.y - dn[1] * x[0].y) * id[1];
+        x[1].x = w1 * x[1].x + w * tx;
+        x[1].y = w1 * x[1].y + w * ty;
       }
     }
 #pragma unroll
-    for (int k = 0; k < LM; ++k) {
-      const int r = rlo + k;
-      if (k < n && r >= 0 && r < t.s) erow(sm, t, h, cur, r)[i] = x[k];
-    }
+    for (int c = 0; c < 2; ++c)
+      if (on[c] && rr[c] >= 0 && rr[c] < t.s) er[c][i ^ sw[c]] = x[c];
   }
 }
 
-__device__ void t_rstep(const LevelDev& L, unsigned char* sm, const TailLevel& t, int h, int cur,
+__device__ void t_tstep(const LevelDev& L, unsigned char* sm, const TailLevel& t, int h, int b,
                         int j0, float s2, int n_sor, int color) {
-  switch (L.nr <= 32 ? 1 : L.nr >> 5) {
-    case 1: t_rlines<1>(L, sm, t, h, cur, j0, s2, n_sor, color); break;
-    case 2: t_rlines<2>(L, sm, t, h, cur, j0, s2, n_sor, color); break;
-    case 4: t_rlines<4>(L, sm, t, h, cur, j0, s2, n_sor, color); break;
-    default: t_rlines<8>(L, sm, t, h, cur, j0, s2, n_sor, color); break;
-  }
+  if (t.s + 2 * h <= 16) t_tcols<8>(L, sm, t, h, b, j0, s2, n_sor, color);
+  else t_tcols<16>(L, sm, t, h, b, j0, s2, n_sor, color);
 }
 
-__device__ void t_tstep(const LevelDev& L, unsigned char* sm, const TailLevel& t, int h, int cur,
-                        int j0, float s2, int n_sor, int color) {
-  const int n = t.s + 2 * h;
-  if (n <= 8) t_tcols<8>(L, sm, t, h, cur, j0, s2, n_sor, color);
-  else if (n <= 12) t_tcols<12>(L, sm, t, h, cur, j0, s2, n_sor, color);
-  else if (n <= 16) t_tcols<16>(L, sm, t, h, cur, j0, s2, n_sor, color);
-  else t_tcols<24>(L, sm, t, h, cur, j0, s2, n_sor, color);
-}
-
-// `cycles` smoothing cycles of one level: radial colours 0, 1, polar colours
-// 0, 1; after each step the boundary rows go to the neighbours' other halo
-// buffer and the cluster synchronises.
+// `cycles` smoothing cycles of one level (Algorithm 1: radial lines, then
+// polar lines, each in zebra order); after each step the own rows are
+// published and the cluster synchronises.
 __device__ void t_smooth(cg::cluster_group& cl, const LevelDev& L, unsigned char* sm,
-                         const TailLevel& t, int h, int& cur, int rank, int C, float s2, int n_sor,
+                         const TailLevel& t, int h, int& b, int rank, int C, float s2, int n_sor,
                          int cycles) {
   const int j0 = rank * t.s;
   for (int cyc = 0; cyc < cycles; ++cyc)
-    for (int dir = 0; dir < 2; ++dir)
-      for (int color = 0; color < 2; ++color) {
-        if (dir == 0) t_rstep(L, sm, t, h, cur, j0, s2, n_sor, color);
-        else t_tstep(L, sm, t, h, cur, j0, s2, n_sor, color);
-        __syncthreads();
-        const int nb = cur ? t.eh0 : t.eh1;
-        push_halo(cl, sm, reinterpret_cast<V*>(sm) + t.eo, t.s, L.nr, h, nb, nb + h * L.nr, rank, C);
-        cl.sync();
-        cur ^= 1;
-      }
+    for (int step = 0; step < 3; ++step) {
+      if (step == 0) t_rstep(L, sm, t, h, b, j0, s2, n_sor);
+      else t_tstep(L, sm, t, h, b, j0, s2, n_sor, step - 1);
+      __syncthreads();
+      publish(cl, sm, t, h, b, rank, C);
+      cl.sync();
+      b ^= 1;
+    }
 }
 
 // Coarse right-hand side of the CTA's own coarse rows: the area-weighted
 // restriction of the defect f - L e (Sec. 3.1), with the expression of the
-// other restriction kernels.
+// other restriction kernels.  out: the coarse row block (swizzled) or, with
+// swz = 0, a plain [s_c][n_r] array.
 __device__ void t_restrict(const LevelDev& L, const LevelDev& Cl, unsigned char* sm,
-                           const TailLevel& tf, const TailLevel& tc, int h, int cur, int rank,
-                           float s2, V* out) {
-  const int nr = L.nr, nt = L.nt, NR = nr + 2, NT = nt + 2;
+                           const TailLevel& tf, const TailLevel& tc, int h, int b, int rank,
+                           float s2, V* out, bool swz) {
+  const int nr = L.nr, nt = L.nt, NR = nr + 2, NT = nt + 2, ncr = Cl.nr;
   const float* rt = L.rf;
   const float* tt = L.tf;
-  const int j0 = rank * tf.s;
-  const int n = tc.s * Cl.nr;
+  const int j0 = rank * tf.s, j0c = rank * tc.s;
+  const int n = tc.s * ncr;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const int R = idx / Cl.nr, I = idx - R * Cl.nr;
+    const int R = idx / ncr, I = idx - R * ncr;
     float ax = 0.f, ay = 0.f;
-    for (int b = 0; b < 2; ++b)
+    for (int bb = 0; bb < 2; ++bb)
       for (int a = 0; a < 2; ++a) {
-        const int i = 2 * I + a, rr = 2 * R + b, j = j0 + rr;
-        const V* er = erow(sm, tf, h, cur, rr);
-        const V c = er[i];
-        const V E = (i + 1 < nr) ? er[i + 1] : vz();
-        const V W = (i > 0) ? er[i - 1] : vz();
-        const V N = (j + 1 < nt) ? erow(sm, tf, h, cur, rr + 1)[i] : vz();
-        const V S = (j > 0) ? erow(sm, tf, h, cur, rr - 1)[i] : vz();
+        const int i = 2 * I + a, rr = 2 * R + bb, j = j0 + rr;
+        const V* er = erow(sm, tf, h, b, rr);
+        const int sw = tsw(nr, j);
+        const V c = er[i ^ sw];
+        const V E = (i + 1 < nr) ? er[(i + 1) ^ sw] : vz();
+        const V W = (i > 0) ? er[(i - 1) ^ sw] : vz();
+        const V N = (j + 1 < nt) ? erow(sm, tf, h, b, rr + 1)[i ^ tsw(nr, j + 1)] : vz();
+        const V S = (j > 0) ? erow(sm, tf, h, b, rr - 1)[i ^ tsw(nr, j - 1)] : vz();
         const float aE = rt[RT_AE * NR + i + 1], aW = rt[RT_AW * NR + i + 1], P = rt[RT_P * NR + i + 1];
         const float aN = P * tt[TT_AN * NT + j + 1], aS = P * tt[TT_AS * NT + j + 1];
         const float d = rt[RT_DR * NR + i + 1] + P * tt[TT_DT * NT + j + 1] -
                         s2 * rt[RT_Q * NR + i + 1] * tt[TT_T * NT + j + 1];
-        const V fv = frow(sm, tf, h, rr)[i];
+        const V fv = rowp(sm, tf.fo, nr, h, rr)[i ^ sw];
         const float rx = fv.x - (aE * E.x + aW * W.x + aN * N.x + aS * S.x + d * c.x);
         const float ry = fv.y - (aE * E.y + aW * W.y + aN * N.y + aS * S.y + d * c.y);
         const float wgt = rt[RT_RW * NR + i + 1] * tt[TT_RW * NT + j + 1];
         ax += wgt * rx;
         ay += wgt * ry;
       }
-    out[R * Cl.nr + I] = make_float2(ax, ay);
+    out[R * ncr + (swz ? (I ^ tsw(ncr, j0c + R)) : I)] = make_float2(ax, ay);
   }
 }
 
@@ -263,7 +327,7 @@ __device__ void t_restrict(const LevelDev& L, const LevelDev& Cl, unsigned char*
 // neighbour across a pole or the axis, the neighbour itself across a
 // Neumann face or the origin).
 __device__ __forceinline__ V t_cval(const LevelDev& Cl, unsigned char* sm, const TailLevel& tc,
-                                    int h, int cur, int j0c, int I, int J, int m) {
+                                    int h, int bc, int j0c, int I, int J, int m) {
   float fac = 1.f;
   const float sgn = (m & 1) ? -1.f : 1.f;
   int Ic = I, Jc = J;
@@ -271,14 +335,14 @@ __device__ __forceinline__ V t_cval(const LevelDev& Cl, unsigned char* sm, const
   if (I == Cl.nr + 1) { if (Cl.gR == GH_ZERO) return vz(); Ic = Cl.nr; if (Cl.gR == GH_PARITY) fac *= sgn; }
   if (J == 0) { if (Cl.gB == GH_ZERO) return vz(); Jc = 1; if (Cl.gB == GH_PARITY) fac *= sgn; }
   if (J == Cl.nt + 1) { if (Cl.gT == GH_ZERO) return vz(); Jc = Cl.nt; if (Cl.gT == GH_PARITY) fac *= sgn; }
-  const V v = erow(sm, tc, h, cur, Jc - 1 - j0c)[Ic - 1];
+  const V v = erow(sm, tc, h, bc, Jc - 1 - j0c)[(Ic - 1) ^ tsw(Cl.nr, Jc - 1)];
   return make_float2(fac * v.x, fac * v.y);
 }
 
-// e += P e_coarse on the fine rows [rlo, rhi) (own rows and halo rows,
-// clipped to the plane), bilinear in (r^2, theta) / (R, z) (Sec. 3.1).
+// e += P e_coarse on the fine rows [rlo, rhi) of block b (own rows and halo
+// rows, clipped to the plane), bilinear in (r^2, theta) / (R, z) (Sec. 3.1).
 __device__ void t_prolong(const LevelDev& L, const LevelDev& Cl, unsigned char* sm,
-                          const TailLevel& tf, const TailLevel& tc, int h, int curf, int curc,
+                          const TailLevel& tf, const TailLevel& tc, int h, int bf, int bc,
                           int rank, int m) {
   const int nr = L.nr, nt = L.nt, NR = nr + 2, NT = nt + 2;
   const float* rt = L.rf;
@@ -292,14 +356,14 @@ __device__ void t_prolong(const LevelDev& L, const LevelDev& Cl, unsigned char* 
     const int I1 = (i1 & 1) ? (i1 + 1) / 2 - 1 : i1 / 2, J1 = (j1 & 1) ? (j1 + 1) / 2 - 1 : j1 / 2;
     const float p1 = rt[RT_P1 * NR + i1], p2 = rt[RT_P2 * NR + i1];
     const float q1 = tt[TT_P1 * NT + j1], q2 = tt[TT_P2 * NT + j1];
-    const V a = t_cval(Cl, sm, tc, h, curc, j0c, I1, J1, m);
-    const V b = t_cval(Cl, sm, tc, h, curc, j0c, I1 + 1, J1, m);
-    const V c = t_cval(Cl, sm, tc, h, curc, j0c, I1, J1 + 1, m);
-    const V d = t_cval(Cl, sm, tc, h, curc, j0c, I1 + 1, J1 + 1, m);
-    V* e = erow(sm, tf, h, curf, r) + i;
+    const V a = t_cval(Cl, sm, tc, h, bc, j0c, I1, J1, m);
+    const V bv = t_cval(Cl, sm, tc, h, bc, j0c, I1 + 1, J1, m);
+    const V c = t_cval(Cl, sm, tc, h, bc, j0c, I1, J1 + 1, m);
+    const V d = t_cval(Cl, sm, tc, h, bc, j0c, I1 + 1, J1 + 1, m);
+    V* e = erow(sm, tf, h, bf, r) + (i ^ tsw(nr, j));
     V u = *e;
-    u.x += p1 * q1 * a.x + p2 * q1 * b.x + p1 * q2 * c.x + p2 * q2 * d.x;
-    u.y += p1 * q1 * a.y + p2 * q1 * b.y + p1 * q2 * c.y + p2 * q2 * d.y;
+    u.x += p1 * q1 * a.x + p2 * q1 * bv.x + p1 * q2 * c.x + p2 * q2 * d.x;
+    u.y += p1 * q1 * a.y + p2 * q1 * bv.y + p1 * q2 * c.y + p2 * q2 * d.y;
     *e = u;
   }
 }
@@ -310,8 +374,7 @@ __device__ void t_prolong(const LevelDev& L, const LevelDev& Cl, unsigned char* 
 // back-transforms its own rows and the coarse halo rows its prolongation
 // reads.  G: the gathered coarse right-hand side [nt][nr] (all rows).
 __device__ void t_coarsest(cg::cluster_group& cl, const TailArgs& a, const LevelDev& Lc,
-                           unsigned char* sm, const TailLevel& tc, int h, int cur, int rank,
-                           int slot) {
+                           unsigned char* sm, const TailLevel& tc, int h, int rank, int slot) {
   const int nr = Lc.nr, nt = Lc.nt, nc = nr * nt, C = a.C, sc = tc.s, k0 = rank * sc;
   const V* G = reinterpret_cast<const V*>(sm + a.g_off);
   double2* Z = reinterpret_cast<double2*>(sm + a.z_off);    // [nt][nr], both components
@@ -321,8 +384,6 @@ __device__ void t_coarsest(cg::cluster_group& cl, const TailArgs& a, const Level
   const double* Vm = Fq;
   const double* Vi = Vm + vr * nt;
   const double* invd = Vi + nt * vr;
-  const double* cp = invd + nt * nr;
-  const double* lid = cp + nt * nr;
   (void)nc;
   // z_k = (1/pivot) (V^-1 f)_k for the own k (mirror-symmetric: sums of
   // mirrored rows for even eigenvectors, differences for odd ones)
@@ -346,31 +407,43 @@ __device__ void t_coarsest(cg::cluster_group& cl, const TailArgs& a, const Level
     else zl[kk * nr + i].x = zv;
   }
   __syncthreads();
-  // Thomas sweeps, one FMA per step each way (2 sc independent systems on
-  // the first warp)
-  for (int q = threadIdx.x < 32 ? int(threadIdx.x) : 2 * sc; q < 2 * sc; q += 32) {
-    const int c = q / sc, kk = q - c * sc, k = k0 + kk;
-    double* zz = reinterpret_cast<double*>(zl + kk * nr) + c;   // stride 2
-    const double* lk = lid + k * nr;
-    const double* ck = cp + k * nr;
-    double dp = zz[0];
-    for (int i = 1; i < nr; ++i) {
-      dp = fma(-lk[i], dp, zz[2 * i]);
-      zz[2 * i] = dp;
-    }
-    double xv = dp;
-    for (int i = nr - 2; i >= 0; --i) {
-      xv = fma(-ck[i], xv, zz[2 * i]);
-      zz[2 * i] = xv;
+  // the Thomas sweeps of the own eigenvalues as the precomputed matrix
+  // product x = A_k z (written into the own rows of Z): `parts` threads per
+  // output share its dot product
+  {
+    const int nout = 2 * sc * nr;
+    int parts = 1;
+    while (parts < 32 && parts * 2 * nout <= int(blockDim.x)) parts *= 2;
+    const int seg = (nr + parts - 1) / parts;
+    for (int t = threadIdx.x; t < ((nout * parts + 31) / 32) * 32; t += blockDim.x) {
+      const int o = t / parts, part = t - o * parts;
+      double acc = 0.0;
+      int kk = 0, c = 0, i = 0;
+      if (o < nout) {
+        c = o / (sc * nr);
+        const int rq = o - c * sc * nr;
+        kk = rq / nr;
+        i = rq - kk * nr;
+        const double* Ak = a.cinv + ((size_t(slot) * nt + k0 + kk) * nr + i) * nr;
+        const double* zk = reinterpret_cast<const double*>(zl + kk * nr) + c;
+        for (int mm = part * seg; mm < min(nr, (part + 1) * seg); ++mm) acc = fma(Ak[mm], zk[2 * mm], acc);
+      }
+      for (int off = parts >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (o < nout && part == 0) {
+        double2* zo = Z + (k0 + kk) * nr + i;
+        if (c) zo->y = acc;
+        else zo->x = acc;
+      }
     }
   }
   __syncthreads();
-  // every CTA receives the own z rows
+  // every other CTA receives the own rows of x
   {
     const int n = sc * nr;
     for (int tgt = 0; tgt < C; ++tgt) {
+      if (tgt == rank) continue;
       double2* zt = cl.map_shared_rank(Z, tgt);
-      for (int q = threadIdx.x; q < n; q += blockDim.x) zt[k0 * nr + q] = zl[q];
+      for (int q = threadIdx.x; q < n; q += blockDim.x) zt[k0 * nr + q] = Z[k0 * nr + q];
     }
   }
   cl.sync();
@@ -406,7 +479,7 @@ __device__ void t_coarsest(cg::cluster_group& cl, const TailArgs& a, const Level
       ex = float(ax);
       ey = float(ay);
     }
-    erow(sm, tc, h, cur, j - j0c)[i] = make_float2(ex, ey);
+    erow(sm, tc, h, 0, j - j0c)[i ^ tsw(nr, j)] = make_float2(ex, ey);
   }
   __syncthreads();
 }
@@ -443,22 +516,26 @@ __global__ void __launch_bounds__(kTailThreads, 1)
       sL[threadIdx.x] = d;
     }
   }
-  // FP64 solution rows -1 .. s0 of level 0 (own rows and one halo row each side)
+  // FP64 solution: the own rows stay in global memory (L2-resident, written
+  // only by this CTA); the halo rows j0 - 1 and j0 + s0 are kept here and
+  // updated with the same values their owners add, so no CTA reads a row
+  // another CTA writes during the kernel
   const TailLevel& t0 = a.lv[0];
   const int nr0 = t0.L.nr, nt0 = t0.L.nt, s0 = t0.s, j00 = rank * s0, n0 = nr0 * nt0;
   const size_t base = size_t(p) * n0;
-  double2* U = reinterpret_cast<double2*>(sm + a.u_off);
-  for (int idx = threadIdx.x; idx < (s0 + 2) * nr0; idx += blockDim.x) {
-    const int j = j00 - 1 + idx / nr0, i = idx - (idx / nr0) * nr0;
-    U[idx] = (j >= 0 && j < nt0) ? ug[base + size_t(j) * nr0 + i] : make_double2(0.0, 0.0);
+  double2* Uh = reinterpret_cast<double2*>(sm + a.u_off);   // [2][nr0]: rows -1 and s0
+  double2* Uo = ug + base + size_t(j00) * nr0;               // own rows (global)
+  for (int idx = threadIdx.x; idx < 2 * nr0; idx += blockDim.x) {
+    const int side = idx / nr0, i = idx - side * nr0, j = side ? j00 + s0 : j00 - 1;
+    Uh[idx] = (j >= 0 && j < nt0) ? ug[base + size_t(j) * nr0 + i] : make_double2(0.0, 0.0);
   }
   cp_async_wait_all();
   // every CTA of the cluster has started before any writes into a peer's
   // shared memory
   cl.sync();
-  int cur[8];
+  int bl[8];   // per level: the row block the next step reads
 #pragma unroll
-  for (int l = 0; l < 8; ++l) cur[l] = 0;
+  for (int l = 0; l < 8; ++l) bl[l] = 0;
   int it = *S.iter;
   double px = S.nr2[p].x, py = S.nr2[p].y;
   const double2 nf = S.nf2[p];
@@ -474,15 +551,16 @@ __global__ void __launch_bounds__(kTailThreads, 1)
     float ax = 0.f, ay = 0.f;
     {
       const LevelDev& L0 = sL[0];
-      V* f0 = frow(sm, t0, h, 0);
       for (int idx = threadIdx.x; idx < s0 * nr0; idx += blockDim.x) {
         const int r = idx / nr0, i = idx - r * nr0, j = j00 + r;
-        const double2* ur = U + (r + 1) * nr0;
+        const double2* ur = Uo + r * nr0;
+        const double2* un = r + 1 < s0 ? ur + nr0 : Uh + nr0;
+        const double2* us = r > 0 ? ur - nr0 : Uh;
         const double2 c = ur[i];
         const double2 E = (i + 1 < nr0) ? ur[i + 1] : make_double2(0.0, 0.0);
         const double2 W = (i > 0) ? ur[i - 1] : make_double2(0.0, 0.0);
-        const double2 N = (j + 1 < nt0) ? ur[i + nr0] : make_double2(0.0, 0.0);
-        const double2 Sv = (j > 0) ? ur[i - nr0] : make_double2(0.0, 0.0);
+        const double2 N = (j + 1 < nt0) ? un[i] : make_double2(0.0, 0.0);
+        const double2 Sv = (j > 0) ? us[i] : make_double2(0.0, 0.0);
         const size_t cq = size_t(j) * nr0 + i;
         const double aE = rd0[RT_AE * NR0 + i + 1], aW = rd0[RT_AW * NR0 + i + 1];
         const double aN = a.ctab[cq], aS = a.ctab[n0 + cq];
@@ -491,7 +569,7 @@ __global__ void __launch_bounds__(kTailThreads, 1)
         const double rx = fv.x - (aE * E.x + aW * W.x + aN * N.x + aS * Sv.x + d * c.x);
         const double ry = fv.y - (aE * E.y + aW * W.y + aN * N.y + aS * Sv.y + d * c.y);
         const V ro = make_float2(float(rx), float(ry));
-        f0[idx] = ro;
+        rowp(sm, t0.fo, nr0, h, r)[i ^ tsw(nr0, j)] = ro;
         const float dv = L0.rf[RT_V * NR0 + i + 1] * L0.tf[TT_V * NT0 + j + 1];
         ax += dv * ro.x * ro.x;
         ay += dv * ro.y * ro.y;
@@ -508,7 +586,8 @@ __global__ void __launch_bounds__(kTailThreads, 1)
       for (int w = 0; w < int(blockDim.x >> 5); ++w) { tsum.x += red[w].x; tsum.y += red[w].y; }
       *cl.map_shared_rank(part + rank, int(threadIdx.x)) = tsum;
     }
-    push_halo(cl, sm, frow(sm, t0, h, 0), s0, nr0, h, t0.fo, t0.fo + (h + s0) * nr0, rank, C);
+    __syncthreads();
+    push_halo(cl, sm, rowp(sm, t0.fo, nr0, h, 0), t0.fo, 0, s0, nr0, h, rank, C);
     cl.sync();
     // App. B criterion, evaluated identically by every thread of the cluster
     double sx = 0.0, sy = 0.0;
@@ -530,27 +609,25 @@ __global__ void __launch_bounds__(kTailThreads, 1)
     for (int l = 0; l < K - 1; ++l) {
       const TailLevel& t = a.lv[l];
       const LevelDev L = sL[l];
-      {
+      {   // e = 0 on the own rows and the halo buffer the first step reads
         V* eo = reinterpret_cast<V*>(sm) + t.eo;
-        V* eh = reinterpret_cast<V*>(sm) + (cur[l] ? t.eh1 : t.eh0);
+        V* eh = reinterpret_cast<V*>(sm) + t.eh[bl[l]];
         for (int k = threadIdx.x; k < t.s * L.nr; k += blockDim.x) eo[k] = vz();
         for (int k = threadIdx.x; k < 2 * h * L.nr; k += blockDim.x) eh[k] = vz();
       }
       __syncthreads();
-      t_smooth(cl, L, sm, t, h, cur[l], rank, C, s2, a.n_sor, t.nu1);
+      t_smooth(cl, L, sm, t, h, bl[l], rank, C, s2, a.n_sor, t.nu1);
       const TailLevel& tc = a.lv[l + 1];
       const LevelDev Lq = sL[l + 1];
       if (l + 1 < K - 1) {
-        V* fo = frow(sm, tc, h, 0);
-        t_restrict(L, Lq, sm, t, tc, h, cur[l], rank, s2, fo);
+        t_restrict(L, Lq, sm, t, tc, h, bl[l], rank, s2, rowp(sm, tc.fo, Lq.nr, h, 0), true);
         __syncthreads();
-        push_halo(cl, sm, fo, tc.s, Lq.nr, h, tc.fo, tc.fo + (h + tc.s) * Lq.nr, rank, C);
-        // the coarse level's first step reads only its own rows; the
-        // synchronisation after that step publishes these halo rows
+        push_halo(cl, sm, rowp(sm, tc.fo, Lq.nr, h, 0), tc.fo, 0, tc.s, Lq.nr, h, rank, C);
+        cl.sync();   // the coarse level's first step reads the halo row s of f
       } else {
         V* G = reinterpret_cast<V*>(sm + a.g_off);
         V* own = G + rank * tc.s * Lq.nr;
-        t_restrict(L, Lq, sm, t, tc, h, cur[l], rank, s2, own);
+        t_restrict(L, Lq, sm, t, tc, h, bl[l], rank, s2, own, false);
         __syncthreads();
         const int n = tc.s * Lq.nr;
         for (int tgt = 0; tgt < C; ++tgt) {
@@ -561,30 +638,29 @@ __global__ void __launch_bounds__(kTailThreads, 1)
         cl.sync();
       }
     }
-    t_coarsest(cl, a, sL[K - 1], sm, a.lv[K - 1], h, cur[K - 1], rank, slot);
+    t_coarsest(cl, a, sL[K - 1], sm, a.lv[K - 1], h, rank, slot);
     for (int l = K - 2; l >= 0; --l) {
       const TailLevel& t = a.lv[l];
       const LevelDev L = sL[l];
-      t_prolong(L, sL[l + 1], sm, t, a.lv[l + 1], h, cur[l], cur[l + 1], rank, m);
+      t_prolong(L, sL[l + 1], sm, t, a.lv[l + 1], h, bl[l], bl[l + 1], rank, m);
       __syncthreads();
-      t_smooth(cl, L, sm, t, h, cur[l], rank, C, s2, a.n_sor, t.nu2);
+      t_smooth(cl, L, sm, t, h, bl[l], rank, C, s2, a.n_sor, t.nu2);
     }
     // u += e on the own rows and the two halo rows (the halo rows of e are
     // current, so every copy of a row gets the owner's values)
     for (int idx = threadIdx.x; idx < (s0 + 2) * nr0; idx += blockDim.x) {
       const int r = idx / nr0 - 1, i = idx - (idx / nr0) * nr0, j = j00 + r;
       if (j < 0 || j >= nt0) continue;
-      const V v = erow(sm, t0, h, cur[0], r)[i];
-      double2 x = U[idx];
-      x.x += double(v.x);
-      x.y += double(v.y);
-      U[idx] = x;
+      const V v = erow(sm, t0, h, bl[0], r)[i ^ tsw(nr0, j)];
+      double2* x = r < 0 ? Uh + i : (r >= s0 ? Uh + nr0 + i : Uo + r * nr0 + i);
+      double2 y = *x;
+      y.x += double(v.x);
+      y.y += double(v.y);
+      *x = y;
     }
     __syncthreads();
     ++it;
   }
-  for (int idx = threadIdx.x; idx < s0 * nr0; idx += blockDim.x)
-    ug[base + size_t(j00) * nr0 + idx] = U[nr0 + idx];
   if (rank == 0 && threadIdx.x == 0) {
     // the solve's iteration count is the largest over the planes; the last
     // cluster to finish folds it into the counter and clears the scratch

@@ -151,15 +151,14 @@ void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t 
 
 // ---- cluster-resident tail iterations (k_tail.cu) ------------------------------
 // One level of the tail kernel's per-CTA layout: each CTA of a cluster owns
-// `s` consecutive rows of the level (rows rank * s ..), keeps them in shared
-// memory (eo), plus two buffers of the 2h rows around them owned by its
-// neighbours (eh0 / eh1, alternating between smoothing steps) and the
-// right-hand side of its rows and their halo (fo, rows -h .. s + h - 1).
-// Offsets in complex FP32 elements.
+// `s` consecutive rows of the level (rows rank * s ..).  Its error lives in
+// the own rows eo and two halo buffers eh[0], eh[1] (h rows above, then h
+// rows below), used in turn by the smoothing steps; the right-hand side in
+// one block fo of rows -h .. s + h - 1.  Offsets in complex FP32 elements.
 struct TailLevel {
   LevelDev L;        // global tables, ghost rules
   int s;             // rows per CTA
-  int eo, eh0, eh1, fo;
+  int eo, eh[2], fo;
   int tab;           // offset (floats) of this level's tables in a slot's packed block
   int nu1, nu2;      // smoothing cycles before / after the coarse correction
 };
@@ -173,6 +172,8 @@ struct TailArgs {
   const double* ctab;       // level-0 per-cell FP64 products [4][nt][nr]
   const double* sep;        // separable coarsest-level factors per slot
   int sep_stride, sep_sym;
+  const double* cinv;       // per slot and eigenvalue k: the radial Thomas sweeps as a
+                            // matrix [nt][nr][nr] (x = A_k z, z the scaled transform)
   double tol;
   int max_cycles, stagnation;
   int* titer;               // scratch: max iteration count over the clusters

@@ -241,14 +241,11 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
     // tail: per level, at the next odd element offset, RT_N x (nr+2) radial
     // and TT_N x (nt+2) polar entries, then nt r-line and nr polar-line
     // omegas of the slot
-    size_t tab = 0;
+    std::vector<int> nrs(nl), nts(nl);
+    for (int l = 0; l < nl; ++l) { nrs[l] = lv[l].nr; nts[l] = lv[l].nt; }
+    const size_t tab = tail_tables(nrs, nts, tl);
     std::vector<size_t> off(nl);
-    for (int l = 0; l < nl && l < 8; ++l) {
-      tab = (tab + 1) / 2 * 2 + 1;
-      off[l] = tab;
-      tab += size_t(RT_N) * (lv[l].nr + 2) + size_t(TT_N) * (lv[l].nt + 2) + lv[l].nr + lv[l].nt;
-    }
-    tab = (tab + 3) / 4 * 4;
+    for (int l = 0; l < nl && l < 8; ++l) off[l] = size_t(tl.lv[l].tab);
     const size_t S_ = modes.size();
     std::vector<float> pk(S_ * tab, 0.f);
     for (size_t q = 0; q < S_; ++q)
@@ -262,8 +259,34 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
         std::copy(hl.om_t.begin() + q * nr, hl.om_t.begin() + (q + 1) * nr, o);
       }
     d_tail_tabs = upload(A, pk);
-    tl.tab_stride = int(tab);
-    for (int l = 0; l < nl && l < 8; ++l) tl.lv[l].tab = int(off[l]);
+    if (H.sep_stride > 0) {
+      // per slot and eigenvalue k the two Thomas sweeps of the coarsest
+      // radial systems applied to unit vectors: column m of A_k is the
+      // sweeps' result for z = e_m (the tail applies them as one FP64
+      // matrix product instead of a chain of dependent steps)
+      const int nrc = lv[nl - 1].nr, ntc = lv[nl - 1].nt, vr = H.sep_sym ? ntc / 2 : ntc;
+      std::vector<double> ci(S_ * size_t(ntc) * nrc * nrc);
+      std::vector<double> zz(nrc);
+      for (size_t q = 0; q < S_; ++q) {
+        const double* Fq = H.coarse_sep.data() + q * H.sep_stride;
+        const double* invd = Fq + size_t(vr) * ntc + size_t(ntc) * vr;
+        const double* cp = invd + size_t(ntc) * nrc;
+        const double* lid = cp + size_t(ntc) * nrc;
+        for (int k = 0; k < ntc; ++k)
+          for (int m = 0; m < nrc; ++m) {
+            std::fill(zz.begin(), zz.end(), 0.0);
+            zz[m] = 1.0;
+            double dp = zz[0];
+            for (int i = 1; i < nrc; ++i) { dp = std::fma(-lid[k * nrc + i], dp, zz[i]); zz[i] = dp; }
+            double xv = dp;
+            for (int i = nrc - 2; i >= 0; --i) { xv = std::fma(-cp[k * nrc + i], xv, zz[i]); zz[i] = xv; }
+            double* Ak = ci.data() + ((q * ntc + k) * size_t(nrc)) * nrc;
+            for (int i = 0; i < nrc; ++i) Ak[size_t(i) * nrc + m] = zz[i];
+          }
+      }
+      tl.cinv = upload(A, ci);
+      if (!tl.cinv) { err = "out of device memory"; return false; }
+    }
     tl.titer = static_cast<int*>(A.get(2 * sizeof(int)));
     tl.tdone = tl.titer ? tl.titer + 1 : nullptr;
     if (!d_tail_tabs || !tl.titer) { err = "out of device memory"; return false; }
@@ -357,36 +380,49 @@ void MGSolver::set_schedule(int nu1, int nu2, int n_sor, Tiles tiles, int nu1f, 
 // level), radial lines of at most 256 cells, polar segments (own rows plus
 // h = 2 n_sor halo rows each side) of at most 24 cells, and a shared-memory
 // layout within the SM's 227 KB.
-bool MGSolver::prepare_tail() {
-  tail_planes = 0;
-  if (!opt.precision || tail_cap == 0 || !d_tail_tabs || H.sep_stride <= 0) return false;
-  const int nl = int(lv.size());
-  if (nl < 2 || nl > 8) return false;
-  const int h = 2 * opt.n_sor;
-  const int ntc = lv[nl - 1].nt, nrc = lv[nl - 1].nr;
+size_t tail_tables(const std::vector<int>& nr, const std::vector<int>& nt, TailArgs& t) {
+  size_t tab = 0;
+  for (size_t l = 0; l < nr.size() && l < 8; ++l) {
+    tab = (tab + 1) / 2 * 2 + 1;   // odd offset: pairs of table entries are aligned vector loads
+    t.lv[l].tab = int(tab);
+    tab += size_t(RT_N) * (nr[l] + 2) + size_t(TT_N) * (nt[l] + 2) + nr[l] + nt[l];
+  }
+  tab = (tab + 3) / 4 * 4;
+  t.tab_stride = int(tab);
+  return tab;
+}
+
+size_t tail_layout(const std::vector<int>& nr, const std::vector<int>& nt, int n_sor, bool separable,
+                   TailArgs& t) {
+  const int nl = int(nr.size());
+  if (!separable || nl < 2 || nl > 8) return 0;
+  const int h = 2 * n_sor;
+  const int ntc = nt[nl - 1], nrc = nr[nl - 1];
   int C = 16;
   while (C > ntc) C /= 2;
-  if (C < 2 || ntc % C) return false;
-  TailArgs t = tl;
+  if (C < 2 || ntc % C) return 0;
   t.nlev = nl;
   t.C = C;
   t.h = h;
-  t.n_sor = opt.n_sor;
+  t.n_sor = n_sor;
+  tail_tables(nr, nt, t);
   size_t off = 0;   // complex FP32 elements
   for (int l = 0; l < nl; ++l) {
-    const int nr = lv[l].nr, nt = lv[l].nt, s = nt / C;
-    if (nt % C || s < 1 || nr > 256 || (nr & 1)) return false;
-    if (l < nl - 1 && (s < 2 || (s & 1) || s + 2 * h > 24)) return false;
+    const int s = nt[l] / C;
+    if (nt[l] % C || s < 1 || nr[l] > 256 || (nr[l] & 1)) return 0;
+    if (l < nl - 1 && (s < 2 || (s & 1) || s + 2 * h > 24 || nr[l] < 16)) return 0;
     TailLevel& q = t.lv[l];
-    q.L = lv[l];
+    const size_t halo = size_t(2 * h) * nr[l];
     q.s = s;
-    q.eo = int(off); off += size_t(s) * nr;
-    q.eh0 = int(off); off += size_t(2 * h) * nr;
-    q.eh1 = int(off); off += size_t(2 * h) * nr;
-    q.fo = int(off); off += size_t(s + 2 * h) * nr;
-    const bool fused = l >= first;
-    q.nu1 = fused ? vs.nu1 : opt.nu1;
-    q.nu2 = fused ? vs.nu2 : opt.nu2;
+    q.eo = int(off); off += size_t(s) * nr[l];
+    q.eh[0] = int(off); off += halo;
+    if (l < nl - 1) {   // smoothed levels: a second halo buffer and the right-hand side
+      q.eh[1] = int(off); off += halo;
+      q.fo = int(off); off += size_t(s + 2 * h) * nr[l];
+    } else {            // the coarsest level's right-hand side is gathered whole (g_off)
+      q.eh[1] = q.eh[0];
+      q.fo = q.eo;
+    }
   }
   t.g_off = int(off * sizeof(float2));
   off += size_t(ntc) * nrc;
@@ -396,19 +432,39 @@ bool MGSolver::prepare_tail() {
   t.zl_off = int(bytes);
   bytes += size_t(ntc / C) * nrc * sizeof(double2);
   t.u_off = int(bytes);
-  bytes += size_t(lv[0].nt / C + 2) * lv[0].nr * sizeof(double2);
+  bytes += size_t(2) * nr[0] * sizeof(double2);   // the FP64 solution's two halo rows
   t.part_off = int(bytes);
   bytes += size_t(C) * 32;
   t.tab_off = int(bytes);
   bytes += size_t(t.tab_stride) * sizeof(float);
   bytes = (bytes + 15) / 16 * 16;
   t.smem_bytes = bytes;
-  if (bytes > 200 * 1024) return false;   // leaves the kernel's static shared memory room
+  return bytes <= kTailSmemMax ? bytes : 0;
+}
+
+// Layout of the cluster-resident tail for the current schedule (see
+// tail_layout): the mixed path only.
+bool MGSolver::prepare_tail() {
+  tail_planes = 0;
+  if (!opt.precision || tail_cap == 0 || !d_tail_tabs) return false;
+  const int nl = int(lv.size());
+  std::vector<int> nr(nl), nt(nl);
+  for (int l = 0; l < nl; ++l) { nr[l] = lv[l].nr; nt[l] = lv[l].nt; }
+  TailArgs t = tl;
+  if (!tail_layout(nr, nt, opt.n_sor, H.sep_stride > 0, t)) return false;
+  for (int l = 0; l < nl; ++l) {
+    TailLevel& q = t.lv[l];
+    q.L = lv[l];
+    const bool fused = l >= first;
+    q.nu1 = fused ? vs.nu1 : opt.nu1;
+    q.nu2 = fused ? vs.nu2 : opt.nu2;
+  }
   t.ctab = d_ctab;
   t.sep = d_sep;
   t.sep_stride = H.sep_stride;
   t.sep_sym = H.sep_sym;
   t.tabs = d_tail_tabs;
+  if (!t.cinv) return false;
   const int fit = tail_max_clusters(t);
   if (fit < 1) return false;
   tl = t;

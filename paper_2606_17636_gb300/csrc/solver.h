@@ -27,6 +27,18 @@ struct MGOptions {
   int stagnation = 0;  // retire planes whose residual stops falling
 };
 
+// Shared-memory layout of the cluster-resident tail (k_tail.cu) for levels of
+// nr[l] x nt[l] cells and n_sor SOR sweeps: fills t's cluster size, rows per
+// CTA, offsets and table layout; returns the bytes per CTA, or 0 when the
+// plan does not allow the tail (a coarsest level without the separable form,
+// cluster slabs that do not divide the levels, radial lines above 256 cells
+// (or below 16 on a smoothed level),
+// polar segments above 24 cells, or more than kTailSmemMax bytes).
+constexpr size_t kTailSmemMax = 224 * 1024;
+size_t tail_layout(const std::vector<int>& nr, const std::vector<int>& nt, int n_sor, bool separable,
+                   TailArgs& t);
+size_t tail_tables(const std::vector<int>& nr, const std::vector<int>& nt, TailArgs& t);
+
 class MGSolver {
  public:
   // fine: plane geometry; modes[s]: azimuthal mode number of slot s;

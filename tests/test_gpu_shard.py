@@ -29,11 +29,19 @@ def test_slab_transforms_equal_the_whole_transform(ps, key):
     rho = torch.from_numpy(clumps(sp, 50)).cuda()
     f = s.stage_forward(rho)
     n_r = sp["n_r"]
-    for a, b in ((0, 5), (5, n_r - 3), (n_r - 3, n_r), (0, n_r)):
+    inv = s.stage_inverse(f)
+    # the transform packs two real rows (i, i + 1) into one complex sequence,
+    # counted from the slab's first row (a last unpaired row is packed with
+    # zeros): slabs with even ends pair the rows as the whole transform does
+    # (bitwise equal), others agree to rounding
+    for a, b in ((0, 5), (6, n_r - 2), (n_r - 4, n_r), (0, n_r), (5, n_r - 3), (n_r - 3, n_r)):
         fr = s.stage_forward_rows(rho[a:b].contiguous())
-        assert torch.equal(fr, f[:, :, a:b])
         back = s.stage_inverse_rows(fr.contiguous())
-        assert torch.equal(back, s.stage_inverse(f)[a:b])
+        if a % 2 == 0 and b % 2 == 0:
+            assert torch.equal(fr, f[:, :, a:b]) and torch.equal(back, inv[a:b])
+        else:
+            assert (fr - f[:, :, a:b]).abs().max() <= 1e-14 * f.abs().max()
+            assert (back - inv[a:b]).abs().max() <= 1e-14 * inv.abs().max()
     with pytest.raises(ps.PSolveError):
         s.stage_forward_rows(rho[:0].contiguous())
     s.close()

@@ -127,3 +127,29 @@ def test_batched_solve_matches_single_solves(ps):
         assert torch.equal(a, b)
     for s in solvers:
         s.close()
+
+
+def test_batch_graph_matches_single_solves_and_times_each_problem(ps):
+    """Independent problems captured in one graph (psolve_batch_*), each on
+    its own branch: every potential equals its single solve bit for bit, the
+    graph replays, and every problem reports a completion time."""
+    keys = ["cyl_axis", "sph_log", "cyl_cavity", "sph_offcentre"]
+    solvers = [ps.Solver.from_spec(SMALL[k], precision=ps.MIXED) for k in keys]
+    rhos = [torch.from_numpy(clumps(SMALL[k], 60 + i)).cuda() for i, k in enumerate(keys)]
+    singles = [s.solve(r, tol=1e-8)[0].clone() for s, r in zip(solvers, rhos)]
+    phis = [torch.empty_like(r) for r in rhos]
+    b = ps.Batch(solvers, rhos, phis, tol=1e-8)
+    for _ in range(2):
+        for p in phis:
+            p.zero_()
+        rc, lat = b.run()
+        assert rc == ps.OK
+        for a, c in zip(phis, singles):
+            assert torch.equal(a, c)
+        assert all(0.0 < t for t in lat) and len(lat) == len(keys)
+    b.close()
+    with pytest.raises(ps.PSolveError) as e:
+        ps.Batch([solvers[0], solvers[0]], [rhos[0], rhos[0]], [phis[0], torch.empty_like(phis[0])])
+    assert e.value.code == ps.ERR_ARG
+    for s in solvers:
+        s.close()

@@ -110,3 +110,24 @@ def test_coarsest_factors_solve_the_coarsest_operator(ps, sp, bound):
 def test_block_factors_report_no_separable_check(ps):
     p = ps.plan_inspect(wl.spec(wl.CYLINDRICAL, 8, 128, 8, wl.UNIFORM, 0.2, 1.0))
     assert p["coarsest"] == "block-tridiagonal" and p["coarse_check"] == -1.0
+
+
+def test_tail_layout_of_the_benchmark_grid():
+    """The cluster-resident tail's shared-memory layout (16 CTAs per plane,
+    row slabs of 8/4/2/1 rows on the 256 x 128 .. 32 x 16 levels) fits one
+    SM for the smoothing sweeps the autotuner picks (halo depth 2 n_sor, up
+    to three sweeps); four need too deep a halo, and the FP64 path keeps the
+    batched loop."""
+    import paper_2606_17636_gb300 as ps
+    from paper_2606_17636_gb300 import workloads
+    w3 = workloads.spec(workloads.SPHERICAL, 256, 128, 256, workloads.LOG, 0.05, 20.0)
+    for n_sor in (1, 2, 3):
+        p = ps.plan_inspect(w3, n_sor=n_sor)
+        assert p["tail_cluster_ctas"] == 16
+        assert 0 < p["tail_smem_bytes"] <= 224 * 1024
+    assert ps.plan_inspect(w3, n_sor=1)["tail_smem_bytes"] < ps.plan_inspect(w3, n_sor=2)["tail_smem_bytes"]
+    assert ps.plan_inspect(w3, n_sor=4)["tail_cluster_ctas"] == 0
+    assert ps.plan_inspect(w3, precision=0)["tail_cluster_ctas"] == 0
+    # radial lines of 512 cells are beyond the tail kernel's line relaxation
+    w4 = workloads.spec(workloads.CYLINDRICAL, 512, 256, 512, workloads.UNIFORM, 0.2, 4.0, -1.0, 1.0)
+    assert ps.plan_inspect(w4)["tail_cluster_ctas"] == 0
