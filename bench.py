@@ -39,6 +39,7 @@ def args_():
     a.add_argument("--warmup", type=int, default=3)
     a.add_argument("--impl", default="ours", choices=["ours", "reference"])
     a.add_argument("--no-baseline", action="store_true")
+    a.add_argument("--no-serving", action="store_true", help="skip the sixteen-problem one-graph batch")
     a.add_argument("--no-tune", action="store_true",
                    help="keep the default smoothing schedule and tile shapes (skip psolve_autotune)")
     a.add_argument("--replicas", action="store_true",
@@ -319,6 +320,8 @@ def ours(a, ws, rank, local):
     roof = vcycle_roofline(torch, ps, sm, stream)
     roof_stream = smoother_roofline(torch, ps, sm, stream)
     launches = launches_per_solve(sm, st)
+    serve = serving(torch, ps, workloads) if (rank == 0 and not a.no_serving) else None
+    multi = multi_density(torch, ps, workloads, w) if (rank == 0 and not a.no_serving) else None
     if rank != 0:
         return
     cells = spec["n_r"] * spec["n_tz"] * spec["n_phi"]
@@ -349,6 +352,8 @@ def ours(a, ws, rank, local):
         "warm_timestepping": warm,
         "roofline": roof,
         "roofline_streaming": roof_stream,
+        "serving": serve,
+        "multi_density": multi,
         "clocks": clocks,
     }
     if not a.no_baseline:
@@ -441,6 +446,92 @@ def sharded(a, ws, rank, local):
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+
+
+def multi_density(torch, ps, workloads, w, nd=8, warm=2, runs=5):
+    """One plan, nd densities of the workload's geometry per solve
+    (psolve_create_multi): the workload's density and nd - 1 seeded
+    variations of it, mixed precision, captured graph, tol 1e-8.  The modes of
+    all densities iterate together, so the slow low modes share the late
+    iterations.  Reports solves (densities) per second."""
+    import numpy as np
+    spec = w["spec"]
+    rng = np.random.default_rng(7)
+    _, _, ph = workloads.midpoints(spec)
+    rhos = [w["rho"]] + [w["rho"] * (1.0 + 0.2 * rng.uniform(-1, 1) * np.cos((k + 1) * ph))[None, None, :]
+                         for k in range(nd - 1)]
+    rho = torch.from_numpy(np.ascontiguousarray(np.stack(rhos))).cuda()
+    s = ps.Solver.from_spec(spec, precision=ps.MIXED, n_densities=nd)
+    phi = torch.empty_like(rho)
+    for _ in range(warm):
+        s.solve(rho, phi, tol=TOL)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(runs):
+        s.solve(rho, phi, tol=TOL)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    st = s.stats()
+    s.close()
+    return {"n_densities": nd, "solves_per_s": nd * runs / t, "ms_per_call": 1e3 * t / runs,
+            "iterations": [st["iterations_psi"], st["iterations_phi"]],
+            "densities": "the workload's density and %d variations rho (1 + a_k cos((k+1) phi)), "
+                         "a_k uniform in [-0.2, 0.2]" % (nd - 1)}
+
+
+def serving(torch, ps, workloads, warm=2, runs=5):
+    """Workload 5 (serving-style): sixteen independent seeded problems of
+    uneven sizes (spherical log r in [0.05, 20] and cylindrical R in [4/33, 4]
+    with an inner cavity, N x N/2 x N with N in {64, 128, 256}), mixed
+    precision, all in ONE captured CUDA graph (psolve_batch_*) with every
+    problem on its own branch.  Reports the aggregate solves/s and the p50 /
+    p99 per-problem completion latency within a launch (completion events in
+    the graph), against the same problems solved one by one in FP64."""
+    import numpy as np
+    ws = workloads.workload(5)
+    t0 = time.perf_counter()
+    mixed = [ps.Solver.from_spec(w["spec"], precision=ps.MIXED) for w in ws]
+    setup_s = time.perf_counter() - t0
+    rhos = [torch.from_numpy(w["rho"]).cuda() for w in ws]
+    phis = [torch.empty_like(r) for r in rhos]
+    b = ps.Batch(mixed, rhos, phis, tol=TOL)
+    for _ in range(warm):
+        b.run()
+    lat = []
+    t0 = time.perf_counter()
+    for _ in range(runs):
+        lat += b.run()[1]
+    t_batch = time.perf_counter() - t0
+    b.close()
+    for s in mixed:
+        s.close()
+    seq = []
+    for w, r in zip(ws, rhos):
+        s = ps.Solver.from_spec(w["spec"], precision=ps.FP64)
+        phi = torch.empty_like(r)
+        s.solve(r, phi, tol=TOL)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.solve(r, phi, tol=TOL)
+        e1.record()
+        torch.cuda.synchronize()
+        seq.append(e0.elapsed_time(e1))
+        s.close()
+    sizes = [(w["spec"]["geometry"], w["spec"]["n_r"]) for w in ws]
+    return {"workload": "16 problems: even index spherical log r in [0.05, 20], odd index cylindrical "
+                        "R in [4/33, 4], z in [-2, 2]; N x N/2 x N, N in {64, 128, 256}; Gaussian clumps; "
+                        "tol 1e-8",
+            "sizes": [("sph" if g == 0 else "cyl") + str(n) for g, n in sizes],
+            "one_graph_mixed": {"solves_per_s": len(ws) * runs / t_batch,
+                                "latency_ms_p50": float(np.percentile(lat, 50)),
+                                "latency_ms_p99": float(np.percentile(lat, 99)),
+                                "launches_timed": runs, "host_wall_per_launch_ms": 1e3 * t_batch / runs},
+            "sequential_fp64": {"solves_per_s": len(ws) / (sum(seq) / 1e3),
+                                "latency_ms_p50": float(np.percentile(seq, 50)),
+                                "latency_ms_p99": float(np.percentile(seq, 99))},
+            "setup_s_16_handles": setup_s}
 
 
 def cell_volumes(spec):

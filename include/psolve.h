@@ -100,6 +100,21 @@ int psolve_create(psolve_t* out, int geometry, int n_r, int n_theta_or_z, int n_
 /* Same with every option; fields left zero take their defaults. */
 int psolve_create_ex(psolve_t* out, const psolve_desc* d);
 
+/* Same-geometry batch: a plan whose solves take n_densities (1..64)
+ * densities of the geometry d at once.  psolve_solve's rho and phi then hold
+ * n_densities fields back to back ([n_densities][n_r][n_tz][n_phi]).  The
+ * modes of all densities iterate together (planes b M + m), so the slow low
+ * modes of every density share the late iterations, and the boundary
+ * convolution (Eqs. theta_left..theta_top) reads each mode's DGF table once
+ * for up to eight densities: a [nb x nb] by [nb x 2 n_densities] product per
+ * mode instead of n_densities products with one vector.  Workspaces grow
+ * with n_densities; the DGF tables and level tables are shared.  The
+ * statistics' per-mode arrays describe the first density; the relative
+ * residuals and iteration counts cover all.  Stage entry points act on the
+ * first density's planes.  Errors as psolve_create_ex, and PSOLVE_ERR_ARG
+ * for n_densities outside 1..64. */
+int psolve_create_multi(psolve_t* out, const psolve_desc* d, int n_densities);
+
 /* The multigrid plan psolve_create_ex would build for d, computed on the
  * host only (no device memory, no kernels: usable without a GPU).  Levels
  * halve both sides while the short side exceeds 16, or exceeds 4 with more
@@ -217,10 +232,13 @@ typedef struct {
   double ms;           /* psolve_autotune: median solve time of the choice, ms    */
   int candidates;      /* psolve_autotune: candidates timed (0: from a cache)      */
   int cached;          /* psolve_autotune: 1 when the choice came from a cache     */
+  int tail_planes;     /* the cluster-resident tail (psolve_set_tail): -1 as many
+                          planes as fit, 0 off, n > 0 at most n                   */
 } psolve_schedule;
 
 /* The handle's current schedule (ms, candidates, cached = 0; the fused-level
- * counts 0 when they equal nu_pre / nu_post). */
+ * counts 0 when they equal nu_pre / nu_post; tail_planes as psolve_set_tail
+ * last set it). */
 int psolve_get_schedule(psolve_t h, psolve_schedule* s);
 /* Install a schedule for later solves (a captured solve is captured again).
  * PSOLVE_ERR_ARG, with the handle unchanged, when a field is out of range. */
@@ -239,6 +257,8 @@ int psolve_set_schedule(psolve_t h, const psolve_schedule* s);
  *     level: that kernel's own smoothing counts, nu_post_fused <=
  *     nu_pre_fused <= 3, with the stage-1 and stage-2 choices (5 candidates
  *     besides the stage-1 counts).
+ *   Stage 4, when the cluster-resident tail can run with the chosen
+ *     schedule: the tail off against on (psolve_set_tail).
  * Each candidate runs one untimed solve (graph capture, caches), then three
  * timed solves (CUDA events on the handle's stream); its time is their
  * median.  Candidates whose solve fails are skipped.  Warm start is
@@ -249,7 +269,7 @@ int psolve_set_schedule(psolve_t h, const psolve_schedule* s);
  * choice without timing.  When the environment variable PSOLVE_TUNE_CACHE
  * names a file, it is read on a process-cache miss and every new choice is
  * appended to it (text, one line per key: key nu_pre nu_post n_sor lines_r
- * cols_t nu_pre_fused nu_post_fused ms; the last line of a key wins).
+ * cols_t nu_pre_fused nu_post_fused ms tail_planes; the last line of a key wins).
  * out (may be NULL) receives the choice.  Returns PSOLVE_OK, or the error of
  * the solve with the handle's current schedule, which then stays installed. */
 int psolve_autotune(psolve_t h, const double* rho, double* phi, double tol,

@@ -47,7 +47,7 @@ class Schedule(ctypes.Structure):
     _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("n_sor", ctypes.c_int),
                 ("lines_r", ctypes.c_int), ("cols_t", ctypes.c_int), ("nu_pre_fused", ctypes.c_int),
                 ("nu_post_fused", ctypes.c_int), ("ms", ctypes.c_double),
-                ("candidates", ctypes.c_int), ("cached", ctypes.c_int)]
+                ("candidates", ctypes.c_int), ("cached", ctypes.c_int), ("tail_planes", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,6 +97,7 @@ def lib():
         sig = {
             "psolve_create": (I, [ctypes.POINTER(P), I, I, I, I, I, D, D]),
             "psolve_create_ex": (I, [ctypes.POINTER(P), ctypes.POINTER(Desc)]),
+            "psolve_create_multi": (I, [ctypes.POINTER(P), ctypes.POINTER(Desc), I]),
             "psolve_solve": (I, [P, P, P, D]),
             "psolve_solve_batched": (I, [P, P, P, I, D]),
             "psolve_set_stream": (I, [P, P]),
@@ -185,7 +186,7 @@ class Solver:
 
     def __init__(self, geometry, n_r, n_tz, n_phi, spacing, r_in, r_out, t_min=None, t_max=None,
                  G=1.0, precision=MIXED, max_cycles=0, nu_pre=0, nu_post=0, n_sor=0,
-                 use_graph=True, torch_alloc=True):
+                 use_graph=True, torch_alloc=True, n_densities=1):
         import torch
         self.torch = torch
         L = lib()
@@ -200,9 +201,16 @@ class Solver:
         if self._alloc is not None:
             d.alloc_fn, d.free_fn = self._alloc.alloc, self._alloc.free
         self.desc = d
-        self.shape = (n_r, n_tz, n_phi)
+        self.n_densities = int(n_densities)
+        # one density: [n_r][n_tz][n_phi]; several: [n_densities][n_r][n_tz][n_phi]
+        self.shape = (n_r, n_tz, n_phi) if self.n_densities == 1 else (self.n_densities, n_r, n_tz, n_phi)
+        self.grid = (n_r, n_tz, n_phi)
         h = ctypes.c_void_p()
-        check(L.psolve_create_ex(ctypes.byref(h), ctypes.byref(d)), "psolve_create_ex")
+        if self.n_densities == 1:
+            check(L.psolve_create_ex(ctypes.byref(h), ctypes.byref(d)), "psolve_create_ex")
+        else:
+            check(L.psolve_create_multi(ctypes.byref(h), ctypes.byref(d), self.n_densities),
+                  "psolve_create_multi")
         self.h = h
         check(L.psolve_set_stream(h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
               "psolve_set_stream")
@@ -222,9 +230,10 @@ class Solver:
         check(lib().psolve_get_schedule(self.h, ctypes.byref(s)), "psolve_get_schedule")
         return s.as_dict()
 
-    def set_schedule(self, nu_pre, nu_post, n_sor, lines_r=8, cols_t=0, nu_pre_fused=0, nu_post_fused=0):
+    def set_schedule(self, nu_pre, nu_post, n_sor, lines_r=8, cols_t=0, nu_pre_fused=0, nu_post_fused=0,
+                     tail_planes=-1):
         s = Schedule(nu_pre=nu_pre, nu_post=nu_post, n_sor=n_sor, lines_r=lines_r, cols_t=cols_t,
-                     nu_pre_fused=nu_pre_fused, nu_post_fused=nu_post_fused)
+                     nu_pre_fused=nu_pre_fused, nu_post_fused=nu_post_fused, tail_planes=tail_planes)
         check(lib().psolve_set_schedule(self.h, ctypes.byref(s)), "psolve_set_schedule")
 
     def autotune(self, rho, tol=1e-8, phi=None):
@@ -299,7 +308,7 @@ class Solver:
     def planes(self, level=0, dtype=None):
         """Empty complex planes [M, n_tz_l, n_r_l] of a multigrid level."""
         torch = self.torch
-        n_r, n_tz = self.shape[0] >> level, self.shape[1] >> level
+        n_r, n_tz = self.grid[0] >> level, self.grid[1] >> level
         dtype = dtype or torch.complex128
         return torch.zeros((self.n_modes, n_tz, n_r), dtype=dtype, device="cuda")
 
@@ -309,7 +318,7 @@ class Solver:
         return f
 
     def stage_inverse(self, phi_hat):
-        phi = self.torch.empty(self.shape, dtype=self.torch.float64, device="cuda")
+        phi = self.torch.empty(self.grid, dtype=self.torch.float64, device="cuda")
         check(lib().psolve_stage_inverse(self.h, _ptr(phi_hat), _ptr(phi)), "psolve_stage_inverse")
         return phi
 
@@ -317,8 +326,8 @@ class Solver:
         """Transform a radial slab [rows][n_tz][n_phi] -> [M][n_tz][rows] complex."""
         torch = self.torch
         rows = rho_rows.shape[0]
-        self._need(rho_rows, (rows, self.shape[1], self.shape[2]), torch.float64)
-        f = torch.empty((self.n_modes, self.shape[1], rows), dtype=torch.complex128, device="cuda")
+        self._need(rho_rows, (rows, self.grid[1], self.grid[2]), torch.float64)
+        f = torch.empty((self.n_modes, self.grid[1], rows), dtype=torch.complex128, device="cuda")
         check(lib().psolve_stage_forward_rows(self.h, _ptr(rho_rows), rows, _ptr(f)),
               "psolve_stage_forward_rows")
         return f
@@ -326,8 +335,8 @@ class Solver:
     def stage_inverse_rows(self, phi_hat_rows):
         torch = self.torch
         rows = phi_hat_rows.shape[2]
-        self._need(phi_hat_rows, (self.n_modes, self.shape[1], rows), torch.complex128)
-        phi = torch.empty((rows, self.shape[1], self.shape[2]), dtype=torch.float64, device="cuda")
+        self._need(phi_hat_rows, (self.n_modes, self.grid[1], rows), torch.complex128)
+        phi = torch.empty((rows, self.grid[1], self.grid[2]), dtype=torch.float64, device="cuda")
         check(lib().psolve_stage_inverse_rows(self.h, _ptr(phi_hat_rows), rows, _ptr(phi)),
               "psolve_stage_inverse_rows")
         return phi
@@ -337,7 +346,7 @@ class Solver:
         complex (list order) -> (phi_hat of the same layout, return code)."""
         torch = self.torch
         n = len(modes)
-        self._need(f_hat, (n, self.shape[1], self.shape[0]), torch.complex128)
+        self._need(f_hat, (n, self.grid[1], self.grid[0]), torch.complex128)
         phi = torch.empty_like(f_hat)
         arr = (ctypes.c_int * max(n, 1))(*[int(m) for m in modes])
         rc = lib().psolve_solve_modes(self.h, arr, n, _ptr(f_hat), _ptr(phi), float(tol))

@@ -34,6 +34,8 @@ struct psolve_ctx {
   PlaneGeo g;
   Law rlaw, tlaw;
   int M = 0, nb = 0, construction = -1;
+  int nd = 1;   // densities per solve (same geometry): planes p = b M + m
+  int P = 0;    // nd M mode planes
   MGSolver mg;
   std::vector<BPoint> bp;
   BDev bdev{};
@@ -57,7 +59,7 @@ struct psolve_ctx {
   int g_warm = -1;   // warm state the graph was captured with
 };
 
-static size_t plane_bytes(psolve_t h) { return sizeof(double2) * size_t(h->M) * h->d.n_r * h->d.n_tz; }
+static size_t plane_bytes(psolve_t h) { return sizeof(double2) * size_t(h->P) * h->d.n_r * h->d.n_tz; }
 static int warm_state(psolve_t h) { return h->warm ? (h->warm_hist ? 2 : 1) : 0; }
 
 static int fail(int code, const std::string& msg) {
@@ -96,7 +98,7 @@ __global__ void k_worst(const int* a, const int* b, int n, int* out) {
 }
 
 static void snapshot(psolve_ctx* h, SolveStats& s) {
-  const int M = h->M;
+  const int M = h->P;
   cudaMemcpyAsync(s.cycles, h->mg.d_cycles, sizeof(int) * M, cudaMemcpyDeviceToDevice, h->st);
   cudaMemcpyAsync(s.status, h->mg.d_status, sizeof(int) * M, cudaMemcpyDeviceToDevice, h->st);
   cudaMemcpyAsync(s.nf2, h->mg.d_nf2, sizeof(double2) * M, cudaMemcpyDeviceToDevice, h->st);
@@ -149,7 +151,7 @@ static void make_geo(const psolve_desc& d, PlaneGeo& g, Law& rlaw, Law& tlaw) {
   g.build();
 }
 
-static int create_impl(psolve_t* out, const psolve_desc* din) {
+static int create_impl(psolve_t* out, const psolve_desc* din, int nd) {
   auto t0 = std::chrono::steady_clock::now();
   if (!out || !din) return fail(PSOLVE_ERR_ARG, "null argument");
   *out = nullptr;
@@ -165,6 +167,9 @@ static int create_impl(psolve_t* out, const psolve_desc* din) {
   make_geo(d, h->g, h->rlaw, h->tlaw);
   h->M = d.n_phi / 2 + 1;
   const int M = h->M;
+  h->nd = nd;
+  h->P = nd * M;
+  const int P = h->P;
   const size_t plane = size_t(d.n_r) * d.n_tz;
   std::string err;
   std::vector<int> modes(M);
@@ -175,12 +180,17 @@ static int create_impl(psolve_t* out, const psolve_desc* din) {
   o.nu2 = d.nu_post;
   o.n_sor = d.n_sor;
   o.max_cycles = d.max_cycles;
-  if (!h->mg.init(h->A, h->g, false, modes, {}, M, o, err)) {
+  std::vector<int> plane_slot;   // several densities: plane b M + m solves mode m
+  if (nd > 1) {
+    plane_slot.resize(P);
+    for (int q = 0; q < P; ++q) plane_slot[q] = q % M;
+  }
+  if (!h->mg.init(h->A, h->g, false, modes, plane_slot, P, o, err)) {
     h->A.release_all();
     return fail(PSOLVE_ERR_NOMEM, "multigrid setup: " + err);
   }
-  h->u = static_cast<double2*>(h->A.get(sizeof(double2) * plane * M));
-  h->f = static_cast<double2*>(h->A.get(sizeof(double2) * plane * M));
+  h->u = static_cast<double2*>(h->A.get(sizeof(double2) * plane * P));
+  h->f = static_cast<double2*>(h->A.get(sizeof(double2) * plane * P));
   // twiddles e^{-2 pi i k / N}
   std::vector<double2> tw(d.n_phi / 2);
   for (int k = 0; k < d.n_phi / 2; ++k)
@@ -226,14 +236,14 @@ static int create_impl(psolve_t* out, const psolve_desc* din) {
   h->bdev.cell = up_i(cells);
   h->bdev.cbp = up_i(cbp);
   h->bdev.plane_cells = int(plane);
-  h->sigma = static_cast<double2*>(h->A.get(sizeof(double2) * size_t(M) * std::max(nb, 1)));
-  h->theta = static_cast<double2*>(h->A.get(sizeof(double2) * size_t(M) * std::max(nb, 1)));
+  h->sigma = static_cast<double2*>(h->A.get(sizeof(double2) * size_t(P) * std::max(nb, 1)));
+  h->theta = static_cast<double2*>(h->A.get(sizeof(double2) * size_t(P) * std::max(nb, 1)));
   h->gt = static_cast<double*>(h->A.get(sizeof(double) * size_t(M) * nb * nb));
   for (SolveStats* s : {&h->sp, &h->sf}) {
-    s->cycles = static_cast<int*>(h->A.get(sizeof(int) * M));
-    s->status = static_cast<int*>(h->A.get(sizeof(int) * M));
-    s->nf2 = static_cast<double2*>(h->A.get(sizeof(double2) * M));
-    s->nr2 = static_cast<double2*>(h->A.get(sizeof(double2) * M));
+    s->cycles = static_cast<int*>(h->A.get(sizeof(int) * P));
+    s->status = static_cast<int*>(h->A.get(sizeof(int) * P));
+    s->nf2 = static_cast<double2*>(h->A.get(sizeof(double2) * P));
+    s->nr2 = static_cast<double2*>(h->A.get(sizeof(double2) * P));
     s->iter = static_cast<int*>(h->A.get(sizeof(int)));
   }
   h->d_worst = static_cast<int*>(h->A.get(sizeof(int)));
@@ -318,7 +328,17 @@ extern "C" int psolve_plan_inspect(const psolve_desc* din, psolve_plan* out) {
 
 extern "C" int psolve_create_ex(psolve_t* out, const psolve_desc* d) {
   try {
-    return create_impl(out, d);
+    return create_impl(out, d, 1);
+  } catch (const std::exception& e) {
+    return fail(PSOLVE_ERR_NOMEM, std::string("create: ") + e.what());
+  }
+}
+
+extern "C" int psolve_create_multi(psolve_t* out, const psolve_desc* d, int n_densities) {
+  if (n_densities < 1 || n_densities > 64)
+    return fail(PSOLVE_ERR_ARG, "n_densities must lie in 1..64");
+  try {
+    return create_impl(out, d, n_densities);
   } catch (const std::exception& e) {
     return fail(PSOLVE_ERR_NOMEM, std::string("create: ") + e.what());
   }
@@ -393,9 +413,13 @@ extern "C" int psolve_get_sizes(psolve_t h, int* n_modes, int* n_boundary, int* 
 // ---------------------------------------------------------------------------
 // the solve (Sec. 5.1 steps 2-7)
 // ---------------------------------------------------------------------------
+static size_t cells(psolve_t h) { return size_t(h->d.n_r) * h->d.n_tz * h->d.n_phi; }
+static size_t mode_plane(psolve_t h) { return size_t(h->d.n_r) * h->d.n_tz; }
+
 static void enqueue_front(psolve_t h, const double* rho) {
-  launch_fft_forward(rho, h->f, h->d.n_r, h->d.n_tz, h->d.n_phi, 4.0 * kPi * h->d.G / h->d.n_phi,
-                     h->tw, h->st);
+  for (int b = 0; b < h->nd; ++b)
+    launch_fft_forward(rho + b * cells(h), h->f + size_t(b) * h->M * mode_plane(h), h->d.n_r, h->d.n_tz,
+                       h->d.n_phi, 4.0 * kPi * h->d.G / h->d.n_phi, h->tw, h->st);
   if (warm_state(h) == 2)
     cudaMemcpyAsync(h->u, h->psi_prev, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
   else
@@ -407,9 +431,10 @@ static void enqueue_front(psolve_t h, const double* rho) {
 static void enqueue_middle(psolve_t h) {
   snapshot(h, h->sp);
   if (h->warm) cudaMemcpyAsync(h->psi_prev, h->u, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
-  launch_screening(h->bdev, h->u, h->sigma, h->M, h->st);
-  launch_boundary_potential(h->gt, h->sigma, h->theta, h->M, h->nb, h->st);
-  launch_rhs_ghosts(h->bdev, h->f, h->theta, h->M, h->st);
+  launch_screening(h->bdev, h->u, h->sigma, h->P, h->st);
+  if (h->nd == 1) launch_boundary_potential(h->gt, h->sigma, h->theta, h->M, h->nb, h->st);
+  else launch_boundary_potential_multi(h->gt, h->sigma, h->theta, h->M, h->nb, h->nd, h->st);
+  launch_rhs_ghosts(h->bdev, h->f, h->theta, h->P, h->st);
   // initial guess of the Phi solve: the previous Phi (warm start), else Psi
   if (warm_state(h) == 2)
     cudaMemcpyAsync(h->u, h->phi_prev, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
@@ -420,8 +445,10 @@ static void enqueue_middle(psolve_t h) {
 static void enqueue_back(psolve_t h, double* phi) {
   snapshot(h, h->sf);
   if (h->warm) cudaMemcpyAsync(h->phi_prev, h->u, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
-  launch_fft_inverse(h->u, phi, h->d.n_r, h->d.n_tz, h->d.n_phi, h->tw, h->st);
-  k_worst<<<1, 256, 0, h->st>>>(h->sp.status, h->sf.status, h->M, h->d_worst);
+  for (int b = 0; b < h->nd; ++b)
+    launch_fft_inverse(h->u + size_t(b) * h->M * mode_plane(h), phi + b * cells(h), h->d.n_r, h->d.n_tz,
+                       h->d.n_phi, h->tw, h->st);
+  k_worst<<<1, 256, 0, h->st>>>(h->sp.status, h->sf.status, h->P, h->d_worst);
   cudaMemcpyAsync(h->h_worst, h->d_worst, sizeof(int), cudaMemcpyDeviceToHost, h->st);
 }
 
@@ -698,6 +725,7 @@ extern "C" int psolve_get_schedule(psolve_t h, psolve_schedule* s) {
   s->cols_t = o.tiles.cols_t;
   s->nu_pre_fused = o.nu1f;
   s->nu_post_fused = o.nu2f;
+  s->tail_planes = h->mg.tail_cap;
   return PSOLVE_OK;
 }
 
@@ -708,6 +736,7 @@ static bool schedule_ok(const psolve_schedule& s, std::string& why) {
   else if (s.cols_t != 0 && s.cols_t != 8 && s.cols_t != 16 && s.cols_t != 32) why = "cols_t must be 0, 8, 16 or 32";
   else if (s.nu_pre_fused < 0 || s.nu_pre_fused > 8 || s.nu_post_fused < 0 || s.nu_post_fused > 8)
     why = "nu_pre_fused and nu_post_fused must be 0..8";
+  else if (s.tail_planes < -1) why = "tail_planes must be -1, 0 or positive";
   else return true;
   return false;
 }
@@ -716,6 +745,7 @@ static void install_schedule(psolve_t h, const psolve_schedule& s) {
   Tiles t;
   t.lines_r = s.lines_r;
   t.cols_t = s.cols_t;
+  h->mg.tail_cap = s.tail_planes;
   h->mg.set_schedule(s.nu_pre, s.nu_post, s.n_sor, t, s.nu_pre_fused, s.nu_post_fused);
   h->d.nu_pre = s.nu_pre;
   h->d.nu_post = s.nu_post;
@@ -755,8 +785,8 @@ static bool tune_file_read(const char* path, const std::string& key, psolve_sche
   char line[512], k[384];
   while (std::fgets(line, sizeof line, fp)) {
     psolve_schedule s{};
-    if (std::sscanf(line, "%383s %d %d %d %d %d %d %d %lf", k, &s.nu_pre, &s.nu_post, &s.n_sor,
-                    &s.lines_r, &s.cols_t, &s.nu_pre_fused, &s.nu_post_fused, &s.ms) != 9)
+    if (std::sscanf(line, "%383s %d %d %d %d %d %d %d %lf %d", k, &s.nu_pre, &s.nu_post, &s.n_sor,
+                    &s.lines_r, &s.cols_t, &s.nu_pre_fused, &s.nu_post_fused, &s.ms, &s.tail_planes) != 10)
       continue;
     std::string why;
     if (key == k && schedule_ok(s, why)) {
@@ -771,8 +801,8 @@ static bool tune_file_read(const char* path, const std::string& key, psolve_sche
 static void tune_file_append(const char* path, const std::string& key, const psolve_schedule& s) {
   FILE* fp = std::fopen(path, "a");
   if (!fp) return;
-  std::fprintf(fp, "%s %d %d %d %d %d %d %d %.4f\n", key.c_str(), s.nu_pre, s.nu_post, s.n_sor,
-               s.lines_r, s.cols_t, s.nu_pre_fused, s.nu_post_fused, s.ms);
+  std::fprintf(fp, "%s %d %d %d %d %d %d %d %.4f %d\n", key.c_str(), s.nu_pre, s.nu_post, s.n_sor,
+               s.lines_r, s.cols_t, s.nu_pre_fused, s.nu_post_fused, s.ms, s.tail_planes);
   std::fclose(fp);
 }
 
@@ -891,6 +921,19 @@ extern "C" int psolve_autotune(psolve_t h, const double* rho, double* phi, doubl
           if (ms < best.ms) { best = s; best.ms = ms; }
         }
     }
+    // stage 4: the cluster-resident tail off against on
+    {
+      psolve_schedule s = best;
+      s.tail_planes = best.tail_planes == 0 ? -1 : 0;
+      install_schedule(h, s);
+      double ms = 0;
+      if (h->mg.tail_planes > 0 || s.tail_planes == 0) {
+        if (time_solves(h, rho, phi, tol, e0, e1, ms) == PSOLVE_OK) {
+          ++n_timed;
+          if (ms < best.ms) { best = s; best.ms = ms; }
+        }
+      }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -914,15 +957,16 @@ extern "C" int psolve_get_stats(psolve_t h, psolve_stats* s) {
   const int M = h->M;
   s->n_modes = M;
   s->setup_ms = h->setup_ms;
-  std::vector<double2> nf(M), nr(M);
+  const int P = h->P;   // the residual covers every density's planes
+  std::vector<double2> nf(P), nr(P);
   for (int pass = 0; pass < 2; ++pass) {
     SolveStats& q = pass ? h->sf : h->sp;
     int it = 0;
     cudaMemcpy(&it, q.iter, sizeof(int), cudaMemcpyDeviceToHost);
-    cudaMemcpy(nf.data(), q.nf2, sizeof(double2) * M, cudaMemcpyDeviceToHost);
-    cudaMemcpy(nr.data(), q.nr2, sizeof(double2) * M, cudaMemcpyDeviceToHost);
+    cudaMemcpy(nf.data(), q.nf2, sizeof(double2) * P, cudaMemcpyDeviceToHost);
+    cudaMemcpy(nr.data(), q.nr2, sizeof(double2) * P, cudaMemcpyDeviceToHost);
     double a = 0, b = 0;
-    for (int m = 0; m < M; ++m) { a += nr[m].x + nr[m].y; b += nf[m].x + nf[m].y; }
+    for (int m = 0; m < P; ++m) { a += nr[m].x + nr[m].y; b += nf[m].x + nf[m].y; }
     const double rel = b > 0 ? std::sqrt(a / b) : 0.0;
     int* cyc = pass ? s->cycles_phi : s->cycles_psi;
     if (cyc) cudaMemcpy(cyc, q.cycles, sizeof(int) * M, cudaMemcpyDeviceToHost);
@@ -1011,7 +1055,7 @@ extern "C" int psolve_solve_modes(psolve_t h, const int* modes_host, int n, cons
   for (int k = 0; k < n; ++k)
     cudaMemcpyAsync(reinterpret_cast<double2*>(phi_hat) + k * plane, h->u + size_t(modes_host[k]) * plane,
                     plane * sizeof(double2), cudaMemcpyDeviceToDevice, h->st);
-  k_worst<<<1, 256, 0, h->st>>>(h->sp.status, h->sf.status, h->M, h->d_worst);
+  k_worst<<<1, 256, 0, h->st>>>(h->sp.status, h->sf.status, h->P, h->d_worst);
   cudaMemcpyAsync(h->h_worst, h->d_worst, sizeof(int), cudaMemcpyDeviceToHost, h->st);
   return finish(h);
 }

@@ -203,6 +203,10 @@ struct BDev {
 void launch_screening(const BDev& b, const double2* psi, double2* sigma, int M, cudaStream_t st);
 void launch_boundary_potential(const double* gt, const double2* sigma, double2* theta, int M,
                                int nb, cudaStream_t st);
+// nd densities of one geometry, planes p = b M + m: every mode's table is read
+// once for up to eight densities
+void launch_boundary_potential_multi(const double* gt, const double2* sigma, double2* theta, int M,
+                                     int nb, int nd, cudaStream_t st);
 // f2 = f - sum over the adjacent ghosts of cpl * (-theta), in place on f
 void launch_rhs_ghosts(const BDev& b, double2* f, const double2* theta, int M, cudaStream_t st);
 

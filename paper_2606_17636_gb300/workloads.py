@@ -17,7 +17,8 @@ Workloads (sizes n_r x n_theta_or_z x n_phi):
      exponential disc exp(-R) sech^2(z / 0.05 R) (1 + 0.3 cos(2 phi - 2.5 ln R))
      times (1 + 0.01 white noise).
   5  sixteen problems: even index spherical log r in [0.05, 20], odd index
-     cylindrical uniform R in [0, 4], z in [-2, 2]; N x N/2 x N with
+     cylindrical uniform R in [4/33, 4] (an inner cavity of 2, 4 or 8 cells'
+     width, so that r = 0 is a cell face), z in [-2, 2]; N x N/2 x N with
      N in {64, 128, 256} (each size at least twice); four Gaussian clumps.
 """
 import numpy as np
@@ -179,7 +180,7 @@ def workload(workload_id):
             if i % 2 == 0:
                 sp = spec(SPHERICAL, N, N // 2, N, LOG, 0.05, 20.0)
             else:
-                sp = spec(CYLINDRICAL, N, N // 2, N, UNIFORM, 0.0, 4.0, -2.0, 2.0)
+                sp = spec(CYLINDRICAL, N, N // 2, N, UNIFORM, 4.0 / 33.0, 4.0, -2.0, 2.0)
             out.append(dict(spec=sp, rho=_clumps(sp, rng), tol=1e-8, precision=1))
         return out
     raise ValueError(workload_id)

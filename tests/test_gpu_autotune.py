@@ -140,7 +140,8 @@ def test_autotune_file_cache(ps, tmp_path, monkeypatch):
     f = lines[0].split()
     assert [int(x) for x in f[1:8]] == [ch[k] for k in KEYS]
     # another process reads the file: rewrite the entry and check it is used
-    path.write_text("%s 3 1 1 4 8 2 1 1.0\n" % f[0])
+    assert len(f) == 10 and int(f[9]) == ch["tail_planes"]
+    path.write_text("%s 3 1 1 4 8 2 1 1.0 0\n" % f[0])
     code = ("import json, sys, torch; sys.path.insert(0, %r)\n"
             "import paper_2606_17636_gb300 as ps\n"
             "s = ps.Solver.from_spec(json.loads(%r), precision=ps.MIXED)\n"
@@ -151,7 +152,7 @@ def test_autotune_file_cache(ps, tmp_path, monkeypatch):
     assert out.returncode == 0, out.stderr[-2000:]
     got = json.loads(out.stdout.strip().splitlines()[-1])
     assert got["cached"] == 1 and got["candidates"] == 0
-    assert [got[k] for k in KEYS] == [3, 1, 1, 4, 8, 2, 1]
+    assert [got[k] for k in KEYS] == [3, 1, 1, 4, 8, 2, 1] and got["tail_planes"] == 0
 
 
 def test_autotune_reports_a_failing_solve_and_keeps_the_schedule(ps):
