@@ -42,6 +42,8 @@ def args_():
     a.add_argument("--no-serving", action="store_true", help="skip the sixteen-problem one-graph batch")
     a.add_argument("--no-tune", action="store_true",
                    help="keep the default smoothing schedule and tile shapes (skip psolve_autotune)")
+    a.add_argument("--no-setup4", action="store_true",
+                   help="skip timing psolve_create for the 512 x 256 x 512 cylindrical workload")
     a.add_argument("--replicas", action="store_true",
                    help="with N > 1 GPUs: an independent copy of the problem per GPU (weak scaling) "
                         "instead of one problem sharded by mode over all GPUs (strong scaling)")
@@ -271,19 +273,24 @@ def ours(a, ws, rank, local):
     wv = torch.from_numpy(cell_volumes(spec)).to(dev)[:, :, None]
     err_tight = float(torch.sqrt((wv * (phi - phi_t) ** 2).sum() / (wv * phi_t ** 2).sum()))
     err_tight_plain = float(torch.linalg.vector_norm(phi - phi_t) / torch.linalg.vector_norm(phi_t))
-    # end to end through the public call with host buffers
+    # end to end through the public call with host buffers: psolve_solve_host
+    # uploads each solve's density from pinned host memory and downloads its
+    # potential, overlapping both with the solves; every step copies its own
+    # bytes (the same pinned buffers every step).  One untimed call first (it
+    # allocates the staging buffers and captures the graph for them).
     phi_host = torch.empty_like(rho_host).pin_memory()
+    sm.solve_host([rho_host] * 3, [phi_host] * 3, tol=TOL)
+    torch.cuda.synchronize()
+    barrier(ws)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(a.steps):
-        rho.copy_(rho_host, non_blocking=True)
-        sm.solve(rho, phi, tol=TOL)
-        phi_host.copy_(phi, non_blocking=True)
+    _, e2e_status, _ = sm.solve_host([rho_host] * a.steps, [phi_host] * a.steps, tol=TOL)
     ev1.record(stream)
     torch.cuda.synchronize()
     te2e = allmax(ws, ev0.elapsed_time(ev1) / 1e3, dev)
     e2e = ws * a.steps / te2e
+    e2e_err = float(torch.linalg.vector_norm(phi_host.to(dev) - phi) / torch.linalg.vector_norm(phi))
     # time stepping with warm start (App. B): a sequence of slowly changing
     # densities (a growing m = 2 perturbation, 2 % over the run), each solve
     # starting from the previous Psi and Phi; all densities resident in HBM
@@ -319,9 +326,13 @@ def ours(a, ws, rank, local):
     # smoothing cycle of the finest level over all modes, FP32 planes
     roof = vcycle_roofline(torch, ps, sm, stream)
     roof_stream = smoother_roofline(torch, ps, sm, stream)
+    fp64_peak = fp64_peak_tflops(torch)
+    roof_fft = fft_roofline(torch, ps, sd, fp64_peak)
+    roof_res = residual_roofline(torch, ps, sm, stream, fp64_peak)
     launches = launches_per_solve(sm, st)
     serve = serving(torch, ps, workloads) if (rank == 0 and not a.no_serving) else None
     multi = multi_density(torch, ps, workloads, w) if (rank == 0 and not a.no_serving) else None
+    setup4 = setup_large(torch, ps, workloads) if (rank == 0 and not a.no_setup4) else None
     if rank != 0:
         return
     cells = spec["n_r"] * spec["n_tz"] * spec["n_phi"]
@@ -345,15 +356,20 @@ def ours(a, ws, rank, local):
                    "sum_mode_cycles_psi": sum(st["cycles_psi"]), "sum_mode_cycles_phi": sum(st["cycles_phi"]),
                    "cycles_m0": [st["cycles_psi"][0], st["cycles_phi"][0]],
                    "fp64_iterations": [st64["iterations_psi"], st64["iterations_phi"]],
-                   "setup_ms": st["setup_ms"]},
+                   "setup_ms": st["setup_ms"], "dgf_ms": sm.setup_times()[1]},
         "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": rho.numel() * 8,
+                "api": "psolve_solve_host (copies overlapped with the solves)",
+                "result_vs_device_solve_rel_l2": e2e_err,
                 "d2h_bytes_per_step": phi.numel() * 8},
         "gpu_launches": launches * a.steps,
         "warm_timestepping": warm,
         "roofline": roof,
         "roofline_streaming": roof_stream,
+        "roofline_fft": roof_fft,
+        "roofline_residual": roof_res,
         "serving": serve,
         "multi_density": multi,
+        "setup_workload4": setup4,
         "clocks": clocks,
     }
     if not a.no_baseline:
@@ -564,20 +580,141 @@ def launches_per_solve(s, st):
 # inverse diagonal 6, each even-odd SOR sweep 16); nu_pre + nu_post cycles of
 # 2 passes each; defect restriction and prolongation add 40 (424 for the
 # default schedule nu = (2, 2), n_sor = 2).
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu --set full capture of k_vsmem on workload 3 (all 129 modes).  They
-# hold for the kernel as captured; a changed kernel needs a new capture.  The
-# smoothing passes changed after their capture, so their traffic is not
-# reported.
-VSMEM_TRAFFIC_BYTES = 12149760
-SMOOTH_CYCLE_TRAFFIC_BYTES = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of full-batch
+# launches on workload 3 (all 129 modes), from the ncu captures of the
+# profiling case (python -m paper_2606_17636_gb300.profile_case
+# --smooth-first): one k_vsmem launch, one finest-level smoothing cycle
+# (k_rpass2 + k_tpass2) and the first stencil launch of k_residual.  They
+# hold for the kernels as captured; a changed kernel needs a new capture.
+VSMEM_TRAFFIC_BYTES = 12151552
+SMOOTH_CYCLE_TRAFFIC_BYTES = 67735552 + 7611136 + 67792896 + 5309440
+RESIDUAL_TRAFFIC_BYTES = 136386304 + 17248512
+# ncu sm__inst_executed_pipe_fp64 (percent of peak, sustained active) of the
+# kernels bound by the FP64 pipe, at 256 x 128 x 128 (the same kernels with
+# 65 mode planes)
+FP64_PIPE_PCT = {"k_residual": 81.4, "k_fft_fwd": 84.3, "k_fft_inv": 83.4, "k_boundary": 87.1}
 
 
 def vcycle_flops_per_cell(sched):
     """On the fused levels (their own smoothing counts when set)."""
     nu = (sched["nu_pre_fused"] or sched["nu_pre"]) + (sched["nu_post_fused"] or sched["nu_post"])
     return nu * 2 * (16 + 16 * sched["n_sor"]) + 40
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+def setup_large(torch, ps, workloads):
+    """psolve_create of workload 4 (cylindrical, uniform R in [0.2, 4],
+    z in [-1, 1], 512 x 256 x 512; auxiliary-window DGF with 1536 boundary
+    points x 257 modes): wall time and its DGF part, on the device the bench
+    runs on.  Untimed by the solve clock; one handle, destroyed after."""
+    sp = workloads.BASE[4][0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = ps.Solver.from_spec(sp, precision=ps.MIXED, use_graph=False)
+    wall = time.perf_counter() - t0
+    setup_ms, dgf_ms = s.setup_times()
+    nb = s.n_boundary
+    s.close()
+    torch.cuda.empty_cache()
+    return {"workload": "cylindrical 512x256x512, R in [0.2, 4], z in [-1, 1]",
+            "create_s": wall, "setup_ms": setup_ms, "dgf_ms": dgf_ms,
+            "boundary_points": nb, "modes": sp["n_phi"] // 2 + 1}
+
+
+def fp32_peak_tflops(torch):
+    """SMs (from the device) x 128 FP32 lanes x 2 (FMA) x the maximum SM clock
+    (MEASURED_PEAKS.json, else 2.07 GHz)."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = peaks().get("sm_max_mhz") or 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
+def fp64_peak_tflops(torch):
+    """Measured FP64 rate of this GPU: a cuBLAS FP64 GEMM (torch.matmul of
+    4096 x 4096 float64 matrices), best of three, 2 N^3 flops."""
+    n = 4096
+    a = torch.randn((n, n), dtype=torch.float64, device="cuda")
+    b = torch.randn((n, n), dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def fft_roofline(torch, ps, s, fp64_peak, reps=20):
+    """The forward azimuthal transform (k_fft_fwd) of the workload, timed
+    alone through psolve_stage_forward with CUDA events.  Work: n_r n_tz / 2
+    complex FFTs of n_phi points (two real rows packed in one), 5 N log2 N
+    flops each, against the measured FP64 GEMM rate: the kernel runs on the
+    FP64 pipe (ncu: FP64_PIPE_PCT)."""
+    import math
+    n_r, n_tz, n_phi = s.grid
+    rho = torch.rand((n_r, n_tz, n_phi), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        s.stage_forward(rho)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        s.stage_forward(rho)
+    e1.record()
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3 / reps
+    flops = (n_r * n_tz / 2) * 5 * n_phi * math.log2(n_phi)
+    ach = flops / dt / 1e12
+    return {"kernel": "forward azimuthal transform k_fft_fwd", "bound": "fp64", "achieved": ach,
+            "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+            "peak_source": "measured: cuBLAS FP64 GEMM 4096^3 on this GPU",
+            "ncu_fp64_pipe_pct": FP64_PIPE_PCT["k_fft_fwd"],
+            "algorithmic_flops_per_launch": flops, "avg_ms": dt * 1e3,
+            "bytes_per_launch": 8.0 * n_r * n_tz * n_phi + 16.0 * n_r * n_tz * (n_phi // 2 + 1)}
+
+
+def residual_roofline(torch, ps, s, stream, fp64_peak, reps=20):
+    """The refinement's FP64 defect (k_residual) over all modes at the
+    finest level, timed alone through psolve_stage_residual (each call: the
+    full active list, then the kernel) with CUDA events on the library's
+    stream.  Algorithmic work per complex cell: 24 FP64 flops (the mode's
+    diagonal d0 - s2 q: 2; per real component five stencil products and
+    their sum: 10, and f minus it: 1) and 40 bytes (read u and f as FP64
+    complex, write r as FP32 complex).  The kernel runs on the FP64 pipe
+    (ncu, FP64_PIPE_PCT), so the bound is the measured FP64 rate; the HBM
+    figures are given beside it."""
+    M = s.n_modes
+    n_r, n_tz = s.shape[0], s.shape[1]
+    g = torch.Generator(device="cuda").manual_seed(7)
+    u = torch.randn((M, n_tz, n_r), dtype=torch.complex128, device="cuda", generator=g)
+    f = torch.randn((M, n_tz, n_r), dtype=torch.complex128, device="cuda", generator=g)
+    for _ in range(3):
+        s.stage_residual(f, u)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        s.stage_residual(f, u)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dt = ev0.elapsed_time(ev1) / 1e3 / reps
+    cells = M * n_tz * n_r
+    flops, bytes_ = 24.0 * cells, 40.0 * cells
+    ach = flops / dt / 1e12
+    pk = peaks().get("hbm_gbs")
+    full = M == 129 and (n_r, n_tz) == (256, 128)
+    return {"kernel": "FP64 residual k_residual (finest level, all %d modes)" % M,
+            "bound": "fp64", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": ach / fp64_peak, "peak_source": "measured: cuBLAS FP64 GEMM 4096^3 on this GPU",
+            "ncu_fp64_pipe_pct": FP64_PIPE_PCT["k_residual"],
+            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
+            "hbm_achieved_gbs": bytes_ / dt / 1e9,
+            "hbm_frac": (bytes_ / dt / 1e9 / pk) if pk else None,
+            "traffic": RESIDUAL_TRAFFIC_BYTES if full else None,
+            "traffic_unit": "bytes per launch (ncu)", "avg_ms": dt * 1e3,
+            "note": "each timed call also launches the small active-list reset kernel"}
 
 
 def vcycle_roofline(torch, ps, s, stream):
@@ -590,6 +727,7 @@ def vcycle_roofline(torch, ps, s, stream):
     M = s.n_modes
     lev = s.fused_level()
     n_r, n_tz = s.shape[0], s.shape[1]
+    peak32, sms, mhz = fp32_peak_tflops(torch)
     f = torch.randn((M, n_tz >> lev, n_r >> lev), dtype=torch.complex64, device="cuda")
     for _ in range(3):
         s.stage_vcycle(f)
@@ -615,9 +753,9 @@ def vcycle_roofline(torch, ps, s, stream):
     ach = flops / dt / 1e12
     return {"kernel": "fused coarse V-cycle k_vsmem (levels %d..%d in shared memory, all %d modes)"
                       % (lev, s.n_levels - 1, M),
-            "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP32_PEAK_TFLOPS,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
+            "bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
+            "frac": ach / peak32,
+            "peak_source": "derived: %d SMs (device property) x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % (sms, mhz),
             "traffic": VSMEM_TRAFFIC_BYTES if M == 129 and (n_r, n_tz) == (256, 128) else None,
             "traffic_unit": "bytes per launch (ncu)", "algorithmic_flops_per_launch": flops, "avg_ms": dt * 1e3,
             "note": "one block per mode plane: latency-bound line relaxations"}

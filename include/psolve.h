@@ -149,6 +149,23 @@ int psolve_plan_inspect(const psolve_desc* d, psolve_plan* out);
  * holds the last iterate) or another error. */
 int psolve_solve(psolve_t h, const double* rho, double* phi, double tol);
 
+/* n solves of this handle from host memory, with the copies overlapped
+ * with the solves (Sec. 5.1 steps 2-7 for each): rho_host[k] ->
+ * phi_host[k], host buffers of n_r n_tz n_phi doubles (times the number of
+ * densities of a psolve_create_multi handle), layout as psolve_solve.  The
+ * handle stages through device buffers of its own (two for rho, two for phi,
+ * allocated at the first call through the handle's allocator and kept):
+ * while solve k runs on the handle's stream, rho_host[k+1] is uploaded on a
+ * second stream and phi of solve k-1 downloaded on a third.  Page-locked
+ * host buffers (cudaHostAlloc, or registered) let the copies overlap;
+ * pageable ones work but serialise.  phi_host[k] may repeat a pointer (the
+ * downloads run in order); rho_host[k] may repeat too.  status (n ints, may
+ * be NULL) receives each solve's PSOLVE_OK / NOT_CONVERGED / NONFINITE.
+ * With warm start, each solve continues from the one before.  Returns when
+ * every potential is on the host: PSOLVE_OK, the first failing solve's code,
+ * PSOLVE_ERR_ARG (n < 0, a null buffer) or PSOLVE_ERR_NOMEM. */
+int psolve_solve_host(psolve_t h, int n, const double* const* rho_host, double* const* phi_host,
+                      double tol, int* status);
 /* n independent solves (handles may differ in size and kind), enqueued on
  * each handle's own stream; the same return convention, first error wins. */
 int psolve_solve_batched(psolve_t* hs, const double* const* rhos, double* const* phis, int n,
@@ -176,6 +193,12 @@ int psolve_batch_create(psolve_batch_t* out, psolve_t* hs, const double* const* 
                         double* const* phis, int n, double tol);
 int psolve_batch_run(psolve_batch_t b, void* stream, float* latency_ms);
 void psolve_batch_destroy(psolve_batch_t b);
+
+/* Wall time of psolve_create (ms, as psolve_stats.setup_ms) and the part of
+ * it spent building the discrete Green's function tables (Sec. 4.2: far-field
+ * closed forms and window or extended-domain solves).  PSOLVE_ERR_ARG for a
+ * null argument. */
+int psolve_get_setup_times(psolve_t h, double* setup_ms, double* dgf_ms);
 
 /* Warm start for time stepping (Sec. 5.1 and App. B: in a simulation the
  * previous step's solution is the initial guess, which cuts the V-cycles
@@ -327,6 +350,20 @@ int psolve_stage_smooth(psolve_t h, int level, int precision, void* e, const voi
 int psolve_stage_restrict(psolve_t h, int level, int precision, const void* e, const void* f,
                           void* coarse);
 int psolve_stage_prolong(psolve_t h, int level, int precision, void* e, const void* coarse);
+/* Sec. 3 (the refinement's defect, Sec. 3.3): r = f - L_m u on the finest
+ * level for every mode, evaluated in FP64 from FP64 u and f and stored in the
+ * handle's buffer precision (precision 1: FP32 planes, as the mixed V-cycle
+ * consumes it; 0: FP64), with the zero ghost values of the Psi problem.  This
+ * is the solve's own residual kernel, with its volume-weighted norms and a
+ * convergence test at tolerance 0, so that no mode retires.
+ * f, u: device double2 planes [M][n_tz][n_r] (interleaved Re/Im FP64);
+ * r: device planes [M][n_tz][n_r] of the buffer precision, overwritten.
+ * Caller-owned.  The launches are enqueued on the handle's stream
+ * (psolve_set_stream) and the call returns without waiting for them, so
+ * that calls can be timed back to back; a launch error is returned at once.
+ * PSOLVE_ERR_ARG for a null pointer or a precision other than the
+ * handle's. */
+int psolve_stage_residual(psolve_t h, int precision, const double* f, const double* u, void* r);
 /* Sec. 3: the coarse part of one V-cycle, fused into one kernel: from
  * level `level` (which must be the handle's fused level, see
  * psolve_get_fused_level) down to the coarsest, on L_m e = f with a zero

@@ -119,6 +119,9 @@ def lib():
             "psolve_get_tail": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
             "psolve_get_fused_level": (I, [P, ctypes.POINTER(ctypes.c_int)]),
             "psolve_stage_restrict": (I, [P, I, I, P, P, P]),
+            "psolve_stage_residual": (I, [P, I, P, P, P]),
+            "psolve_get_setup_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+            "psolve_solve_host": (I, [P, I, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
             "psolve_stage_prolong": (I, [P, I, I, P, P]),
             "psolve_stage_screening": (I, [P, P, P]),
             "psolve_stage_boundary": (I, [P, P, P]),
@@ -395,6 +398,48 @@ class Solver:
         check(lib().psolve_stage_restrict(self.h, level, prec, _ptr(e), _ptr(f), _ptr(c)),
               "psolve_stage_restrict")
         return c
+
+    def setup_times(self):
+        """(setup_ms, dgf_ms): psolve_create's wall time and its DGF part."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        check(lib().psolve_get_setup_times(self.h, ctypes.byref(a), ctypes.byref(b)),
+              "psolve_get_setup_times")
+        return a.value, b.value
+
+    def solve_host(self, rhos, phis=None, tol=1e-8, raise_on_error=True):
+        """Solves from host memory with copies overlapped (psolve_solve_host).
+        rhos: list of CPU float64 tensors (pinned for overlap), one per solve;
+        phis: CPU float64 tensors for the results (allocated pinned when
+        None; a list may repeat a tensor).  Returns (phis, statuses, rc)."""
+        torch = self.torch
+        n = len(rhos)
+        if phis is None:
+            phis = [torch.empty(self.shape, dtype=torch.float64).pin_memory() for _ in range(n)]
+        if len(phis) != n:
+            raise ValueError("one result buffer per density")
+        want = 1
+        for v in self.shape:
+            want *= v
+        for t in list(rhos) + list(phis):
+            if (t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous()
+                    or t.numel() != want):
+                raise ValueError("host buffers must be contiguous CPU float64 tensors of %s" % (self.shape,))
+        R = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in rhos])
+        F = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in phis])
+        st = (ctypes.c_int * max(n, 1))()
+        rc = lib().psolve_solve_host(self.h, n, R, F, float(tol), st)
+        if raise_on_error:
+            check(rc, "psolve_solve_host")
+        return phis, list(st)[:n], rc
+
+    def stage_residual(self, f, u):
+        """FP64 defect r = f - L_m u on the finest level of every mode, in the
+        buffer precision (complex64 mixed, complex128 FP64)."""
+        prec = 1 if self.desc.precision == MIXED else 0
+        r = self.planes(0, self.torch.complex64 if prec else self.torch.complex128)
+        check(lib().psolve_stage_residual(self.h, prec, _ptr(f), _ptr(u), _ptr(r)),
+              "psolve_stage_residual")
+        return r
 
     def stage_prolong(self, level, e, coarse):
         prec = 1 if self.desc.precision == MIXED else 0

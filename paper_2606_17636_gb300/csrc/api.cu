@@ -51,12 +51,23 @@ struct psolve_ctx {
   cudaStream_t st = 0;
   int device = 0;     // the device current at create: the handle's memory lives there
   double setup_ms = 0;
+  double dgf_ms = 0;   // of which the DGF tables (Sec. 4.2)
   // captured solve
   cudaGraphExec_t gexec = nullptr;
   const double* g_rho = nullptr;
   double* g_phi = nullptr;
   double g_tol = -1;
   int g_warm = -1;   // warm state the graph was captured with
+  // host-buffer pipeline (psolve_solve_host): device staging buffers, the
+  // upload and download streams and their events, per-solve status
+  struct Pipe {
+    double *rho_dev = nullptr, *rho_b = nullptr, *phi_dev = nullptr, *phi_b = nullptr;
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t in_ready = nullptr, rho_free = nullptr, out_ready = nullptr, phi_free = nullptr;
+    int* h_status = nullptr;   // pinned, one int per solve of a call
+    int cap = 0;
+  };
+  Pipe* pipe = nullptr;
 };
 
 static size_t plane_bytes(psolve_t h) { return sizeof(double2) * size_t(h->P) * h->d.n_r * h->d.n_tz; }
@@ -255,6 +266,7 @@ static int create_impl(psolve_t* out, const psolve_desc* din, int nd) {
   cudaMallocHost(&h->h_worst, sizeof(int));
   // discrete Green's function tables (Sec. 5.1 step 1), scratch released after
   {
+    const auto td = std::chrono::steady_clock::now();
     Arena scratch;
     scratch.alloc_fn = d.alloc_fn;
     scratch.free_fn = d.free_fn;
@@ -262,6 +274,7 @@ static int create_impl(psolve_t* out, const psolve_desc* din, int nd) {
     bool ok = build_dgf(h->g, h->rlaw, h->tlaw, h->bp, h->gt, scratch, h->st, h->construction, err);
     cudaDeviceSynchronize();
     scratch.release_all();
+    h->dgf_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - td).count();
     if (!ok) {
       h->A.release_all();
       return fail(err.find("memory") != std::string::npos ? PSOLVE_ERR_NOMEM : PSOLVE_ERR_ARG,
@@ -352,14 +365,36 @@ extern "C" int psolve_create(psolve_t* out, int geometry, int n_r, int n_tz, int
   return psolve_create_ex(out, &d);
 }
 
+static void pipe_release(psolve_t h) {
+  psolve_ctx::Pipe* p = h->pipe;
+  if (!p) return;
+  if (p->up) cudaStreamSynchronize(p->up);
+  if (p->down) cudaStreamSynchronize(p->down);
+  for (cudaEvent_t e : {p->in_ready, p->rho_free, p->out_ready, p->phi_free})
+    if (e) cudaEventDestroy(e);
+  if (p->up) cudaStreamDestroy(p->up);
+  if (p->down) cudaStreamDestroy(p->down);
+  if (p->h_status) cudaFreeHost(p->h_status);
+  delete p;   // the device buffers belong to the handle's arena
+  h->pipe = nullptr;
+}
+
 extern "C" void psolve_destroy(psolve_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  pipe_release(h);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->mg.h_cont) cudaFreeHost(h->mg.h_cont);
   if (h->h_worst) cudaFreeHost(h->h_worst);
   h->A.release_all();
   delete h;
+}
+
+extern "C" int psolve_get_setup_times(psolve_t h, double* setup_ms, double* dgf_ms) {
+  if (!h || !setup_ms || !dgf_ms) return fail(PSOLVE_ERR_ARG, "null argument");
+  *setup_ms = h->setup_ms;
+  *dgf_ms = h->dgf_ms;
+  return PSOLVE_OK;
 }
 
 extern "C" int psolve_set_warm_start(psolve_t h, int enable) {
@@ -569,6 +604,107 @@ extern "C" int psolve_solve(psolve_t h, const double* rho, double* phi, double t
   rc = finish(h);
   note_history(h, rc);
   return rc;
+}
+
+// ---- solves from host memory, copies overlapped with the solves -------------
+
+static int pipe_ensure(psolve_t h, int n) {
+  psolve_ctx::Pipe* p = h->pipe;
+  if (!p) {
+    p = h->pipe = new psolve_ctx::Pipe();
+    const size_t bytes = sizeof(double) * size_t(h->nd) * cells(h);
+    p->rho_dev = static_cast<double*>(h->A.get(bytes));
+    p->rho_b = static_cast<double*>(h->A.get(bytes));
+    p->phi_dev = static_cast<double*>(h->A.get(bytes));
+    p->phi_b = static_cast<double*>(h->A.get(bytes));
+    bool ok = p->rho_dev && p->rho_b && p->phi_dev && p->phi_b;
+    ok = ok && cudaStreamCreateWithFlags(&p->up, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&p->down, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t* e : {&p->in_ready, &p->rho_free, &p->out_ready, &p->phi_free})
+      ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      pipe_release(h);
+      return fail(PSOLVE_ERR_NOMEM, "host pipeline: staging buffers, streams or events");
+    }
+  }
+  if (n > p->cap) {
+    if (p->h_status) cudaFreeHost(p->h_status);
+    p->h_status = nullptr;
+    p->cap = 0;
+    if (cudaMallocHost(&p->h_status, sizeof(int) * size_t(n)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PSOLVE_ERR_NOMEM, "host pipeline: status array");
+    }
+    p->cap = n;
+  }
+  return PSOLVE_OK;
+}
+
+static int status_code(int worst) {
+  return worst == -5 ? PSOLVE_ERR_NONFINITE : worst == -4 ? PSOLVE_ERR_NOT_CONVERGED : PSOLVE_OK;
+}
+
+extern "C" int psolve_solve_host(psolve_t h, int n, const double* const* rho_host,
+                                 double* const* phi_host, double tol, int* status) {
+  if (!h || n < 0 || (n > 0 && (!rho_host || !phi_host)))
+    return fail(PSOLVE_ERR_ARG, "null argument or n < 0");
+  for (int k = 0; k < n; ++k)
+    if (!rho_host[k] || !phi_host[k]) return fail(PSOLVE_ERR_ARG, "null host buffer");
+  if (n == 0) return PSOLVE_OK;
+  if (tol <= 0) tol = 1e-8;
+  int rc = pipe_ensure(h, n);
+  if (rc != PSOLVE_OK) return rc;
+  psolve_ctx::Pipe* p = h->pipe;
+  const size_t cnt = size_t(h->nd) * cells(h), bytes = sizeof(double) * cnt;
+  cudaStream_t C = h->st;
+  // Stream C (the handle's): wait for the upload, move rho to the solve's
+  // buffer, solve, wait until the previous download left phi_b, move phi
+  // there.  Stream up: the next upload once rho_b is free.  Stream down: the
+  // download of this solve's phi, overlapping the next solve.
+  cudaEventRecord(p->phi_free, C);
+  cudaMemcpyAsync(p->rho_b, rho_host[0], bytes, cudaMemcpyHostToDevice, p->up);
+  cudaEventRecord(p->in_ready, p->up);
+  int first = PSOLVE_OK;
+  for (int k = 0; k < n; ++k) {
+    cudaStreamWaitEvent(C, p->in_ready, 0);
+    cudaMemcpyAsync(p->rho_dev, p->rho_b, bytes, cudaMemcpyDeviceToDevice, C);
+    cudaEventRecord(p->rho_free, C);
+    rc = enqueue_solve(h, p->rho_dev, p->phi_dev, tol);
+    if (rc != PSOLVE_OK) {
+      first = rc;
+      break;
+    }
+    cudaMemcpyAsync(p->h_status + k, h->d_worst, sizeof(int), cudaMemcpyDeviceToHost, C);
+    // a warm-started sequence continues from this solve (a failed one shows
+    // in its status)
+    note_history(h, PSOLVE_OK);
+    cudaStreamWaitEvent(C, p->phi_free, 0);
+    cudaMemcpyAsync(p->phi_b, p->phi_dev, bytes, cudaMemcpyDeviceToDevice, C);
+    cudaEventRecord(p->out_ready, C);
+    if (k + 1 < n) {
+      cudaStreamWaitEvent(p->up, p->rho_free, 0);
+      cudaMemcpyAsync(p->rho_b, rho_host[k + 1], bytes, cudaMemcpyHostToDevice, p->up);
+      cudaEventRecord(p->in_ready, p->up);
+    }
+    cudaStreamWaitEvent(p->down, p->out_ready, 0);
+    cudaMemcpyAsync(phi_host[k], p->phi_b, bytes, cudaMemcpyDeviceToHost, p->down);
+    cudaEventRecord(p->phi_free, p->down);
+  }
+  const cudaError_t e1 = cudaStreamSynchronize(p->up), e2 = cudaStreamSynchronize(C),
+                    e3 = cudaStreamSynchronize(p->down);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !cuda_ok("solve_host"))
+    return fail(PSOLVE_ERR_CUDA, g_err.empty() ? "host pipeline failed" : g_err);
+  if (first != PSOLVE_OK) return first;
+  for (int k = 0; k < n; ++k) {
+    const int c = status_code(p->h_status[k]);
+    if (status) status[k] = c;
+    if (c != PSOLVE_OK && first == PSOLVE_OK) first = c;
+  }
+  if (h->warm && status_code(p->h_status[n - 1]) == PSOLVE_ERR_NONFINITE) h->warm_hist = 0;
+  if (first == PSOLVE_ERR_NONFINITE) return fail(first, "non-finite residual norm in a solve");
+  if (first == PSOLVE_ERR_NOT_CONVERGED) return fail(first, "a mode did not reach the tolerance in a solve");
+  return PSOLVE_OK;
 }
 
 extern "C" int psolve_solve_batched(psolve_t* hs, const double* const* rhos, double* const* phis,
@@ -1135,6 +1271,17 @@ extern "C" int psolve_stage_prolong(psolve_t h, int level, int precision, void* 
   h->mg.prolong(level, e, coarse, h->st);
   return cudaStreamSynchronize(h->st) == cudaSuccess && cuda_ok("prolong") ? PSOLVE_OK
                                                                              : PSOLVE_ERR_CUDA;
+}
+
+extern "C" int psolve_stage_residual(psolve_t h, int precision, const double* f, const double* u,
+                                     void* r) {
+  if (!h || !f || !u || !r) return fail(PSOLVE_ERR_ARG, "null argument");
+  int rc = check_level(h, 0, precision, false);
+  if (rc) return rc;
+  full_batch(h);
+  h->mg.residual_to(reinterpret_cast<const double2*>(f), reinterpret_cast<const double2*>(u), r,
+                    h->st);
+  return cuda_ok("residual") ? PSOLVE_OK : PSOLVE_ERR_CUDA;   // asynchronous
 }
 
 extern "C" int psolve_get_fused_level(psolve_t h, int* level) {

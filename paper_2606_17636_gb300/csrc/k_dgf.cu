@@ -6,51 +6,88 @@ namespace ps {
 
 // G^m (deriv = 0) or dG^m/dr (deriv = 1) of -G/|x - x'| for a list of point
 // pairs (Eqs. DGF_bc_sph, DGF_bc_cyl and their radial derivatives), all
-// modes m = 0..M-1, one warp per pair.  out[m * mstride + pair * pstride],
+// modes m = 0..M-1.  The kernel of a pair depends on phi - phi' only through
+// cos(2 pi k / N), so its samples v[k] are real and even in k and their DFT
+// is real: G^m = sum_k v[k] cos(2 pi m k / N).  A warp takes two pairs a, b,
+// packs z[k] = v_a[k] + i v_b[k] and computes the length-N DFT of z by a
+// radix-2 FFT in its shared memory (bit-reversed input order): then
+// G_a^m = Re Z[m] and G_b^m = Im Z[m].  out[m * mstride + pair * pstride],
 // multiplied by scale[pair % scale_mod] when scale != nullptr.
-__global__ void __launch_bounds__(256) k_green(GreenArgs a) {
-  extern __shared__ double gsm[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long pair = long(blockIdx.x) * (blockDim.x >> 5) + warp;
-  double* v = gsm + size_t(warp) * a.N;
-  if (pair >= a.npairs) return;
+__device__ __forceinline__ double green_sample(const GreenArgs& a, long pair, double c, bool& bad) {
   const double xt = a.xt[pair], yt = a.yt[pair], xs = a.xs[pair], ys = a.ys[pair];
-  bool bad = false;
-  for (int k = lane; k < a.N; k += 32) {
-    const double c = a.cosk[k];
-    double d2, num = 1.0;
-    if (a.geometry == SPH) {
-      const double ct = cos(yt), st = sin(yt), cs = cos(ys), ss = sin(ys);
-      d2 = xt * xt + xs * xs - 2.0 * xt * xs * (ct * cs + st * ss * c);
-      if (a.deriv) num = (xt - xs * ct * cs) - xs * st * ss * c;
-    } else {
-      d2 = xt * xt + xs * xs - 2.0 * xt * xs * c + (yt - ys) * (yt - ys);
-      if (a.deriv) num = xt - xs * c;
-    }
-    if (!(d2 > 0.0)) bad = true;
-    const double id = 1.0 / sqrt(d2);
-    v[k] = a.deriv ? a.G * num * id * id * id : -a.G * id;
+  double d2, num = 1.0;
+  if (a.geometry == SPH) {
+    const double ct = cos(yt), st = sin(yt), cs = cos(ys), ss = sin(ys);
+    d2 = xt * xt + xs * xs - 2.0 * xt * xs * (ct * cs + st * ss * c);
+    if (a.deriv) num = (xt - xs * ct * cs) - xs * st * ss * c;
+  } else {
+    d2 = xt * xt + xs * xs - 2.0 * xt * xs * c + (yt - ys) * (yt - ys);
+    if (a.deriv) num = xt - xs * c;
   }
-  bad = __any_sync(0xffffffffu, bad);
+  if (!(d2 > 0.0)) {
+    bad = true;
+    return 0.0;
+  }
+  const double id = 1.0 / sqrt(d2);
+  return a.deriv ? a.G * num * id * id * id : -a.G * id;
+}
+
+__global__ void __launch_bounds__(128) k_green(GreenArgs a, int lg) {
+  extern __shared__ double2 gz[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int N = a.N;
+  const long pa = (long(blockIdx.x) * (blockDim.x >> 5) + warp) * 2, pb = pa + 1;
+  if (pa >= a.npairs) return;
+  const bool has_b = pb < a.npairs;
+  double2* z = gz + size_t(warp) * N;
+  bool bad_a = false, bad_b = false;
+  for (int k = lane; k < N; k += 32) {
+    const double c = a.cosk[k];
+    const double va = green_sample(a, pa, c, bad_a);
+    const double vb = has_b ? green_sample(a, pb, c, bad_b) : 0.0;
+    const int kr = lg ? int(__brev(unsigned(k)) >> (32 - lg)) : 0;
+    z[kr] = make_double2(va, vb);
+  }
+  bad_a = __any_sync(0xffffffffu, bad_a);
+  bad_b = __any_sync(0xffffffffu, bad_b);
   __syncwarp();
-  const double sc = a.scale ? a.scale[pair % a.scale_mod] : 1.0;
+  // decimation in time: butterflies of span `half`, twiddle e^{-2 pi i t / N}
+  // with sin(2 pi t / N) = cos(2 pi (t - N/4) / N)
+  for (int half = 1; half < N; half <<= 1) {
+    const int step = N / (2 * half);
+    for (int j = lane; j < N / 2; j += 32) {
+      const int pos = j & (half - 1);
+      const int i0 = ((j - pos) << 1) + pos, i1 = i0 + half;
+      const int t = pos * step;
+      const double wr = a.cosk[t];
+      const double wi = t ? -a.cosk[(t + 3 * (N >> 2)) & (N - 1)] : 0.0;
+      const double2 u = z[i0], v = z[i1];
+      const double vr = v.x * wr - v.y * wi, vi = v.x * wi + v.y * wr;
+      z[i0] = make_double2(u.x + vr, u.y + vi);
+      z[i1] = make_double2(u.x - vr, u.y - vi);
+    }
+    __syncwarp();
+  }
+  const double sa = a.scale ? a.scale[pa % a.scale_mod] : 1.0;
+  const double sb = (a.scale && has_b) ? a.scale[pb % a.scale_mod] : 1.0;
   for (int m = lane; m < a.M; m += 32) {
-    double s = 0.0;
-    if (!bad)
-      for (int k = 0; k < a.N; ++k) s += a.cosk[(long(m) * k) & (a.N - 1)] * v[k];
-    a.out[long(m) * a.mstride + pair * a.pstride] = bad ? 0.0 : s * sc;
+    const double2 v = z[m];
+    a.out[long(m) * a.mstride + pa * a.pstride] = bad_a ? 0.0 : v.x * sa;
+    if (has_b) a.out[long(m) * a.mstride + pb * a.pstride] = bad_b ? 0.0 : v.y * sb;
   }
 }
 
 void launch_green(const GreenArgs& a, cudaStream_t st) {
   if (a.npairs == 0) return;
-  const long blocks = (a.npairs + 7) / 8;
+  int lg = 0;
+  while ((1 << lg) < a.N) ++lg;
+  const long blocks = (a.npairs + 7) / 8;   // 4 warps x 2 pairs
   static bool attr = false;
-  if (!attr) {   // 8 warps x N doubles: 64 KB at the largest N = 1024
-    cudaFuncSetAttribute(k_green, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 1024 * int(sizeof(double)));
+  if (!attr) {   // 4 warps x N complex doubles: 64 KB at the largest N = 1024
+    cudaFuncSetAttribute(k_green, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 1024 * int(sizeof(double2)));
     attr = true;
   }
-  k_green<<<unsigned(blocks), 256, 8 * a.N * sizeof(double), st>>>(a);
+  k_green<<<unsigned(blocks), 128, 4 * a.N * sizeof(double2), st>>>(a, lg);
 }
 
 // ---------------------------------------------------------------------------
@@ -109,10 +146,16 @@ void launch_ext_extract(const ExtArgs& a, const double2* u, double* gt, int p0, 
 }
 
 // ---------------------------------------------------------------------------
-// Auxiliary windows: one block solves one (source, mode) window problem with
-// Jacobi-preconditioned conjugate gradients on the symmetric positive form
-// -dV L_m (the operator is volume-symmetric), FP64, to a relative residual
-// of 1e-14, and writes the window values at the targets inside the window.
+// Auxiliary windows: one block solves one (source, mode) window problem on
+// the symmetric positive form -dV L_m (the operator is volume-symmetric) to a
+// relative residual of 1e-14 (Jacobi-preconditioned norm), and writes the
+// window values at the targets inside the window.  Mixed-precision iterative
+// refinement: the solution x and the defect r = b - A x are FP64; each
+// correction A d = r is solved by Jacobi-preconditioned conjugate gradients
+// in FP32 (coefficients staged once per block as FP32) until its own
+// preconditioned residual falls by 1e-8, then x += d and the FP64 defect is
+// formed again.  GB300's FP32 rate is about 64 times its FP64 rate, so the
+// FP64 work is a few stencil passes per window instead of one per CG step.
 // ---------------------------------------------------------------------------
 __device__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -125,18 +168,40 @@ __device__ double block_sum(double v, double* sh) {
   return s;
 }
 
+__device__ float block_sumf(float v, float* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  float s = 0.f;
+  for (int w = 0; w < int(blockDim.x >> 5); ++w) s += sh[w];
+  return s;
+}
+
+// FP32 coefficients of one window cell of -dV L_m: east, west, north, south
+// neighbours and the diagonal (A c = diag c - sum nb c_nb)
+struct AuxCoef {
+  float e, w, n, s, d;
+};
+
 __global__ void __launch_bounds__(256) k_aux_cg(AuxArgs a) {
   extern __shared__ double asm_[];
   __shared__ double red[8];
+  __shared__ float redf[8];
   const int prob = blockIdx.x;          // = slot * nb + s
   const int slot = prob / a.nb, s = prob - slot * a.nb;
   const AuxWin w = a.win[s];
   const int wr = w.i1 - w.i0 + 1, wt = w.j1 - w.j0 + 1, n = wr * wt;
-  double* x = asm_;
-  double* r = x + n;
-  double* pp = r + n;
-  double* ap = pp + n;
-  double* dinv = ap + n;
+  double* x = asm_;                     // FP64 solution
+  double* b = x + n;                    // FP64 right-hand side
+  double* r64 = b + n;                  // FP64 defect
+  float* d = reinterpret_cast<float*>(r64 + n);   // FP32 correction
+  float* r = d + n;
+  float* pp = r + n;
+  float* ap = pp + n;
+  float* dinv = ap + n;
+  AuxCoef* cf = reinterpret_cast<AuxCoef*>(dinv + n + (n & 1));   // 8-byte aligned
   const double s2 = a.s2[slot];
   const int NR = a.nr_big + 2, NT = a.nt_big + 2;
   auto AE = [&](int i) { return a.rt[RT_AE * NR + i]; };
@@ -150,7 +215,7 @@ __global__ void __launch_bounds__(256) k_aux_cg(AuxArgs a) {
   auto VT = [&](int j) { return a.tt[TT_V * NT + j]; };
   const double* ring = a.ring + (long(s) * a.ring_max) * a.M;   // [k][M]
   // right-hand side b = -dV (4 pi G delta / dV_s - ghost terms); x = 0
-  double rr0 = 0.0;
+  double rz = 0.0;
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
     const int jj = c / wr, ii = c - jj * wr;
     const int i = w.i0 + ii, j = w.j0 + jj;
@@ -161,47 +226,84 @@ __global__ void __launch_bounds__(256) k_aux_cg(AuxArgs a) {
     if (ii == 0 && w.ring_l >= 0) rhs -= AW(i) * ring[long(w.ring_l + jj) * a.M + slot];
     if (jj == 0 && w.ring_b >= 0) rhs -= PP(i) * AS(j) * ring[long(w.ring_b + ii) * a.M + slot];
     if (jj == wt - 1 && w.ring_t >= 0) rhs -= PP(i) * AN(j) * ring[long(w.ring_t + ii) * a.M + slot];
-    const double b = -dv * rhs;
+    const double bc = -dv * rhs;
     const double diag = dv * ((AE(i) + AW(i)) + PP(i) * (AN(j) + AS(j)) + s2 * QQ(i) * TT(j));
-    dinv[c] = 1.0 / diag;
+    AuxCoef q;
+    q.e = ii + 1 < wr ? float(dv * AE(i)) : 0.f;
+    q.w = ii > 0 ? float(dv * AW(i)) : 0.f;
+    q.n = jj + 1 < wt ? float(dv * PP(i) * AN(j)) : 0.f;
+    q.s = jj > 0 ? float(dv * PP(i) * AS(j)) : 0.f;
+    q.d = float(diag);
+    cf[c] = q;
+    dinv[c] = float(1.0 / diag);
     x[c] = 0.0;
-    r[c] = b;
-    pp[c] = b * dinv[c];
-    rr0 += b * b * dinv[c];
+    b[c] = bc;
+    r64[c] = bc;
+    rz += bc * bc / diag;
   }
-  double rz = block_sum(rr0, red);
+  rz = block_sum(rz, red);
   const double stop = rz * 1e-28;
   int it = 0;
-  for (; it < a.max_iter && rz > stop; ++it) {
-    double pap = 0.0;
+  for (int outer = 0; outer < 12 && rz > stop; ++outer) {
+    // FP32 conjugate gradients on A d = r64, d = 0
+    float rzf = 0.f;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const float rc = float(r64[c]);
+      r[c] = rc;
+      d[c] = 0.f;
+      pp[c] = rc * dinv[c];
+      rzf += rc * rc * dinv[c];
+    }
+    rzf = block_sumf(rzf, redf);
+    const float inner_stop = rzf * 1e-8f;
+    for (; it < a.max_iter && rzf > inner_stop; ++it) {
+      float pap = 0.f;
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const AuxCoef q = cf[c];
+        const int ii = c % wr;
+        float v = q.d * pp[c];
+        if (ii + 1 < wr) v -= q.e * pp[c + 1];
+        if (ii > 0) v -= q.w * pp[c - 1];
+        if (c + wr < n) v -= q.n * pp[c + wr];
+        if (c >= wr) v -= q.s * pp[c - wr];
+        ap[c] = v;
+        pap += pp[c] * v;
+      }
+      pap = block_sumf(pap, redf);
+      const float alpha = rzf / pap;
+      float rzn = 0.f;
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        d[c] += alpha * pp[c];
+        const float rc = r[c] - alpha * ap[c];
+        r[c] = rc;
+        rzn += rc * rc * dinv[c];
+      }
+      rzn = block_sumf(rzn, redf);
+      const float beta = rzn / rzf;
+      rzf = rzn;
+      for (int c = threadIdx.x; c < n; c += blockDim.x) pp[c] = r[c] * dinv[c] + beta * pp[c];
+      __syncthreads();
+    }
+    // x += d; FP64 defect r64 = b - A x with the FP64 coefficients
+    for (int c = threadIdx.x; c < n; c += blockDim.x) x[c] += double(d[c]);
+    __syncthreads();
+    double rzd = 0.0;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
       const int jj = c / wr, ii = c - jj * wr;
       const int i = w.i0 + ii, j = w.j0 + jj;
       const double dv = VR(i) * VT(j);
-      const double pc = pp[c];
-      double lp = -(AE(i) + AW(i) + PP(i) * (AN(j) + AS(j)) + s2 * QQ(i) * TT(j)) * pc;
-      if (ii + 1 < wr) lp += AE(i) * pp[c + 1];
-      if (ii > 0) lp += AW(i) * pp[c - 1];
-      if (jj + 1 < wt) lp += PP(i) * AN(j) * pp[c + wr];
-      if (jj > 0) lp += PP(i) * AS(j) * pp[c - wr];
-      ap[c] = -dv * lp;
-      pap += pc * ap[c];
+      double lx = -(AE(i) + AW(i) + PP(i) * (AN(j) + AS(j)) + s2 * QQ(i) * TT(j)) * x[c];
+      if (ii + 1 < wr) lx += AE(i) * x[c + 1];
+      if (ii > 0) lx += AW(i) * x[c - 1];
+      if (jj + 1 < wt) lx += PP(i) * AN(j) * x[c + wr];
+      if (jj > 0) lx += PP(i) * AS(j) * x[c - wr];
+      const double rc = b[c] + dv * lx;
+      r64[c] = rc;
+      rzd += rc * rc * double(dinv[c]);
     }
-    pap = block_sum(pap, red);
-    const double alpha = rz / pap;
-    double rzn = 0.0;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-      x[c] += alpha * pp[c];
-      r[c] -= alpha * ap[c];
-      rzn += r[c] * r[c] * dinv[c];
-    }
-    rzn = block_sum(rzn, red);
-    const double beta = rzn / rz;
-    rz = rzn;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) pp[c] = r[c] * dinv[c] + beta * pp[c];
-    __syncthreads();
+    rz = block_sum(rzd, red);
   }
-  if (threadIdx.x == 0 && it >= a.max_iter && a.fail) atomicAdd(a.fail, 1);
+  if (threadIdx.x == 0 && (rz > stop || !(rz == rz)) && a.fail) atomicAdd(a.fail, 1);
   // targets inside the window
   for (int k = threadIdx.x; k < w.ntarget; k += blockDim.x) {
     const int t = a.tlist[w.tfirst + k];
@@ -212,10 +314,11 @@ __global__ void __launch_bounds__(256) k_aux_cg(AuxArgs a) {
 }
 
 void launch_aux_cg(const AuxArgs& a, int nprob, int max_cells, cudaStream_t st) {
-  const size_t sm = size_t(5) * max_cells * sizeof(double);
+  // FP64 x, b, r; FP32 d, r, p, Ap, 1/diag; five FP32 coefficients per cell
+  const size_t sm = size_t(max_cells) * (3 * sizeof(double) + 5 * sizeof(float) + sizeof(AuxCoef)) + 8;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_aux_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(k_aux_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     attr = true;
   }
   k_aux_cg<<<nprob, 256, sm, st>>>(a);

@@ -343,6 +343,23 @@ void MGSolver::residual(const double2* ff, const double2* u, double tol, cudaStr
     launch_residual<double>(lv[0], batch, ff, u, (double2*)f[0], d_part, d_psum, d_cnt, ra, st, d_ctab);
 }
 
+void MGSolver::residual_to(const double2* ff, const double2* u, void* r, cudaStream_t st) {
+  RetireArgs ra;
+  ra.S = S;
+  ra.tol = 0.0;
+  ra.max_cycles = opt.max_cycles;
+  ra.stagnation = opt.stagnation;
+  ra.use_cond = 0;
+  ra.handle = 0;
+  ra.gcnt = d_gcnt;
+  ra.zero_guess = 0;
+  ra.tail_planes = 0;
+  if (opt.precision)
+    launch_residual<float>(lv[0], batch, ff, u, (float2*)r, d_part, d_psum, d_cnt, ra, st, d_ctab);
+  else
+    launch_residual<double>(lv[0], batch, ff, u, (double2*)r, d_part, d_psum, d_cnt, ra, st, d_ctab);
+}
+
 // One V-cycle on the error equation L e_0 = f_0 (f_0 = FP64 residual in the
 // buffer precision), e_0 starting from zero (Sec. 3: pre-smoothing, defect
 // restriction, coarse correction, prolongation, post-smoothing).  Levels

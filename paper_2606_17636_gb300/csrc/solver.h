@@ -84,6 +84,8 @@ class MGSolver {
   void fused(cudaStream_t st);   // levels first .. coarsest in shared memory
   void residual(const double2* f, const double2* u, double tol, cudaStream_t st, int use_cond,
                 unsigned long long cond);
+  // the defect alone into r (tolerance 0: no plane retires)
+  void residual_to(const double2* f, const double2* u, void* r, cudaStream_t st);
   int* d_act = nullptr;
   int* d_nact = nullptr;
   int* d_slot = nullptr;

@@ -91,6 +91,42 @@ def test_smooth_restrict_prolong(ps, key, precision, tol, level):
 
 
 @pytest.mark.parametrize("key", list(SMALL))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fp64_residual_stage(ps, key, precision):
+    """The refinement's defect (FP64 arithmetic, stored in the buffer
+    precision) against the oracle's residual on the finest level."""
+    from oracle import mg, operator
+    sp = SMALL[key]
+    s = _solver(ps, key, precision)
+    p = oracle_plane(sp)
+    H = mg.Hierarchy(p)
+    nr, nt, M = sp["n_r"], sp["n_tz"], s.n_modes
+    u = _rand_planes((M, nt, nr), 40)
+    f = _rand_planes((M, nt, nr), 41)
+    got = s.stage_residual(torch.from_numpy(f).cuda(), torch.from_numpy(u).cuda())
+    assert got.dtype == (torch.complex64 if precision else torch.complex128)
+    got = got.cpu().numpy().astype(np.complex128)
+    for m in range(M):
+        uu = np.zeros((nr + 2, nt + 2), complex)
+        uu[1:-1, 1:-1] = u[m].T
+        ref = H.residual(0, m, uu, f[m].T).T
+        absLu = operator.from_vec(abs(operator.matrix(p, m)) @ operator.to_vec(np.abs(u[m].T)), nr, nt).T
+        scale = np.abs(f[m]) + absLu
+        # elementwise against |f| + |L_m| |u|: the plan's FP64 coefficient
+        # tables agree with the oracle's to about 1e-12 relative (products of
+        # face areas, spacings, metric factors and the mode's s_m^2 formed in
+        # another order); then (mixed) one rounding to FP32
+        bound = 1e-11 * scale + (2.0 ** -24 * np.abs(ref) if precision else 0.0)
+        assert np.all(np.abs(got[m] - ref) <= bound), m
+    with pytest.raises(ps.PSolveError):
+        bad = torch.zeros(1, dtype=torch.complex128, device="cuda")
+        from paper_2606_17636_gb300 import lib, check
+        check(lib().psolve_stage_residual(s.h, 1 - precision, bad.data_ptr(), bad.data_ptr(),
+                                          bad.data_ptr()), "psolve_stage_residual")
+    s.close()
+
+
+@pytest.mark.parametrize("key", list(SMALL))
 def test_mg_solve_reaches_direct_solution_and_counts_cycles(ps, key):
     import scipy.sparse.linalg as spla
 
