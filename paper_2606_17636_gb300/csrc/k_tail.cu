@@ -105,10 +105,105 @@ __device__ void push_halo(cg::cluster_group& cl, unsigned char* sm, const V* src
   }
 }
 
-// End of a smoothing step: the own rows into the neighbours' halo buffer b^1.
-__device__ void publish(cg::cluster_group& cl, unsigned char* sm, const TailLevel& t, int h, int b,
-                        int rank, int C) {
-  push_halo(cl, sm, reinterpret_cast<const V*>(sm) + t.eo, t.eh[b ^ 1], 1, t.s, t.L.nr, h, rank, C);
+// ---- neighbour signalling for the smoothing steps ---------------------------
+// A smoothing step ends with the CTA's boundary rows stored into the
+// neighbours' halo buffer b^1 by asynchronous distributed-shared-memory
+// stores that also count their bytes on the receiver's mbarrier of that
+// buffer (st.async ... complete_tx); the receiver announces the bytes it
+// expects and waits for that mbarrier phase.  So a CTA waits only for the
+// CTAs whose rows it reads, not for the whole cluster, and no memory fence
+// is needed.  Every CTA that sends to a CTA also receives from it (the halos
+// are symmetric), so neighbours are never more than one step apart: a
+// buffer is not rewritten before its reader has finished the step that
+// reads it, and one phase's bytes never mix with the next phase's.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return unsigned(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned peer_u32(unsigned local, int rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait (about one second of polling at the maximum SM clock); false
+// when it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+__device__ __forceinline__ void st_async16(unsigned addr, float4 v, unsigned bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+      "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+      "r"(__float_as_uint(v.w)), "r"(bar)
+      : "memory");
+}
+
+// Own rows [r0, r1) into CTA tgt's error halo buffer at dst (slots as
+// push_rows with eblock = 1), counted on tgt's mbarrier `bar` (local address).
+__device__ void push_rows_async(unsigned char* sm, const V* src, int dst, int s, int nr, int h, int r0,
+                                int r1, int tgt, int delta, unsigned bar) {
+  if (r1 <= r0) return;
+  const unsigned rb = peer_u32(smem_u32(sm), tgt), rbar = peer_u32(bar, tgt);
+  const int chunks = nr >> 1;
+  const int n = (r1 - r0) * chunks;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int q = idx / chunks, c = idx - q * chunks, r = r0 + q, rt = r - delta;
+    const int slot = rt < 0 ? rt + h : h + rt - s;
+    st_async16(rb + unsigned((dst + slot * nr + 2 * c) * sizeof(V)),
+               *reinterpret_cast<const float4*>(src + r * nr + 2 * c), rbar);
+  }
+}
+
+// Halo rows a CTA receives per step: from rank - d its rows
+// [max(0, d s - h), s), from rank + d its rows [0, min(s, h - (d - 1) s)).
+__device__ __forceinline__ int halo_rows_in(int s, int h, int rank, int C) {
+  int n = 0;
+  for (int d = 1; (d - 1) * s < h; ++d) {
+    if (rank - d >= 0) n += s - max(0, d * s - h);
+    if (rank + d < C) n += min(s, h - (d - 1) * s);
+  }
+  return n;
+}
+
+// End of a smoothing step: the own rows into the neighbours' halo buffer
+// b^1, then wait until the neighbours' rows have arrived in ours.  `bars`:
+// local addresses of this level's two mbarriers; bit pb + b of `phase` is
+// the parity of the next completion of mbarrier b.  A wait that gives up
+// sets `dead`.
+__device__ void publish_wait(unsigned char* sm, const TailLevel& t, int h, int b, int rank, int C,
+                             const unsigned* bars, unsigned& phase, int pb, bool& dead) {
+  const V* src = reinterpret_cast<const V*>(sm) + t.eo;
+  const int s = t.s, nr = t.L.nr, bn = b ^ 1;
+  for (int d = 1; (d - 1) * s < h; ++d) {
+    if (rank + d < C) push_rows_async(sm, src, t.eh[bn], s, nr, h, max(0, d * s - h), s, rank + d, d * s, bars[bn]);
+    if (rank - d >= 0)
+      push_rows_async(sm, src, t.eh[bn], s, nr, h, 0, min(s, h - (d - 1) * s), rank - d, -d * s, bars[bn]);
+  }
+  if (threadIdx.x == 0)
+    mbar_expect(bars[bn], unsigned(halo_rows_in(s, h, rank, C) * nr * int(sizeof(V))));
+  if (!dead && !mbar_wait(bars[bn], (phase >> (pb + bn)) & 1u)) dead = true;
+  phase ^= 1u << (pb + bn);
+  __syncthreads();   // the next step rewrites the own rows this step sent
 }
 
 // One radial line (own row r, or the first row of the next CTA) relaxed in
@@ -266,18 +361,17 @@ __device__ void t_tstep(const LevelDev& L, unsigned char* sm, const TailLevel& t
 
 // `cycles` smoothing cycles of one level (Algorithm 1: radial lines, then
 // polar lines, each in zebra order); after each step the own rows are
-// published and the cluster synchronises.
-__device__ void t_smooth(cg::cluster_group& cl, const LevelDev& L, unsigned char* sm,
-                         const TailLevel& t, int h, int& b, int rank, int C, float s2, int n_sor,
-                         int cycles) {
+// published to the neighbours, whose rows are awaited.
+__device__ void t_smooth(const LevelDev& L, unsigned char* sm, const TailLevel& t, int h, int& b,
+                         int rank, int C, float s2, int n_sor, int cycles, const unsigned* bars,
+                         unsigned& phase, int pb, bool& dead) {
   const int j0 = rank * t.s;
   for (int cyc = 0; cyc < cycles; ++cyc)
     for (int step = 0; step < 3; ++step) {
       if (step == 0) t_rstep(L, sm, t, h, b, j0, s2, n_sor);
       else t_tstep(L, sm, t, h, b, j0, s2, n_sor, step - 1);
       __syncthreads();
-      publish(cl, sm, t, h, b, rank, C);
-      cl.sync();
+      publish_wait(sm, t, h, b, rank, C, bars, phase, pb, dead);
       b ^= 1;
     }
 }
@@ -489,6 +583,7 @@ __global__ void __launch_bounds__(kTailThreads, 1)
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ LevelDev sL[8];
   __shared__ D4 red[kTailThreads / 32];
+  __shared__ __align__(8) unsigned long long hbar[8][2];   // per level and halo buffer
   cg::cluster_group cl = cg::this_cluster();
   const int C = a.C, rank = int(cl.block_rank());
   const int q = int(blockIdx.x) / C;
@@ -530,9 +625,15 @@ __global__ void __launch_bounds__(kTailThreads, 1)
     Uh[idx] = (j >= 0 && j < nt0) ? ug[base + size_t(j) * nr0 + i] : make_double2(0.0, 0.0);
   }
   cp_async_wait_all();
-  // every CTA of the cluster has started before any writes into a peer's
-  // shared memory
+  if (threadIdx.x < 2 * K) {
+    mbar_init(smem_u32(&hbar[threadIdx.x >> 1][threadIdx.x & 1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // every CTA of the cluster has started, and its mbarriers are initialised,
+  // before any writes into a peer's shared memory
   cl.sync();
+  unsigned phase = 0;   // bit 2 l + b: parity of the next completion of hbar[l][b]
+  bool dead = false;    // a neighbour wait gave up (reported as non-finite)
   int bl[8];   // per level: the row block the next step reads
 #pragma unroll
   for (int l = 0; l < 8; ++l) bl[l] = 0;
@@ -582,7 +683,7 @@ __global__ void __launch_bounds__(kTailThreads, 1)
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = D4{ax, ay, 0.0, 0.0};
     __syncthreads();
     if (threadIdx.x < C) {   // the CTA's partial to every CTA of the cluster
-      D4 tsum{0.0, 0.0, 0.0, 0.0};
+      D4 tsum{0.0, 0.0, dead ? 1.0 : 0.0, 0.0};
       for (int w = 0; w < int(blockDim.x >> 5); ++w) { tsum.x += red[w].x; tsum.y += red[w].y; }
       *cl.map_shared_rank(part + rank, int(threadIdx.x)) = tsum;
     }
@@ -590,10 +691,10 @@ __global__ void __launch_bounds__(kTailThreads, 1)
     push_halo(cl, sm, rowp(sm, t0.fo, nr0, h, 0), t0.fo, 0, s0, nr0, h, rank, C);
     cl.sync();
     // App. B criterion, evaluated identically by every thread of the cluster
-    double sx = 0.0, sy = 0.0;
-    for (int c = 0; c < C; ++c) { sx += part[c].x; sy += part[c].y; }
+    double sx = 0.0, sy = 0.0, sdead = 0.0;
+    for (int c = 0; c < C; ++c) { sx += part[c].x; sy += part[c].y; sdead += part[c].z; }
     int st = TS_ACTIVE;
-    if (!isfinite(sx) || !isfinite(sy)) st = TS_NONFINITE;
+    if (!isfinite(sx) || !isfinite(sy) || sdead != 0.0) st = TS_NONFINITE;
     else if (sx <= tol2 * fmax(nf.x, floor2) && sy <= tol2 * fmax(nf.y, floor2)) st = TS_OK;
     else if (it >= a.max_cycles) st = TS_NOTCONV;
     else if (a.stagnation && it >= 3 && sx + sy > 0.81 * (px + py)) st = TS_STAGNATED;
@@ -616,7 +717,8 @@ __global__ void __launch_bounds__(kTailThreads, 1)
         for (int k = threadIdx.x; k < 2 * h * L.nr; k += blockDim.x) eh[k] = vz();
       }
       __syncthreads();
-      t_smooth(cl, L, sm, t, h, bl[l], rank, C, s2, a.n_sor, t.nu1);
+      const unsigned bars[2] = {smem_u32(&hbar[l][0]), smem_u32(&hbar[l][1])};
+      t_smooth(L, sm, t, h, bl[l], rank, C, s2, a.n_sor, t.nu1, bars, phase, 2 * l, dead);
       const TailLevel& tc = a.lv[l + 1];
       const LevelDev Lq = sL[l + 1];
       if (l + 1 < K - 1) {
@@ -644,7 +746,8 @@ __global__ void __launch_bounds__(kTailThreads, 1)
       const LevelDev L = sL[l];
       t_prolong(L, sL[l + 1], sm, t, a.lv[l + 1], h, bl[l], bl[l + 1], rank, m);
       __syncthreads();
-      t_smooth(cl, L, sm, t, h, bl[l], rank, C, s2, a.n_sor, t.nu2);
+      const unsigned bars[2] = {smem_u32(&hbar[l][0]), smem_u32(&hbar[l][1])};
+      t_smooth(L, sm, t, h, bl[l], rank, C, s2, a.n_sor, t.nu2, bars, phase, 2 * l, dead);
     }
     // u += e on the own rows and the two halo rows (the halo rows of e are
     // current, so every copy of a row gets the owner's values)
