@@ -74,7 +74,14 @@ typedef struct {
   psolve_alloc_fn alloc_fn; /* optional allocation hooks (see above)            */
   psolve_free_fn free_fn;
   void* alloc_user;
+  int dgf_construction; /* Sec. 4.2: PSOLVE_DGF_AUTO (0: the extended domain for
+                          logarithmic radial grids with r_out / r_in >= 100 and
+                          n_r >= 32, auxiliary windows otherwise),
+                          PSOLVE_DGF_AUX (1) or PSOLVE_DGF_EXTENDED (2, needs
+                          logarithmic spacing and n_r >= 32)                     */
 } psolve_desc;
+
+enum { PSOLVE_DGF_AUTO = 0, PSOLVE_DGF_AUX = 1, PSOLVE_DGF_EXTENDED = 2 };
 
 /* Per-solve statistics (psolve_get_stats).  Arrays sized by the caller:
  * cycles_psi / cycles_phi / status hold M entries when non-NULL. */

@@ -146,6 +146,10 @@ static int prepare_desc(const psolve_desc& din, psolve_desc& d) {
   if (d.n_sor <= 0) d.n_sor = 2;
   if (d.precision != PSOLVE_FP64 && d.precision != PSOLVE_MIXED)
     return fail(PSOLVE_ERR_ARG, "precision must be PSOLVE_FP64 or PSOLVE_MIXED");
+  if (d.dgf_construction < PSOLVE_DGF_AUTO || d.dgf_construction > PSOLVE_DGF_EXTENDED)
+    return fail(PSOLVE_ERR_ARG, "dgf_construction must be PSOLVE_DGF_AUTO, _AUX or _EXTENDED");
+  if (d.dgf_construction == PSOLVE_DGF_EXTENDED && (d.spacing != PSOLVE_LOG || d.n_r < 32))
+    return fail(PSOLVE_ERR_ARG, "the extended-domain DGF needs logarithmic radial spacing and n_r >= 32");
   return PSOLVE_OK;
 }
 
@@ -271,6 +275,7 @@ static int create_impl(psolve_t* out, const psolve_desc* din, int nd) {
     scratch.alloc_fn = d.alloc_fn;
     scratch.free_fn = d.free_fn;
     scratch.user = d.alloc_user;
+    h->construction = d.dgf_construction;   // the request in, the construction used out
     bool ok = build_dgf(h->g, h->rlaw, h->tlaw, h->bp, h->gt, scratch, h->st, h->construction, err);
     cudaDeviceSynchronize();
     scratch.release_all();

@@ -61,6 +61,8 @@ void launch_aux_cg(const AuxArgs& a, int nprob, int max_cells, cudaStream_t st);
 
 // Build the table gt[m][t][s] (device, M * nb * nb doubles) for the plane `g`
 // whose boundary points are `bp`.  Scratch comes from a temporary arena.
+// `construction`: in, 0 automatic (Sec. 4.2), 1 auxiliary windows, 2 the
+// extended domain; out, 1 when the extended domain was used, else 0.
 bool build_dgf(const PlaneGeo& g, const Law& rlaw, const Law& tlaw,
                const std::vector<BPoint>& bp, double* gt, Arena& scratch, cudaStream_t st,
                int& construction, std::string& err);

@@ -328,7 +328,10 @@ bool build_dgf(const PlaneGeo& g, const Law& rlaw, const Law& tlaw, const std::v
   const double* cosk = up(A, ck);
   if (!cosk) { err = "out of device memory"; return false; }
   bool ok;
-  if (uses_extended(rlaw, g.r.n)) {
+  // construction on entry: 0 the paper's rule, 1 auxiliary windows, 2 the
+  // extended domain; on return 1 for the extended domain, 0 for windows
+  const bool ext = construction == 2 || (construction == 0 && uses_extended(rlaw, g.r.n));
+  if (ext) {
     construction = 1;
     ok = build_extended(g, rlaw, tlaw, bp, gt, A, cosk, st, err);
   } else {
