@@ -438,27 +438,57 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
     L.gR = GH_ZERO;
     L.gB = p.has_lower() ? GH_ZERO : GH_PARITY;
     L.gT = p.has_upper() ? GH_ZERO : GH_PARITY;
-    // App. A relaxation parameters per line and mode
+    // App. A relaxation parameters per line and mode (the sums of
+    // wkb_omega).  The weights and the off-diagonal sums do not depend on the
+    // mode, and the diagonal is d0 - s_m^2 Q T with d0 its m = 0 value, so
+    // each line's sums over the mode-independent parts are formed once and
+    // every mode then costs O(1) per line.
     L.om_r.assign(size_t(M) * nt, 1.0);
     L.om_t.assign(size_t(M) * nr, 1.0);
-    std::vector<double> a(std::max(nr, nt)), cc(std::max(nr, nt)), b(std::max(nr, nt));
-    for (int k = 0; k < M; ++k) {
-      int m = modes[k];
-      for (int j = 1; j <= nt; ++j) {
-        for (int i = 1; i <= nr; ++i) {
-          a[i - 1] = L.g.aW[i];
-          cc[i - 1] = L.g.aE[i];
-          b[i - 1] = L.g.diag(m, i, j);
+    {
+      auto weights = [](const std::vector<double>& x, int N, std::vector<double>& w,
+                        std::vector<double>& c) {
+        const double len = x[N + 1] - x[0];
+        w.assign(N + 1, 0.0);
+        c.assign(N + 1, 0.0);
+        for (int q = 1; q <= N; ++q) {
+          const double sn = std::sin(kPi * (x[q] - x[0]) / len);
+          w[q] = sn * sn;
+          c[q] = std::cos(kPi * (x[q] - x[q - 1]) / len);
         }
-        L.om_r[size_t(k) * nt + j - 1] = wkb_omega(a.data(), cc.data(), b.data(), p.r.x.data(), nr);
+      };
+      auto omega = [](double num, double den) {
+        const double rho = std::min(std::fabs(num / den), 1.0);
+        return 2.0 / (1.0 + std::sqrt(1.0 - rho * rho));
+      };
+      std::vector<double> wr, cr, wt, ct;
+      weights(p.r.x, nr, wr, cr);
+      weights(p.t.x, nt, wt, ct);
+      // radial line j: num = sum_i (aW + aE) c_i w_i; den = D0r_j - s2 T_j sum_i Q_i w_i
+      double numr = 0.0, qr = 0.0;
+      for (int i = 1; i <= nr; ++i) {
+        numr += (p.aW[i] + p.aE[i]) * cr[i] * wr[i];
+        qr += p.Q[i] * wr[i];
+      }
+      std::vector<double> d0r(nt + 1, 0.0), numt(nr + 1, 0.0), d0t(nr + 1, 0.0);
+      for (int j = 1; j <= nt; ++j)
+        for (int i = 1; i <= nr; ++i) d0r[j] += p.diag(0, i, j) * wr[i];
+      // polar line i: num = P_i sum_j (aS + aN) c_j w_j; den = D0t_i - s2 Q_i sum_j T_j w_j
+      double st = 0.0, qt = 0.0;
+      for (int j = 1; j <= nt; ++j) {
+        st += (p.aS[j] + p.aN[j]) * ct[j] * wt[j];
+        qt += p.T[j] * wt[j];
       }
       for (int i = 1; i <= nr; ++i) {
-        for (int j = 1; j <= nt; ++j) {
-          a[j - 1] = p.P[i] * p.aS[j];
-          cc[j - 1] = p.P[i] * p.aN[j];
-          b[j - 1] = L.g.diag(m, i, j);
-        }
-        L.om_t[size_t(k) * nr + i - 1] = wkb_omega(a.data(), cc.data(), b.data(), p.t.x.data(), nt);
+        numt[i] = p.P[i] * st;
+        for (int j = 1; j <= nt; ++j) d0t[i] += p.diag(0, i, j) * wt[j];
+      }
+      for (int k = 0; k < M; ++k) {
+        const double s2 = p.s2(modes[k]);
+        for (int j = 1; j <= nt; ++j)
+          L.om_r[size_t(k) * nt + j - 1] = omega(numr, d0r[j] - s2 * p.T[j] * qr);
+        for (int i = 1; i <= nr; ++i)
+          L.om_t[size_t(k) * nr + i - 1] = omega(numt[i], d0t[i] - s2 * p.Q[i] * qt);
       }
     }
   }
