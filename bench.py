@@ -255,6 +255,7 @@ def ours(a, ws, rank, local):
     clocks = clk.stop()
     t = allmax(ws, t, dev)
     st = sm.stats()
+    stages = sm.stage_times()               # the last timed solve, from its event nodes
     value = ws * a.steps / t
     # FP64 GPU path on the same input and tolerance
     phi64 = torch.empty_like(rho)
@@ -263,6 +264,7 @@ def ours(a, ws, rank, local):
     k64 = max(2, a.steps // 2)
     t64 = allmax(ws, time_solves(torch, sd, rho, phi64, k64, stream, "bench_fp64"), dev)
     st64 = sd.stats()
+    stages64 = sd.stage_times()
     fp64_value = ws * k64 / t64
     diff = float(torch.linalg.vector_norm(phi - phi64) / torch.linalg.vector_norm(phi64))
     # accuracy of the timed mixed result (tuned schedule, tol 1e-8) against a
@@ -344,7 +346,8 @@ def ours(a, ws, rank, local):
                        parallelism="replicas" if ws > 1 else "single GPU"),
         "cell_updates_per_s": value * cells,
         "fp64_gpu": {"value": fp64_value, "unit": "solves/s", "ms_per_step": 1e3 * t64 / k64,
-                     "speedup_mixed_vs_fp64": value / fp64_value},
+                     "speedup_mixed_vs_fp64": value / fp64_value, "stage_ms": stages64},
+        "stage_ms": stages,
         "mixed_vs_fp64_rel_l2": diff,
         "mixed_vs_fp64_tol1e-11_rel_l2": err_tight,
         "mixed_vs_fp64_tol1e-11_rel_l2_unweighted": err_tight_plain,

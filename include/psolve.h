@@ -206,6 +206,15 @@ void psolve_batch_destroy(psolve_batch_t b);
  * closed forms and window or extended-domain solves).  PSOLVE_ERR_ARG for a
  * null argument. */
 int psolve_get_setup_times(psolve_t h, double* setup_ms, double* dgf_ms);
+/* Device time of the stages of the handle's last completed solve (Sec. 5.1;
+ * the split of the paper's component-wise breakdown), ms: [0] forward
+ * transform (step 2), [1] Psi multigrid (step 3, with the cluster-resident
+ * tail), [2] screening mass, boundary convolution and ghost right-hand side
+ * (steps 4-5), [3] Phi multigrid (step 6), [4] inverse transform (step 7).
+ * Recorded by events on the handle's stream (event nodes in a captured
+ * solve); for psolve_solve_host, its last solve.  Synchronises the stream.
+ * PSOLVE_ERR_ARG for a null argument or before the first solve. */
+int psolve_get_stage_times(psolve_t h, float* ms);
 
 /* Warm start for time stepping (Sec. 5.1 and App. B: in a simulation the
  * previous step's solution is the initial guess, which cuts the V-cycles

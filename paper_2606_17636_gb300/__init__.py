@@ -122,6 +122,7 @@ def lib():
             "psolve_stage_restrict": (I, [P, I, I, P, P, P]),
             "psolve_stage_residual": (I, [P, I, P, P, P]),
             "psolve_get_setup_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+            "psolve_get_stage_times": (I, [P, ctypes.POINTER(ctypes.c_float)]),
             "psolve_solve_host": (I, [P, I, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
             "psolve_stage_prolong": (I, [P, I, I, P, P]),
             "psolve_stage_screening": (I, [P, P, P]),
@@ -407,6 +408,14 @@ class Solver:
         check(lib().psolve_get_setup_times(self.h, ctypes.byref(a), ctypes.byref(b)),
               "psolve_get_setup_times")
         return a.value, b.value
+
+    STAGES = ("fft_forward", "mg_psi", "boundary", "mg_phi", "fft_inverse")
+
+    def stage_times(self):
+        """Device ms per stage of the last solve (psolve_get_stage_times)."""
+        ms = (ctypes.c_float * 5)()
+        check(lib().psolve_get_stage_times(self.h, ms), "psolve_get_stage_times")
+        return dict(zip(self.STAGES, list(ms)))
 
     def solve_host(self, rhos, phis=None, tol=1e-8, raise_on_error=True):
         """Solves from host memory with copies overlapped (psolve_solve_host).

@@ -68,6 +68,9 @@ struct psolve_ctx {
     int cap = 0;
   };
   Pipe* pipe = nullptr;
+  // stage marks of the last solve: start, after the forward transform, after
+  // the Psi multigrid, after the boundary steps, after the Phi multigrid, end
+  cudaEvent_t mark[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 static size_t plane_bytes(psolve_t h) { return sizeof(double2) * size_t(h->P) * h->d.n_r * h->d.n_tz; }
@@ -268,6 +271,8 @@ static int create_impl(psolve_t* out, const psolve_desc* din, int nd) {
   }
   cudaMemcpy(h->tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice);
   cudaMallocHost(&h->h_worst, sizeof(int));
+  for (cudaEvent_t& e : h->mark)
+    if (cudaEventCreate(&e) != cudaSuccess) e = nullptr;
   // discrete Green's function tables (Sec. 5.1 step 1), scratch released after
   {
     const auto td = std::chrono::steady_clock::now();
@@ -388,11 +393,26 @@ extern "C" void psolve_destroy(psolve_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
   pipe_release(h);
+  for (cudaEvent_t e : h->mark)
+    if (e) cudaEventDestroy(e);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->mg.h_cont) cudaFreeHost(h->mg.h_cont);
   if (h->h_worst) cudaFreeHost(h->h_worst);
   h->A.release_all();
   delete h;
+}
+
+extern "C" int psolve_get_stage_times(psolve_t h, float* ms) {
+  if (!h || !ms) return fail(PSOLVE_ERR_ARG, "null argument");
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(PSOLVE_ERR_CUDA, "stage times");
+  for (int k = 0; k < 5; ++k) {
+    ms[k] = 0.f;
+    if (!h->mark[k] || !h->mark[k + 1] || cudaEventElapsedTime(&ms[k], h->mark[k], h->mark[k + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PSOLVE_ERR_ARG, "no completed solve to report");
+    }
+  }
+  return PSOLVE_OK;
 }
 
 extern "C" int psolve_get_setup_times(psolve_t h, double* setup_ms, double* dgf_ms) {
@@ -456,10 +476,24 @@ extern "C" int psolve_get_sizes(psolve_t h, int* n_modes, int* n_boundary, int* 
 static size_t cells(psolve_t h) { return size_t(h->d.n_r) * h->d.n_tz * h->d.n_phi; }
 static size_t mode_plane(psolve_t h) { return size_t(h->d.n_r) * h->d.n_tz; }
 
+// Records stage mark k on the handle's stream (an event node when the stream
+// is being captured, so that every replay records it).
+static void mark(psolve_t h, int k) {
+  if (!h->mark[k]) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(h->st, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(h->mark[k], h->st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(h->mark[k], h->st);
+}
+
 static void enqueue_front(psolve_t h, const double* rho) {
+  mark(h, 0);
   for (int b = 0; b < h->nd; ++b)
     launch_fft_forward(rho + b * cells(h), h->f + size_t(b) * h->M * mode_plane(h), h->d.n_r, h->d.n_tz,
                        h->d.n_phi, 4.0 * kPi * h->d.G / h->d.n_phi, h->tw, h->st);
+  mark(h, 1);
   if (warm_state(h) == 2)
     cudaMemcpyAsync(h->u, h->psi_prev, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
   else
@@ -469,6 +503,7 @@ static void enqueue_front(psolve_t h, const double* rho) {
 }
 
 static void enqueue_middle(psolve_t h) {
+  mark(h, 2);
   snapshot(h, h->sp);
   if (h->warm) cudaMemcpyAsync(h->psi_prev, h->u, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
   launch_screening(h->bdev, h->u, h->sigma, h->P, h->st);
@@ -480,9 +515,11 @@ static void enqueue_middle(psolve_t h) {
     cudaMemcpyAsync(h->u, h->phi_prev, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
   h->mg.zero_guess = 0;   // the Phi loop starts from Psi or the previous Phi
   h->mg.init_loop(h->st);
+  mark(h, 3);
 }
 
 static void enqueue_back(psolve_t h, double* phi) {
+  mark(h, 4);
   snapshot(h, h->sf);
   if (h->warm) cudaMemcpyAsync(h->phi_prev, h->u, plane_bytes(h), cudaMemcpyDeviceToDevice, h->st);
   for (int b = 0; b < h->nd; ++b)
@@ -490,6 +527,7 @@ static void enqueue_back(psolve_t h, double* phi) {
                        h->d.n_phi, h->tw, h->st);
   k_worst<<<1, 256, 0, h->st>>>(h->sp.status, h->sf.status, h->P, h->d_worst);
   cudaMemcpyAsync(h->h_worst, h->d_worst, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+  mark(h, 5);
 }
 
 static int add_while(psolve_t h, cudaGraph_t graph, double tol, cudaStream_t body_st) {

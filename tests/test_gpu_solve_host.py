@@ -125,3 +125,32 @@ def test_host_solve_arguments_and_setup_times(ps):
     assert 0.0 < dgf_ms <= setup_ms
     assert setup_ms == pytest.approx(s.stats()["setup_ms"])
     s.close()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_stage_times_split_the_solve(ps, use_graph):
+    """psolve_get_stage_times: the five stages of the last solve (event marks
+    on the handle's stream, event nodes in the captured graph) add up to the
+    solve's own device time."""
+    sp = SMALL["sph_log"]
+    s = ps.Solver.from_spec(sp, precision=ps.MIXED, use_graph=use_graph)
+    with pytest.raises(ps.PSolveError):
+        s.stage_times()
+    rho = torch.from_numpy(clumps(sp, 95)).cuda()
+    phi = torch.empty_like(rho)
+    s.solve(rho, phi, tol=1e-9)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.solve(rho, phi, tol=1e-9)
+    e1.record()
+    torch.cuda.synchronize()
+    st = s.stage_times()
+    assert set(st) == set(ps.Solver.STAGES)
+    assert all(v > 0.0 for v in st.values()), st
+    total = e0.elapsed_time(e1)
+    assert sum(st.values()) <= total * 1.01 + 0.05, (st, total)
+    if use_graph:   # host gaps of the eager loop are not in the marks' spans alone
+        assert sum(st.values()) >= 0.8 * total, (st, total)
+    assert st["mg_psi"] > st["fft_forward"] and st["mg_phi"] > st["fft_inverse"]
+    s.close()
