@@ -57,8 +57,9 @@ typedef void (*psolve_free_fn)(void* ptr, void* user);
 
 typedef struct {
   int geometry;        /* PSOLVE_SPHERICAL or PSOLVE_CYLINDRICAL                  */
-  int n_r;             /* radial cells, power of two >= 8                         */
-  int n_tz;            /* theta (spherical) or z (cylindrical) cells, power of 2 >= 8 */
+  int n_r;             /* radial cells, power of two in [8, 1024] (FP64: <= 512)  */
+  int n_tz;            /* theta (spherical) or z (cylindrical) cells, power of 2
+                          in [8, 1024] (FP64: <= 512); n_r / n_tz in [1/16, 16]  */
   int n_phi;           /* azimuthal cells, power of two, 4 <= n_phi <= 1024       */
   int spacing;         /* radial spacing PSOLVE_UNIFORM or PSOLVE_LOG             */
   double r_in, r_out;  /* radial extent, 0 <= r_in < r_out (log: r_in > 0)        */
@@ -78,7 +79,10 @@ typedef struct {
                           logarithmic radial grids with r_out / r_in >= 100 and
                           n_r >= 32, auxiliary windows otherwise),
                           PSOLVE_DGF_AUX (1) or PSOLVE_DGF_EXTENDED (2, needs
-                          logarithmic spacing and n_r >= 32)                     */
+                          logarithmic spacing and n_r >= 32).  The extended
+                          domain doubles n_r (and a bounded theta or z range),
+                          so it needs n_r <= 512 (and n_tz <= 512 when bounded):
+                          PSOLVE_ERR_ARG otherwise                               */
 } psolve_desc;
 
 enum { PSOLVE_DGF_AUTO = 0, PSOLVE_DGF_AUX = 1, PSOLVE_DGF_EXTENDED = 2 };

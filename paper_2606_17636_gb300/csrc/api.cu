@@ -153,6 +153,21 @@ static int prepare_desc(const psolve_desc& din, psolve_desc& d) {
     return fail(PSOLVE_ERR_ARG, "dgf_construction must be PSOLVE_DGF_AUTO, _AUX or _EXTENDED");
   if (d.dgf_construction == PSOLVE_DGF_EXTENDED && (d.spacing != PSOLVE_LOG || d.n_r < 32))
     return fail(PSOLVE_ERR_ARG, "the extended-domain DGF needs logarithmic radial spacing and n_r >= 32");
+  if (d.precision == PSOLVE_FP64 && (d.n_r > 512 || d.n_tz > 512))
+    return fail(PSOLVE_ERR_ARG, "the FP64 path holds lines of at most 512 cells (n_r, n_tz <= 512); "
+                                "use PSOLVE_MIXED for longer lines");
+  {
+    // the extended domain doubles n_r (and a bounded theta or z direction):
+    // its multigrid lines must stay within 1024 cells
+    const bool ext = d.dgf_construction == PSOLVE_DGF_EXTENDED ||
+                     (d.dgf_construction == PSOLVE_DGF_AUTO && d.spacing == PSOLVE_LOG &&
+                      d.r_out / d.r_in >= 100.0 && d.n_r >= 32);
+    const bool bounded_t = d.geometry == PSOLVE_CYLINDRICAL || d.t_min > 1e-12 || d.t_max < kPi - 1e-12;
+    if (ext && (d.n_r > 512 || (bounded_t && d.n_tz > 512)))
+      return fail(PSOLVE_ERR_ARG, "the extended-domain DGF (logarithmic grids with r_out / r_in >= 100) "
+                                  "needs n_r <= 512 (and n_tz <= 512 for a bounded theta or z range); "
+                                  "dgf_construction = PSOLVE_DGF_AUX uses auxiliary windows instead");
+  }
   return PSOLVE_OK;
 }
 

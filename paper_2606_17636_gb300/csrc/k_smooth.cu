@@ -211,12 +211,28 @@ static int tile_w(int nr, int nt, size_t vb, int want) {
 
 int smooth_tile_cols(int nr, int nt, size_t vb, int want) { return tile_w(nr, nt, vb, want); }
 
+// Shared memory of a radial block of Wmax lines: e lines (W + 3), f lines
+// (W + 1) and the relaxed colour-0 lines (W / 2 + 1).
+static size_t rpass_smem(int nr, int Wmax, size_t vb) {
+  return size_t(Wmax + 3 + Wmax + 1 + Wmax / 2 + 1) * nr * vb;
+}
+// The widest radial block (8, 4 or 2 lines, at most `want`) within 200 KB.
+static int rpass_lines(int nr, size_t vb, int want) {
+  int w = want >= 8 ? 8 : (want >= 4 ? 4 : 2);
+  while (w > 2 && rpass_smem(nr, w, vb) > 200 * 1024) w /= 2;
+  return w;
+}
+
+bool smooth_fits(int nr, int nt, size_t vb) {
+  const int tw = tile_w(nr, nt, vb, 2);
+  return rpass_smem(nr, 2, vb) <= 200 * 1024 && size_t(nt) * 2 * (tw + 5) * vb <= 200 * 1024;
+}
+
 template <typename T, int CPL>
 static void rpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
                    const vec2_t<T>* f, bool zi, int n_sor, int Wmax,
                    cudaStream_t st) {
-  // e lines (W + 3), f lines (W + 1) and relaxed colour-0 lines (W / 2 + 1)
-  const size_t sm = size_t(Wmax + 3 + Wmax + 1 + Wmax / 2 + 1) * L.nr * sizeof(vec2_t<T>);
+  const size_t sm = rpass_smem(L.nr, Wmax, sizeof(vec2_t<T>));
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_rpass2<T, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -273,7 +289,7 @@ template <typename T>
 void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
                    vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, Tiles tiles,
                    cudaStream_t st) {
-  const int Wmax = tiles.lines_r == 4 ? 4 : 8;
+  const int Wmax = rpass_lines(L.nr, sizeof(vec2_t<T>), tiles.lines_r == 4 ? 4 : 8);
   for (int c = 0; c < cycles; ++c) {
     rpass2_any<T>(L, B, e, tmp, f, zero_init && c == 0, n_sor, Wmax, st);
     tpass2_any<T>(L, B, tmp, e, f, n_sor, tiles.cols_t, st);

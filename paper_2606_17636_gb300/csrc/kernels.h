@@ -67,6 +67,9 @@ struct Tiles {
 // Polar columns per block that the polar pass uses for a level of nr x nt
 // cells of vb bytes each when `want` are requested (0: the widest).
 int smooth_tile_cols(int nr, int nt, size_t vb, int want);
+// Whether lines of nr (radial) and nt (polar) cells of vb-byte values fit the
+// level-wide passes' shared-memory staging.
+bool smooth_fits(int nr, int nt, size_t vb);
 // `cycles` alternating-line smoothing cycles (k_smooth.cu); tmp is a
 // scratch buffer of the level's size (ping-pong between the two passes).
 template <typename T>

@@ -69,6 +69,18 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   max_planes = mp;
   if (!build_hierarchy(fine, neumann, modes, H, err)) return false;
   const int nl = int(H.lv.size());
+  // line lengths the level-wide passes hold in registers and shared memory:
+  // at most 1024 cells (FP32) or 512 (FP64), and a staged polar tile that
+  // fits (smooth_fits)
+  {
+    const int lim = opt.precision ? 1024 : 512;
+    const int nr0 = H.lv[0].g.r.n, nt0 = H.lv[0].g.t.n;
+    if (nr0 > lim || nt0 > lim || !smooth_fits(nr0, nt0, opt.precision ? sizeof(float2) : sizeof(double2))) {
+      err = "lines of " + std::to_string(nr0 > nt0 ? nr0 : nt0) + " cells exceed the " +
+            (opt.precision ? "FP32" : "FP64") + " smoothing kernels (at most " + std::to_string(lim) + ")";
+      return false;
+    }
+  }
   lv.resize(nl);
   for (int l = 0; l < nl; ++l) {
     const LevelHost& h = H.lv[l];

@@ -116,3 +116,46 @@ def test_elongated_grids(ps, geometry):
     s.close()
     p, ref = _oracle(sp, rho)
     assert rel_l2(p, phi.cpu().numpy(), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("geometry", ["cyl_radial", "sph_polar"])
+def test_largest_radial_and_polar_sizes(ps, geometry):
+    """The largest accepted line lengths at the largest accepted aspect
+    ratio: 1024 radial cells (a cylindrical shell whose cells are square in
+    (R, z)) and 1024 polar cells (uniform spherical shell), on the mixed
+    path against the oracle.  The FP64 path holds lines of at most 512
+    cells and refuses these grids at create.  (Cells far from square along
+    1024-cell lines, e.g. a logarithmic sphere with 1024 radial and 64 polar
+    cells, defeat the single-sweep SOR line relaxation: the low modes then
+    stop at the cycle cap and report it.)"""
+    from paper_2606_17636_gb300 import workloads as wl
+    if geometry == "cyl_radial":
+        sp = _spec(wl.CYLINDRICAL, 1024, 64, 4, wl.UNIFORM, 0.5, 1.5, -1.0 / 32, 1.0 / 32)
+    else:
+        sp = _spec(wl.SPHERICAL, 64, 1024, 4, wl.UNIFORM, 1.0, 2.0)
+    with pytest.raises(ps.PSolveError) as ei:
+        ps.Solver.from_spec(sp, precision=ps.FP64)
+    assert ei.value.code == ps.ERR_ARG and "512" in str(ei.value)
+    rho = clumps(sp, 24)
+    p, ref = _oracle(sp, rho)
+    s = ps.Solver.from_spec(sp, precision=ps.MIXED)
+    phi, rc = s.solve(torch.from_numpy(rho).cuda(), tol=1e-10)
+    assert rc == ps.OK
+    s.close()
+    err = rel_l2(p, phi.cpu().numpy(), ref)
+    assert err <= 1e-7, err
+
+
+def test_extended_domain_size_limit(ps):
+    """The extended-domain DGF doubles n_r, so a logarithmic grid with
+    r_out / r_in >= 100 and 1024 radial cells is refused with a message
+    that names the auxiliary-window alternative, which it accepts."""
+    from paper_2606_17636_gb300 import workloads as wl
+    sp = _spec(wl.SPHERICAL, 1024, 64, 4, wl.LOG, 0.1, 10.0)
+    with pytest.raises(ps.PSolveError) as ei:
+        ps.Solver.from_spec(sp, precision=ps.MIXED)
+    assert ei.value.code == ps.ERR_ARG and "PSOLVE_DGF_AUX" in str(ei.value)
+    s = ps.Solver.from_spec(sp, precision=ps.MIXED, dgf_construction=ps.DGF_AUX)
+    phi, rc = s.solve(torch.from_numpy(clumps(sp, 25)).cuda(), tol=1e-9)
+    assert rc == ps.OK and torch.isfinite(phi).all()
+    s.close()
