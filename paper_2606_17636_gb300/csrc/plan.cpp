@@ -118,20 +118,6 @@ void PlaneGeo::build() {
   }
 }
 
-// App. A: mu_1 = sum (a_j + c_j) cos(pi delta_j / L) w_j / sum b_j w_j,
-// omega = 2 / (1 + sqrt(1 - mu_1^2)), x_0 and x_{N+1} the boundary points.
-double wkb_omega(const double* a, const double* c, const double* b, const double* x, int N) {
-  double L = x[N + 1] - x[0], num = 0.0, den = 0.0;
-  for (int j = 1; j <= N; ++j) {
-    double s = std::sin(kPi * (x[j] - x[0]) / L);
-    double w = s * s;
-    num += (a[j - 1] + c[j - 1]) * std::cos(kPi * (x[j] - x[j - 1]) / L) * w;
-    den += b[j - 1] * w;
-  }
-  double rho = std::min(std::fabs(num / den), 1.0);
-  return 2.0 / (1.0 + std::sqrt(1.0 - rho * rho));
-}
-
 static bool invert(std::vector<double>& A, int n) {  // Gauss-Jordan, partial pivoting
   std::vector<double> I(size_t(n) * n, 0.0);
   for (int i = 0; i < n; ++i) I[size_t(i) * n + i] = 1.0;
@@ -438,11 +424,15 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
     L.gR = GH_ZERO;
     L.gB = p.has_lower() ? GH_ZERO : GH_PARITY;
     L.gT = p.has_upper() ? GH_ZERO : GH_PARITY;
-    // App. A relaxation parameters per line and mode (the sums of
-    // wkb_omega).  The weights and the off-diagonal sums do not depend on the
-    // mode, and the diagonal is d0 - s_m^2 Q T with d0 its m = 0 value, so
-    // each line's sums over the mode-independent parts are formed once and
-    // every mode then costs O(1) per line.
+    // App. A relaxation parameters per line and mode: for a line of N cells
+    // with neighbour couplings a_q, c_q and diagonal b_q,
+    //   mu_1 = sum_q (a_q + c_q) cos(pi (x_q - x_{q-1}) / L) w_q / sum_q b_q w_q,
+    //   w_q = sin^2(pi (x_q - x_0) / L), L = x_{N+1} - x_0,
+    //   omega = 2 / (1 + sqrt(1 - mu_1^2)).
+    // The weights and the off-diagonal sums do not depend on the mode, and
+    // the diagonal is d0 - s_m^2 Q T with d0 its m = 0 value, so each line's
+    // sums over the mode-independent parts are formed once and every mode
+    // then costs O(1) per line.
     L.om_r.assign(size_t(M) * nt, 1.0);
     L.om_t.assign(size_t(M) * nr, 1.0);
     {

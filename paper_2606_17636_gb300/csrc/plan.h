@@ -100,7 +100,6 @@ struct Hierarchy {
 bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,
                      Hierarchy& H, std::string& err);
 
-double wkb_omega(const double* a, const double* c, const double* b, const double* x, int N);
 
 struct BPoint {
   char side;       // 'L','R','B','T'

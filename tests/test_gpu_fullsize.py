@@ -69,8 +69,9 @@ def test_fp64_full_size_matches_oracle_whole_field(ps, full):
 
 
 def test_mixed_full_size_matches_oracle_whole_field(ps, full):
-    """The benchmark spec's contract at the metric's tolerance, on the whole
-    field; the unweighted figure is reported in the failure message."""
+    """The mixed path at tol 1e-8 within 1e-7 (relative L2) of the FP64
+    oracle on the whole field; the unweighted figure is reported in the
+    failure message."""
     w, p, ref = full
     phi, st = _solve(ps, w, ps.MIXED, 1e-8)
     assert st["rel_residual_psi"] <= 1e-8 and st["rel_residual_phi"] <= 1e-8
