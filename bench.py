@@ -45,8 +45,8 @@ def args_():
     a.add_argument("--no-setup4", action="store_true",
                    help="skip timing psolve_create for the 512 x 256 x 512 cylindrical workload")
     a.add_argument("--replicas", action="store_true",
-                   help="with N > 1 GPUs: an independent copy of the problem per GPU (weak scaling) "
-                        "instead of one problem sharded by mode over all GPUs (strong scaling)")
+                   help="with N > 1 GPUs: only the independent copies of the problem per GPU (weak "
+                        "scaling, the headline value), without the one-problem mode-sharded measurement")
     a.add_argument("--eager", action="store_true",
                    help="host-driven loop instead of the captured graph (for per-kernel profiling)")
     return a.parse_args()
@@ -335,6 +335,8 @@ def ours(a, ws, rank, local):
     serve = serving(torch, ps, workloads) if (rank == 0 and not a.no_serving) else None
     multi = multi_density(torch, ps, workloads, w) if (rank == 0 and not a.no_serving) else None
     setup4 = setup_large(torch, ps, workloads) if (rank == 0 and not a.no_setup4) else None
+    # N > 1: one problem sharded by mode over all GPUs, beside the replicas
+    shard_one = sharded_measure(a, ws, rank, local, min(a.steps, 10)) if (ws > 1 and not a.replicas) else None
     if rank != 0:
         return
     cells = spec["n_r"] * spec["n_tz"] * spec["n_phi"]
@@ -343,7 +345,7 @@ def ours(a, ws, rank, local):
         "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": dict(CONFIG, l2="working set ~0.45 GB per solve > 129 MB L2; no flush needed",
-                       parallelism="replicas" if ws > 1 else "single GPU"),
+                       parallelism=("replicas: an independent problem per GPU" if ws > 1 else "single GPU")),
         "cell_updates_per_s": value * cells,
         "fp64_gpu": {"value": fp64_value, "unit": "solves/s", "ms_per_step": 1e3 * t64 / k64,
                      "speedup_mixed_vs_fp64": value / fp64_value, "stage_ms": stages64},
@@ -373,6 +375,7 @@ def ours(a, ws, rank, local):
         "serving": serve,
         "multi_density": multi,
         "setup_workload4": setup4,
+        "sharded_one_problem": shard_one,
         "clocks": clocks,
     }
     if not a.no_baseline:
@@ -389,20 +392,19 @@ def ours(a, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def sharded(a, ws, rank, local):
+def sharded_measure(a, ws, rank, local, steps):
     """N > 1 GPUs: one problem of the workload solved by all ranks together,
     its azimuthal modes sharded over the GPUs (paper_2606_17636_gb300/shard.py:
     slab transforms, an all-to-all to the modes' owners, mode-subset solves,
     the reverse all-to-all; modes assigned by LPT over the previous solve's
-    V-cycles).  value = solves of the one problem per second of the whole
-    job (strong scaling)."""
+    V-cycles).  Returns (on every rank) solves of the one problem per second
+    of the whole job (strong scaling) and its end-to-end figure."""
     import numpy as np
     import torch
 
     import paper_2606_17636_gb300 as ps
     from paper_2606_17636_gb300 import shard, workloads
     dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     w = workloads.workload(WORKLOAD)
     spec = w["spec"]
     stream = torch.cuda.current_stream()
@@ -420,51 +422,37 @@ def sharded(a, ws, rank, local):
     torch.cuda.synchronize()
     barrier(ws)
     torch.cuda.synchronize()
-    clk = Clocks(local)
-    time.sleep(0.5)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(a.steps):
+    for _ in range(steps):
         phi_rows = ms.solve(rho_rows, TOL)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
     torch.cuda.synchronize()
-    clocks = clk.stop()
     t = allmax(ws, ev0.elapsed_time(ev1) / 1e3, dev)
-    value = a.steps / t
     # end to end: the slab of the density from pinned host memory and the
     # slab of the potential back, inside the timed region
     phi_host = torch.empty((i1 - i0, spec["n_tz"], spec["n_phi"]), dtype=torch.float64).pin_memory()
     barrier(ws)
     ev0.record(stream)
-    for _ in range(a.steps):
+    for _ in range(steps):
         rho_rows.copy_(rho_host, non_blocking=True)
         phi_rows = ms.solve(rho_rows, TOL)
         phi_host.copy_(phi_rows, non_blocking=True)
     ev1.record(stream)
     torch.cuda.synchronize()
     te2e = allmax(ws, ev0.elapsed_time(ev1) / 1e3, dev)
-    st = s.stats()
-    launches = launches_per_solve(s, st)
-    if rank != 0:
-        return
-    line = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
-        "scaling": "strong", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": dict(CONFIG, l2="working set ~0.45 GB per solve > 129 MB L2; no flush needed",
-                       parallelism="one problem, modes sharded over %d GPUs (LPT over V-cycles, "
-                                   "all-to-all exchanges)" % ws),
-        "cell_updates_per_s": value * spec["n_r"] * spec["n_tz"] * spec["n_phi"],
-        "owners_last": [len(o) for o in ms.owners],
-        "e2e": {"value": a.steps / te2e, "unit": "solves/s",
-                "h2d_bytes_per_step": rho_rows.numel() * 8 * ws, "d2h_bytes_per_step": phi_rows.numel() * 8 * ws},
-        "gpu_launches": launches * a.steps,
-        "clocks": clocks,
-    }
-    print(json.dumps(line), flush=True)
+    out = {"workload": "one workload-3 problem, modes sharded over %d GPUs (LPT over V-cycles, "
+                       "all-to-all exchanges, host-driven mode-subset solves)" % ws,
+           "scaling": "strong", "steps": steps, "value": steps / t, "unit": "solves/s",
+           "ms_per_step": 1e3 * t / steps, "owners_last": [len(o) for o in ms.owners],
+           "e2e": {"value": steps / te2e, "unit": "solves/s",
+                   "h2d_bytes_per_step": rho_rows.numel() * 8 * ws,
+                   "d2h_bytes_per_step": phi_rows.numel() * 8 * ws}}
+    s.close()
+    return out
 
 
 def multi_density(torch, ps, workloads, w, nd=8, warm=2, runs=5):
@@ -802,8 +790,6 @@ def main():
     ws, rank, local = dist()
     if a.impl == "reference":
         reference_arm(a, ws, rank)
-    elif ws > 1 and not a.replicas:
-        sharded(a, ws, rank, local)
     else:
         ours(a, ws, rank, local)
     if ws > 1:
