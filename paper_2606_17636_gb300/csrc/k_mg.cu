@@ -197,8 +197,8 @@ __global__ void k_update(int n, Batch B, double2* __restrict__ u, const vec2_t<T
     const size_t o = size_t(B.act[k]) * n + idx;
     const vec2_t<T> v = e[o];
     double2 x = u[o];
-    x.x += double(v.x);
-    x.y += double(v.y);
+    x.x += from_buf<T>(v.x);
+    x.y += from_buf<T>(v.y);
     u[o] = x;
   }
 }
@@ -241,7 +241,8 @@ __device__ void retire_block(int* act, int* nact, const Sum4* __restrict__ psum,
                              unsigned long long handle, int* scan, int tail_planes);
 
 // FP64 defect at (i, j) from the per-cell products (one FP64 operation for
-// the mode's diagonal, five per component for the stencil).
+// the mode's diagonal, five fused multiply-adds per component starting from
+// the right-hand side).
 __device__ __forceinline__ double2 defect_tab(const LevelDev& L, const double* __restrict__ ct,
                                               int n, double s2, const double2* __restrict__ e,
                                               const double2* __restrict__ f, int i, int j) {
@@ -255,9 +256,16 @@ __device__ __forceinline__ double2 defect_tab(const LevelDev& L, const double* _
   const double aN = ct[idx], aS = ct[n + idx];
   const double d = fma(-s2, ct[3 * n + idx], ct[2 * n + idx]);
   const double2 fv = f[idx];
-  return make_double2(fv.x - (aE * E.x + aW * W.x + aN * N.x + aS * S.x + d * c.x),
-                      fv.y - (aE * E.y + aW * W.y + aN * N.y + aS * S.y + d * c.y));
+  double rx = fma(-aE, E.x, fv.x), ry = fma(-aE, E.y, fv.y);
+  rx = fma(-aW, W.x, rx);
+  ry = fma(-aW, W.y, ry);
+  rx = fma(-aN, N.x, rx);
+  ry = fma(-aN, N.y, ry);
+  rx = fma(-aS, S.x, rx);
+  ry = fma(-aS, S.y, ry);
+  return make_double2(fma(-d, c.x, rx), fma(-d, c.y, ry));
 }
+
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const double2* __restrict__ f,
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
         const size_t base = size_t(p) * n;
         const double s2 = B.s2d[slot];
         const double2 rv = r_is_f ? f[base + idx] : defect_tab(L, ctab, n, s2, u + base, f + base, i, j);
-        const vec2_t<T> ro = vmk<vec2_t<T>, T>(T(rv.x), T(rv.y));
+        const vec2_t<T> ro = vmk<vec2_t<T>, T>(to_buf<T>(rv.x), to_buf<T>(rv.y));
         r[base + idx] = ro;
         const float dv = L.rf[RT_V * (nr + 2) + i + 1] * L.tf[TT_V * (nt + 2) + j + 1];
         const float rx = float(ro.x), ry = float(ro.y);
@@ -306,7 +314,7 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
         accf.y += dv * ry * ry;
         if (want_f) {
           const double2 fv = f[base + idx];
-          const float fx = float(fv.x), fy = float(fv.y);
+          const float fx = f64_to_f32(fv.x), fy = f64_to_f32(fv.y);
           accf.z += dv * fx * fx;
           accf.w += dv * fy * fy;
         }

@@ -667,9 +667,16 @@ __global__ void __launch_bounds__(kTailThreads, 1)
         const double aN = a.ctab[cq], aS = a.ctab[n0 + cq];
         const double d = fma(-s2d, a.ctab[3 * size_t(n0) + cq], a.ctab[2 * size_t(n0) + cq]);
         const double2 fv = fg[base + cq];
-        const double rx = fv.x - (aE * E.x + aW * W.x + aN * N.x + aS * Sv.x + d * c.x);
-        const double ry = fv.y - (aE * E.y + aW * W.y + aN * N.y + aS * Sv.y + d * c.y);
-        const V ro = make_float2(float(rx), float(ry));
+        double rx = fma(-aE, E.x, fv.x), ry = fma(-aE, E.y, fv.y);
+        rx = fma(-aW, W.x, rx);
+        ry = fma(-aW, W.y, ry);
+        rx = fma(-aN, N.x, rx);
+        ry = fma(-aN, N.y, ry);
+        rx = fma(-aS, Sv.x, rx);
+        ry = fma(-aS, Sv.y, ry);
+        rx = fma(-d, c.x, rx);
+        ry = fma(-d, c.y, ry);
+        const V ro = make_float2(f64_to_f32(rx), f64_to_f32(ry));
         rowp(sm, t0.fo, nr0, h, r)[i ^ tsw(nr0, j)] = ro;
         const float dv = L0.rf[RT_V * NR0 + i + 1] * L0.tf[TT_V * NT0 + j + 1];
         ax += dv * ro.x * ro.x;
@@ -757,8 +764,8 @@ __global__ void __launch_bounds__(kTailThreads, 1)
       const V v = erow(sm, t0, h, bl[0], r)[i ^ tsw(nr0, j)];
       double2* x = r < 0 ? Uh + i : (r >= s0 ? Uh + nr0 + i : Uo + r * nr0 + i);
       double2 y = *x;
-      y.x += double(v.x);
-      y.y += double(v.y);
+      y.x += f32_to_f64(v.x);
+      y.y += f32_to_f64(v.y);
       *x = y;
     }
     __syncthreads();

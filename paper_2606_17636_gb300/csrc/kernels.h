@@ -17,6 +17,52 @@ template <typename T> using vec2_t = typename Vec2<T>::type;
 struct __align__(16) Sum4 {
   double x, y, z, w;
 };
+#ifdef __CUDACC__
+// IEEE 754 conversions between binary64 and binary32 on the integer pipes:
+// GB300 runs FP64 arithmetic at about 1/64 of its FP32 rate, and the FP64
+// kernels of the refinement loop are bound by that pipe.  Only results in
+// the normal range are formed here; zeros, subnormals, overflow, infinities
+// and NaN take the hardware conversion.
+// binary64 -> binary32, round to nearest, ties to even: the sign, the
+// rebiased exponent, the top 23 fraction bits, and one unit added when the
+// 29 dropped bits exceed half a unit or equal it with an odd kept part (a
+// carry into the exponent is the correct rounding, up to infinity).
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
+  const int e = int((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e <= 0 || e >= 255) return __double2float_rn(x);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu, half = 0x10000000u;
+  unsigned f = (hi & 0x80000000u) | (unsigned(e) << 23) | m;
+  f += (rest > half || (rest == half && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float(f);
+}
+// binary32 -> binary64, exact: the exponent rebiased by 1023 - 127 and the
+// 23 fraction bits moved to the top of the 52.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return double(x);
+  const unsigned long long d = (static_cast<unsigned long long>(b & 0x80000000u) << 32) |
+                               (static_cast<unsigned long long>(e + 896u) << 52) |
+                               (static_cast<unsigned long long>(b & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(d));
+}
+
+// An FP64 value in the buffer precision T, and back.
+template <typename T>
+__device__ __forceinline__ T to_buf(double x) {
+  if constexpr (sizeof(T) == sizeof(float)) return f64_to_f32(x);
+  else return x;
+}
+template <typename T>
+__device__ __forceinline__ double from_buf(T x) {
+  if constexpr (sizeof(T) == sizeof(float)) return f32_to_f64(x);
+  else return x;
+}
+#endif
+
 __host__ __device__ __forceinline__ Sum4 sum4(double x, double y, double z, double w) {
   return Sum4{x, y, z, w};
 }

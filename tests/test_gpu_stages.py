@@ -126,6 +126,52 @@ def test_fp64_residual_stage(ps, key, precision):
     s.close()
 
 
+def _crafted_doubles(n, seed):
+    """FP64 values whose FP32 rounding exercises every branch: normal values
+    over the whole FP32 range, exact ties (the 29 dropped fraction bits equal
+    to half a unit) with even and odd kept parts, one bit either side of a
+    tie, values that round up to the largest FP32 number or overflow to
+    infinity, results in the FP32 subnormal range, FP64 subnormals, zeros,
+    infinities and NaN."""
+    rng = np.random.default_rng(seed)
+    out = [rng.standard_normal(n // 2) * 10.0 ** rng.uniform(-37, 38, n // 2)]
+    bits = []
+    for _ in range(64):
+        e = int(rng.integers(1023 - 126, 1023 + 127))
+        kept = int(rng.integers(0, 1 << 23))
+        for rest in (1 << 28, (1 << 28) - 1, (1 << 28) + 1, 0, (1 << 29) - 1):
+            for sign in (0, 1):
+                bits.append((sign << 63) | (e << 52) | (kept << 29) | rest)
+    out.append(np.array(bits, dtype=np.uint64).view(np.float64))
+    fmax = float(np.finfo(np.float32).max)
+    out.append(np.array([fmax, np.nextafter(fmax, np.inf), fmax * (1 + 2.0 ** -25), fmax * (1 + 2.0 ** -24),
+                         -fmax * (1 + 2.0 ** -24), 1e39, 1e-39, 1e-45, 7e-46, 1e-310, -1e-310,
+                         1.1754943508222875e-38, 1.1754942e-38, 0.0, -0.0, np.inf, -np.inf, np.nan]))
+    v = np.concatenate(out)
+    return np.resize(v, n)
+
+
+def test_residual_rounds_to_fp32_as_ieee(ps):
+    """The mixed path stores the FP64 defect in FP32 with its own
+    integer-pipe conversion: with u = 0 the defect is f itself, so every
+    stored value must be f rounded to nearest even, as numpy's binary64 to
+    binary32 conversion gives it (zeros compared by value)."""
+    sp = SMALL["sph_log"]
+    s = _solver(ps, "sph_log", ps.MIXED)
+    M, nt, nr = s.n_modes, sp["n_tz"], sp["n_r"]
+    n = M * nt * nr
+    f = (_crafted_doubles(n, 60) + 1j * _crafted_doubles(n, 61)[::-1]).reshape(M, nt, nr)
+    r = s.stage_residual(torch.from_numpy(f).cuda(), torch.zeros((M, nt, nr), dtype=torch.complex128,
+                                                                 device="cuda"))
+    got = torch.view_as_real(r).cpu().numpy().reshape(-1)
+    want = np.stack([f.real, f.imag], axis=-1).reshape(-1).astype(np.float32)
+    nan = np.isnan(want)
+    assert np.array_equal(np.isnan(got), nan)
+    same = got[~nan].view(np.uint32) == want[~nan].view(np.uint32)
+    assert np.all(same | (got[~nan] == want[~nan])), got[~nan][~same][:8]
+    s.close()
+
+
 @pytest.mark.parametrize("key", list(SMALL))
 def test_mg_solve_reaches_direct_solution_and_counts_cycles(ps, key):
     import scipy.sparse.linalg as spla
