@@ -669,10 +669,10 @@ def residual_roofline(torch, ps, s, stream, fp64_peak, reps=20):
     """The refinement's FP64 defect (k_residual) over all modes at the
     finest level, timed alone through psolve_stage_residual (each call: the
     full active list, then the kernel) with CUDA events on the library's
-    stream.  Algorithmic work per complex cell: 24 FP64 flops (the mode's
-    diagonal d0 - s2 q: 2; per real component five stencil products and
-    their sum: 10, and f minus it: 1) and 40 bytes (read u and f as FP64
-    complex, write r as FP32 complex).  The kernel runs on the FP64 pipe
+    stream.  Algorithmic work per complex cell: 22 FP64 flops (the mode's
+    diagonal d0 - s2 q: 2; per real component f minus five stencil
+    products: 10) and 40 bytes (read u and f as FP64 complex, write r as
+    FP32 complex).  The kernel runs on the FP64 pipe
     (ncu, FP64_PIPE_PCT), so the bound is the measured FP64 rate; the HBM
     figures are given beside it."""
     M = s.n_modes
@@ -692,7 +692,7 @@ def residual_roofline(torch, ps, s, stream, fp64_peak, reps=20):
     torch.cuda.synchronize()
     dt = ev0.elapsed_time(ev1) / 1e3 / reps
     cells = M * n_tz * n_r
-    flops, bytes_ = 24.0 * cells, 40.0 * cells
+    flops, bytes_ = 22.0 * cells, 40.0 * cells
     ach = flops / dt / 1e12
     pk = peaks().get("hbm_gbs")
     full = M == 129 and (n_r, n_tz) == (256, 128)
