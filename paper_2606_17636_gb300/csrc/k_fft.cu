@@ -24,11 +24,23 @@ __device__ double2* warp_fft(double2* x, double2* y, int N, int logN, const doub
       const int p = b >> t, q = b & (s - 1);
       const double2 a = x[q + s * p];
       const double2 c = x[q + s * (p + m)];
-      double2 w = tw[p * s];
-      if (sign > 0) w.y = -w.y;
       const double2 d = make_double2(a.x - c.x, a.y - c.y);
       y[q + s * (2 * p)] = make_double2(a.x + c.x, a.y + c.y);
-      y[q + s * (2 * p + 1)] = make_double2(d.x * w.x - d.y * w.y, d.x * w.y + d.y * w.x);
+      // twiddle e^{-+2 pi i p s / N}: the factors 1 (p s = 0) and -+i
+      // (p s = N/4) take no FP64 multiplies; the branch is uniform over a
+      // warp's 32 consecutive butterflies once s >= 32 (the last stages)
+      const int k = p * s;
+      double2 t;
+      if (k == 0) {
+        t = d;
+      } else if (k == (N >> 2)) {
+        t = sign < 0 ? make_double2(d.y, -d.x) : make_double2(-d.y, d.x);
+      } else {
+        double2 w = tw[k];
+        if (sign > 0) w.y = -w.y;
+        t = make_double2(d.x * w.x - d.y * w.y, d.x * w.y + d.y * w.x);
+      }
+      y[q + s * (2 * p + 1)] = t;
     }
     __syncwarp();
     double2* z = x;
