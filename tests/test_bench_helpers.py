@@ -39,8 +39,8 @@ def test_vcycle_flops_per_cell(bench):
 
 
 class _FakeSolver:
-    def __init__(self, sched, first):
-        self._s, self._f = sched, first
+    def __init__(self, sched, first, tail=0):
+        self._s, self._f, self._t = sched, first, tail
 
     def schedule(self):
         return self._s
@@ -48,18 +48,30 @@ class _FakeSolver:
     def fused_level(self):
         return self._f
 
+    def tail(self):
+        return (self._t, 16 if self._t else 0)
+
 
 def test_launches_per_solve_counts_the_loop_body(bench):
     """One iteration at the benchmark's shape (fused from level 1, nu = (2, 2)):
     residual, 2 x 2 smoothing passes, restriction, fused V-cycle,
-    prolongation, 2 x 2 passes, update = 13 launches; a solve adds 8 fixed
-    launches and runs each loop body once per residual evaluation."""
+    prolongation, 2 x 2 passes, update = 13 launches; a loop of I
+    iterations runs I + 1 residuals and I V-cycles; a solve adds 8 fixed
+    launches.  With the tail kernel (P planes) a loop hands over after the
+    first iteration that leaves at most P planes active."""
+    cyc_psi = [21, 9, 5] + [1] * 126
+    cyc_phi = [16, 7, 3] + [1] * 126
+    st = {"cycles_psi": cyc_psi, "cycles_phi": cyc_phi}
     s = _FakeSolver(dict(nu_pre=2, nu_post=2, n_sor=1), 1)
-    st = {"iterations_psi": 21, "iterations_phi": 16}
-    assert bench.launches_per_solve(s, st) == 8 + 13 * (22 + 17)
+    assert bench.launches_per_solve(s, st) == 8 + (22 + 21 * 12) + (17 + 16 * 12)
     s = _FakeSolver(dict(nu_pre=3, nu_post=1, n_sor=2), 2)
     # two level-wide levels: each 2 x 3 + 1 + 1 + 2 x 1 = 10 launches
-    assert bench.launches_per_solve(s, st) == 8 + (1 + 2 * 10 + 1 + 1) * (22 + 17)
+    v = 2 * 10 + 1 + 1
+    assert bench.launches_per_solve(s, st) == 8 + (22 + 21 * v) + (17 + 16 * v)
+    # tail of 2 planes: Psi hands over after iteration 5 (planes with more
+    # than 5 cycles: 21 and 9), Phi after iteration 3 (16 and 7)
+    s = _FakeSolver(dict(nu_pre=2, nu_post=2, n_sor=1), 1, tail=2)
+    assert bench.launches_per_solve(s, st) == 8 + (6 * 13 + 1) + (4 * 13 + 1)
 
 
 def test_oracle_timings_runs_the_full_oracle_solve(bench):
