@@ -367,6 +367,7 @@ def ours(a, ws, rank, local):
                 "result_vs_device_solve_rel_l2": e2e_err,
                 "d2h_bytes_per_step": phi.numel() * 8},
         "gpu_launches": launches * a.steps,
+        "whole_solve_hbm": whole_solve_hbm(spec, st, 1e3 * t / a.steps, sm.n_boundary),
         "warm_timestepping": warm,
         "roofline": roof,
         "roofline_streaming": roof_stream,
@@ -551,6 +552,34 @@ def cell_volumes(spec):
     if spec["geometry"] == workloads.SPHERICAL:
         return np.outer(np.diff(fr ** 3) / 3.0, -np.diff(np.cos(ft)))
     return np.outer(np.diff(fr ** 2) / 2.0, np.diff(ft))
+
+
+def whole_solve_hbm(spec, st, ms, nb):
+    """The whole mixed solve against the measured HBM bandwidth: the
+    algorithmic bytes of solve_algorithmic_bytes (with this solve's
+    per-mode cycle counts) over its time.  A low fraction says the solve is
+    bound by latency and the FP64 pipe, not by bytes."""
+    b = solve_algorithmic_bytes(spec, st, nb)
+    pk = peaks().get("hbm_gbs")
+    ach = b / (ms * 1e-3) / 1e9
+    return {"algorithmic_bytes": b, "achieved_gbs": ach, "peak_gbs": pk,
+            "frac": (ach / pk) if pk else None, "ms": ms}
+
+
+def solve_algorithmic_bytes(spec, st, nb):
+    """What a mixed solve must move through HBM (the per-unknown model of
+    the solver's design: per real unknown of a mode plane, a V-cycle moves
+    152 B (two smoothing directions x 4 cycles x 12 B, residual and
+    restriction 9 B, prolongation and correction 9 B, times 4/3 for the
+    coarser levels) and a refinement step 40 B (FP64 residual 20 B, FP64
+    update 20 B)); plus both transforms (32 B per cell) and one read of the
+    DGF tables."""
+    unknowns = 2 * spec["n_r"] * spec["n_tz"]          # Re and Im of one mode plane
+    cycles = sum(st["cycles_psi"]) + sum(st["cycles_phi"])
+    steps = cycles + 2 * len(st["cycles_psi"])         # residual evaluations: cycles + 1 per mode and solve
+    cells = spec["n_r"] * spec["n_tz"] * spec["n_phi"]
+    dgf = 8 * len(st["cycles_psi"]) * nb * nb          # nb boundary points per mode
+    return unknowns * (152 * cycles + 40 * steps) + 32 * cells + dgf
 
 
 def launches_per_solve(s, st):

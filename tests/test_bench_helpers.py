@@ -83,3 +83,14 @@ def test_oracle_timings_runs_the_full_oracle_solve(bench):
     assert tm["procs"] == 2 and tm["dgf_setup_s"] > 0
     assert len(tm["solve_s"]) == 2 and all(t > 0 for t in tm["solve_s"])
     assert len(tm["solve_1thread_s"]) == 1 and tm["solve_1thread_s"][0] > 0
+
+
+def test_solve_algorithmic_bytes_follow_the_per_unknown_model(bench):
+    """Per real unknown: 152 B per V-cycle and 40 B per refinement step
+    (cycles + 1 residual evaluations per mode and solve), plus 32 B per cell
+    for the two transforms and one read of the DGF tables."""
+    sp = dict(n_r=256, n_tz=128, n_phi=256)
+    st = {"cycles_psi": [19] + [3] * 128, "cycles_phi": [15] + [1] * 128}
+    cyc = 19 + 3 * 128 + 15 + 128
+    want = 2 * 256 * 128 * (152 * cyc + 40 * (cyc + 2 * 129)) + 32 * 256 * 128 * 256 + 8 * 129 * 256 * 256
+    assert bench.solve_algorithmic_bytes(sp, st, 256) == want
