@@ -7,10 +7,12 @@
 // memory.
 //
 // Shared-memory layout of a level (nr x nt, unpadded rows): cell (j, i) sits
-// at j * nr + (i ^ h(j)).  The row swizzle h(j) < min(16, nr) is (j >> 1) or j
-// (masked), matching the rows a half-warp holds in a polar line (pairs or
-// single cells), so both the row-wise vector accesses of radial lines and the
-// column accesses of polar lines are free of bank conflicts.
+// at j * nr + (i ^ h(j)).  The row swizzle h(j) < min(16, nr) follows the
+// rows a half-warp holds in a polar line (pairs of rows or single rows):
+// (j >> 1) or j, doubled for FP32 planes so that the two cells of an aligned
+// pair (16 bytes, one bank group) stay together.  Row-wise vector accesses of
+// radial lines and the column accesses of polar lines (pairs of columns for
+// FP32) are then free of bank conflicts.
 #include <cstdio>
 #include <type_traits>
 
@@ -21,12 +23,16 @@ namespace ps {
 #define R_(id, i) rt[(id) * (L.nr + 2) + (i)]
 #define T_(id, j) tt[(id) * (L.nt + 2) + (j)]
 
+template <typename T>
 __device__ __forceinline__ int vswz(const LevelDev& L, int j) {
   const int mask = (L.nr < 16 ? L.nr : 16) - 1;
-  return ((L.nt > 32 ? j >> 1 : j)) & mask;
+  const int x = L.nt > 32 ? j >> 1 : j;
+  if constexpr (sizeof(T) == 4) return (x << 1) & mask;
+  else return x & mask;
 }
+template <typename T>
 __device__ __forceinline__ int vslot(const LevelDev& L, int j, int i) {
-  return j * L.nr + (i ^ vswz(L, j));
+  return j * L.nr + (i ^ vswz<T>(L, j));
 }
 
 template <typename T, int CPL>
@@ -44,18 +50,18 @@ __device__ void s_rlines(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T 
   if constexpr (sizeof(T) == 4) ld_rtabs<T, CPL>(tabs, L, rt);
   for (int line = warp; 2 * line + color < nt; line += nw) {
     const int j = 2 * line + color;
-    const int sj = vswz(L, j);
+    const int sj = vswz<T>(L, j);
     V ev[CPL], g[CPL], un[CPL], us[CPL];
     ld_line_swz<V, CPL>(ev, e + j * nr, sj, lane, nr);
     ld_line_swz<V, CPL>(g, f + j * nr, sj, lane, nr);
     if (j + 1 < nt) {
-      ld_line_swz<V, CPL>(un, e + (j + 1) * nr, vswz(L, j + 1), lane, nr);
+      ld_line_swz<V, CPL>(un, e + (j + 1) * nr, vswz<T>(L, j + 1), lane, nr);
     } else {
 #pragma unroll
       for (int c = 0; c < CPL; ++c) un[c] = z2<V>();
     }
     if (j > 0) {
-      ld_line_swz<V, CPL>(us, e + (j - 1) * nr, vswz(L, j - 1), lane, nr);
+      ld_line_swz<V, CPL>(us, e + (j - 1) * nr, vswz<T>(L, j - 1), lane, nr);
     } else {
 #pragma unroll
       for (int c = 0; c < CPL; ++c) us[c] = z2<V>();
@@ -85,7 +91,7 @@ __device__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s
     for (int c = 0; c < CPL; ++c) {
       ev[c] = g[c] = ue[c] = uw[c] = z2<V>();
       if (on) {
-        const int j = lcell<CPL>(lane, c), row = j * nr, s = vswz(L, j);
+        const int j = lcell<CPL>(lane, c), row = j * nr, s = vswz<T>(L, j);
         ev[c] = e[row + (i ^ s)];
         g[c] = f[row + (i ^ s)];
         if (i > 0) uw[c] = e[row + ((i - 1) ^ s)];
@@ -98,9 +104,192 @@ __device__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {
         const int j = lcell<CPL>(lane, c);
-        e[j * nr + (i ^ vswz(L, j))] = ev[c];
+        e[j * nr + (i ^ vswz<T>(L, j))] = ev[c];
       }
     }
+  }
+}
+
+// ---- FP32 band smoothing ----------------------------------------------------
+// Both colours of one direction as a band per warp: warp w owns lines
+// w B .. w B + B - 1 (B = lines / warps, even).  It relaxes the band's even
+// (first-colour) lines, then its odd lines but the last, keeping every line
+// it touches in registers; the last odd line needs the first even line of the
+// band above, so it waits for a block barrier.  The band's first even line is
+// stored before that barrier (the band below needs it for its last odd line).
+// Each line relaxation receives exactly the operands of the line-by-line
+// schedule (the lines of one colour are independent), so the results are
+// bitwise the same; a line is loaded once per half-cycle instead of up to
+// three times, and polar columns move as 16-byte pairs.
+
+// Row j of an FP32 level held as the lane's cells (even swizzle s: pairs stay
+// whole).
+template <int CPL>
+__device__ __forceinline__ void b_ld_row(float2 (&d)[CPL], const float2* row, int s, int lane) {
+  if constexpr (CPL == 1) {
+    d[0] = row[lane ^ s];
+  } else {
+#pragma unroll
+    for (int q = 0; q < CPL / 2; ++q) ld_pair(d[2 * q], d[2 * q + 1], row + ((2 * lane + 64 * q) ^ s));
+  }
+}
+template <int CPL>
+__device__ __forceinline__ void b_st_row(float2* row, int s, const float2 (&d)[CPL], int lane) {
+  if constexpr (CPL == 1) {
+    row[lane ^ s] = d[0];
+  } else {
+#pragma unroll
+    for (int q = 0; q < CPL / 2; ++q) st_pair(row + ((2 * lane + 64 * q) ^ s), d[2 * q], d[2 * q + 1]);
+  }
+}
+template <int CPL>
+__device__ __forceinline__ void b_zero(float2 (&d)[CPL]) {
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) d[c] = make_float2(0.f, 0.f);
+}
+
+// Radial lines (rows), nr = 32 CPL, nt = B * warps.  Order: even row j0,
+// then per k the even row j0 + 2k and the odd row j0 + 2k - 1 below it, each
+// row stored once final; the last odd row after the barrier.
+template <int CPL, int B>
+__device__ __forceinline__ void band_r(const LevelDev& L, float2* e, const float2* f, float s2,
+                                       int n_sor) {
+  const int nr = L.nr, nt = L.nt, lane = threadIdx.x & 31;
+  const int j0 = (threadIdx.x >> 5) * B;
+  const float* tt = L.tf;
+  const float* om = L.omr_f;
+  RLineTabs<float, CPL> tabs;
+  ld_rtabs<float, CPL>(tabs, L, L.rf);
+  float2 u[B + 2][CPL];   // u[r] = row j0 - 1 + r
+#pragma unroll
+  for (int r = 0; r <= B; ++r) {
+    const int j = j0 - 1 + r;
+    if (j >= 0) b_ld_row<CPL>(u[r], e + j * nr, vswz<float>(L, j), lane);
+    else b_zero<CPL>(u[r]);
+  }
+  auto relax = [&](int r) {   // row j0 - 1 + r between rows r - 1 and r + 1
+    const int j = j0 - 1 + r;
+    float2 g[CPL];
+    b_ld_row<CPL>(g, f + j * nr, vswz<float>(L, j), lane);
+    relax_r<float, CPL>(L, tabs, tt, s2, om[j], j, g, u[r + 1], u[r - 1], n_sor, u[r]);
+    b_st_row<CPL>(e + j * nr, vswz<float>(L, j), u[r], lane);
+  };
+  relax(1);
+#pragma unroll
+  for (int k = 1; k < B / 2; ++k) {
+    relax(2 * k + 1);
+    relax(2 * k);
+  }
+  __syncthreads();
+  {
+    const int ja = j0 + B;
+    if (ja < nt) b_ld_row<CPL>(u[B + 1], e + ja * nr, vswz<float>(L, ja), lane);
+    else b_zero<CPL>(u[B + 1]);
+  }
+  relax(B);
+}
+
+// Polar lines (columns), nt = 32 CPL, nr = B * warps; the lane's cells are the
+// rows lcell(lane, c).  Same order as the rows; the two columns of a pair are
+// stored together once both are final (column i0 alone when B = 2: the band
+// to the left reads it after the barrier).
+template <int CPL, int B>
+__device__ __forceinline__ void band_t(const LevelDev& L, float2* e, const float2* f, float s2,
+                                       int n_sor) {
+  const int nr = L.nr, lane = threadIdx.x & 31;
+  const int i0 = (threadIdx.x >> 5) * B;
+  const float* rt = L.rf;
+  const float* om = L.omt_f;
+  TLineTabs<float, CPL> tabs;
+  ld_ttabs<float, CPL>(tabs, L, L.tf);
+  int base[CPL], sw[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    const int j = lcell<CPL>(lane, c);
+    base[c] = j * nr;
+    sw[c] = vswz<float>(L, j);
+  }
+  float2 u[B + 2][CPL];   // u[r] = column i0 - 1 + r
+  float2 g[B][CPL];       // right-hand side of column i0 + r at g[r]
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    u[0][c] = i0 > 0 ? e[base[c] + ((i0 - 1) ^ sw[c])] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < B / 2; ++k) ld_pair(u[2 * k + 1][c], u[2 * k + 2][c], e + base[c] + ((i0 + 2 * k) ^ sw[c]));
+  }
+  auto relax = [&](int r) {   // column i0 - 1 + r between columns r - 1 and r + 1
+    const int i = i0 - 1 + r;
+    if ((r & 1) == 1) {   // even column: its pair brings the odd column's right-hand side
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) ld_pair(g[r - 1][c], g[r][c], f + base[c] + (i ^ sw[c]));
+    }
+    relax_t<float, CPL>(L, rt, tabs, s2, om[i], i, g[r - 1], u[r + 1], u[r - 1], n_sor, u[r]);
+  };
+  auto store_pair = [&](int k) {   // columns i0 + 2k, i0 + 2k + 1
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) st_pair(e + base[c] + ((i0 + 2 * k) ^ sw[c]), u[2 * k + 1][c], u[2 * k + 2][c]);
+  };
+  relax(1);
+  if constexpr (B == 2) {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) e[base[c] + (i0 ^ sw[c])] = u[1][c];
+  }
+#pragma unroll
+  for (int k = 1; k < B / 2; ++k) {
+    relax(2 * k + 1);
+    relax(2 * k);
+    store_pair(k - 1);
+  }
+  __syncthreads();
+  {
+    const int ia = i0 + B;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) u[B + 1][c] = ia < nr ? e[base[c] + (ia ^ sw[c])] : make_float2(0.f, 0.f);
+  }
+  relax(B);
+  if constexpr (B == 2) {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) e[base[c] + ((i0 + 1) ^ sw[c])] = u[2][c];
+  } else {
+    store_pair(B / 2 - 1);
+  }
+}
+
+// Lines of n = 32, 64 or 128 cells (lanes x CPL) in bands of B = m / 16 lines
+// for m = 32, 64 or 128 lines, with B CPL <= 16 (registers): the band kind
+// (CPL, B) as 3 * log2(CPL) + log2(B / 2), or -1 when the level takes the
+// line-by-line schedule.
+__device__ __forceinline__ int band_kind(int n, int m, int nw) {
+  if (nw != 16 || (n != 32 && n != 64 && n != 128) || (m != 32 && m != 64 && m != 128)) return -1;
+  const int cpl = n / 32, b = m / 16;
+  if (cpl * b > 16) return -1;
+  return 3 * (cpl == 1 ? 0 : cpl == 2 ? 1 : 2) + (b == 2 ? 0 : b == 4 ? 1 : 2);
+}
+
+__device__ __forceinline__ void band_r_any(int kind, const LevelDev& L, float2* e, const float2* f,
+                                           float s2, int n_sor) {
+  switch (kind) {
+    case 0: band_r<1, 2>(L, e, f, s2, n_sor); break;
+    case 1: band_r<1, 4>(L, e, f, s2, n_sor); break;
+    case 2: band_r<1, 8>(L, e, f, s2, n_sor); break;
+    case 3: band_r<2, 2>(L, e, f, s2, n_sor); break;
+    case 4: band_r<2, 4>(L, e, f, s2, n_sor); break;
+    case 5: band_r<2, 8>(L, e, f, s2, n_sor); break;
+    case 6: band_r<4, 2>(L, e, f, s2, n_sor); break;
+    default: band_r<4, 4>(L, e, f, s2, n_sor); break;
+  }
+}
+__device__ __forceinline__ void band_t_any(int kind, const LevelDev& L, float2* e, const float2* f,
+                                           float s2, int n_sor) {
+  switch (kind) {
+    case 0: band_t<1, 2>(L, e, f, s2, n_sor); break;
+    case 1: band_t<1, 4>(L, e, f, s2, n_sor); break;
+    case 2: band_t<1, 8>(L, e, f, s2, n_sor); break;
+    case 3: band_t<2, 2>(L, e, f, s2, n_sor); break;
+    case 4: band_t<2, 4>(L, e, f, s2, n_sor); break;
+    case 5: band_t<2, 8>(L, e, f, s2, n_sor); break;
+    case 6: band_t<4, 2>(L, e, f, s2, n_sor); break;
+    default: band_t<4, 4>(L, e, f, s2, n_sor); break;
   }
 }
 
@@ -108,9 +297,22 @@ __device__ void s_tcols(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s
 // (L's table and omega pointers point at shared-memory copies; the omega
 // rows are those of this block's mode).
 template <typename T>
-__device__ void s_smooth(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int cycles,
+__device__ __noinline__ void s_smooth(const LevelDev& L, vec2_t<T>* e, const vec2_t<T>* f, T s2, int cycles,
                          int n_sor) {
   const int cr = L.nr <= 32 ? 1 : L.nr / 32, ct = L.nt <= 32 ? 1 : L.nt / 32;
+  if constexpr (sizeof(T) == 4) {
+    const int nw = blockDim.x >> 5;
+    const int kr = band_kind(L.nr, L.nt, nw), kt = band_kind(L.nt, L.nr, nw);
+    if (kr >= 0 && kt >= 0) {
+      for (int cyc = 0; cyc < cycles; ++cyc) {
+        band_r_any(kr, L, e, f, s2, n_sor);
+        __syncthreads();
+        band_t_any(kt, L, e, f, s2, n_sor);
+        __syncthreads();
+      }
+      return;
+    }
+  }
   for (int cyc = 0; cyc < cycles; ++cyc) {
     for (int color = 0; color < 2; ++color) {
       if (cr == 1) s_rlines<T, 1>(L, e, f, s2, n_sor, color);
@@ -140,22 +342,22 @@ __device__ void s_restrict(const LevelDev& L, const LevelDev& C, const vec2_t<T>
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) {
         const int i = 2 * I + a, j = 2 * J + b;
-        const V c = e[vslot(L, j, i)];
-        const V E = (i + 1 < nr) ? e[vslot(L, j, i + 1)] : V{0, 0};
-        const V W = (i > 0) ? e[vslot(L, j, i - 1)] : V{0, 0};
-        const V N = (j + 1 < nt) ? e[vslot(L, j + 1, i)] : V{0, 0};
-        const V S = (j > 0) ? e[vslot(L, j - 1, i)] : V{0, 0};
+        const V c = e[vslot<T>(L, j, i)];
+        const V E = (i + 1 < nr) ? e[vslot<T>(L, j, i + 1)] : V{0, 0};
+        const V W = (i > 0) ? e[vslot<T>(L, j, i - 1)] : V{0, 0};
+        const V N = (j + 1 < nt) ? e[vslot<T>(L, j + 1, i)] : V{0, 0};
+        const V S = (j > 0) ? e[vslot<T>(L, j - 1, i)] : V{0, 0};
         const T aE = R_(RT_AE, i + 1), aW = R_(RT_AW, i + 1), P = R_(RT_P, i + 1);
         const T aN = P * T_(TT_AN, j + 1), aS = P * T_(TT_AS, j + 1);
-        const T d = R_(RT_DR, i + 1) + P * T_(TT_DT, j + 1) - s2 * R_(RT_Q, i + 1) * T_(TT_T, j + 1);
-        const V fv = f[vslot(L, j, i)];
-        const T rx = fv.x - (aE * E.x + aW * W.x + aN * N.x + aS * S.x + d * c.x);
-        const T ry = fv.y - (aE * E.y + aW * W.y + aN * N.y + aS * S.y + d * c.y);
+        const T d = fmac(-(s2 * R_(RT_Q, i + 1)), T_(TT_T, j + 1), fmac(P, T_(TT_DT, j + 1), R_(RT_DR, i + 1)));
+        const V fv = f[vslot<T>(L, j, i)];
+        const T rx = fv.x - fmac(d, c.x, fmac(aS, S.x, fmac(aN, N.x, fmac(aW, W.x, aE * E.x))));
+        const T ry = fv.y - fmac(d, c.y, fmac(aS, S.y, fmac(aN, N.y, fmac(aW, W.y, aE * E.y))));
         const T wgt = R_(RT_RW, i + 1) * T_(TT_RW, j + 1);
-        ax += wgt * rx;
-        ay += wgt * ry;
+        ax = fmac(wgt, rx, ax);
+        ay = fmac(wgt, ry, ay);
       }
-    fc[vslot(C, J, I)] = V{ax, ay};
+    fc[vslot<T>(C, J, I)] = V{ax, ay};
   }
   __syncthreads();
 }
@@ -170,7 +372,7 @@ __device__ __forceinline__ vec2_t<T> s_cval(const LevelDev& C, const vec2_t<T>* 
   if (I == C.nr + 1) { if (C.gR == GH_ZERO) return V{0, 0}; Ic = C.nr; if (C.gR == GH_PARITY) fac *= sgn; }
   if (J == 0) { if (C.gB == GH_ZERO) return V{0, 0}; Jc = 1; if (C.gB == GH_PARITY) fac *= sgn; }
   if (J == C.nt + 1) { if (C.gT == GH_ZERO) return V{0, 0}; Jc = C.nt; if (C.gT == GH_PARITY) fac *= sgn; }
-  const V v = ec[vslot(C, Jc - 1, Ic - 1)];
+  const V v = ec[vslot<T>(C, Jc - 1, Ic - 1)];
   return V{fac * v.x, fac * v.y};
 }
 
@@ -198,10 +400,11 @@ __device__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, co
         const int i = 2 * I + a;
         const T p1 = R_(RT_P1, i + 1), p2 = R_(RT_P2, i + 1);
         const V A = cv[b][a], Bv = cv[b][a + 1], Cv = cv[b + 1][a], D = cv[b + 1][a + 1];
-        V u = e[vslot(L, j, i)];
-        u.x += p1 * q1 * A.x + p2 * q1 * Bv.x + p1 * q2 * Cv.x + p2 * q2 * D.x;
-        u.y += p1 * q1 * A.y + p2 * q1 * Bv.y + p1 * q2 * Cv.y + p2 * q2 * D.y;
-        e[vslot(L, j, i)] = u;
+        V u = e[vslot<T>(L, j, i)];
+        const T w11 = p1 * q1, w21 = p2 * q1, w12 = p1 * q2, w22 = p2 * q2;
+        u.x += fmac(w22, D.x, fmac(w12, Cv.x, fmac(w21, Bv.x, w11 * A.x)));
+        u.y += fmac(w22, D.y, fmac(w12, Cv.y, fmac(w21, Bv.y, w11 * A.y)));
+        e[vslot<T>(L, j, i)] = u;
       }
     }
   }
@@ -269,7 +472,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
   {
     RowWalk w(threadIdx.x, blockDim.x, nr0);
     for (int k = threadIdx.x; k < n0; k += blockDim.x, w.next())
-      cp_async_v(sm + a.off_f[0] + vslot(a.L[0], w.j, w.c), gf + size_t(p) * n0 + k, true);
+      cp_async_v(sm + a.off_f[0] + vslot<T>(a.L[0], w.j, w.c), gf + size_t(p) * n0 + k, true);
   }
   for (int l = 0; l < K; ++l) {
     const int n = a.L[l].nr * a.L[l].nt;
@@ -312,7 +515,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     double* fd = z + 2 * nc;   // [2][nt][nr]
     if (a.sep_sym) {
       for (RowWalk w(threadIdx.x, blockDim.x, nr); w.j < h; w.next()) {
-        const V u = fc[vslot(Lc, w.j, w.c)], v = fc[vslot(Lc, nt - 1 - w.j, w.c)];
+        const V u = fc[vslot<T>(Lc, w.j, w.c)], v = fc[vslot<T>(Lc, nt - 1 - w.j, w.c)];
         const double ux = u.x, uy = u.y, vx = v.x, vy = v.y;
         fd[w.j * nr + w.c] = ux + vx;
         fd[(h + w.j) * nr + w.c] = ux - vx;
@@ -321,7 +524,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
       }
     } else {
       for (RowWalk w(threadIdx.x, blockDim.x, nr); w.j < nt; w.next()) {
-        const V v = fc[vslot(Lc, w.j, w.c)];
+        const V v = fc[vslot<T>(Lc, w.j, w.c)];
         fd[w.j * nr + w.c] = double(v.x);
         fd[nc + w.j * nr + w.c] = double(v.y);
       }
@@ -378,8 +581,8 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
           ox += vk * z[k * nr + i];
           oy += vk * z[nc + k * nr + i];
         }
-        ec[vslot(Lc, j, i)] = V{T(ex + ox), T(ey + oy)};
-        ec[vslot(Lc, nt - 1 - j, i)] = V{T(ex - ox), T(ey - oy)};
+        ec[vslot<T>(Lc, j, i)] = V{T(ex + ox), T(ey + oy)};
+        ec[vslot<T>(Lc, nt - 1 - j, i)] = V{T(ex - ox), T(ey - oy)};
       }
     } else {
       for (int q = threadIdx.x; q < nc; q += blockDim.x) {
@@ -390,7 +593,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
           ax += vk * z[k * nr + i];
           ay += vk * z[nc + k * nr + i];
         }
-        ec[vslot(Lc, j, i)] = V{T(ax), T(ay)};
+        ec[vslot<T>(Lc, j, i)] = V{T(ax), T(ay)};
       }
     }
     __syncthreads();
@@ -415,7 +618,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
       const int g = 64 / n;
       const int sub = t & (g - 1), r = (t / g) % n, c = t / (n * g);
       auto fval = [&](int J) {
-        const V v = fc[vslot(Lc, J, r)];
+        const V v = fc[vslot<T>(Lc, J, r)];
         return double(c ? v.y : v.x);
       };
       if (sub == 0) z[c * nc + r] = fval(0);
@@ -448,7 +651,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     __syncthreads();
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
       const int J = q / n, i = q - J * n;
-      ec[vslot(Lc, J, i)] = V{T(x[q]), T(x[nc + q])};
+      ec[vslot<T>(Lc, J, i)] = V{T(x[q]), T(x[nc + q])};
     }
     __syncthreads();
   } else {   // coarsest level: e = L^{-1} f, FP64 dot products, g threads per row
@@ -468,7 +671,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
       double sx = 0.0, sy = 0.0;
       for (int k = sub; k < nc; k += g) {
         const double c = A[size_t(row) * nc + k];
-        const V fk = fc[vslot(Lc, k / ncr, k % ncr)];
+        const V fk = fc[vslot<T>(Lc, k / ncr, k % ncr)];
         sx += c * double(fk.x);
         sy += c * double(fk.y);
       }
@@ -476,7 +679,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
       }
-      if (sub == 0) ec[vslot(Lc, row / ncr, row % ncr)] = V{T(sx), T(sy)};
+      if (sub == 0) ec[vslot<T>(Lc, row / ncr, row % ncr)] = V{T(sx), T(sy)};
     }
     __syncthreads();
   }
@@ -488,7 +691,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
   {
     RowWalk w(threadIdx.x, blockDim.x, nr0);
     for (int k = threadIdx.x; k < n0; k += blockDim.x, w.next())
-      ge[size_t(p) * n0 + k] = sm[a.off_e[0] + vslot(a.L[0], w.j, w.c)];
+      ge[size_t(p) * n0 + k] = sm[a.off_e[0] + vslot<T>(a.L[0], w.j, w.c)];
   }
 }
 

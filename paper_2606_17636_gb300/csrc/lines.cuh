@@ -44,6 +44,13 @@ template <typename V> __device__ __forceinline__ V z2() { V v; v.x = 0; v.y = 0;
 __device__ __forceinline__ float rcp_diag(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp_diag(double x) { return __drcp_rn(x); }
 
+// a * b + c with one rounding.  The relaxation formulas spell out which
+// products fuse into which additions, so that every kernel that relaxes a
+// line rounds exactly the same way whatever the code around it (left to the
+// compiler, a sum of two products may fuse either one).
+__device__ __forceinline__ float fmac(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmac(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename V> __device__ __forceinline__ V shup(V v) {
   v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
   v.y = __shfl_up_sync(0xffffffffu, v.y, 1);
@@ -191,10 +198,10 @@ __device__ __forceinline__ void sor_line(vec2_t<T> (&ev)[CPL], const vec2_t<T> (
   const int lane = threadIdx.x & 31;
   const T w1 = T(1) - w;
   auto upd = [&](int c, const V& em, const V& ep) {
-    const T tx = (g[c].x - up[c] * ep.x - dn[c] * em.x) * id[c];
-    const T ty = (g[c].y - up[c] * ep.y - dn[c] * em.y) * id[c];
-    ev[c].x = w1 * ev[c].x + w * tx;
-    ev[c].y = w1 * ev[c].y + w * ty;
+    const T tx = fmac(-dn[c], em.x, fmac(-up[c], ep.x, g[c].x)) * id[c];
+    const T ty = fmac(-dn[c], em.y, fmac(-up[c], ep.y, g[c].y)) * id[c];
+    ev[c].x = fmac(w, tx, w1 * ev[c].x);
+    ev[c].y = fmac(w, ty, w1 * ev[c].y);
   };
   if constexpr (CPL == 1) {
     const bool on = lane < n, last = lane == n - 1;
@@ -277,9 +284,9 @@ __device__ __forceinline__ void relax_r(const LevelDev& L, const RLineTabs<T, CP
   T id[CPL];
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
-    g[c].x = g[c].x - a.P[c] * (aN * un[c].x + aS * us[c].x);
-    g[c].y = g[c].y - a.P[c] * (aN * un[c].y + aS * us[c].y);
-    id[c] = on ? rcp_diag(a.dr[c] + a.P[c] * dtj - s2 * a.q[c] * Tj) : T(0);
+    g[c].x = fmac(-a.P[c], fmac(aS, us[c].x, aN * un[c].x), g[c].x);
+    g[c].y = fmac(-a.P[c], fmac(aS, us[c].y, aN * un[c].y), g[c].y);
+    id[c] = on ? rcp_diag(fmac(-(s2 * a.q[c]), Tj, fmac(a.P[c], dtj, a.dr[c]))) : T(0);
   }
   sor_line<T, CPL>(ev, g, a.up, a.dn, id, w, nr, n_sor);
 }
@@ -300,15 +307,15 @@ __device__ __forceinline__ void relax_r(const LevelDev& L, const T* rt, const T*
   ld_tab<T, CPL>(P, rt + RT_P * NR, lane, nr);
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
-    g[c].x = g[c].x - P[c] * (aN * un[c].x + aS * us[c].x);
-    g[c].y = g[c].y - P[c] * (aN * un[c].y + aS * us[c].y);
+    g[c].x = fmac(-P[c], fmac(aS, us[c].x, aN * un[c].x), g[c].x);
+    g[c].y = fmac(-P[c], fmac(aS, us[c].y, aN * un[c].y), g[c].y);
   }
   {
     T dr[CPL], q[CPL];
     ld_tab<T, CPL>(dr, rt + RT_DR * NR, lane, nr);
     ld_tab<T, CPL>(q, rt + RT_Q * NR, lane, nr);
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) id[c] = on ? rcp_diag(dr[c] + P[c] * dtj - s2 * q[c] * Tj) : T(0);
+    for (int c = 0; c < CPL; ++c) id[c] = on ? rcp_diag(fmac(-(s2 * q[c]), Tj, fmac(P[c], dtj, dr[c]))) : T(0);
   }
   ld_tab<T, CPL>(up, rt + RT_AE * NR, lane, nr);
   ld_tab<T, CPL>(dn, rt + RT_AW * NR, lane, nr);
@@ -331,9 +338,9 @@ __device__ __forceinline__ void relax_t(const LevelDev& L, const T* rt, const TL
   T up[CPL], dn[CPL], id[CPL];
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
-    g[c].x = g[c].x - aE * ue[c].x - aW * uw[c].x;
-    g[c].y = g[c].y - aE * ue[c].y - aW * uw[c].y;
-    id[c] = on ? rcp_diag(dr + P * a.dt[c] - s2 * Qi * a.tj[c]) : T(0);
+    g[c].x = fmac(-aW, uw[c].x, fmac(-aE, ue[c].x, g[c].x));
+    g[c].y = fmac(-aW, uw[c].y, fmac(-aE, ue[c].y, g[c].y));
+    id[c] = on ? rcp_diag(fmac(-(s2 * Qi), a.tj[c], fmac(P, a.dt[c], dr))) : T(0);
     up[c] = P * a.an[c];
     dn[c] = P * a.as[c];
   }
@@ -353,15 +360,15 @@ __device__ __forceinline__ void relax_t(const LevelDev& L, const T* rt, const T*
   T up[CPL], dn[CPL], id[CPL];
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
-    g[c].x = g[c].x - aE * ue[c].x - aW * uw[c].x;
-    g[c].y = g[c].y - aE * ue[c].y - aW * uw[c].y;
+    g[c].x = fmac(-aW, uw[c].x, fmac(-aE, ue[c].x, g[c].x));
+    g[c].y = fmac(-aW, uw[c].y, fmac(-aE, ue[c].y, g[c].y));
   }
   {
     T dt[CPL], tj[CPL];
     ld_tab<T, CPL>(dt, tt + TT_DT * NT, lane, nt);
     ld_tab<T, CPL>(tj, tt + TT_T * NT, lane, nt);
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) id[c] = on ? rcp_diag(dr + P * dt[c] - s2 * Qi * tj[c]) : T(0);
+    for (int c = 0; c < CPL; ++c) id[c] = on ? rcp_diag(fmac(-(s2 * Qi), tj[c], fmac(P, dt[c], dr))) : T(0);
   }
   ld_tab<T, CPL>(up, tt + TT_AN * NT, lane, nt);
   ld_tab<T, CPL>(dn, tt + TT_AS * NT, lane, nt);
