@@ -619,7 +619,7 @@ def launches_per_solve(s, st):
 # --smooth-first): one k_vsmem launch, one finest-level smoothing cycle
 # (k_rpass2 + k_tpass2) and the first stencil launch of k_residual.  They
 # hold for the kernels as captured; a changed kernel needs a new capture.
-VSMEM_TRAFFIC_BYTES = 12151552
+VSMEM_TRAFFIC_BYTES = None
 SMOOTH_CYCLE_TRAFFIC_BYTES = 67735552 + 7611136 + 67792896 + 5309440
 RESIDUAL_TRAFFIC_BYTES = 136468480 + 16737024
 # ncu sm__inst_executed_pipe_fp64 (percent of peak, sustained active) of the
@@ -755,8 +755,9 @@ def vcycle_roofline(torch, ps, s, stream):
     mode plane, levels held in shared memory), all modes, timed alone
     through psolve_stage_vcycle with CUDA events on the library's stream.
     Algorithmic work per launch: M x sum over the fused smoothed levels of
-    cells x vcycle_flops_per_cell(schedule) FP32 flops, plus the FP64 separable solve
-    of the coarsest level (8 n_r n_t^2 + 10 n_r n_t per mode)."""
+    cells x vcycle_flops_per_cell(schedule) FP32 flops, plus the separable solve
+    of the coarsest level (8 n_r n_t^2 + 10 n_r n_t per mode: FP32 polar
+    transforms, FP64 radial sweeps)."""
     M = s.n_modes
     lev = s.fused_level()
     n_r, n_tz = s.shape[0], s.shape[1]
@@ -780,8 +781,9 @@ def vcycle_roofline(torch, ps, s, stream):
         cells += (n_r >> l) * (n_tz >> l)
         l += 1
     cr, ct = n_r >> (s.n_levels - 1), n_tz >> (s.n_levels - 1)
-    # separable coarsest solve: two FP64 transforms along theta (2 components)
-    # and n_theta Thomas solves along r
+    # separable coarsest solve: two transforms along theta (2 components;
+    # FP32 in the mixed path, counted in the general form) and n_theta
+    # Thomas solves along r (FP64)
     flops = M * (cells * vcycle_flops_per_cell(s.schedule()) + 8 * cr * ct * ct + 10 * cr * ct)
     ach = flops / dt / 1e12
     return {"kernel": "fused coarse V-cycle k_vsmem (levels %d..%d in shared memory, all %d modes)"

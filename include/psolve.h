@@ -83,9 +83,25 @@ typedef struct {
                           domain doubles n_r (and a bounded theta or z range),
                           so it needs n_r <= 512 (and n_tz <= 512 when bounded):
                           PSOLVE_ERR_ARG otherwise                               */
+  int coarsest_size;   /* size of the directly solved coarsest level (Sec. 3.3
+                          leaves it open); levels halve both sides while the
+                          short side exceeds S cells, or exceeds 4 cells with
+                          more than C cells in the plane.
+                          PSOLVE_COARSEST_SMALL (1): S = 16, C = 1024.
+                          PSOLVE_COARSEST_LARGE (2): S = 32, C = 2048 when
+                          that coarsest level is separable (its operator is
+                          L_r (x) I + D_r (x) L_t), else the small rule.
+                          PSOLVE_COARSEST_AUTO (0): the large rule for the
+                          mixed path when it leaves at least two levels, the
+                          small rule otherwise and for the FP64 path.  The
+                          mixed path solves a separable coarsest level with
+                          FP32 polar transforms and FP64 radial sweeps, the
+                          FP64 path in FP64 throughout; other values are
+                          PSOLVE_ERR_ARG                                      */
 } psolve_desc;
 
 enum { PSOLVE_DGF_AUTO = 0, PSOLVE_DGF_AUX = 1, PSOLVE_DGF_EXTENDED = 2 };
+enum { PSOLVE_COARSEST_AUTO = 0, PSOLVE_COARSEST_SMALL = 1, PSOLVE_COARSEST_LARGE = 2 };
 
 /* Per-solve statistics (psolve_get_stats).  Arrays sized by the caller:
  * cycles_psi / cycles_phi / status hold M entries when non-NULL. */
@@ -128,10 +144,9 @@ int psolve_create_multi(psolve_t* out, const psolve_desc* d, int n_densities);
 
 /* The multigrid plan psolve_create_ex would build for d, computed on the
  * host only (no device memory, no kernels: usable without a GPU).  Levels
- * halve both sides while the short side exceeds 16, or exceeds 4 with more
- * than 1024 cells (Sec. 3; the paper leaves the coarsest size open); the
- * coarsest level is solved exactly in FP64 (Sec. 3.3 allows a direct
- * solver) in one of four forms, reported in `coarsest`. */
+ * follow d->coarsest_size (Sec. 3; the paper leaves the coarsest size open);
+ * the coarsest level is solved directly (Sec. 3.3 allows a direct solver)
+ * in one of four forms, reported in `coarsest`. */
 enum { PSOLVE_COARSE_SEPARABLE_MIRROR = 0, /* separable, mirror-symmetric polar operator */
        PSOLVE_COARSE_SEPARABLE = 1,        /* separable, general polar operator          */
        PSOLVE_COARSE_BLOCK = 2,            /* block-tridiagonal (Schur complements)      */
@@ -388,7 +403,8 @@ int psolve_stage_residual(psolve_t h, int precision, const double* f, const doub
  * level `level` (which must be the handle's fused level, see
  * psolve_get_fused_level) down to the coarsest, on L_m e = f with a zero
  * initial guess: nu_pre smoothing cycles, defect restriction, recursion,
- * the exact coarsest solve (FP64), prolongation, nu_post smoothing cycles.
+ * the direct coarsest solve (see psolve_desc.coarsest_size), prolongation,
+ * nu_post smoothing cycles.
  * f, e: planes [M][n_tz_l][n_r_l] complex in FP64 (precision 0) or FP32 (1);
  * e is overwritten.  PSOLVE_ERR_ARG for another level or precision. */
 int psolve_stage_vcycle(psolve_t h, int level, int precision, const void* f, void* e);

@@ -15,6 +15,7 @@ UNIFORM, LOG = 0, 1
 FP64, MIXED = 0, 1
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NOT_CONVERGED, ERR_NONFINITE = 0, -1, -2, -3, -4, -5
 DGF_AUTO, DGF_AUX, DGF_EXTENDED = 0, 1, 2
+COARSEST_AUTO, COARSEST_SMALL, COARSEST_LARGE = 0, 1, 2
 STATIC_SCRATCH_BYTES = 32 * 1024 * 1024   # PSOLVE_STATIC_SCRATCH_BYTES
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -32,7 +33,8 @@ class Desc(ctypes.Structure):
                 ("G", ctypes.c_double), ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("n_sor", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("alloc_fn", ALLOC_FN), ("free_fn", FREE_FN),
-                ("alloc_user", ctypes.c_void_p), ("dgf_construction", ctypes.c_int)]
+                ("alloc_user", ctypes.c_void_p), ("dgf_construction", ctypes.c_int),
+                ("coarsest_size", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -65,7 +67,7 @@ class Plan(ctypes.Structure):
 COARSE_FORMS = {0: "separable, mirror-symmetric", 1: "separable", 2: "block-tridiagonal", 3: "dense"}
 
 
-def plan_inspect(spec, precision=1, n_sor=0):
+def plan_inspect(spec, precision=1, n_sor=0, coarsest_size=0):
     """The multigrid plan of a problem spec (psolve_plan_inspect: host only,
     no GPU needed): levels (n_r, n_tz), finest first, and the coarsest-level
     solve's form and factor size per mode."""
@@ -77,6 +79,7 @@ def plan_inspect(spec, precision=1, n_sor=0):
     d.t_max = spec.get("t_max") or 0.0
     d.precision = precision
     d.n_sor = n_sor
+    d.coarsest_size = coarsest_size
     p = Plan()
     check(lib().psolve_plan_inspect(ctypes.byref(d), ctypes.byref(p)), "psolve_plan_inspect")
     return {"n_modes": p.n_modes,
@@ -191,7 +194,8 @@ class Solver:
 
     def __init__(self, geometry, n_r, n_tz, n_phi, spacing, r_in, r_out, t_min=None, t_max=None,
                  G=1.0, precision=MIXED, max_cycles=0, nu_pre=0, nu_post=0, n_sor=0,
-                 use_graph=True, torch_alloc=True, n_densities=1, dgf_construction=DGF_AUTO):
+                 use_graph=True, torch_alloc=True, n_densities=1, dgf_construction=DGF_AUTO,
+                 coarsest_size=COARSEST_AUTO):
         import torch
         self.torch = torch
         L = lib()
@@ -201,6 +205,7 @@ class Solver:
         d.t_min = 0.0 if t_min is None else t_min
         d.t_max = 0.0 if t_max is None else t_max
         d.dgf_construction = dgf_construction
+        d.coarsest_size = coarsest_size
         d.G, d.precision, d.max_cycles = G, precision, max_cycles
         d.nu_pre, d.nu_post, d.n_sor, d.use_graph = nu_pre, nu_post, n_sor, int(bool(use_graph))
         self._alloc = _TorchAllocator() if torch_alloc else None

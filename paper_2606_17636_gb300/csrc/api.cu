@@ -151,6 +151,8 @@ static int prepare_desc(const psolve_desc& din, psolve_desc& d) {
     return fail(PSOLVE_ERR_ARG, "precision must be PSOLVE_FP64 or PSOLVE_MIXED");
   if (d.dgf_construction < PSOLVE_DGF_AUTO || d.dgf_construction > PSOLVE_DGF_EXTENDED)
     return fail(PSOLVE_ERR_ARG, "dgf_construction must be PSOLVE_DGF_AUTO, _AUX or _EXTENDED");
+  if (d.coarsest_size < PSOLVE_COARSEST_AUTO || d.coarsest_size > PSOLVE_COARSEST_LARGE)
+    return fail(PSOLVE_ERR_ARG, "coarsest_size must be PSOLVE_COARSEST_AUTO, _SMALL or _LARGE");
   if (d.dgf_construction == PSOLVE_DGF_EXTENDED && (d.spacing != PSOLVE_LOG || d.n_r < 32))
     return fail(PSOLVE_ERR_ARG, "the extended-domain DGF needs logarithmic radial spacing and n_r >= 32");
   if (d.precision == PSOLVE_FP64 && (d.n_r > 512 || d.n_tz > 512))
@@ -213,6 +215,7 @@ static int create_impl(psolve_t* out, const psolve_desc* din, int nd) {
   o.nu2 = d.nu_post;
   o.n_sor = d.n_sor;
   o.max_cycles = d.max_cycles;
+  o.coarsest_size = d.coarsest_size;
   std::vector<int> plane_slot;   // several densities: plane b M + m solves mode m
   if (nd > 1) {
     plane_slot.resize(P);
@@ -329,7 +332,8 @@ extern "C" int psolve_plan_inspect(const psolve_desc* din, psolve_plan* out) {
     for (int m = 0; m < M; ++m) modes[m] = m;
     Hierarchy H;
     std::string err;
-    if (!build_hierarchy(g, false, modes, H, err)) return fail(PSOLVE_ERR_ARG, "multigrid plan: " + err);
+    if (!plan_hierarchy(g, false, modes, d.coarsest_size, d.precision, H, err))
+      return fail(PSOLVE_ERR_ARG, "multigrid plan: " + err);
     *out = psolve_plan{};
     out->n_modes = M;
     out->n_levels = int(H.lv.size());
@@ -354,7 +358,7 @@ extern "C" int psolve_plan_inspect(const psolve_desc* din, psolve_plan* out) {
       std::vector<int> nr(out->n_levels), nt(out->n_levels);
       for (int l = 0; l < out->n_levels; ++l) { nr[l] = H.lv[l].g.r.n; nt[l] = H.lv[l].g.t.n; }
       TailArgs t{};
-      const size_t bytes = tail_layout(nr, nt, d.n_sor, H.sep_stride > 0, t);
+      const size_t bytes = tail_layout(nr, nt, d.n_sor, H.sep_stride > 0 && !H.large, t);
       out->tail_cluster_ctas = bytes ? t.C : 0;
       out->tail_smem_bytes = int(bytes);
     }

@@ -4,7 +4,9 @@
 // alternating zebra line relaxation), defect restriction, the coarsest
 // exact solve, prolongation and post-smoothing with block barriers instead
 // of kernel boundaries.  Input f[first] and output e[first] live in global
-// memory.
+// memory.  The coarsest level is solved directly: FP64 throughout in the
+// FP64 kernel; in the FP32 kernel a separable coarsest level takes FP32 polar
+// transforms around FP64 radial sweeps (coarsest_f32c).
 //
 // Shared-memory layout of a level (nr x nt, unpadded rows): cell (j, i) sits
 // at j * nr + (i ^ h(j)).  The row swizzle h(j) < min(16, nr) follows the
@@ -411,6 +413,139 @@ __device__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, co
   __syncthreads();
 }
 
+// ---- separable coarsest level of the FP32 V-cycle --------------------------
+// L_m = L_r (x) I + D_r (x) L_t with L_t = V diag(lambda) V^-1 (Sec. 3.3
+// allows any direct solver).  The polar transforms run in FP32, the
+// arithmetic of the V-cycle around them; the radial systems
+// (L_r + lambda_k D_r), whose conditioning grows with the radial stretching,
+// are swept in FP64 with the factors computed in FP64 on the host.
+
+// Stage this slot's factors into shared memory at blk_off: the FP64
+// upper/pivot and lower/pivot tables [nt][nr] each, then the FP32 block
+// (V, V^-1, 1/pivot), all by asynchronous copies.
+__device__ __forceinline__ void stage_f32c(const VSmemArgs& a, int slot, unsigned char* vraw,
+                                           int nc, int vr, int nt) {
+  const double2* src = reinterpret_cast<const double2*>(a.sep + size_t(slot) * a.sep_stride +
+                                                        2 * size_t(vr) * nt + nc);
+  double2* dst = reinterpret_cast<double2*>(vraw + a.blk_off);
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) cp_async_v(dst + k, src + k, true);
+  const float4* fs = reinterpret_cast<const float4*>(a.sepf + size_t(slot) * a.sepf_stride);
+  float4* fd = reinterpret_cast<float4*>(vraw + a.blk_off + 16 * size_t(nc));
+  for (int k = threadIdx.x; k < a.sepf_stride / 4; k += blockDim.x) cp_async_v(fd + k, fs + k, true);
+}
+
+// e = L_m^-1 f on the coarsest level Lc (cells in the FP32 swizzled layout).
+// Scratch at dbl_off: z [2][nt][nr] FP64, then zf [2][nt][nr] FP32.
+__device__ void coarsest_f32c(const VSmemArgs& a, int slot, unsigned char* vraw, const LevelDev& Lc,
+                              const float2* fc, float2* ec) {
+  const int nr = Lc.nr, nt = Lc.nt, nc = nr * nt, h = nt / 2;
+  const bool sym = a.sep_sym != 0;
+  const int vr = sym ? h : nt;
+  double* z = reinterpret_cast<double*>(vraw + a.dbl_off);
+  float* zf = reinterpret_cast<float*>(z + 2 * nc);
+  const double* cp;
+  const float* F;
+  if (a.blk_smem) {
+    cp = reinterpret_cast<const double*>(vraw + a.blk_off);
+    F = reinterpret_cast<const float*>(cp + 2 * nc);
+  } else {
+    cp = a.sep + size_t(slot) * a.sep_stride + 2 * size_t(vr) * nt + nc;
+    F = a.sepf + size_t(slot) * a.sepf_stride;
+  }
+  const double* lid = cp + nc;
+  const float* Vm = F;              // [vr][nt]
+  const float* Vi = Vm + vr * nt;   // [nt][vr]
+  const float* invd = Vi + nt * vr; // [nt][nr]
+  // f by component (mirror-symmetric: rows j < h hold f_j + f_{nt-1-j},
+  // rows h + j hold f_j - f_{nt-1-j})
+  if (sym) {
+    for (RowWalk w(threadIdx.x, blockDim.x, nr); w.j < h; w.next()) {
+      const float2 u = fc[vslot<float>(Lc, w.j, w.c)], v = fc[vslot<float>(Lc, nt - 1 - w.j, w.c)];
+      zf[w.j * nr + w.c] = u.x + v.x;
+      zf[(h + w.j) * nr + w.c] = u.x - v.x;
+      zf[nc + w.j * nr + w.c] = u.y + v.y;
+      zf[nc + (h + w.j) * nr + w.c] = u.y - v.y;
+    }
+  } else {
+    for (RowWalk w(threadIdx.x, blockDim.x, nr); w.j < nt; w.next()) {
+      const float2 v = fc[vslot<float>(Lc, w.j, w.c)];
+      zf[w.j * nr + w.c] = v.x;
+      zf[nc + w.j * nr + w.c] = v.y;
+    }
+  }
+  __syncthreads();
+  // z = (1/pivot) .* ((V^-1 (x) I) f), FP32, widened exactly to FP64
+  for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
+    const int c = q / nc, r = q - c * nc, k = r / nr, i = r - k * nr;
+    const float* col = zf + c * nc + (sym && k >= h ? h * nr : 0) + i;
+    const float* vk = Vi + k * vr;
+    float acc = 0.f;
+    for (int j = 0; j < vr; ++j) acc = fmaf(vk[j], col[j * nr], acc);
+    z[q] = f32_to_f64(acc * invd[k * nr + i]);
+  }
+  __syncthreads();
+  // Thomas sweeps per (component, eigenvalue), FP64, one FMA per step each
+  // way: dp_i = z_i - lid_i dp_{i-1}, then x_i = dp_i - cp_i x_{i+1},
+  // rounded to FP32 into zf.  The 2 nt systems run on the first four warps
+  // (one per scheduler: the FP64 pipe is narrow).
+  {
+    const int nsys = 2 * nt, per = (nsys + 3) / 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 4 && lane < per && warp * per + lane < nsys) {
+      const int q = warp * per + lane, c = q / nt, k = q - c * nt;
+      double* __restrict__ zz = z + c * nc + k * nr;
+      float* __restrict__ xo = zf + c * nc + k * nr;
+      const double* __restrict__ lk = lid + k * nr;
+      const double* __restrict__ ck = cp + k * nr;
+      double dp = zz[0];
+#pragma unroll 4
+      for (int i = 1; i < nr; ++i) {
+        dp = fma(-lk[i], dp, zz[i]);
+        zz[i] = dp;
+      }
+      double xv = dp;
+      xo[nr - 1] = f64_to_f32(xv);
+#pragma unroll 4
+      for (int i = nr - 2; i >= 0; --i) {
+        xv = fma(-ck[i], xv, zz[i]);
+        xo[i] = f64_to_f32(xv);
+      }
+    }
+  }
+  __syncthreads();
+  // e = (V (x) I) x, FP32 (mirror-symmetric: e_j = E + O and
+  // e_{nt-1-j} = E - O from the even and odd eigenvector parts)
+  if (sym) {
+    for (int q = threadIdx.x; q < h * nr; q += blockDim.x) {
+      const int j = q / nr, i = q - j * nr;
+      const float* vj = Vm + j * nt;
+      float ex = 0.f, ey = 0.f, ox = 0.f, oy = 0.f;
+      for (int k = 0; k < h; ++k) {
+        ex = fmaf(vj[k], zf[k * nr + i], ex);
+        ey = fmaf(vj[k], zf[nc + k * nr + i], ey);
+      }
+      for (int k = h; k < nt; ++k) {
+        ox = fmaf(vj[k], zf[k * nr + i], ox);
+        oy = fmaf(vj[k], zf[nc + k * nr + i], oy);
+      }
+      ec[vslot<float>(Lc, j, i)] = make_float2(ex + ox, ey + oy);
+      ec[vslot<float>(Lc, nt - 1 - j, i)] = make_float2(ex - ox, ey - oy);
+    }
+  } else {
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      const int j = q / nr, i = q - j * nr;
+      const float* vj = Vm + j * nt;
+      float ax = 0.f, ay = 0.f;
+      for (int k = 0; k < nt; ++k) {
+        ax = fmaf(vj[k], zf[k * nr + i], ax);
+        ay = fmaf(vj[k], zf[nc + k * nr + i], ay);
+      }
+      ec[vslot<float>(Lc, j, i)] = make_float2(ax, ay);
+    }
+  }
+  __syncthreads();
+}
+
 template <typename T, int NTH>
 __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const vec2_t<T>* __restrict__ gf,
                                                vec2_t<T>* __restrict__ ge) {
@@ -462,7 +597,15 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
   // this mode's coarsest-level factors (when they fit)
   const size_t blk_stride = size_t(a.blk_nt) * a.blk_n * (a.blk_n + 2);
   const size_t fac_stride = a.sep_stride > 0 ? size_t(a.sep_stride) : blk_stride;
-  if (a.blk_smem) {
+  const LevelDev& Lcst = a.L[K - 1];
+  if (a.f32c) {
+    // FP32 V-cycle, separable coarsest level: its own factor block, staged
+    // now unless it shares the first level's right-hand side space
+    if constexpr (sizeof(T) == 4) {
+      if (a.blk_smem && !a.restage)
+        stage_f32c(a, slot, vraw, Lcst.nr * Lcst.nt, a.sep_sym ? Lcst.nt / 2 : Lcst.nt, Lcst.nt);
+    }
+  } else if (a.blk_smem) {
     const double2* src = reinterpret_cast<const double2*>(
         (a.sep_stride > 0 ? a.sep : a.blk) + size_t(slot) * fac_stride);
     double2* dst = reinterpret_cast<double2*>(vraw + a.blk_off);
@@ -489,7 +632,21 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     s_smooth<T>(Lf, sm + a.off_e[l], sm + a.off_f[l], s2, a.nu1, a.n_sor);
     s_restrict<T>(Lf, Lq, sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
   }
-  if (a.sep_stride > 0) {
+  if (a.f32c) {
+    if constexpr (sizeof(T) == 4) {
+      if (a.restage) {   // the factors take the first level's right-hand side space
+        stage_f32c(a, slot, vraw, Lcst.nr * Lcst.nt, a.sep_sym ? Lcst.nt / 2 : Lcst.nt, Lcst.nt);
+        cp_async_wait_all();
+        __syncthreads();
+      }
+      coarsest_f32c(a, slot, vraw, Lcst, sm + a.off_f[K - 1], sm + a.off_e[K - 1]);
+      if (a.restage) {   // the first level's right-hand side again, in flight during the prolongation
+        RowWalk w(threadIdx.x, blockDim.x, nr0);
+        for (int k = threadIdx.x; k < n0; k += blockDim.x, w.next())
+          cp_async_v(sm + a.off_f[0] + vslot<T>(a.L[0], w.j, w.c), gf + size_t(p) * n0 + k, true);
+      }
+    }
+  } else if (a.sep_stride > 0) {
     // coarsest level, exact FP64 separable solve: L_m = L_r (x) I + D_r (x) L_t
     // with L_t = V diag(lambda) V^-1: z = (V^-1 (x) I) f, one tridiagonal
     // radial solve (L_r + lambda_k D_r) per eigenvalue k (Thomas), then
@@ -686,6 +843,10 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
   for (int l = K - 2; l >= 0; --l) {
     const LevelDev Lf = sL[l], Lq = sL[l + 1];
     s_prolong<T>(Lf, Lq, sm + a.off_e[l], sm + a.off_e[l + 1], m);
+    if (l == 0 && a.restage) {
+      cp_async_wait_all();
+      __syncthreads();
+    }
     s_smooth<T>(Lf, sm + a.off_e[l], sm + a.off_f[l], s2, a.nu2, a.n_sor);
   }
   {

@@ -137,6 +137,15 @@ struct VSmemArgs {
   const double* sep;     // separable coarsest-level factors [slots][sep_stride] (sep_stride > 0)
   int sep_stride;
   int sep_sym;           // mirror-symmetric separable layout (see Hierarchy::sep_sym)
+  // FP32 V-cycle with a separable coarsest level: polar transforms in FP32
+  // (sepf per slot: V, V^-1 and 1/pivot as floats, sepf_stride floats), the
+  // radial sweeps in FP64 with sep's upper/pivot and lower/pivot tables.
+  // Staged factors (blk_smem) hold those two tables, then the FP32 block;
+  // restage = 1: they lie over the first level's right-hand side, which is
+  // copied in again from the input after the coarsest solve.
+  int f32c, restage;
+  const float* sepf;
+  int sepf_stride;
   int nu1, nu2, n_sor;
   int tab_off;           // shared-memory offset (complex elements) of the staged tables
   const void* tabs;      // per-slot packed tables (T), tab_stride elements per slot

@@ -190,9 +190,10 @@ static void jacobi_eig(std::vector<double>& S, int n, std::vector<double>& U,
 }
 
 // Mirror symmetry j <-> n-1-j of the symmetrised polar operator S and its
-// weights w (relative 1e-13).
+// weights w (relative 1e-12: the weights come from a running product over
+// the polar faces).
 static bool mirror_symmetric(const std::vector<double>& S, const std::vector<double>& w, int n) {
-  auto near = [](double x, double y) { return std::fabs(x - y) <= 1e-13 * std::fmax(std::fabs(x), std::fabs(y)); };
+  auto near = [](double x, double y) { return std::fabs(x - y) <= 1e-12 * std::fmax(std::fabs(x), std::fabs(y)); };
   if (n % 2) return false;
   for (int j = 0; j < n; ++j) {
     if (!near(S[size_t(j) * n + j], S[size_t(n - 1 - j) * n + (n - 1 - j)])) return false;
@@ -339,8 +340,23 @@ static bool separable_factors(const PlaneGeo& g, int m, double* out, bool sym, d
   return rn <= 1e-20 * bn;   // 1e-10 relative: a sound factorisation (rounding only)
 }
 
+bool plan_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,
+                    int coarsest_size, int precision, Hierarchy& H, std::string& err) {
+  const bool try_large = coarsest_size == 2 || (coarsest_size == 0 && precision == 1);
+  if (try_large) {
+    if (!build_hierarchy(fine, neumann, modes, H, err, 32, 2048, true)) return false;
+    const bool keep = H.sep_stride > 0 && (coarsest_size == 2 || H.lv.size() >= 2);
+    if (keep) {
+      H.large = 1;
+      return true;
+    }
+  }
+  H = Hierarchy();
+  return build_hierarchy(fine, neumann, modes, H, err);
+}
+
 bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,
-                     Hierarchy& H, std::string& err) {
+                     Hierarchy& H, std::string& err, int min_side, int max_cells, bool sep_only) {
   H.lv.clear();
   PlaneGeo g = fine;
   g.build();
@@ -349,10 +365,11 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
     L.g = g;
     if (neumann) L.g.aW[1] = 0.0;
     H.lv.push_back(L);
-    // coarsen while the short side exceeds 16 cells, or exceeds 4 cells while
-    // the plane has more than 1024 (the coarsest level is solved exactly)
+    // coarsen while the short side exceeds min_side cells, or exceeds 4 cells
+    // while the plane has more than max_cells (the coarsest level is solved
+    // directly)
     const int mn = std::min(g.r.n, g.t.n);
-    if (!(mn > 16 || (mn > 4 && g.r.n * g.t.n > 1024))) break;
+    if (!(mn > min_side || (mn > 4 && g.r.n * g.t.n > max_cells))) break;
     if (g.r.n % 2 || g.t.n % 2) { err = "grid sizes must be powers of two"; return false; }
     PlaneGeo c;
     c.geometry = g.geometry; c.n_phi = g.n_phi; c.G = g.G;
@@ -510,6 +527,7 @@ bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>&
     H.sep_stride = 0;
     H.sep_sym = 0;
   }
+  if (sep_only) return true;   // the caller takes another rule
   const bool blocks = nr <= 64;
   H.blk_n = blocks ? nr : 0;
   H.blk_nt = blocks ? nt : 0;

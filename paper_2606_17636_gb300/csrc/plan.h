@@ -91,14 +91,26 @@ struct Hierarchy {
   int sep_stride = 0;
   int sep_sym = 0;
   double sep_check = -1.0;   // largest relative residual of the factors' check over the modes
+  int large = 0;             // 1: built with the large coarsest-level rule
 };
 
-// Build levels (coarsening stops at a short side of 8 cells, or 4 cells when
-// the plane would exceed 256 cells); neumann zeroes the inner radial
-// face coefficient on every level.  modes: list of azimuthal mode numbers
-// whose omega tables / coarse inverses are needed (index = plane-mode slot).
+// Build levels: halve both sides while the short side exceeds min_side
+// cells, or exceeds 4 cells while the plane has more than max_cells; neumann
+// zeroes the inner radial face coefficient on every level.  modes: list of
+// azimuthal mode numbers whose omega tables / coarse factors are needed
+// (index = plane-mode slot).  sep_only: compute the coarsest level's factors
+// only in the separable form (none when it does not apply).
 bool build_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,
-                     Hierarchy& H, std::string& err);
+                     Hierarchy& H, std::string& err, int min_side = 16, int max_cells = 1024,
+                     bool sep_only = false);
+
+// The levels for a coarsest-size choice (0 automatic, 1 small, 2 large; see
+// psolve_desc.coarsest_size) and precision (0 FP64, 1 mixed): the large rule
+// (short side up to 32, up to 2048 cells) is kept only when its coarsest
+// level has the separable form (and, automatic, for the mixed path with at
+// least two levels); otherwise the small rule (16, 1024).
+bool plan_hierarchy(const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,
+                    int coarsest_size, int precision, Hierarchy& H, std::string& err);
 
 
 struct BPoint {

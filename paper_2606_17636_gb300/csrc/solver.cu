@@ -67,7 +67,7 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
                     std::string& err) {
   opt = o;
   max_planes = mp;
-  if (!build_hierarchy(fine, neumann, modes, H, err)) return false;
+  if (!plan_hierarchy(fine, neumann, modes, opt.coarsest_size, opt.precision, H, err)) return false;
   const int nl = int(H.lv.size());
   // line lengths the level-wide passes hold in registers and shared memory:
   // at most 1024 cells (FP32) or 512 (FP64), and a staged polar tile that
@@ -136,16 +136,21 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   tmp = A.get(size_t(mp) * lv[0].nr * lv[0].nt * vb);
   if (!tmp) { err = "out of device memory"; return false; }
   // shared-memory V-cycle: the deepest levels whose error and right-hand
-  // side fit in 200 KB (lines of at most 128 cells)
+  // side fit next to the coarse-solve scratch (lines of at most 128 cells).
+  // The mixed path solves a separable coarsest level with FP32 polar
+  // transforms: scratch z (FP64) and its FP32 copy, 24 bytes per cell; the
+  // FP64 path keeps f and z in FP64, 32 bytes per cell.
+  const bool f32c = opt.precision && H.sep_stride > 0;
   first = nl - 1;
   {
-    const size_t zx_bytes = 4 * size_t(H.nc) * sizeof(double) + 16;   // FP64 coarse-solve scratch
+    const size_t zx_bytes = (f32c ? 24 : 32) * size_t(H.nc) + 16;
+    const size_t budget = (f32c ? 224 : 210) * 1024;
     size_t bytes = zx_bytes;
     const size_t tb = vb / 2;   // bytes of one real table entry
     for (int l = nl - 1; l >= 0; --l) {
       bytes += 2 * size_t(lv[l].nr) * lv[l].nt * vb;
       bytes += (size_t(RT_N) * (lv[l].nr + 2) + size_t(TT_N) * (lv[l].nt + 2) + lv[l].nr + lv[l].nt + 2) * tb;
-      if (bytes > 210 * 1024 || lv[l].nr > 128 || lv[l].nt > 128 || nl - l > 8) break;
+      if (bytes > budget || lv[l].nr > 128 || lv[l].nt > 128 || nl - l > 8) break;
       first = l;
     }
     vs.nlev = nl - first;
@@ -195,7 +200,7 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
     }
     size_t sbytes = (off * vb + tab * (vb / 2) + 15) / 16 * 16;
     vs.dbl_off = int(sbytes);
-    sbytes += 4 * size_t(H.nc) * sizeof(double);
+    sbytes += (f32c ? 24 : 32) * size_t(H.nc);
     vs.inv = d_inv;
     vs.blk = d_blk;
     vs.nc = H.nc;
@@ -209,7 +214,43 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
                                  : size_t(H.blk_nt) * H.blk_n * (H.blk_n + 2) * sizeof(double);
     vs.blk_smem = ((H.blk_n > 0 || H.sep_stride > 0) && sbytes + blk_bytes <= 220 * 1024) ? 1 : 0;
     vs.blk_off = int(sbytes);
-    if (vs.blk_smem) sbytes += blk_bytes;
+    vs.f32c = f32c ? 1 : 0;
+    vs.restage = 0;
+    vs.sepf = nullptr;
+    vs.sepf_stride = 0;
+    if (f32c) {
+      // FP32 copies of V, V^-1 and 1/pivot per slot; the radial sweeps'
+      // factors (upper/pivot, lower/pivot) stay FP64.  Staged factors: those
+      // two tables, then the FP32 block; in their own space when it fits,
+      // else over the first fused level's right-hand side (K >= 2: it is the
+      // kernel's input, staged again from global memory after the coarsest
+      // solve), else read from global memory.
+      const int nrc = lv[nl - 1].nr, ntc = lv[nl - 1].nt, vr = H.sep_sym ? ntc / 2 : ntc;
+      const size_t ncc = size_t(nrc) * ntc;
+      vs.sepf_stride = int((2 * size_t(vr) * ntc + ncc + 3) / 4 * 4);
+      const size_t S_ = modes.size();
+      std::vector<float> pf(S_ * size_t(vs.sepf_stride), 0.f);
+      for (size_t q = 0; q < S_; ++q) {
+        const double* Fq = H.coarse_sep.data() + q * H.sep_stride;
+        for (size_t x = 0; x < 2 * size_t(vr) * ntc + ncc; ++x) pf[q * vs.sepf_stride + x] = float(Fq[x]);
+      }
+      vs.sepf = upload(A, pf);
+      if (!vs.sepf) { err = "out of device memory"; return false; }
+      const size_t fac = 16 * ncc + 4 * size_t(vs.sepf_stride);
+      const size_t f0 = size_t(vs.L[0].nr) * vs.L[0].nt * vb;
+      if (sbytes + fac <= 224 * 1024) {
+        vs.blk_smem = 1;
+      } else if (vs.nlev >= 2 && fac <= f0) {
+        vs.blk_smem = 1;
+        vs.restage = 1;
+        vs.blk_off = int(size_t(vs.off_f[0]) * vb);
+      } else {
+        vs.blk_smem = 0;
+      }
+      if (vs.blk_smem && !vs.restage) sbytes += fac;
+    } else if (vs.blk_smem) {
+      sbytes += blk_bytes;
+    }
     vs.smem_bytes = sbytes + 16;
     if (H.nc < 16 || (H.nc & (H.nc - 1))) { err = "coarsest level must have a power-of-two size >= 16"; return false; }
     vs.nu1 = opt.nu1;
@@ -271,7 +312,7 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
         std::copy(hl.om_t.begin() + q * nr, hl.om_t.begin() + (q + 1) * nr, o);
       }
     d_tail_tabs = upload(A, pk);
-    if (H.sep_stride > 0) {
+    if (H.sep_stride > 0 && !H.large) {   // the tail kernel takes the small coarsest level only
       // per slot and eigenvalue k the two Thomas sweeps of the coarsest
       // radial systems applied to unit vectors: column m of A_k is the
       // sweeps' result for z = e_m (the tail applies them as one FP64
@@ -480,7 +521,7 @@ bool MGSolver::prepare_tail() {
   std::vector<int> nr(nl), nt(nl);
   for (int l = 0; l < nl; ++l) { nr[l] = lv[l].nr; nt[l] = lv[l].nt; }
   TailArgs t = tl;
-  if (!tail_layout(nr, nt, opt.n_sor, H.sep_stride > 0, t)) return false;
+  if (!tail_layout(nr, nt, opt.n_sor, H.sep_stride > 0 && !H.large, t)) return false;
   for (int l = 0; l < nl; ++l) {
     TailLevel& q = t.lv[l];
     q.L = lv[l];

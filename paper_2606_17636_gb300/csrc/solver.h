@@ -25,6 +25,7 @@ struct MGOptions {
   Tiles tiles;         // tile shapes of the level-wide smoothing passes
   int max_cycles = 100;
   int stagnation = 0;  // retire planes whose residual stops falling
+  int coarsest_size = 1;   // coarsest-level rule (psolve_desc.coarsest_size; 1: small)
 };
 
 // Shared-memory layout of the cluster-resident tail (k_tail.cu) for levels of

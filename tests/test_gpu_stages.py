@@ -243,3 +243,50 @@ def test_fused_vcycle_matches_oracle_vcycle(ps, key, precision, tol):
     err = np.abs(got - ref).max() / np.abs(ref).max()
     assert err <= tol, err
     s.close()
+
+
+# grids whose large-rule coarsest level differs from the small rule's:
+# 64 x 32 under a fused 128 x 64 level (full theta: the mirror-symmetric
+# form), 32 x 32 under 64 x 64 (cylinder with the axis), and 64 x 32 with an
+# off-centre polar range (the general separable form)
+LARGE = {
+    "sph_log_128x64": dict(geometry=0, n_r=128, n_tz=64, n_phi=8, spacing=1, r_in=0.05, r_out=20.0,
+                           t_min=None, t_max=None),
+    "cyl_axis_128x128": dict(geometry=1, n_r=128, n_tz=128, n_phi=8, spacing=0, r_in=0.0, r_out=1.0,
+                             t_min=-0.5, t_max=0.5),
+    "sph_band_128x64": dict(geometry=0, n_r=128, n_tz=64, n_phi=8, spacing=0, r_in=1.0, r_out=2.0,
+                            t_min=0.3 * np.pi, t_max=0.65 * np.pi),
+}
+
+
+@pytest.mark.parametrize("key", list(LARGE))
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-4)])
+def test_fused_vcycle_with_the_large_coarsest_level(ps, key, precision, tol):
+    """The fused V-cycle on the large coarsest-level rule (short side up to
+    32, up to 2048 cells; Sec. 3.3 leaves the size open), against the
+    oracle's V-cycle on the same levels.  The mixed path solves that level
+    with FP32 polar transforms around FP64 radial sweeps: its error stays
+    within the FP32 V-cycle's 1e-4."""
+    from oracle import mg
+    from oracle.geometry import Plane
+    sp = LARGE[key]
+    s = ps.Solver.from_spec(sp, precision=precision, use_graph=False, coarsest_size=ps.COARSEST_LARGE)
+    plan = ps.plan_inspect(sp, precision=precision, coarsest_size=ps.COARSEST_LARGE)
+    p = Plane.make(sp["geometry"], sp["n_r"], sp["n_tz"], sp["n_phi"], sp["spacing"], sp["r_in"], sp["r_out"],
+                   t_min=sp["t_min"], t_max=sp["t_max"])
+    H = mg.Hierarchy(p, min_cells=32, max_coarse=2048)
+    assert [(l.plane.n_r, l.plane.n_t) for l in H.levels] == plan["levels"]
+    assert s.n_levels == len(plan["levels"]) >= 2
+    lev = s.fused_level()
+    nr, nt, M = sp["n_r"] >> lev, sp["n_tz"] >> lev, s.n_modes
+    cdt = torch.complex128 if precision == 0 else torch.complex64
+    f = torch.from_numpy(_rand_planes((M, nt, nr), 60 + lev)).to(cdt).cuda()
+    got = s.stage_vcycle(f).cpu().numpy().astype(np.complex128)
+    fh = f.cpu().numpy().astype(np.complex128)
+    for m in range(M):
+        u = np.zeros((nr + 2, nt + 2), complex)
+        H.vcycle(lev, m, u, fh[m].T)
+        ref = u[1:-1, 1:-1].T
+        err = np.abs(got[m] - ref).max() / np.abs(ref).max()
+        assert err <= tol, (m, err)
+    s.close()

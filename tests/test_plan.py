@@ -1,6 +1,7 @@
 """The multigrid plan (psolve_plan_inspect), computed on the host with no
-GPU: the coarsening rule, the form of the exact coarsest solve (Sec. 3.3
-allows a direct solver) and its factor sizes, and argument checks."""
+GPU: the coarsening rules (small and large coarsest level), the form of the
+direct coarsest solve (Sec. 3.3 allows a direct solver) and its factor
+sizes, and argument checks."""
 import numpy as np
 import pytest
 
@@ -17,34 +18,59 @@ def ps():
     return m
 
 
-def _coarsen(nr, nt):
-    """The coarsening reading: halve both sides while the short side exceeds
-    16, or exceeds 4 with more than 1024 cells."""
+def _coarsen(nr, nt, side=16, cells=1024):
+    """The coarsening rule: halve both sides while the short side exceeds
+    `side`, or exceeds 4 with more than `cells` cells (small rule 16 / 1024,
+    large rule 32 / 2048)."""
     out = [(nr, nt)]
     while True:
         mn = min(nr, nt)
-        if not (mn > 16 or (mn > 4 and nr * nt > 1024)):
+        if not (mn > side or (mn > 4 and nr * nt > cells)):
             return out
         nr, nt = nr // 2, nt // 2
         out.append((nr, nt))
 
 
 def test_benchmark_grid_plan(ps):
-    p = ps.plan_inspect(wl.spec(wl.SPHERICAL, 256, 128, 256, wl.LOG, 0.05, 20.0))
+    sp = wl.spec(wl.SPHERICAL, 256, 128, 256, wl.LOG, 0.05, 20.0)
+    # the mixed path's automatic choice: the large coarsest level (64 x 32)
+    p = ps.plan_inspect(sp)
     assert p["n_modes"] == 129
-    assert p["levels"] == [(256, 128), (128, 64), (64, 32), (32, 16)]
+    assert p["levels"] == [(256, 128), (128, 64), (64, 32)]
     # full theta range: the polar operator is mirror-symmetric about the equator
     assert p["coarsest"] == "separable, mirror-symmetric"
     nr, nt = p["levels"][-1]
     # half of V and of V^-1 (nt^2 in all), three Thomas factor tables nt x nr
     assert p["coarse_doubles_per_mode"] == nt * nt + 3 * nt * nr
+    # the FP64 path, and the small rule on request: 32 x 16
+    for q in (ps.plan_inspect(sp, precision=0), ps.plan_inspect(sp, coarsest_size=ps.COARSEST_SMALL)):
+        assert q["levels"] == [(256, 128), (128, 64), (64, 32), (32, 16)]
+        assert q["coarsest"] == "separable, mirror-symmetric"
+    assert ps.plan_inspect(sp, precision=0, coarsest_size=ps.COARSEST_LARGE)["levels"] == p["levels"]
 
 
 @pytest.mark.parametrize("nr,nt", [(8, 8), (16, 8), (32, 32), (64, 16), (128, 8), (256, 16), (8, 128),
                                    (512, 256), (1024, 64), (64, 1024)])
 def test_levels_follow_the_coarsening_rule(ps, nr, nt):
-    p = ps.plan_inspect(wl.spec(wl.CYLINDRICAL, nr, nt, 8, wl.UNIFORM, 0.2, 1.0))
-    assert p["levels"] == _coarsen(nr, nt)
+    sp = wl.spec(wl.CYLINDRICAL, nr, nt, 8, wl.UNIFORM, 0.2, 1.0)
+    small, large = _coarsen(nr, nt), _coarsen(nr, nt, 32, 2048)
+    if max(nr, nt) <= 512:   # the FP64 path's line limit
+        assert ps.plan_inspect(sp, precision=0)["levels"] == small
+    assert ps.plan_inspect(sp, coarsest_size=ps.COARSEST_SMALL)["levels"] == small
+    # the large rule when the coarsest level is separable (at most 64 polar
+    # cells); the automatic choice takes it only with two levels or more
+    sep = large[-1][1] <= 64
+    assert ps.plan_inspect(sp, coarsest_size=ps.COARSEST_LARGE)["levels"] == (large if sep else small)
+    auto = large if sep and len(large) >= 2 else small
+    assert ps.plan_inspect(sp)["levels"] == auto
+
+
+def test_coarsest_size_is_checked(ps):
+    sp = wl.spec(wl.SPHERICAL, 32, 32, 8, wl.UNIFORM, 0.5, 2.0)
+    for bad in (-1, 3):
+        with pytest.raises(ps.PSolveError) as e:
+            ps.plan_inspect(sp, coarsest_size=bad)
+        assert e.value.code == ps.ERR_ARG and "coarsest_size" in str(e.value)
 
 
 def test_off_centre_polar_range_takes_the_general_separable_form(ps):
@@ -92,8 +118,9 @@ def test_invalid_descriptors_are_rejected(ps, bad, word):
     # factors' residual sits near 1e-12 in either separable form
     (wl.spec(wl.SPHERICAL, 256, 128, 16, wl.LOG, 0.05, 20.0), 1e-11),
     (wl.spec(wl.SPHERICAL, 128, 64, 16, wl.LOG, 0.1, 10.0), 1e-12),
-    # away from the poles both forms reach rounding level
-    (wl.spec(wl.SPHERICAL, 256, 128, 16, wl.LOG, 0.05, 20.0, 0.3 * np.pi, 0.7 * np.pi), 1e-13),
+    # away from the poles both forms reach rounding level (64 x 32 coarsest
+    # level for the mixed path's large rule here)
+    (wl.spec(wl.SPHERICAL, 256, 128, 16, wl.LOG, 0.05, 20.0, 0.3 * np.pi, 0.7 * np.pi), 2e-13),
     (wl.spec(wl.SPHERICAL, 32, 32, 8, wl.UNIFORM, 1.0, 2.0, 0.3 * np.pi, 0.65 * np.pi), 1e-13),
     (wl.spec(wl.CYLINDRICAL, 64, 64, 16, wl.UNIFORM, 0.0, 1.0), 1e-13),
     (wl.spec(wl.CYLINDRICAL, 512, 256, 16, wl.UNIFORM, 0.2, 4.0, -1.0, 1.0), 1e-13),
@@ -121,13 +148,17 @@ def test_tail_layout_of_the_benchmark_grid():
     import paper_2606_17636_gb300 as ps
     from paper_2606_17636_gb300 import workloads
     w3 = workloads.spec(workloads.SPHERICAL, 256, 128, 256, workloads.LOG, 0.05, 20.0)
+    small = dict(coarsest_size=ps.COARSEST_SMALL)
     for n_sor in (1, 2, 3):
-        p = ps.plan_inspect(w3, n_sor=n_sor)
+        p = ps.plan_inspect(w3, n_sor=n_sor, **small)
         assert p["tail_cluster_ctas"] == 16
         assert 0 < p["tail_smem_bytes"] <= 224 * 1024
-    assert ps.plan_inspect(w3, n_sor=1)["tail_smem_bytes"] < ps.plan_inspect(w3, n_sor=2)["tail_smem_bytes"]
-    assert ps.plan_inspect(w3, n_sor=4)["tail_cluster_ctas"] == 0
+    assert (ps.plan_inspect(w3, n_sor=1, **small)["tail_smem_bytes"]
+            < ps.plan_inspect(w3, n_sor=2, **small)["tail_smem_bytes"])
+    assert ps.plan_inspect(w3, n_sor=4, **small)["tail_cluster_ctas"] == 0
     assert ps.plan_inspect(w3, precision=0)["tail_cluster_ctas"] == 0
+    # the tail kernel takes the small coarsest level only
+    assert ps.plan_inspect(w3)["tail_cluster_ctas"] == 0
     # radial lines of 512 cells are beyond the tail kernel's line relaxation
     w4 = workloads.spec(workloads.CYLINDRICAL, 512, 256, 512, workloads.UNIFORM, 0.2, 4.0, -1.0, 1.0)
     assert ps.plan_inspect(w4)["tail_cluster_ctas"] == 0
