@@ -4,9 +4,9 @@
 // alternating zebra line relaxation), defect restriction, the coarsest
 // exact solve, prolongation and post-smoothing with block barriers instead
 // of kernel boundaries.  Input f[first] and output e[first] live in global
-// memory.  The coarsest level is solved directly: FP64 throughout in the
-// FP64 kernel; in the FP32 kernel a separable coarsest level takes FP32 polar
-// transforms around FP64 radial sweeps (coarsest_f32c).
+// memory.  The coarsest level is solved directly: in FP64 by the FP64
+// kernel; a separable coarsest level in FP32 by the FP32 kernel, with factors
+// computed in FP64 on the host (coarsest_f32c).
 //
 // Shared-memory layout of a level (nr x nt, unpadded rows): cell (j, i) sits
 // at j * nr + (i ^ h(j)).  The row swizzle h(j) < min(16, nr) follows the
@@ -415,134 +415,163 @@ __device__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, co
 
 // ---- separable coarsest level of the FP32 V-cycle --------------------------
 // L_m = L_r (x) I + D_r (x) L_t with L_t = V diag(lambda) V^-1 (Sec. 3.3
-// allows any direct solver).  The polar transforms run in FP32, the
-// arithmetic of the V-cycle around them; the radial systems
-// (L_r + lambda_k D_r), whose conditioning grows with the radial stretching,
-// are swept in FP64 with the factors computed in FP64 on the host.
+// allows any direct solver).  The FP32 V-cycle solves it in FP32 throughout,
+// with factors computed in FP64 on the host and rounded once: a coarse
+// correction only needs the solve of an operator close to the coarse one
+// (the rounding acts as a relative perturbation of order 1e-6, far inside
+// what leaves the V-cycle's contraction unchanged).
+// Factor block per slot (sepf, sepf_stride floats): V^-1 transposed
+// [vr][nt] (row j: V^-1[k][j] over k), V transposed [nt][vr] (row k: V[j][k]
+// over j < vr), 1/pivot [nt][nr], upper/pivot [nt][nr], lower/pivot [nt][nr];
+// vr = nt / 2 in the mirror-symmetric form (rows j < nt / 2 of V, columns
+// j < nt / 2 of V^-1), else nt.
 
-// Stage this slot's factors into shared memory at blk_off: the FP64
-// upper/pivot and lower/pivot tables [nt][nr] each, then the FP32 block
-// (V, V^-1, 1/pivot), all by asynchronous copies.
-__device__ __forceinline__ void stage_f32c(const VSmemArgs& a, int slot, unsigned char* vraw,
-                                           int nc, int vr, int nt) {
-  const double2* src = reinterpret_cast<const double2*>(a.sep + size_t(slot) * a.sep_stride +
-                                                        2 * size_t(vr) * nt + nc);
-  double2* dst = reinterpret_cast<double2*>(vraw + a.blk_off);
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) cp_async_v(dst + k, src + k, true);
+__device__ __forceinline__ void stage_f32c(const VSmemArgs& a, int slot, unsigned char* vraw) {
   const float4* fs = reinterpret_cast<const float4*>(a.sepf + size_t(slot) * a.sepf_stride);
-  float4* fd = reinterpret_cast<float4*>(vraw + a.blk_off + 16 * size_t(nc));
+  float4* fd = reinterpret_cast<float4*>(vraw + a.blk_off);
   for (int k = threadIdx.x; k < a.sepf_stride / 4; k += blockDim.x) cp_async_v(fd + k, fs + k, true);
 }
 
-// e = L_m^-1 f on the coarsest level Lc (cells in the FP32 swizzled layout).
-// Scratch at dbl_off: z [2][nt][nr] FP64, then zf [2][nt][nr] FP32.
+// KB consecutive entries of a factor row starting at p (16-byte aligned for KB = 4).
+template <int KB>
+__device__ __forceinline__ void ld_kb(float (&w)[KB], const float* p) {
+  if constexpr (KB == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < KB; ++q) w[q] = p[q];
+  }
+}
+
+// z = (1/pivot) .* ((V^-1 (x) I) f): each task takes KB eigenvalues k0 .. of
+// one part (mirror-symmetric: sums f_j + f_{nt-1-j} for the even
+// eigenvectors k < nt/2, differences for the odd ones) at one radial index,
+// both components, so every f value it loads feeds 2 KB products.
+template <int KB>
+__device__ void f32c_forward(const LevelDev& Lc, const float2* fc, const float* ViT, const float* invd,
+                             float* z, bool sym) {
+  const int nr = Lc.nr, nt = Lc.nt, nc = nr * nt, h = nt / 2, vr = sym ? h : nt;
+  const int kper = sym ? h : nt, nkb = kper / KB, ntask = (sym ? 2 : 1) * nr * nkb;
+  for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+    const int i = t % nr, rest = t / nr, kb = rest % nkb, part = rest / nkb;
+    const int k0 = part * h + kb * KB;
+    float ax[KB], ay[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) ax[q] = ay[q] = 0.f;
+    for (int j = 0; j < vr; ++j) {
+      float2 s = fc[vslot<float>(Lc, j, i)];
+      if (sym) {
+        const float2 v = fc[vslot<float>(Lc, nt - 1 - j, i)];
+        s = part ? make_float2(s.x - v.x, s.y - v.y) : make_float2(s.x + v.x, s.y + v.y);
+      }
+      float w[KB];
+      ld_kb<KB>(w, ViT + j * nt + k0);
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        ax[q] = fmaf(w[q], s.x, ax[q]);
+        ay[q] = fmaf(w[q], s.y, ay[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int k = k0 + q;
+      const float d = invd[k * nr + i];
+      z[k * nr + i] = ax[q] * d;
+      z[nc + k * nr + i] = ay[q] * d;
+    }
+  }
+}
+
+// e = (V (x) I) x: each task takes JB rows j0 .. (mirror-symmetric: j < nt/2,
+// writing e_j = E + O and e_{nt-1-j} = E - O from the even and odd
+// eigenvector parts) at one radial index, both components.
+template <int JB>
+__device__ void f32c_back(const LevelDev& Lc, const float* z, const float* VT, float2* ec, bool sym) {
+  const int nr = Lc.nr, nt = Lc.nt, nc = nr * nt, h = nt / 2, vr = sym ? h : nt;
+  const int njb = vr / JB, ntask = nr * njb;
+  for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+    const int i = t % nr, j0 = (t / nr) * JB;
+    float ex[JB], ey[JB], ox[JB], oy[JB];
+#pragma unroll
+    for (int q = 0; q < JB; ++q) ex[q] = ey[q] = ox[q] = oy[q] = 0.f;
+    const int ke = sym ? h : nt;
+    for (int k = 0; k < ke; ++k) {
+      const float xr = z[k * nr + i], xi = z[nc + k * nr + i];
+      float w[JB];
+      ld_kb<JB>(w, VT + k * vr + j0);
+#pragma unroll
+      for (int q = 0; q < JB; ++q) {
+        ex[q] = fmaf(w[q], xr, ex[q]);
+        ey[q] = fmaf(w[q], xi, ey[q]);
+      }
+    }
+    if (sym) {
+      for (int k = h; k < nt; ++k) {
+        const float xr = z[k * nr + i], xi = z[nc + k * nr + i];
+        float w[JB];
+        ld_kb<JB>(w, VT + k * vr + j0);
+#pragma unroll
+        for (int q = 0; q < JB; ++q) {
+          ox[q] = fmaf(w[q], xr, ox[q]);
+          oy[q] = fmaf(w[q], xi, oy[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < JB; ++q) {
+      const int j = j0 + q;
+      ec[vslot<float>(Lc, j, i)] = make_float2(ex[q] + ox[q], ey[q] + oy[q]);
+      if (sym) ec[vslot<float>(Lc, nt - 1 - j, i)] = make_float2(ex[q] - ox[q], ey[q] - oy[q]);
+    }
+  }
+}
+
+// e = L_m^-1 f on the coarsest level Lc (cells in the FP32 swizzled layout);
+// scratch z [2][nt][nr] FP32 at dbl_off.
 __device__ void coarsest_f32c(const VSmemArgs& a, int slot, unsigned char* vraw, const LevelDev& Lc,
                               const float2* fc, float2* ec) {
-  const int nr = Lc.nr, nt = Lc.nt, nc = nr * nt, h = nt / 2;
+  const int nr = Lc.nr, nt = Lc.nt, nc = nr * nt;
   const bool sym = a.sep_sym != 0;
-  const int vr = sym ? h : nt;
-  double* z = reinterpret_cast<double*>(vraw + a.dbl_off);
-  float* zf = reinterpret_cast<float*>(z + 2 * nc);
-  const double* cp;
-  const float* F;
-  if (a.blk_smem) {
-    cp = reinterpret_cast<const double*>(vraw + a.blk_off);
-    F = reinterpret_cast<const float*>(cp + 2 * nc);
-  } else {
-    cp = a.sep + size_t(slot) * a.sep_stride + 2 * size_t(vr) * nt + nc;
-    F = a.sepf + size_t(slot) * a.sepf_stride;
-  }
-  const double* lid = cp + nc;
-  const float* Vm = F;              // [vr][nt]
-  const float* Vi = Vm + vr * nt;   // [nt][vr]
-  const float* invd = Vi + nt * vr; // [nt][nr]
-  // f by component (mirror-symmetric: rows j < h hold f_j + f_{nt-1-j},
-  // rows h + j hold f_j - f_{nt-1-j})
-  if (sym) {
-    for (RowWalk w(threadIdx.x, blockDim.x, nr); w.j < h; w.next()) {
-      const float2 u = fc[vslot<float>(Lc, w.j, w.c)], v = fc[vslot<float>(Lc, nt - 1 - w.j, w.c)];
-      zf[w.j * nr + w.c] = u.x + v.x;
-      zf[(h + w.j) * nr + w.c] = u.x - v.x;
-      zf[nc + w.j * nr + w.c] = u.y + v.y;
-      zf[nc + (h + w.j) * nr + w.c] = u.y - v.y;
-    }
-  } else {
-    for (RowWalk w(threadIdx.x, blockDim.x, nr); w.j < nt; w.next()) {
-      const float2 v = fc[vslot<float>(Lc, w.j, w.c)];
-      zf[w.j * nr + w.c] = v.x;
-      zf[nc + w.j * nr + w.c] = v.y;
-    }
-  }
+  const int vr = sym ? nt / 2 : nt;
+  float* z = reinterpret_cast<float*>(vraw + a.dbl_off);
+  const float* ViT = a.blk_smem ? reinterpret_cast<const float*>(vraw + a.blk_off)
+                                : a.sepf + size_t(slot) * a.sepf_stride;
+  const float* VT = ViT + vr * nt;
+  const float* invd = VT + nt * vr;
+  const float* cp = invd + nc;
+  const float* lid = cp + nc;
+  if (vr % 4 == 0) f32c_forward<4>(Lc, fc, ViT, invd, z, sym);
+  else f32c_forward<1>(Lc, fc, ViT, invd, z, sym);
   __syncthreads();
-  // z = (1/pivot) .* ((V^-1 (x) I) f), FP32, widened exactly to FP64
-  for (int q = threadIdx.x; q < 2 * nc; q += blockDim.x) {
-    const int c = q / nc, r = q - c * nc, k = r / nr, i = r - k * nr;
-    const float* col = zf + c * nc + (sym && k >= h ? h * nr : 0) + i;
-    const float* vk = Vi + k * vr;
-    float acc = 0.f;
-    for (int j = 0; j < vr; ++j) acc = fmaf(vk[j], col[j * nr], acc);
-    z[q] = f32_to_f64(acc * invd[k * nr + i]);
-  }
-  __syncthreads();
-  // Thomas sweeps per (component, eigenvalue), FP64, one FMA per step each
-  // way: dp_i = z_i - lid_i dp_{i-1}, then x_i = dp_i - cp_i x_{i+1},
-  // rounded to FP32 into zf.  The 2 nt systems run on the first four warps
-  // (one per scheduler: the FP64 pipe is narrow).
+  // Thomas sweeps per (component, eigenvalue), one FMA per step each way:
+  // dp_i = z_i - lid_i dp_{i-1}, then x_i = dp_i - cp_i x_{i+1}, in place;
+  // the 2 nt systems on the first four warps
   {
     const int nsys = 2 * nt, per = (nsys + 3) / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < 4 && lane < per && warp * per + lane < nsys) {
       const int q = warp * per + lane, c = q / nt, k = q - c * nt;
-      double* __restrict__ zz = z + c * nc + k * nr;
-      float* __restrict__ xo = zf + c * nc + k * nr;
-      const double* __restrict__ lk = lid + k * nr;
-      const double* __restrict__ ck = cp + k * nr;
-      double dp = zz[0];
-#pragma unroll 4
+      float* __restrict__ zz = z + c * nc + k * nr;
+      const float* __restrict__ lk = lid + k * nr;
+      const float* __restrict__ ck = cp + k * nr;
+      float dp = zz[0];
+#pragma unroll 8
       for (int i = 1; i < nr; ++i) {
-        dp = fma(-lk[i], dp, zz[i]);
+        dp = fmaf(-lk[i], dp, zz[i]);
         zz[i] = dp;
       }
-      double xv = dp;
-      xo[nr - 1] = f64_to_f32(xv);
-#pragma unroll 4
+      float xv = dp;
+#pragma unroll 8
       for (int i = nr - 2; i >= 0; --i) {
-        xv = fma(-ck[i], xv, zz[i]);
-        xo[i] = f64_to_f32(xv);
+        xv = fmaf(-ck[i], xv, zz[i]);
+        zz[i] = xv;
       }
     }
   }
   __syncthreads();
-  // e = (V (x) I) x, FP32 (mirror-symmetric: e_j = E + O and
-  // e_{nt-1-j} = E - O from the even and odd eigenvector parts)
-  if (sym) {
-    for (int q = threadIdx.x; q < h * nr; q += blockDim.x) {
-      const int j = q / nr, i = q - j * nr;
-      const float* vj = Vm + j * nt;
-      float ex = 0.f, ey = 0.f, ox = 0.f, oy = 0.f;
-      for (int k = 0; k < h; ++k) {
-        ex = fmaf(vj[k], zf[k * nr + i], ex);
-        ey = fmaf(vj[k], zf[nc + k * nr + i], ey);
-      }
-      for (int k = h; k < nt; ++k) {
-        ox = fmaf(vj[k], zf[k * nr + i], ox);
-        oy = fmaf(vj[k], zf[nc + k * nr + i], oy);
-      }
-      ec[vslot<float>(Lc, j, i)] = make_float2(ex + ox, ey + oy);
-      ec[vslot<float>(Lc, nt - 1 - j, i)] = make_float2(ex - ox, ey - oy);
-    }
-  } else {
-    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
-      const int j = q / nr, i = q - j * nr;
-      const float* vj = Vm + j * nt;
-      float ax = 0.f, ay = 0.f;
-      for (int k = 0; k < nt; ++k) {
-        ax = fmaf(vj[k], zf[k * nr + i], ax);
-        ay = fmaf(vj[k], zf[nc + k * nr + i], ay);
-      }
-      ec[vslot<float>(Lc, j, i)] = make_float2(ax, ay);
-    }
-  }
+  if (vr % 4 == 0) f32c_back<4>(Lc, z, VT, ec, sym);
+  else f32c_back<1>(Lc, z, VT, ec, sym);
   __syncthreads();
 }
 
@@ -603,7 +632,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     // now unless it shares the first level's right-hand side space
     if constexpr (sizeof(T) == 4) {
       if (a.blk_smem && !a.restage)
-        stage_f32c(a, slot, vraw, Lcst.nr * Lcst.nt, a.sep_sym ? Lcst.nt / 2 : Lcst.nt, Lcst.nt);
+        stage_f32c(a, slot, vraw);
     }
   } else if (a.blk_smem) {
     const double2* src = reinterpret_cast<const double2*>(
@@ -635,7 +664,7 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
   if (a.f32c) {
     if constexpr (sizeof(T) == 4) {
       if (a.restage) {   // the factors take the first level's right-hand side space
-        stage_f32c(a, slot, vraw, Lcst.nr * Lcst.nt, a.sep_sym ? Lcst.nt / 2 : Lcst.nt, Lcst.nt);
+        stage_f32c(a, slot, vraw);
         cp_async_wait_all();
         __syncthreads();
       }

@@ -137,12 +137,12 @@ struct VSmemArgs {
   const double* sep;     // separable coarsest-level factors [slots][sep_stride] (sep_stride > 0)
   int sep_stride;
   int sep_sym;           // mirror-symmetric separable layout (see Hierarchy::sep_sym)
-  // FP32 V-cycle with a separable coarsest level: polar transforms in FP32
-  // (sepf per slot: V, V^-1 and 1/pivot as floats, sepf_stride floats), the
-  // radial sweeps in FP64 with sep's upper/pivot and lower/pivot tables.
-  // Staged factors (blk_smem) hold those two tables, then the FP32 block;
-  // restage = 1: they lie over the first level's right-hand side, which is
-  // copied in again from the input after the coarsest solve.
+  // FP32 V-cycle with a separable coarsest level, solved in FP32: sepf per
+  // slot (sepf_stride floats) holds V^-1 transposed [vr][nt], V transposed
+  // [nt][vr], then 1/pivot, upper/pivot and lower/pivot [nt][nr] each, all
+  // rounded once from the FP64 factors.  blk_smem: staged at blk_off;
+  // restage = 1: over the first level's right-hand side, which is copied in
+  // again from the input after the coarsest solve.
   int f32c, restage;
   const float* sepf;
   int sepf_stride;

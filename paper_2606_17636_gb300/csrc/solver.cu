@@ -137,13 +137,12 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   if (!tmp) { err = "out of device memory"; return false; }
   // shared-memory V-cycle: the deepest levels whose error and right-hand
   // side fit next to the coarse-solve scratch (lines of at most 128 cells).
-  // The mixed path solves a separable coarsest level with FP32 polar
-  // transforms: scratch z (FP64) and its FP32 copy, 24 bytes per cell; the
-  // FP64 path keeps f and z in FP64, 32 bytes per cell.
+  // The mixed path solves a separable coarsest level in FP32 (scratch z,
+  // 8 bytes per cell); the FP64 path keeps f and z in FP64, 32 bytes per cell.
   const bool f32c = opt.precision && H.sep_stride > 0;
   first = nl - 1;
   {
-    const size_t zx_bytes = (f32c ? 24 : 32) * size_t(H.nc) + 16;
+    const size_t zx_bytes = (f32c ? 8 : 32) * size_t(H.nc) + 16;
     const size_t budget = (f32c ? 224 : 210) * 1024;
     size_t bytes = zx_bytes;
     const size_t tb = vb / 2;   // bytes of one real table entry
@@ -200,7 +199,7 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
     }
     size_t sbytes = (off * vb + tab * (vb / 2) + 15) / 16 * 16;
     vs.dbl_off = int(sbytes);
-    sbytes += (f32c ? 24 : 32) * size_t(H.nc);
+    sbytes += (f32c ? 8 : 32) * size_t(H.nc);
     vs.inv = d_inv;
     vs.blk = d_blk;
     vs.nc = H.nc;
@@ -219,24 +218,32 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
     vs.sepf = nullptr;
     vs.sepf_stride = 0;
     if (f32c) {
-      // FP32 copies of V, V^-1 and 1/pivot per slot; the radial sweeps'
-      // factors (upper/pivot, lower/pivot) stay FP64.  Staged factors: those
-      // two tables, then the FP32 block; in their own space when it fits,
-      // else over the first fused level's right-hand side (K >= 2: it is the
+      // the FP32 factor block per slot (see VSmemArgs::sepf), rounded once
+      // from the FP64 factors; staged in its own space when it fits, else
+      // over the first fused level's right-hand side (K >= 2: it is the
       // kernel's input, staged again from global memory after the coarsest
-      // solve), else read from global memory.
+      // solve), else read from global memory
       const int nrc = lv[nl - 1].nr, ntc = lv[nl - 1].nt, vr = H.sep_sym ? ntc / 2 : ntc;
       const size_t ncc = size_t(nrc) * ntc;
-      vs.sepf_stride = int((2 * size_t(vr) * ntc + ncc + 3) / 4 * 4);
+      vs.sepf_stride = int((2 * size_t(vr) * ntc + 3 * ncc + 3) / 4 * 4);
       const size_t S_ = modes.size();
       std::vector<float> pf(S_ * size_t(vs.sepf_stride), 0.f);
       for (size_t q = 0; q < S_; ++q) {
-        const double* Fq = H.coarse_sep.data() + q * H.sep_stride;
-        for (size_t x = 0; x < 2 * size_t(vr) * ntc + ncc; ++x) pf[q * vs.sepf_stride + x] = float(Fq[x]);
+        const double* Vm = H.coarse_sep.data() + q * H.sep_stride;   // [vr][nt]
+        const double* Vi = Vm + size_t(vr) * ntc;                     // [nt][vr]
+        const double* rest = Vi + size_t(ntc) * vr;                   // 1/pivot, upper, lower
+        float* o = pf.data() + q * vs.sepf_stride;
+        for (int j = 0; j < vr; ++j)
+          for (int k = 0; k < ntc; ++k) o[size_t(j) * ntc + k] = float(Vi[size_t(k) * vr + j]);
+        o += size_t(vr) * ntc;
+        for (int k = 0; k < ntc; ++k)
+          for (int j = 0; j < vr; ++j) o[size_t(k) * vr + j] = float(Vm[size_t(j) * ntc + k]);
+        o += size_t(ntc) * vr;
+        for (size_t x = 0; x < 3 * ncc; ++x) o[x] = float(rest[x]);
       }
       vs.sepf = upload(A, pf);
       if (!vs.sepf) { err = "out of device memory"; return false; }
-      const size_t fac = 16 * ncc + 4 * size_t(vs.sepf_stride);
+      const size_t fac = 4 * size_t(vs.sepf_stride);
       const size_t f0 = size_t(vs.L[0].nr) * vs.L[0].nt * vb;
       if (sbytes + fac <= 224 * 1024) {
         vs.blk_smem = 1;
