@@ -94,10 +94,12 @@ typedef struct {
                           PSOLVE_COARSEST_AUTO (0): the large rule for the
                           mixed path when it leaves at least two levels, the
                           small rule otherwise and for the FP64 path.  The
-                          mixed path solves a separable coarsest level with
-                          FP32 polar transforms and FP64 radial sweeps, the
-                          FP64 path in FP64 throughout; other values are
-                          PSOLVE_ERR_ARG                                      */
+                          mixed path's FP32 V-cycle solves a separable
+                          coarsest level in FP32 (factors computed in FP64
+                          and rounded once: a coarse correction needs only a
+                          nearby operator's solve), the FP64 path in FP64;
+                          the cluster-resident tail needs the small rule.
+                          Other values are PSOLVE_ERR_ARG                      */
 } psolve_desc;
 
 enum { PSOLVE_DGF_AUTO = 0, PSOLVE_DGF_AUX = 1, PSOLVE_DGF_EXTENDED = 2 };
