@@ -152,7 +152,9 @@ __device__ __forceinline__ void b_zero(float2 (&d)[CPL]) {
 
 // Radial lines (rows), nr = 32 CPL, nt = B * warps.  Order: even row j0,
 // then per k the even row j0 + 2k and the odd row j0 + 2k - 1 below it, each
-// row stored once final; the last odd row after the barrier.
+// row stored once final; the last odd row after the barrier.  The rows move
+// through a window of registers in a loop, so the code holds four line
+// relaxations whatever B (the instruction cache is the kernel's limit).
 template <int CPL, int B>
 __device__ __forceinline__ void band_r(const LevelDev& L, float2* e, const float2* f, float s2,
                                        int n_sor) {
@@ -162,39 +164,46 @@ __device__ __forceinline__ void band_r(const LevelDev& L, float2* e, const float
   const float* om = L.omr_f;
   RLineTabs<float, CPL> tabs;
   ld_rtabs<float, CPL>(tabs, L, L.rf);
-  float2 u[B + 2][CPL];   // u[r] = row j0 - 1 + r
-#pragma unroll
-  for (int r = 0; r <= B; ++r) {
-    const int j = j0 - 1 + r;
-    if (j >= 0) b_ld_row<CPL>(u[r], e + j * nr, vswz<float>(L, j), lane);
-    else b_zero<CPL>(u[r]);
-  }
-  auto relax = [&](int r) {   // row j0 - 1 + r between rows r - 1 and r + 1
-    const int j = j0 - 1 + r;
+  auto ld = [&](float2 (&d)[CPL], const float2* a, int j) { b_ld_row<CPL>(d, a + j * nr, vswz<float>(L, j), lane); };
+  auto relax = [&](int j, float2 (&un)[CPL], float2 (&us)[CPL], float2 (&ev)[CPL]) {
     float2 g[CPL];
-    b_ld_row<CPL>(g, f + j * nr, vswz<float>(L, j), lane);
-    relax_r<float, CPL>(L, tabs, tt, s2, om[j], j, g, u[r + 1], u[r - 1], n_sor, u[r]);
-    b_st_row<CPL>(e + j * nr, vswz<float>(L, j), u[r], lane);
+    ld(g, f, j);
+    relax_r<float, CPL>(L, tabs, tt, s2, om[j], j, g, un, us, n_sor, ev);
+    b_st_row<CPL>(e + j * nr, vswz<float>(L, j), ev, lane);
   };
-  relax(1);
+  // P: the even row j0 + 2k - 2 (relaxed), Q: the odd row j0 + 2k - 1
+  float2 M[CPL], P[CPL], Q[CPL];
+  if (j0 > 0) ld(M, e, j0 - 1);
+  else b_zero<CPL>(M);
+  ld(P, e, j0);
+  ld(Q, e, j0 + 1);
+  relax(j0, Q, M, P);
+  if constexpr (B > 2) {
+#pragma unroll 1
+    for (int k = 1; k < B / 2; ++k) {
+      float2 R[CPL], S[CPL];
+      ld(R, e, j0 + 2 * k);
+      ld(S, e, j0 + 2 * k + 1);
+      relax(j0 + 2 * k, S, Q, R);
+      relax(j0 + 2 * k - 1, R, P, Q);
 #pragma unroll
-  for (int k = 1; k < B / 2; ++k) {
-    relax(2 * k + 1);
-    relax(2 * k);
+      for (int c = 0; c < CPL; ++c) {
+        P[c] = R[c];
+        Q[c] = S[c];
+      }
+    }
   }
   __syncthreads();
-  {
-    const int ja = j0 + B;
-    if (ja < nt) b_ld_row<CPL>(u[B + 1], e + ja * nr, vswz<float>(L, ja), lane);
-    else b_zero<CPL>(u[B + 1]);
-  }
-  relax(B);
+  float2 A[CPL];
+  if (j0 + B < nt) ld(A, e, j0 + B);
+  else b_zero<CPL>(A);
+  relax(j0 + B - 1, A, P, Q);
 }
 
 // Polar lines (columns), nt = 32 CPL, nr = B * warps; the lane's cells are the
-// rows lcell(lane, c).  Same order as the rows; the two columns of a pair are
-// stored together once both are final (column i0 alone when B = 2: the band
-// to the left reads it after the barrier).
+// rows lcell(lane, c).  Same order and window as the rows; the two columns of
+// a pair are stored together once both are final (column i0 alone when
+// B = 2: the band to the left reads it after the barrier).
 template <int CPL, int B>
 __device__ __forceinline__ void band_t(const LevelDev& L, float2* e, const float2* f, float s2,
                                        int n_sor) {
@@ -211,49 +220,59 @@ __device__ __forceinline__ void band_t(const LevelDev& L, float2* e, const float
     base[c] = j * nr;
     sw[c] = vswz<float>(L, j);
   }
-  float2 u[B + 2][CPL];   // u[r] = column i0 - 1 + r
-  float2 g[B][CPL];       // right-hand side of column i0 + r at g[r]
+  auto ld_col = [&](float2 (&d)[CPL], int i) {
 #pragma unroll
-  for (int c = 0; c < CPL; ++c) {
-    u[0][c] = i0 > 0 ? e[base[c] + ((i0 - 1) ^ sw[c])] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < B / 2; ++k) ld_pair(u[2 * k + 1][c], u[2 * k + 2][c], e + base[c] + ((i0 + 2 * k) ^ sw[c]));
-  }
-  auto relax = [&](int r) {   // column i0 - 1 + r between columns r - 1 and r + 1
-    const int i = i0 - 1 + r;
-    if ((r & 1) == 1) {   // even column: its pair brings the odd column's right-hand side
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) ld_pair(g[r - 1][c], g[r][c], f + base[c] + (i ^ sw[c]));
-    }
-    relax_t<float, CPL>(L, rt, tabs, s2, om[i], i, g[r - 1], u[r + 1], u[r - 1], n_sor, u[r]);
+    for (int c = 0; c < CPL; ++c) d[c] = e[base[c] + (i ^ sw[c])];
   };
-  auto store_pair = [&](int k) {   // columns i0 + 2k, i0 + 2k + 1
+  auto ld_pr = [&](float2 (&x)[CPL], float2 (&y)[CPL], const float2* a, int i) {   // columns i, i + 1
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) st_pair(e + base[c] + ((i0 + 2 * k) ^ sw[c]), u[2 * k + 1][c], u[2 * k + 2][c]);
+    for (int c = 0; c < CPL; ++c) ld_pair(x[c], y[c], a + base[c] + (i ^ sw[c]));
   };
-  relax(1);
+  auto st_pr = [&](const float2 (&x)[CPL], const float2 (&y)[CPL], int i) {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) st_pair(e + base[c] + (i ^ sw[c]), x[c], y[c]);
+  };
+  auto relax = [&](int i, float2 (&g)[CPL], float2 (&ue)[CPL], float2 (&uw)[CPL], float2 (&ev)[CPL]) {
+    relax_t<float, CPL>(L, rt, tabs, s2, om[i], i, g, ue, uw, n_sor, ev);
+  };
+  // P, Q: the columns i0 + 2k - 2 (relaxed) and i0 + 2k - 1; gQ: Q's right-hand side
+  float2 M[CPL], P[CPL], Q[CPL], gP[CPL], gQ[CPL];
+  if (i0 > 0) ld_col(M, i0 - 1);
+  else b_zero<CPL>(M);
+  ld_pr(P, Q, e, i0);
+  ld_pr(gP, gQ, f, i0);
+  relax(i0, gP, Q, M, P);
   if constexpr (B == 2) {
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) e[base[c] + (i0 ^ sw[c])] = u[1][c];
-  }
+    for (int c = 0; c < CPL; ++c) e[base[c] + (i0 ^ sw[c])] = P[c];
+  } else {
+#pragma unroll 1
+    for (int k = 1; k < B / 2; ++k) {
+      const int i = i0 + 2 * k;
+      float2 R[CPL], S[CPL], gR[CPL], gS[CPL];
+      ld_pr(R, S, e, i);
+      ld_pr(gR, gS, f, i);
+      relax(i, gR, S, Q, R);
+      relax(i - 1, gQ, R, P, Q);
+      st_pr(P, Q, i - 2);
 #pragma unroll
-  for (int k = 1; k < B / 2; ++k) {
-    relax(2 * k + 1);
-    relax(2 * k);
-    store_pair(k - 1);
+      for (int c = 0; c < CPL; ++c) {
+        P[c] = R[c];
+        Q[c] = S[c];
+        gQ[c] = gS[c];
+      }
+    }
   }
   __syncthreads();
-  {
-    const int ia = i0 + B;
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) u[B + 1][c] = ia < nr ? e[base[c] + (ia ^ sw[c])] : make_float2(0.f, 0.f);
-  }
-  relax(B);
+  float2 A[CPL];
+  if (i0 + B < nr) ld_col(A, i0 + B);
+  else b_zero<CPL>(A);
+  relax(i0 + B - 1, gQ, A, P, Q);
   if constexpr (B == 2) {
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) e[base[c] + ((i0 + 1) ^ sw[c])] = u[2][c];
+    for (int c = 0; c < CPL; ++c) e[base[c] + ((i0 + 1) ^ sw[c])] = Q[c];
   } else {
-    store_pair(B / 2 - 1);
+    st_pr(P, Q, i0 + B - 2);
   }
 }
 

@@ -205,6 +205,7 @@ __device__ __forceinline__ void sor_line(vec2_t<T> (&ev)[CPL], const vec2_t<T> (
   };
   if constexpr (CPL == 1) {
     const bool on = lane < n, last = lane == n - 1;
+#pragma unroll 1
     for (int it = 0; it < n_sor; ++it) {
 #pragma unroll
       for (int par = 0; par < 2; ++par) {
@@ -218,6 +219,7 @@ __device__ __forceinline__ void sor_line(vec2_t<T> (&ev)[CPL], const vec2_t<T> (
   } else {
     constexpr int NP = CPL / 2;
     const int prv = (lane + 31) & 31, nxt = (lane + 1) & 31;
+#pragma unroll 1
     for (int it = 0; it < n_sor; ++it) {
       V r[NP];
 #pragma unroll
