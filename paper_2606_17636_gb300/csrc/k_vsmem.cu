@@ -432,6 +432,123 @@ __device__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, co
   __syncthreads();
 }
 
+// ---- FP32 restriction and prolongation with vector accesses ---------------
+// The same formulas, operands and order of operations as s_restrict and
+// s_prolong (so the same results); a coarse cell's two fine columns
+// 2I, 2I + 1 form an aligned pair (one 16-byte access per fine row, even
+// swizzle), and so do the table entries of two neighbouring cells (one
+// 8-byte access).  Needs an even number of fine columns and rows.
+
+__device__ __forceinline__ float2 tab2(const float* t, int id, int n, int i) {   // entries of cells i, i + 1
+  return *reinterpret_cast<const float2*>(t + id * (n + 2) + i + 1);
+}
+
+__device__ void s_restrict_f32(const LevelDev& L, const LevelDev& C, const float2* e, const float2* f,
+                               float2* fc, float s2) {
+  const int nr = L.nr, nt = L.nt;
+  const float* rt = L.rf;
+  const float* tt = L.tf;
+  const float2 z = make_float2(0.f, 0.f);
+  for (RowWalk w(threadIdx.x, blockDim.x, C.nr); w.j < C.nt; w.next()) {
+    const int J = w.j, I = w.c, i0 = 2 * I, j0 = 2 * J;
+    // e on rows j0 - 1 .. j0 + 2 at columns i0, i0 + 1; the W and E neighbours on rows j0, j0 + 1
+    float2 r[4][2], W[2], E[2], fv[2][2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 - 1 + q;
+      if (j >= 0 && j < nt) ld_pair(r[q][0], r[q][1], e + vslot<float>(L, j, i0));
+      else r[q][0] = r[q][1] = z;
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int j = j0 + b;
+      W[b] = i0 > 0 ? e[vslot<float>(L, j, i0 - 1)] : z;
+      E[b] = i0 + 2 < nr ? e[vslot<float>(L, j, i0 + 2)] : z;
+      ld_pair(fv[b][0], fv[b][1], f + vslot<float>(L, j, i0));
+    }
+    const float2 AE = tab2(rt, RT_AE, nr, i0), AW = tab2(rt, RT_AW, nr, i0), PP = tab2(rt, RT_P, nr, i0);
+    const float2 DR = tab2(rt, RT_DR, nr, i0), QQ = tab2(rt, RT_Q, nr, i0), RW = tab2(rt, RT_RW, nr, i0);
+    const float2 AN = tab2(tt, TT_AN, nt, j0), AS = tab2(tt, TT_AS, nt, j0), DT = tab2(tt, TT_DT, nt, j0);
+    const float2 TT2 = tab2(tt, TT_T, nt, j0), TW = tab2(tt, TT_RW, nt, j0);
+    float ax = 0, ay = 0;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const float2 c = r[b + 1][a];
+        const float2 Ev = a ? E[b] : r[b + 1][1];
+        const float2 Wv = a ? r[b + 1][0] : W[b];
+        const float2 N = r[b + 2][a], S = r[b][a];
+        const float aE = a ? AE.y : AE.x, aW = a ? AW.y : AW.x, P = a ? PP.y : PP.x;
+        const float aN = P * (b ? AN.y : AN.x), aS = P * (b ? AS.y : AS.x);
+        const float d = fmac(-(s2 * (a ? QQ.y : QQ.x)), b ? TT2.y : TT2.x, fmac(P, b ? DT.y : DT.x, a ? DR.y : DR.x));
+        const float rx = fv[b][a].x - fmac(d, c.x, fmac(aS, S.x, fmac(aN, N.x, fmac(aW, Wv.x, aE * Ev.x))));
+        const float ry = fv[b][a].y - fmac(d, c.y, fmac(aS, S.y, fmac(aN, N.y, fmac(aW, Wv.y, aE * Ev.y))));
+        const float wgt = (a ? RW.y : RW.x) * (b ? TW.y : TW.x);
+        ax = fmac(wgt, rx, ax);
+        ay = fmac(wgt, ry, ay);
+      }
+    fc[vslot<float>(C, J, I)] = make_float2(ax, ay);
+  }
+  __syncthreads();
+}
+
+__device__ void s_prolong_f32(const LevelDev& L, const LevelDev& C, float2* e, const float2* ec, int m) {
+  const float* rt = L.rf;
+  const float* tt = L.tf;
+  const int nr = L.nr, nt = L.nt;
+  for (RowWalk w(threadIdx.x, blockDim.x, C.nr); w.j < C.nt; w.next()) {
+    const int J = w.j, I = w.c;
+    // coarse (I - 1 + u, J - 1 + v), 1-based index I + u, J + v: the ghost
+    // rules of s_cval chosen per column and row without branching (the same
+    // values: zero, the mirrored cell, or its negative for odd m across a
+    // parity face, twice negated across two)
+    int ic[3], jc[3];
+    bool zc[3], zr[3], nc[3], nrw[3];
+    const bool odd = (m & 1) != 0;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int x = I + u, rule = x == 0 ? C.gL : (x == C.nr + 1 ? C.gR : -1);
+      ic[u] = min(max(x, 1), C.nr) - 1;
+      zc[u] = rule == GH_ZERO;
+      nc[u] = rule == GH_PARITY && odd;
+      const int y = J + u, rr = y == 0 ? C.gB : (y == C.nt + 1 ? C.gT : -1);
+      jc[u] = min(max(y, 1), C.nt) - 1;
+      zr[u] = rr == GH_ZERO;
+      nrw[u] = rr == GH_PARITY && odd;
+    }
+    float2 cv[3][3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const float2 x = ec[vslot<float>(C, jc[v], ic[u])];
+        cv[v][u] = (zc[u] || zr[v]) ? make_float2(0.f, 0.f) : ((nc[u] != nrw[v]) ? make_float2(-x.x, -x.y) : x);
+      }
+    const int i0 = 2 * I;
+    const float2 P1 = tab2(rt, RT_P1, nr, i0), P2 = tab2(rt, RT_P2, nr, i0);
+    const float2 Q1 = tab2(tt, TT_P1, nt, 2 * J), Q2 = tab2(tt, TT_P2, nt, 2 * J);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int j = 2 * J + b;
+      const float q1 = b ? Q1.y : Q1.x, q2 = b ? Q2.y : Q2.x;
+      float2 uu[2];
+      float2* row = e + vslot<float>(L, j, i0);
+      ld_pair(uu[0], uu[1], row);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const float p1 = a ? P1.y : P1.x, p2 = a ? P2.y : P2.x;
+        const float2 A = cv[b][a], Bv = cv[b][a + 1], Cv = cv[b + 1][a], D = cv[b + 1][a + 1];
+        const float w11 = p1 * q1, w21 = p2 * q1, w12 = p1 * q2, w22 = p2 * q2;
+        uu[a].x += fmac(w22, D.x, fmac(w12, Cv.x, fmac(w21, Bv.x, w11 * A.x)));
+        uu[a].y += fmac(w22, D.y, fmac(w12, Cv.y, fmac(w21, Bv.y, w11 * A.y)));
+      }
+      st_pair(row, uu[0], uu[1]);
+    }
+  }
+  __syncthreads();
+}
+
 // ---- separable coarsest level of the FP32 V-cycle --------------------------
 // L_m = L_r (x) I + D_r (x) L_t with L_t = V diag(lambda) V^-1 (Sec. 3.3
 // allows any direct solver).  The FP32 V-cycle solves it in FP32 throughout,
@@ -441,9 +558,11 @@ __device__ void s_prolong(const LevelDev& L, const LevelDev& C, vec2_t<T>* e, co
 // what leaves the V-cycle's contraction unchanged).
 // Factor block per slot (sepf, sepf_stride floats): V^-1 transposed
 // [vr][nt] (row j: V^-1[k][j] over k), V transposed [nt][vr] (row k: V[j][k]
-// over j < vr), 1/pivot [nt][nr], upper/pivot [nt][nr], lower/pivot [nt][nr];
-// vr = nt / 2 in the mirror-symmetric form (rows j < nt / 2 of V, columns
-// j < nt / 2 of V^-1), else nt.
+// over j < vr), then 1/pivot, upper/pivot and lower/pivot [nt][nr + 1]
+// (rows padded by one entry, so that the lanes of the radial sweeps, one
+// eigenvalue k each, fall in different banks); vr = nt / 2 in the
+// mirror-symmetric form (rows j < nt / 2 of V, columns j < nt / 2 of V^-1),
+// else nt.  The scratch z has the same padded rows.
 
 __device__ __forceinline__ void stage_f32c(const VSmemArgs& a, int slot, unsigned char* vraw) {
   const float4* fs = reinterpret_cast<const float4*>(a.sepf + size_t(slot) * a.sepf_stride);
@@ -470,7 +589,7 @@ __device__ __forceinline__ void ld_kb(float (&w)[KB], const float* p) {
 template <int KB>
 __device__ void f32c_forward(const LevelDev& Lc, const float2* fc, const float* ViT, const float* invd,
                              float* z, bool sym) {
-  const int nr = Lc.nr, nt = Lc.nt, nc = nr * nt, h = nt / 2, vr = sym ? h : nt;
+  const int nr = Lc.nr, nt = Lc.nt, P = nr + 1, nc = P * nt, h = nt / 2, vr = sym ? h : nt;
   const int kper = sym ? h : nt, nkb = kper / KB, ntask = (sym ? 2 : 1) * nr * nkb;
   for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
     const int i = t % nr, rest = t / nr, kb = rest % nkb, part = rest / nkb;
@@ -495,9 +614,9 @@ __device__ void f32c_forward(const LevelDev& Lc, const float2* fc, const float* 
 #pragma unroll
     for (int q = 0; q < KB; ++q) {
       const int k = k0 + q;
-      const float d = invd[k * nr + i];
-      z[k * nr + i] = ax[q] * d;
-      z[nc + k * nr + i] = ay[q] * d;
+      const float d = invd[k * P + i];
+      z[k * P + i] = ax[q] * d;
+      z[nc + k * P + i] = ay[q] * d;
     }
   }
 }
@@ -507,7 +626,7 @@ __device__ void f32c_forward(const LevelDev& Lc, const float2* fc, const float* 
 // eigenvector parts) at one radial index, both components.
 template <int JB>
 __device__ void f32c_back(const LevelDev& Lc, const float* z, const float* VT, float2* ec, bool sym) {
-  const int nr = Lc.nr, nt = Lc.nt, nc = nr * nt, h = nt / 2, vr = sym ? h : nt;
+  const int nr = Lc.nr, nt = Lc.nt, P = nr + 1, nc = P * nt, h = nt / 2, vr = sym ? h : nt;
   const int njb = vr / JB, ntask = nr * njb;
   for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
     const int i = t % nr, j0 = (t / nr) * JB;
@@ -516,7 +635,7 @@ __device__ void f32c_back(const LevelDev& Lc, const float* z, const float* VT, f
     for (int q = 0; q < JB; ++q) ex[q] = ey[q] = ox[q] = oy[q] = 0.f;
     const int ke = sym ? h : nt;
     for (int k = 0; k < ke; ++k) {
-      const float xr = z[k * nr + i], xi = z[nc + k * nr + i];
+      const float xr = z[k * P + i], xi = z[nc + k * P + i];
       float w[JB];
       ld_kb<JB>(w, VT + k * vr + j0);
 #pragma unroll
@@ -527,7 +646,7 @@ __device__ void f32c_back(const LevelDev& Lc, const float* z, const float* VT, f
     }
     if (sym) {
       for (int k = h; k < nt; ++k) {
-        const float xr = z[k * nr + i], xi = z[nc + k * nr + i];
+        const float xr = z[k * P + i], xi = z[nc + k * P + i];
         float w[JB];
         ld_kb<JB>(w, VT + k * vr + j0);
 #pragma unroll
@@ -547,10 +666,10 @@ __device__ void f32c_back(const LevelDev& Lc, const float* z, const float* VT, f
 }
 
 // e = L_m^-1 f on the coarsest level Lc (cells in the FP32 swizzled layout);
-// scratch z [2][nt][nr] FP32 at dbl_off.
+// scratch z [2][nt][nr + 1] FP32 at dbl_off.
 __device__ void coarsest_f32c(const VSmemArgs& a, int slot, unsigned char* vraw, const LevelDev& Lc,
                               const float2* fc, float2* ec) {
-  const int nr = Lc.nr, nt = Lc.nt, nc = nr * nt;
+  const int nr = Lc.nr, nt = Lc.nt, P = nr + 1, nc = P * nt;
   const bool sym = a.sep_sym != 0;
   const int vr = sym ? nt / 2 : nt;
   float* z = reinterpret_cast<float*>(vraw + a.dbl_off);
@@ -571,9 +690,9 @@ __device__ void coarsest_f32c(const VSmemArgs& a, int slot, unsigned char* vraw,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < 4 && lane < per && warp * per + lane < nsys) {
       const int q = warp * per + lane, c = q / nt, k = q - c * nt;
-      float* __restrict__ zz = z + c * nc + k * nr;
-      const float* __restrict__ lk = lid + k * nr;
-      const float* __restrict__ ck = cp + k * nr;
+      float* __restrict__ zz = z + c * nc + k * P;
+      const float* __restrict__ lk = lid + k * P;
+      const float* __restrict__ ck = cp + k * P;
       float dp = zz[0];
 #pragma unroll 8
       for (int i = 1; i < nr; ++i) {
@@ -592,6 +711,25 @@ __device__ void coarsest_f32c(const VSmemArgs& a, int slot, unsigned char* vraw,
   if (vr % 4 == 0) f32c_back<4>(Lc, z, VT, ec, sym);
   else f32c_back<1>(Lc, z, VT, ec, sym);
   __syncthreads();
+}
+
+// The first fused level's right-hand side from global memory (this plane's
+// n0 values at g) into its shared-memory slots by asynchronous copies: FP32
+// as aligned cell pairs of 16 bytes (the even swizzle keeps pairs whole).
+template <typename T>
+__device__ __forceinline__ void stage_f0(const VSmemArgs& a, vec2_t<T>* sm, const vec2_t<T>* g) {
+  const int nr0 = a.L[0].nr, n0 = nr0 * a.L[0].nt;
+  if (sizeof(T) == 4 && nr0 % 2 == 0) {
+    const float4* src = reinterpret_cast<const float4*>(g);
+    float4* dst = reinterpret_cast<float4*>(sm + a.off_f[0]);
+    RowWalk w(2 * threadIdx.x, 2 * blockDim.x, nr0);
+    for (int k = threadIdx.x; 2 * k < n0; k += blockDim.x, w.next())
+      cp_async_v(dst + vslot<T>(a.L[0], w.j, w.c) / 2, src + k, true);
+  } else {
+    RowWalk w(threadIdx.x, blockDim.x, nr0);
+    for (int k = threadIdx.x; k < n0; k += blockDim.x, w.next())
+      cp_async_v(sm + a.off_f[0] + vslot<T>(a.L[0], w.j, w.c), g + k, true);
+  }
 }
 
 template <typename T, int NTH>
@@ -660,14 +798,15 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
     for (int k = threadIdx.x; k < int(fac_stride / 2); k += blockDim.x) cp_async_v(dst + k, src + k, true);
   }
   // stage f of the first level, zero all errors
-  {
-    RowWalk w(threadIdx.x, blockDim.x, nr0);
-    for (int k = threadIdx.x; k < n0; k += blockDim.x, w.next())
-      cp_async_v(sm + a.off_f[0] + vslot<T>(a.L[0], w.j, w.c), gf + size_t(p) * n0 + k, true);
-  }
+  stage_f0<T>(a, sm, gf + size_t(p) * n0);
   for (int l = 0; l < K; ++l) {
     const int n = a.L[l].nr * a.L[l].nt;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) sm[a.off_e[l] + k] = V{0, 0};
+    if (sizeof(T) == 4 && n % 2 == 0 && a.off_e[l] % 2 == 0) {
+      float4* d = reinterpret_cast<float4*>(sm + a.off_e[l]);
+      for (int k = threadIdx.x; 2 * k < n; k += blockDim.x) d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      for (int k = threadIdx.x; k < n; k += blockDim.x) sm[a.off_e[l] + k] = V{0, 0};
+    }
   }
   // tables, factors and f arrive by asynchronous copies, all in flight at once
   cp_async_wait_all();
@@ -678,7 +817,12 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
   for (int l = 0; l < K - 1; ++l) {
     const LevelDev Lf = sL[l], Lq = sL[l + 1];
     s_smooth<T>(Lf, sm + a.off_e[l], sm + a.off_f[l], s2, a.nu1, a.n_sor);
-    s_restrict<T>(Lf, Lq, sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
+    if constexpr (sizeof(T) == 4) {
+      if (Lf.nr % 2 == 0 && Lf.nt % 2 == 0) s_restrict_f32(Lf, Lq, sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
+      else s_restrict<T>(Lf, Lq, sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
+    } else {
+      s_restrict<T>(Lf, Lq, sm + a.off_e[l], sm + a.off_f[l], sm + a.off_f[l + 1], s2);
+    }
   }
   if (a.f32c) {
     if constexpr (sizeof(T) == 4) {
@@ -688,11 +832,8 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
         __syncthreads();
       }
       coarsest_f32c(a, slot, vraw, Lcst, sm + a.off_f[K - 1], sm + a.off_e[K - 1]);
-      if (a.restage) {   // the first level's right-hand side again, in flight during the prolongation
-        RowWalk w(threadIdx.x, blockDim.x, nr0);
-        for (int k = threadIdx.x; k < n0; k += blockDim.x, w.next())
-          cp_async_v(sm + a.off_f[0] + vslot<T>(a.L[0], w.j, w.c), gf + size_t(p) * n0 + k, true);
-      }
+      if (a.restage)   // the first level's right-hand side again, in flight during the prolongation
+        stage_f0<T>(a, sm, gf + size_t(p) * n0);
     }
   } else if (a.sep_stride > 0) {
     // coarsest level, exact FP64 separable solve: L_m = L_r (x) I + D_r (x) L_t
@@ -890,14 +1031,25 @@ __global__ void __launch_bounds__(NTH, 1) k_vsmem(VSmemArgs a, Batch B, const ve
   }
   for (int l = K - 2; l >= 0; --l) {
     const LevelDev Lf = sL[l], Lq = sL[l + 1];
-    s_prolong<T>(Lf, Lq, sm + a.off_e[l], sm + a.off_e[l + 1], m);
+    if constexpr (sizeof(T) == 4) {
+      if (Lf.nr % 2 == 0 && Lf.nt % 2 == 0) s_prolong_f32(Lf, Lq, sm + a.off_e[l], sm + a.off_e[l + 1], m);
+      else s_prolong<T>(Lf, Lq, sm + a.off_e[l], sm + a.off_e[l + 1], m);
+    } else {
+      s_prolong<T>(Lf, Lq, sm + a.off_e[l], sm + a.off_e[l + 1], m);
+    }
     if (l == 0 && a.restage) {
       cp_async_wait_all();
       __syncthreads();
     }
     s_smooth<T>(Lf, sm + a.off_e[l], sm + a.off_f[l], s2, a.nu2, a.n_sor);
   }
-  {
+  if (sizeof(T) == 4 && nr0 % 2 == 0) {   // FP32: aligned cell pairs, 16 bytes each
+    const float4* src = reinterpret_cast<const float4*>(sm + a.off_e[0]);
+    float4* dst = reinterpret_cast<float4*>(ge + size_t(p) * n0);
+    RowWalk w(2 * threadIdx.x, 2 * blockDim.x, nr0);
+    for (int k = threadIdx.x; 2 * k < n0; k += blockDim.x, w.next())
+      dst[k] = src[vslot<T>(a.L[0], w.j, w.c) / 2];
+  } else {
     RowWalk w(threadIdx.x, blockDim.x, nr0);
     for (int k = threadIdx.x; k < n0; k += blockDim.x, w.next())
       ge[size_t(p) * n0 + k] = sm[a.off_e[0] + vslot<T>(a.L[0], w.j, w.c)];

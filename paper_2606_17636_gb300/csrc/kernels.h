@@ -139,8 +139,8 @@ struct VSmemArgs {
   int sep_sym;           // mirror-symmetric separable layout (see Hierarchy::sep_sym)
   // FP32 V-cycle with a separable coarsest level, solved in FP32: sepf per
   // slot (sepf_stride floats) holds V^-1 transposed [vr][nt], V transposed
-  // [nt][vr], then 1/pivot, upper/pivot and lower/pivot [nt][nr] each, all
-  // rounded once from the FP64 factors.  blk_smem: staged at blk_off;
+  // [nt][vr], then 1/pivot, upper/pivot and lower/pivot [nt][nr + 1] each
+  // (padded rows), all rounded once from the FP64 factors.  blk_smem: staged at blk_off;
   // restage = 1: over the first level's right-hand side, which is copied in
   // again from the input after the coarsest solve.
   int f32c, restage;

@@ -138,11 +138,13 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   // shared-memory V-cycle: the deepest levels whose error and right-hand
   // side fit next to the coarse-solve scratch (lines of at most 128 cells).
   // The mixed path solves a separable coarsest level in FP32 (scratch z,
-  // 8 bytes per cell); the FP64 path keeps f and z in FP64, 32 bytes per cell.
+  // 8 bytes per cell, rows padded by one cell); the FP64 path keeps f and z
+  // in FP64, 32 bytes per cell.
   const bool f32c = opt.precision && H.sep_stride > 0;
+  const size_t zf32 = 8 * size_t(lv[nl - 1].nt) * (lv[nl - 1].nr + 1);
   first = nl - 1;
   {
-    const size_t zx_bytes = (f32c ? 8 : 32) * size_t(H.nc) + 16;
+    const size_t zx_bytes = (f32c ? zf32 : 32 * size_t(H.nc)) + 16;
     const size_t budget = (f32c ? 224 : 210) * 1024;
     size_t bytes = zx_bytes;
     const size_t tb = vb / 2;   // bytes of one real table entry
@@ -199,7 +201,7 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
     }
     size_t sbytes = (off * vb + tab * (vb / 2) + 15) / 16 * 16;
     vs.dbl_off = int(sbytes);
-    sbytes += (f32c ? 8 : 32) * size_t(H.nc);
+    sbytes += f32c ? zf32 : 32 * size_t(H.nc);
     vs.inv = d_inv;
     vs.blk = d_blk;
     vs.nc = H.nc;
@@ -225,7 +227,8 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
       // solve), else read from global memory
       const int nrc = lv[nl - 1].nr, ntc = lv[nl - 1].nt, vr = H.sep_sym ? ntc / 2 : ntc;
       const size_t ncc = size_t(nrc) * ntc;
-      vs.sepf_stride = int((2 * size_t(vr) * ntc + 3 * ncc + 3) / 4 * 4);
+      const size_t pc = size_t(ntc) * (nrc + 1);   // padded rows
+      vs.sepf_stride = int((2 * size_t(vr) * ntc + 3 * pc + 3) / 4 * 4);
       const size_t S_ = modes.size();
       std::vector<float> pf(S_ * size_t(vs.sepf_stride), 0.f);
       for (size_t q = 0; q < S_; ++q) {
@@ -239,7 +242,9 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
         for (int k = 0; k < ntc; ++k)
           for (int j = 0; j < vr; ++j) o[size_t(k) * vr + j] = float(Vm[size_t(j) * ntc + k]);
         o += size_t(ntc) * vr;
-        for (size_t x = 0; x < 3 * ncc; ++x) o[x] = float(rest[x]);
+        for (int t = 0; t < 3; ++t)
+          for (int k = 0; k < ntc; ++k)
+            for (int i = 0; i < nrc; ++i) o[t * pc + size_t(k) * (nrc + 1) + i] = float(rest[t * ncc + size_t(k) * nrc + i]);
       }
       vs.sepf = upload(A, pf);
       if (!vs.sepf) { err = "out of device memory"; return false; }
