@@ -497,53 +497,61 @@ __device__ void s_prolong_f32(const LevelDev& L, const LevelDev& C, float2* e, c
   const float* rt = L.rf;
   const float* tt = L.tf;
   const int nr = L.nr, nt = L.nt;
-  for (RowWalk w(threadIdx.x, blockDim.x, C.nr); w.j < C.nt; w.next()) {
-    const int J = w.j, I = w.c;
-    // coarse (I - 1 + u, J - 1 + v), 1-based index I + u, J + v: the ghost
-    // rules of s_cval chosen per column and row without branching (the same
-    // values: zero, the mirrored cell, or its negative for odd m across a
-    // parity face, twice negated across two)
-    int ic[3], jc[3];
-    bool zc[3], zr[3], nc[3], nrw[3];
-    const bool odd = (m & 1) != 0;
+  // each task: coarse column I, coarse rows J0 .. J0 + S - 1 (neighbourhood
+  // rows J0 - 1 .. J0 + S loaded once); the ghost rules of s_cval chosen per
+  // column and row without branching (the same values: zero, the mirrored
+  // cell, or its negative for odd m across a parity face, twice negated
+  // across two)
+  constexpr int S = 4;
+  const bool odd = (m & 1) != 0;
+  const int strips = (C.nt + S - 1) / S;
+  for (int t = threadIdx.x; t < C.nr * strips; t += blockDim.x) {
+    const int I = t % C.nr, J0 = (t / C.nr) * S;
+    int ic[3];
+    bool zc[3], nc[3];
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
+    for (int u = 0; u < 3; ++u) {   // 1-based coarse column I + u
       const int x = I + u, rule = x == 0 ? C.gL : (x == C.nr + 1 ? C.gR : -1);
       ic[u] = min(max(x, 1), C.nr) - 1;
       zc[u] = rule == GH_ZERO;
       nc[u] = rule == GH_PARITY && odd;
-      const int y = J + u, rr = y == 0 ? C.gB : (y == C.nt + 1 ? C.gT : -1);
-      jc[u] = min(max(y, 1), C.nt) - 1;
-      zr[u] = rr == GH_ZERO;
-      nrw[u] = rr == GH_PARITY && odd;
     }
-    float2 cv[3][3];
+    float2 r[S + 2][3];   // 1-based coarse rows J0 .. J0 + S + 1
 #pragma unroll
-    for (int v = 0; v < 3; ++v)
+    for (int v = 0; v < S + 2; ++v) {
+      const int y = J0 + v, rule = y == 0 ? C.gB : (y == C.nt + 1 ? C.gT : -1);
+      const int jc = min(max(y, 1), C.nt) - 1;
+      const bool zr = rule == GH_ZERO, nrw = rule == GH_PARITY && odd;
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
-        const float2 x = ec[vslot<float>(C, jc[v], ic[u])];
-        cv[v][u] = (zc[u] || zr[v]) ? make_float2(0.f, 0.f) : ((nc[u] != nrw[v]) ? make_float2(-x.x, -x.y) : x);
+        const float2 x = ec[vslot<float>(C, jc, ic[u])];
+        r[v][u] = (zc[u] || zr) ? make_float2(0.f, 0.f) : ((nc[u] != nrw) ? make_float2(-x.x, -x.y) : x);
       }
+    }
     const int i0 = 2 * I;
     const float2 P1 = tab2(rt, RT_P1, nr, i0), P2 = tab2(rt, RT_P2, nr, i0);
-    const float2 Q1 = tab2(tt, TT_P1, nt, 2 * J), Q2 = tab2(tt, TT_P2, nt, 2 * J);
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int j = 2 * J + b;
-      const float q1 = b ? Q1.y : Q1.x, q2 = b ? Q2.y : Q2.x;
-      float2 uu[2];
-      float2* row = e + vslot<float>(L, j, i0);
-      ld_pair(uu[0], uu[1], row);
+    for (int q = 0; q < S; ++q) {
+      const int J = J0 + q;
+      if (J >= C.nt) break;
+      const float2 Q1 = tab2(tt, TT_P1, nt, 2 * J), Q2 = tab2(tt, TT_P2, nt, 2 * J);
 #pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const float p1 = a ? P1.y : P1.x, p2 = a ? P2.y : P2.x;
-        const float2 A = cv[b][a], Bv = cv[b][a + 1], Cv = cv[b + 1][a], D = cv[b + 1][a + 1];
-        const float w11 = p1 * q1, w21 = p2 * q1, w12 = p1 * q2, w22 = p2 * q2;
-        uu[a].x += fmac(w22, D.x, fmac(w12, Cv.x, fmac(w21, Bv.x, w11 * A.x)));
-        uu[a].y += fmac(w22, D.y, fmac(w12, Cv.y, fmac(w21, Bv.y, w11 * A.y)));
+      for (int b = 0; b < 2; ++b) {
+        const int j = 2 * J + b;
+        const float q1 = b ? Q1.y : Q1.x, q2 = b ? Q2.y : Q2.x;
+        float2 uu[2];
+        float2* row = e + vslot<float>(L, j, i0);
+        ld_pair(uu[0], uu[1], row);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const float p1 = a ? P1.y : P1.x, p2 = a ? P2.y : P2.x;
+          const float2 A = r[q + b][a], Bv = r[q + b][a + 1], Cv = r[q + b + 1][a], D = r[q + b + 1][a + 1];
+          const float w11 = p1 * q1, w21 = p2 * q1, w12 = p1 * q2, w22 = p2 * q2;
+          uu[a].x += fmac(w22, D.x, fmac(w12, Cv.x, fmac(w21, Bv.x, w11 * A.x)));
+          uu[a].y += fmac(w22, D.y, fmac(w12, Cv.y, fmac(w21, Bv.y, w11 * A.y)));
+        }
+        st_pair(row, uu[0], uu[1]);
       }
-      st_pair(row, uu[0], uu[1]);
     }
   }
   __syncthreads();
@@ -693,15 +701,47 @@ __device__ void coarsest_f32c(const VSmemArgs& a, int slot, unsigned char* vraw,
       float* __restrict__ zz = z + c * nc + k * P;
       const float* __restrict__ lk = lid + k * P;
       const float* __restrict__ ck = cp + k * P;
+      // in batches of eight steps: the loads of a batch are issued together,
+      // so one shared-memory latency is paid per batch, not per step
       float dp = zz[0];
-#pragma unroll 8
-      for (int i = 1; i < nr; ++i) {
+      int i = 1;
+      for (; i + 8 <= nr; i += 8) {
+        float zv[8], lv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          zv[q] = zz[i + q];
+          lv[q] = lk[i + q];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          dp = fmaf(-lv[q], dp, zv[q]);
+          zv[q] = dp;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) zz[i + q] = zv[q];
+      }
+      for (; i < nr; ++i) {
         dp = fmaf(-lk[i], dp, zz[i]);
         zz[i] = dp;
       }
       float xv = dp;
-#pragma unroll 8
-      for (int i = nr - 2; i >= 0; --i) {
+      i = nr - 2;
+      for (; i >= 7; i -= 8) {
+        float zv[8], cv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          zv[q] = zz[i - q];
+          cv[q] = ck[i - q];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          xv = fmaf(-cv[q], xv, zv[q]);
+          zv[q] = xv;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) zz[i - q] = zv[q];
+      }
+      for (; i >= 0; --i) {
         xv = fmaf(-ck[i], xv, zz[i]);
         zz[i] = xv;
       }
