@@ -587,14 +587,16 @@ def launches_per_solve(s, st):
     loop.  A loop iteration is the residual/retirement kernel and, while
     planes remain, one V-cycle (on every level below the fused one nu_pre
     smoothing cycles of two passes, a restriction, later a prolongation and
-    nu_post cycles; the fused V-cycle) and the update.  With I iterations
+    nu_post cycles; the fused V-cycle) and the update, which rides on the
+    last smoothing pass when there is one.  With I iterations
     the loop runs I + 1 residuals and I V-cycles; with the cluster-resident
     tail (P planes) it hands over after the first iteration k that leaves at
     most P planes active (k + 1 residuals and V-cycles), then one tail
     launch finishes them."""
     sc = s.schedule()
     first = s.fused_level()
-    vcycle = first * (2 * sc["nu_pre"] + 1 + 1 + 2 * sc["nu_post"]) + 1 + 1   # + fused, update
+    vcycle = first * (2 * sc["nu_pre"] + 1 + 1 + 2 * sc["nu_post"]) + 1   # + fused
+    vcycle += 0 if (first > 0 and sc["nu_post"] > 0) else 1             # + update
     fixed = 1 + 1 + 3 + 1 + 1 + 1           # fft, init x2, screening/boundary/ghosts, ifft, status
     tail_planes = s.tail()[0]
 

@@ -7,7 +7,7 @@
 // the stencil.
 #include <cstdio>
 
-#include "kernels.h"
+#include "lines.cuh"
 
 namespace ps {
 
@@ -133,28 +133,11 @@ void launch_restrict(const LevelDev& F, const LevelDev& C, const Batch& B, const
 // Bilinear prolongation in (r^2, theta) / (R, z) and correction (Sec. 3.1).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ vec2_t<T> coarse_val(const LevelDev& C, const vec2_t<T>* __restrict__ ec,
-                                               int I, int J, int m) {
-  typedef vec2_t<T> V;
-  T fac = T(1);
-  const T sgn = (m & 1) ? T(-1) : T(1);
-  int Ic = I, Jc = J;
-  if (I == 0) { if (C.gL == GH_ZERO) return vzero<V>(); Ic = 1; if (C.gL == GH_PARITY) fac *= sgn; }
-  if (I == C.nr + 1) { if (C.gR == GH_ZERO) return vzero<V>(); Ic = C.nr; if (C.gR == GH_PARITY) fac *= sgn; }
-  if (J == 0) { if (C.gB == GH_ZERO) return vzero<V>(); Jc = 1; if (C.gB == GH_PARITY) fac *= sgn; }
-  if (J == C.nt + 1) { if (C.gT == GH_ZERO) return vzero<V>(); Jc = C.nt; if (C.gT == GH_PARITY) fac *= sgn; }
-  const V v = ec[size_t(Jc - 1) * C.nr + (Ic - 1)];
-  return vmk<V, T>(fac * v.x, fac * v.y);
-}
-
-template <typename T>
 __global__ void __launch_bounds__(256) k_prolong(LevelDev L, LevelDev C, Batch B,
                                                  vec2_t<T>* __restrict__ e,
                                                  const vec2_t<T>* __restrict__ ec) {
   typedef vec2_t<T> V;
   const int nact = *B.nact, n = L.nr * L.nt, bpp = (n + blockDim.x - 1) / blockDim.x;
-  const T* rt = rtab<T>(L);
-  const T* tt = ttab<T>(L);
   for (int w = blockIdx.x; w < nact * bpp; w += gridDim.x) {
     const int k = w / bpp;
     const int idx = (w - k * bpp) * blockDim.x + threadIdx.x;
@@ -162,17 +145,10 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev L, LevelDev C, Batch B
     const int p = B.act[k];
     const int slot = B.slot ? B.slot[p] : p;
     const int j = idx / L.nr, i = idx - j * L.nr;
-    const int i1 = i + 1, j1 = j + 1;
-    const int I1 = (i1 & 1) ? (i1 + 1) / 2 - 1 : i1 / 2, J1 = (j1 & 1) ? (j1 + 1) / 2 - 1 : j1 / 2;
-    const T p1 = RTAB(rt, RT_P1, i1), p2 = RTAB(rt, RT_P2, i1);
-    const T q1 = TTAB(tt, TT_P1, j1), q2 = TTAB(tt, TT_P2, j1);
-    const int m = B.mode[slot];
-    const V* ecp = ec + size_t(p) * C.nr * C.nt;
-    const V a = coarse_val<T>(C, ecp, I1, J1, m), b = coarse_val<T>(C, ecp, I1 + 1, J1, m);
-    const V c = coarse_val<T>(C, ecp, I1, J1 + 1, m), d = coarse_val<T>(C, ecp, I1 + 1, J1 + 1, m);
+    const V c = prolong_corr<T>(L, C, ec + size_t(p) * C.nr * C.nt, B.mode[slot], i, j);
     V& u = e[size_t(p) * n + idx];
-    u.x += p1 * q1 * a.x + p2 * q1 * b.x + p1 * q2 * c.x + p2 * q2 * d.x;
-    u.y += p1 * q1 * a.y + p2 * q1 * b.y + p1 * q2 * c.y + p2 * q2 * d.y;
+    u.x += c.x;
+    u.y += c.y;
   }
 }
 

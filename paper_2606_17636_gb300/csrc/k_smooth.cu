@@ -133,10 +133,13 @@ __device__ __forceinline__ int tslot(int j, int cc, int SW) {
   return j * SW + (CPL == 1 ? cc : (cc ^ ((j >> 4) & 1)));
 }
 
+// u != nullptr: the last pass of a V-cycle adds its result to the FP64
+// solution (u += e, the refinement's update) instead of storing e.
 template <typename T, int CPL>
 __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_t<T>* __restrict__ ein,
                                                 vec2_t<T>* __restrict__ eout,
-                                                const vec2_t<T>* __restrict__ f, int n_sor, int TWmax) {
+                                                const vec2_t<T>* __restrict__ f, int n_sor, int TWmax,
+                                                double2* __restrict__ u) {
   typedef vec2_t<T> V;
   extern __shared__ __align__(16) unsigned char sraw[];
   const int nact = *B.nact;
@@ -196,8 +199,18 @@ __global__ void __launch_bounds__(256) k_tpass2(LevelDev L, Batch B, const vec2_
     }
     __syncthreads();
   }
-  for (RowWalk w(threadIdx.x, blockDim.x, TW); w.j < nt; w.next())
-    eout[base + size_t(w.j) * nr + i0 + w.c] = se[tslot<CPL>(w.j, w.c + 1, SW)];
+  for (RowWalk w(threadIdx.x, blockDim.x, TW); w.j < nt; w.next()) {
+    const V v = se[tslot<CPL>(w.j, w.c + 1, SW)];
+    const size_t o = base + size_t(w.j) * nr + i0 + w.c;
+    if (u) {
+      double2 x = u[o];
+      x.x += from_buf<T>(v.x);
+      x.y += from_buf<T>(v.y);
+      u[o] = x;
+    } else {
+      eout[o] = v;
+    }
+  }
 }
 
 // Polar tile width: the requested width (0: 32), at most n_r, halved until
@@ -230,8 +243,7 @@ bool smooth_fits(int nr, int nt, size_t vb) {
 
 template <typename T, int CPL>
 static void rpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                   const vec2_t<T>* f, bool zi, int n_sor, int Wmax,
-                   cudaStream_t st) {
+                   const vec2_t<T>* f, bool zi, int n_sor, int Wmax, cudaStream_t st) {
   const size_t sm = rpass_smem(L.nr, Wmax, sizeof(vec2_t<T>));
   static bool attr = false;
   if (!attr) {
@@ -244,7 +256,7 @@ static void rpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2
 
 template <typename T, int CPL>
 static void tpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                   const vec2_t<T>* f, int n_sor, int cols, cudaStream_t st) {
+                   const vec2_t<T>* f, int n_sor, int cols, double2* u, cudaStream_t st) {
   const int TW = tile_w(L.nr, L.nt, sizeof(vec2_t<T>), cols);
   const size_t sm = size_t(L.nt) * 2 * (TW + 5) * sizeof(vec2_t<T>);
   static bool attr = false;
@@ -253,13 +265,12 @@ static void tpass2(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2
     attr = true;
   }
   dim3 grid(L.nr / TW, B.max_planes);
-  k_tpass2<T, CPL><<<grid, 256, sm, st>>>(L, B, ein, eout, f, n_sor, TW);
+  k_tpass2<T, CPL><<<grid, 256, sm, st>>>(L, B, ein, eout, f, n_sor, TW, u);
 }
 
 template <typename T>
 static void rpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                       const vec2_t<T>* f, bool zi, int n_sor, int Wmax,
-                       cudaStream_t st) {
+                       const vec2_t<T>* f, bool zi, int n_sor, int Wmax, cudaStream_t st) {
   switch (L.nr <= 32 ? 1 : L.nr / 32) {
     case 1: rpass2<T, 1>(L, B, ein, eout, f, zi, n_sor, Wmax, st); break;
     case 2: rpass2<T, 2>(L, B, ein, eout, f, zi, n_sor, Wmax, st); break;
@@ -273,14 +284,14 @@ static void rpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, 
 
 template <typename T>
 static void tpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, vec2_t<T>* eout,
-                       const vec2_t<T>* f, int n_sor, int cols, cudaStream_t st) {
+                       const vec2_t<T>* f, int n_sor, int cols, double2* u, cudaStream_t st) {
   switch (L.nt <= 32 ? 1 : L.nt / 32) {
-    case 1: tpass2<T, 1>(L, B, ein, eout, f, n_sor, cols, st); break;
-    case 2: tpass2<T, 2>(L, B, ein, eout, f, n_sor, cols, st); break;
-    case 4: tpass2<T, 4>(L, B, ein, eout, f, n_sor, cols, st); break;
-    case 8: tpass2<T, 8>(L, B, ein, eout, f, n_sor, cols, st); break;
-    case 16: tpass2<T, 16>(L, B, ein, eout, f, n_sor, cols, st); break;
-    case 32: tpass2<T, 32>(L, B, ein, eout, f, n_sor, cols, st); break;
+    case 1: tpass2<T, 1>(L, B, ein, eout, f, n_sor, cols, u, st); break;
+    case 2: tpass2<T, 2>(L, B, ein, eout, f, n_sor, cols, u, st); break;
+    case 4: tpass2<T, 4>(L, B, ein, eout, f, n_sor, cols, u, st); break;
+    case 8: tpass2<T, 8>(L, B, ein, eout, f, n_sor, cols, u, st); break;
+    case 16: tpass2<T, 16>(L, B, ein, eout, f, n_sor, cols, u, st); break;
+    case 32: tpass2<T, 32>(L, B, ein, eout, f, n_sor, cols, u, st); break;
     default: std::fprintf(stderr, "psolve: polar size %d unsupported\n", L.nt);
   }
 }
@@ -288,17 +299,17 @@ static void tpass2_any(const LevelDev& L, const Batch& B, const vec2_t<T>* ein, 
 template <typename T>
 void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
                    vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, Tiles tiles,
-                   cudaStream_t st) {
+                   cudaStream_t st, double2* u) {
   const int Wmax = rpass_lines(L.nr, sizeof(vec2_t<T>), tiles.lines_r == 4 ? 4 : 8);
   for (int c = 0; c < cycles; ++c) {
     rpass2_any<T>(L, B, e, tmp, f, zero_init && c == 0, n_sor, Wmax, st);
-    tpass2_any<T>(L, B, tmp, e, f, n_sor, tiles.cols_t, st);
+    tpass2_any<T>(L, B, tmp, e, f, n_sor, tiles.cols_t, c == cycles - 1 ? u : nullptr, st);
   }
 }
 
 template void launch_smooth<float>(const LevelDev&, const Batch&, float2*, const float2*, float2*,
-                                   int, int, bool, Tiles, cudaStream_t);
+                                   int, int, bool, Tiles, cudaStream_t, double2*);
 template void launch_smooth<double>(const LevelDev&, const Batch&, double2*, const double2*,
-                                    double2*, int, int, bool, Tiles, cudaStream_t);
+                                    double2*, int, int, bool, Tiles, cudaStream_t, double2*);
 
 }  // namespace ps

@@ -118,10 +118,12 @@ int smooth_tile_cols(int nr, int nt, size_t vb, int want);
 bool smooth_fits(int nr, int nt, size_t vb);
 // `cycles` alternating-line smoothing cycles (k_smooth.cu); tmp is a
 // scratch buffer of the level's size (ping-pong between the two passes).
+// u: the last pass adds e to this FP64 solution (the refinement's update)
+// and leaves e unwritten.
 template <typename T>
 void launch_smooth(const LevelDev& L, const Batch& B, vec2_t<T>* e, const vec2_t<T>* f,
                    vec2_t<T>* tmp, int cycles, int n_sor, bool zero_init, Tiles tiles,
-                   cudaStream_t st);
+                   cudaStream_t st, double2* u = nullptr);
 
 // Lower part of a V-cycle in shared memory, one block per plane (k_vsmem.cu).
 struct VSmemArgs {

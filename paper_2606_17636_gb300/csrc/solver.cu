@@ -364,13 +364,14 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
 }
 
 // ---- typed dispatch -----------------------------------------------------------
-void MGSolver::smooth(int l, void* ee, const void* ff, int cycles, bool zi, cudaStream_t st) {
+void MGSolver::smooth(int l, void* ee, const void* ff, int cycles, bool zi, cudaStream_t st,
+                      double2* u) {
   if (opt.precision)
     launch_smooth<float>(lv[l], batch, (float2*)ee, (const float2*)ff, (float2*)tmp, cycles,
-                         opt.n_sor, zi, opt.tiles, st);
+                         opt.n_sor, zi, opt.tiles, st, u);
   else
     launch_smooth<double>(lv[l], batch, (double2*)ee, (const double2*)ff, (double2*)tmp, cycles,
-                          opt.n_sor, zi, opt.tiles, st);
+                          opt.n_sor, zi, opt.tiles, st, u);
 }
 void MGSolver::restrict_(int l, const void* ee, const void* ff, void* fc, cudaStream_t st) {
   if (opt.precision)
@@ -430,17 +431,24 @@ void MGSolver::residual_to(const double2* ff, const double2* u, void* r, cudaStr
 // restriction, coarse correction, prolongation, post-smoothing).  Levels
 // below `first` run as level-wide kernels over all active planes; the rest
 // runs in the shared-memory kernel, one block per plane.
-void MGSolver::vcycle(cudaStream_t st) {
+// With post-smoothing on level 0, the update (with u) rides on its last pass.
+bool MGSolver::vcycle(cudaStream_t st, double2* u) {
   for (int l = 0; l < first; ++l) {
     if (opt.nu1 > 0) smooth(l, e[l], f[l], opt.nu1, true, st);
     else cudaMemsetAsync(e[l], 0, size_t(max_planes) * lv[l].nr * lv[l].nt * vbytes(), st);
     restrict_(l, e[l], f[l], f[l + 1], st);
   }
   fused(st);
+  bool updated = false;
   for (int l = first - 1; l >= 0; --l) {
     prolong(l, e[l], e[l + 1], st);
-    if (opt.nu2 > 0) smooth(l, e[l], f[l], opt.nu2, false, st);
+    if (opt.nu2 > 0) {
+      double2* uu = l == 0 ? u : nullptr;
+      smooth(l, e[l], f[l], opt.nu2, false, st, uu);
+      updated = uu != nullptr;
+    }
   }
+  return updated;
 }
 
 void MGSolver::set_schedule(int nu1, int nu2, int n_sor, Tiles tiles, int nu1f, int nu2f) {
@@ -569,7 +577,7 @@ void MGSolver::init_loop(cudaStream_t st) { launch_init_active(d_act, d_nact, ma
 void MGSolver::loop_body(const double2* ff, double2* u, double tol, cudaStream_t st, int use_cond,
                          unsigned long long cond) {
   residual(ff, u, tol, st, use_cond, cond);
-  vcycle(st);
+  if (vcycle(st, u)) return;
   if (opt.precision)
     launch_update<float>(lv[0], batch, u, (const float2*)e[0], st);
   else
@@ -589,11 +597,12 @@ int MGSolver::eager_solve(const double2* ff, double2* u, double tol, cudaStream_
       return -2;
     }
     if (!*h_cont) return 0;
-    vcycle(st);
-    if (opt.precision)
-      launch_update<float>(lv[0], batch, u, (const float2*)e[0], st);
-    else
-      launch_update<double>(lv[0], batch, u, (const double2*)e[0], st);
+    if (!vcycle(st, u)) {
+      if (opt.precision)
+        launch_update<float>(lv[0], batch, u, (const float2*)e[0], st);
+      else
+        launch_update<double>(lv[0], batch, u, (const double2*)e[0], st);
+    }
     if (*h_cont == 2) {   // at most tail_planes remain: the tail kernel finishes them
       tail(ff, u, tol, st);
       return 0;

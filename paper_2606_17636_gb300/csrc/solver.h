@@ -55,7 +55,10 @@ class MGSolver {
   void loop_body(const double2* f, double2* u, double tol, cudaStream_t st, int use_cond,
                  unsigned long long cond);
   int eager_solve(const double2* f, double2* u, double tol, cudaStream_t st, std::string& err);
-  void vcycle(cudaStream_t st);
+  // One V-cycle; with u, the refinement's update u += e rides on the last
+  // smoothing pass when the schedule post-smooths level 0 with the
+  // level-wide passes (returns true then; else the caller updates).
+  bool vcycle(cudaStream_t st, double2* u = nullptr);
   // Change the smoothing schedule and tile shapes of later V-cycles (a
   // captured solve must be captured again).
   void set_schedule(int nu1, int nu2, int n_sor, Tiles tiles, int nu1f, int nu2f);
@@ -79,7 +82,9 @@ class MGSolver {
   int zero_guess = 0;              // the next solve starts from u = 0 (set by the caller)
   VSmemArgs vs{};
   // stage helpers on explicit buffers
-  void smooth(int level, void* e, const void* f, int cycles, bool zero_init, cudaStream_t st);
+  // u: the last pass adds e to u instead of storing it (see launch_smooth)
+  void smooth(int level, void* e, const void* f, int cycles, bool zero_init, cudaStream_t st,
+              double2* u = nullptr);
   void restrict_(int level, const void* e, const void* f, void* fc, cudaStream_t st);
   void prolong(int level, void* e, const void* ec, cudaStream_t st);
   void fused(cudaStream_t st);   // levels first .. coarsest in shared memory

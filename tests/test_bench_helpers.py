@@ -55,23 +55,28 @@ class _FakeSolver:
 def test_launches_per_solve_counts_the_loop_body(bench):
     """One iteration at the benchmark's shape (fused from level 1, nu = (2, 2)):
     residual, 2 x 2 smoothing passes, restriction, fused V-cycle,
-    prolongation, 2 x 2 passes, update = 13 launches; a loop of I
-    iterations runs I + 1 residuals and I V-cycles; a solve adds 8 fixed
-    launches.  With the tail kernel (P planes) a loop hands over after the
-    first iteration that leaves at most P planes active."""
+    prolongation, 2 x 2 passes (the last does the update) = 12 launches; a
+    loop of I iterations runs I + 1 residuals and I V-cycles; a solve adds 8
+    fixed launches.  Without post-smoothing the update is a launch of its
+    own.  With the tail kernel (P planes) a loop hands over after the first
+    iteration that leaves at most P planes active."""
     cyc_psi = [21, 9, 5] + [1] * 126
     cyc_phi = [16, 7, 3] + [1] * 126
     st = {"cycles_psi": cyc_psi, "cycles_phi": cyc_phi}
     s = _FakeSolver(dict(nu_pre=2, nu_post=2, n_sor=1), 1)
-    assert bench.launches_per_solve(s, st) == 8 + (22 + 21 * 12) + (17 + 16 * 12)
+    assert bench.launches_per_solve(s, st) == 8 + (22 + 21 * 11) + (17 + 16 * 11)
     s = _FakeSolver(dict(nu_pre=3, nu_post=1, n_sor=2), 2)
     # two level-wide levels: each 2 x 3 + 1 + 1 + 2 x 1 = 10 launches
-    v = 2 * 10 + 1 + 1
+    v = 2 * 10 + 1
+    assert bench.launches_per_solve(s, st) == 8 + (22 + 21 * v) + (17 + 16 * v)
+    s = _FakeSolver(dict(nu_pre=2, nu_post=0, n_sor=1), 1)
+    # 2 x 2 + 1, fused V-cycle, prolongation, update
+    v = 4 + 1 + 1 + 1 + 1
     assert bench.launches_per_solve(s, st) == 8 + (22 + 21 * v) + (17 + 16 * v)
     # tail of 2 planes: Psi hands over after iteration 5 (planes with more
     # than 5 cycles: 21 and 9), Phi after iteration 3 (16 and 7)
     s = _FakeSolver(dict(nu_pre=2, nu_post=2, n_sor=1), 1, tail=2)
-    assert bench.launches_per_solve(s, st) == 8 + (6 * 13 + 1) + (4 * 13 + 1)
+    assert bench.launches_per_solve(s, st) == 8 + (6 * 12 + 1) + (4 * 12 + 1)
 
 
 def test_oracle_timings_runs_the_full_oracle_solve(bench):
