@@ -19,34 +19,59 @@ struct __align__(16) Sum4 {
 };
 #ifdef __CUDACC__
 // IEEE 754 conversions between binary64 and binary32 on the integer pipes:
-// GB300 runs FP64 arithmetic at about 1/64 of its FP32 rate, and the FP64
-// kernels of the refinement loop are bound by that pipe.  Only results in
-// the normal range are formed here; zeros, subnormals, overflow, infinities
-// and NaN take the hardware conversion.
-// binary64 -> binary32, round to nearest, ties to even: the sign, the
-// rebiased exponent, the top 23 fraction bits, and one unit added when the
-// 29 dropped bits exceed half a unit or equal it with an odd kept part (a
-// carry into the exponent is the correct rounding, up to infinity).
+// GB300 runs FP64 arithmetic at about 1/64 of its FP32 rate, the hardware
+// conversions occupy that pipe, and the FP64 kernels of the refinement loop
+// are bound by it.  Every case is formed from the bit fields (a hardware
+// fallback for the rare cases would still be issued for every value when the
+// compiler turns the branch into a select).
+// binary64 -> binary32, round to nearest, ties to even.  Normal results: the
+// sign, the rebiased exponent, the top 23 fraction bits, and one unit added
+// when the 29 dropped bits exceed half a unit or equal it with an odd kept
+// part (a carry into the exponent is the correct rounding, up to infinity).
+// Subnormal results: the 53-bit significand shifted right by 30 - e bits
+// (e the rebiased exponent), rounded the same way (a carry gives the smallest
+// normal number).  Overflow gives infinity; NaN stays a quiet NaN.
 __device__ __forceinline__ float f64_to_f32(double x) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
-  const int e = int((hi >> 20) & 0x7ffu) - 1023 + 127;
-  if (e <= 0 || e >= 255) return __double2float_rn(x);
-  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const unsigned rest = lo & 0x1fffffffu, half = 0x10000000u;
-  unsigned f = (hi & 0x80000000u) | (unsigned(e) << 23) | m;
-  f += (rest > half || (rest == half && (m & 1u))) ? 1u : 0u;
-  return __uint_as_float(f);
+  const unsigned sign = hi & 0x80000000u;
+  const int E = int((hi >> 20) & 0x7ffu), e = E - 1023 + 127;
+  if (e > 0 && e < 255) {
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu, half = 0x10000000u;
+    unsigned f = sign | (unsigned(e) << 23) | m;
+    f += (rest > half || (rest == half && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+  }
+  const unsigned long long frac = b & 0xfffffffffffffull;
+  if (E == 0x7ff) return __uint_as_float(frac ? (sign | 0x7fc00000u | unsigned(frac >> 29)) : (sign | 0x7f800000u));
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const int sh = 30 - e;
+  if (sh > 53) return __uint_as_float(sign);   // below half the smallest subnormal (FP64 subnormals, zeros)
+  const unsigned long long sig = frac | (1ull << 52);
+  const unsigned long long m = sig >> sh, rest = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  const unsigned long long r = m + ((rest > half || (rest == half && (m & 1ull))) ? 1ull : 0ull);
+  return __uint_as_float(sign | unsigned(r));
 }
-// binary32 -> binary64, exact: the exponent rebiased by 1023 - 127 and the
-// 23 fraction bits moved to the top of the 52.
+// binary32 -> binary64, exact: normal values rebias the exponent by
+// 1023 - 127 and move the 23 fraction bits to the top of the 52; subnormals
+// are normalised at their leading bit; zeros keep their sign; infinities and
+// NaN (made quiet, payload kept) keep the all-ones exponent.
 __device__ __forceinline__ double f32_to_f64(float x) {
+  typedef unsigned long long u64;
   const unsigned b = __float_as_uint(x);
-  const unsigned e = (b >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return double(x);
-  const unsigned long long d = (static_cast<unsigned long long>(b & 0x80000000u) << 32) |
-                               (static_cast<unsigned long long>(e + 896u) << 52) |
-                               (static_cast<unsigned long long>(b & 0x7fffffu) << 29);
+  const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  u64 d;
+  if (e != 0u && e != 0xffu) {
+    d = (u64(sign) << 32) | (u64(e + 896u) << 52) | (u64(m) << 29);
+  } else if (e == 0xffu) {
+    d = (u64(sign) << 32) | (0x7ffull << 52) | (m ? (1ull << 51) : 0ull) | (u64(m) << 29);
+  } else if (m == 0u) {
+    d = u64(sign) << 32;
+  } else {
+    const int p = 31 - __clz(int(m));   // m 2^-149 = 1.f 2^(p - 149)
+    d = (u64(sign) << 32) | (u64(p - 149 + 1023) << 52) | ((u64(m) << (52 - p)) & 0xfffffffffffffull);
+  }
   return __longlong_as_double(static_cast<long long>(d));
 }
 
