@@ -132,30 +132,80 @@ void launch_restrict(const LevelDev& F, const LevelDev& C, const Batch& B, const
 // ---------------------------------------------------------------------------
 // Bilinear prolongation in (r^2, theta) / (R, z) and correction (Sec. 3.1).
 // ---------------------------------------------------------------------------
+// e += P ec over the active planes: one thread per coarse cell (I, J) updates
+// its four children (2I + a, 2J + b) from the 3 x 3 coarse neighbourhood,
+// loaded once (ghosts by the coarse level's rules, chosen per column and row);
+// the children of one row are an aligned pair.  The values and the order of
+// operations are those of s_prolong in the fused kernel.
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong(LevelDev L, LevelDev C, Batch B,
                                                  vec2_t<T>* __restrict__ e,
                                                  const vec2_t<T>* __restrict__ ec) {
   typedef vec2_t<T> V;
-  const int nact = *B.nact, n = L.nr * L.nt, bpp = (n + blockDim.x - 1) / blockDim.x;
+  const int nact = *B.nact, nc = C.nr * C.nt, n = L.nr * L.nt;
+  const int bpp = (nc + blockDim.x - 1) / blockDim.x;
+  const T* rt = rtab<T>(L);
+  const T* tt = ttab<T>(L);
   for (int w = blockIdx.x; w < nact * bpp; w += gridDim.x) {
     const int k = w / bpp;
-    const int idx = (w - k * bpp) * blockDim.x + threadIdx.x;
-    if (idx >= n) continue;
+    const int q = (w - k * bpp) * blockDim.x + threadIdx.x;
+    if (q >= nc) continue;
     const int p = B.act[k];
     const int slot = B.slot ? B.slot[p] : p;
-    const int j = idx / L.nr, i = idx - j * L.nr;
-    const V c = prolong_corr<T>(L, C, ec + size_t(p) * C.nr * C.nt, B.mode[slot], i, j);
-    V& u = e[size_t(p) * n + idx];
-    u.x += c.x;
-    u.y += c.y;
+    const bool odd = (B.mode[slot] & 1) != 0;
+    const int J = q / C.nr, I = q - J * C.nr;
+    const V* ecp = ec + size_t(p) * nc;
+    int ic[3], jc[3];
+    bool zc[3], zr[3], nc_[3], nr_[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {   // 1-based coarse column I + u and row J + u
+      const int x = I + u, rx = x == 0 ? C.gL : (x == C.nr + 1 ? C.gR : -1);
+      ic[u] = min(max(x, 1), C.nr) - 1;
+      zc[u] = rx == GH_ZERO;
+      nc_[u] = rx == GH_PARITY && odd;
+      const int y = J + u, ry = y == 0 ? C.gB : (y == C.nt + 1 ? C.gT : -1);
+      jc[u] = min(max(y, 1), C.nt) - 1;
+      zr[u] = ry == GH_ZERO;
+      nr_[u] = ry == GH_PARITY && odd;
+    }
+    V cv[3][3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const V x = ecp[size_t(jc[v]) * C.nr + ic[u]];
+        V r;
+        r.x = (zc[u] || zr[v]) ? T(0) : ((nc_[u] != nr_[v]) ? -x.x : x.x);
+        r.y = (zc[u] || zr[v]) ? T(0) : ((nc_[u] != nr_[v]) ? -x.y : x.y);
+        cv[v][u] = r;
+      }
+    const int i0 = 2 * I;
+    const T p1a = RTAB(rt, RT_P1, i0 + 1), p2a = RTAB(rt, RT_P2, i0 + 1);
+    const T p1b = RTAB(rt, RT_P1, i0 + 2), p2b = RTAB(rt, RT_P2, i0 + 2);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int j = 2 * J + b;
+      const T q1 = TTAB(tt, TT_P1, j + 1), q2 = TTAB(tt, TT_P2, j + 1);
+      V* row = e + size_t(p) * n + size_t(j) * L.nr + i0;
+      V uu[2];
+      ld_pair(uu[0], uu[1], row);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const T p1 = a ? p1b : p1a, p2 = a ? p2b : p2a;
+        const V A = cv[b][a], Bv = cv[b][a + 1], Cv = cv[b + 1][a], D = cv[b + 1][a + 1];
+        const T w11 = p1 * q1, w21 = p2 * q1, w12 = p1 * q2, w22 = p2 * q2;
+        uu[a].x += fmac(w22, D.x, fmac(w12, Cv.x, fmac(w21, Bv.x, w11 * A.x)));
+        uu[a].y += fmac(w22, D.y, fmac(w12, Cv.y, fmac(w21, Bv.y, w11 * A.y)));
+      }
+      st_pair(row, uu[0], uu[1]);
+    }
   }
 }
 
 template <typename T>
 void launch_prolong(const LevelDev& F, const LevelDev& C, const Batch& B, vec2_t<T>* e,
                     const vec2_t<T>* ec, cudaStream_t st) {
-  const int n = F.nr * F.nt;
+  const int n = C.nr * C.nt;
   k_prolong<T><<<work_grid(long((n + 255) / 256) * B.max_planes), 256, 0, st>>>(F, C, B, e, ec);
 }
 

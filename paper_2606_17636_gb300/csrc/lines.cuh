@@ -187,51 +187,6 @@ __device__ __forceinline__ void ld_tab(T (&d)[CPL], const T* tab, int lane, int 
   }
 }
 
-// Value of the coarse correction ec (plane of C.nr x C.nt cells, row-major)
-// at 1-based coarse index (I, J), ghosts included: a missing neighbour is
-// zero next to a Dirichlet side, the cell across a parity face (pole, axis)
-// times (-1)^m, or the cell itself across a Neumann face (the level's
-// gL/gR/gB/gT rules).
-template <typename T>
-__device__ __forceinline__ vec2_t<T> coarse_ghost(const LevelDev& C, const vec2_t<T>* ec, int I, int J, int m) {
-  typedef vec2_t<T> V;
-  T fac = T(1);
-  const T sgn = (m & 1) ? T(-1) : T(1);
-  int Ic = I, Jc = J;
-  if (I == 0) { if (C.gL == GH_ZERO) return z2<V>(); Ic = 1; if (C.gL == GH_PARITY) fac *= sgn; }
-  if (I == C.nr + 1) { if (C.gR == GH_ZERO) return z2<V>(); Ic = C.nr; if (C.gR == GH_PARITY) fac *= sgn; }
-  if (J == 0) { if (C.gB == GH_ZERO) return z2<V>(); Jc = 1; if (C.gB == GH_PARITY) fac *= sgn; }
-  if (J == C.nt + 1) { if (C.gT == GH_ZERO) return z2<V>(); Jc = C.nt; if (C.gT == GH_PARITY) fac *= sgn; }
-  const V v = ec[size_t(Jc - 1) * C.nr + (Ic - 1)];
-  V r;
-  r.x = fac * v.x;
-  r.y = fac * v.y;
-  return r;
-}
-
-// Bilinear prolongation (Sec. 3.1, Eqs. prolongation_sph /
-// prolongation_weight_cyl) at fine cell (i, j) of level L: the weighted sum of
-// the four coarse cells around it, weights from the level's P1 / P2 tables,
-// with the sum's fused operations spelled out (every caller rounds alike).
-template <typename T>
-__device__ __forceinline__ vec2_t<T> prolong_corr(const LevelDev& L, const LevelDev& C, const vec2_t<T>* ec,
-                                                  int m, int i, int j) {
-  typedef vec2_t<T> V;
-  const T* rt = rt_<T>(L);
-  const T* tt = tt_<T>(L);
-  const int i1 = i + 1, j1 = j + 1;
-  const int I1 = (i1 & 1) ? (i1 + 1) / 2 - 1 : i1 / 2, J1 = (j1 & 1) ? (j1 + 1) / 2 - 1 : j1 / 2;
-  const T p1 = rt[RT_P1 * (L.nr + 2) + i1], p2 = rt[RT_P2 * (L.nr + 2) + i1];
-  const T q1 = tt[TT_P1 * (L.nt + 2) + j1], q2 = tt[TT_P2 * (L.nt + 2) + j1];
-  const V a = coarse_ghost<T>(C, ec, I1, J1, m), b = coarse_ghost<T>(C, ec, I1 + 1, J1, m);
-  const V c = coarse_ghost<T>(C, ec, I1, J1 + 1, m), d = coarse_ghost<T>(C, ec, I1 + 1, J1 + 1, m);
-  const T w11 = p1 * q1, w21 = p2 * q1, w12 = p1 * q2, w22 = p2 * q2;
-  V r;
-  r.x = fmac(w22, d.x, fmac(w12, c.x, fmac(w21, b.x, w11 * a.x)));
-  r.y = fmac(w22, d.y, fmac(w12, c.y, fmac(w21, b.y, w11 * a.y)));
-  return r;
-}
-
 // n_sor even-odd SOR sweeps of a line of n cells held in registers:
 // x_k <- x_k + w ((g_k - up_k x_{k+1} - dn_k x_{k-1}) id_k - x_k) (the
 // (1 - w) x_k + w (...) id_k of SOR in four fused operations per component),
