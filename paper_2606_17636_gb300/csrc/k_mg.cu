@@ -67,28 +67,12 @@ __device__ __forceinline__ bool plane_of(const Batch& B, int k, int& p, int& slo
 
 // ---------------------------------------------------------------------------
 // Defect and area-weighted restriction (Sec. 3.1): one thread per coarse cell
-// computes the defect f - L e of its four children and their weighted mean.
+// computes the defect f - L e of its four children and their weighted sum.
+// The children 2I, 2I + 1 of a row are an aligned pair, and so are their
+// neighbours in the rows above and below (one vector access each); the
+// defect's fused operations are spelled out as in the fused V-cycle's
+// restriction.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ vec2_t<T> defect(const LevelDev& L, const T* rt, const T* tt, T s2,
-                                           const vec2_t<T>* __restrict__ e,
-                                           const vec2_t<T>* __restrict__ f, int i, int j) {
-  typedef vec2_t<T> V;
-  const int nr = L.nr, nt = L.nt;
-  const V c = e[size_t(j) * nr + i];
-  const V E = (i + 1 < nr) ? e[size_t(j) * nr + i + 1] : vzero<V>();
-  const V W = (i > 0) ? e[size_t(j) * nr + i - 1] : vzero<V>();
-  const V N = (j + 1 < nt) ? e[size_t(j + 1) * nr + i] : vzero<V>();
-  const V S = (j > 0) ? e[size_t(j - 1) * nr + i] : vzero<V>();
-  const T aE = RTAB(rt, RT_AE, i + 1), aW = RTAB(rt, RT_AW, i + 1), P = RTAB(rt, RT_P, i + 1);
-  const T aN = P * TTAB(tt, TT_AN, j + 1), aS = P * TTAB(tt, TT_AS, j + 1);
-  const T d = RTAB(rt, RT_DR, i + 1) + P * TTAB(tt, TT_DT, j + 1) -
-              s2 * RTAB(rt, RT_Q, i + 1) * TTAB(tt, TT_T, j + 1);
-  const V fv = f[size_t(j) * nr + i];
-  return vmk<V, T>(fv.x - (aE * E.x + aW * W.x + aN * N.x + aS * S.x + d * c.x),
-                   fv.y - (aE * E.y + aW * W.y + aN * N.y + aS * S.y + d * c.y));
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(LevelDev L, LevelDev C, Batch B,
                                                   const vec2_t<T>* __restrict__ e,
@@ -96,27 +80,55 @@ __global__ void __launch_bounds__(256) k_restrict(LevelDev L, LevelDev C, Batch 
                                                   vec2_t<T>* __restrict__ fc) {
   typedef vec2_t<T> V;
   const int nact = *B.nact, nc = C.nr * C.nt, bpp = (nc + blockDim.x - 1) / blockDim.x;
+  const int nr = L.nr, nt = L.nt;
   const T* rt = rtab<T>(L);
   const T* tt = ttab<T>(L);
+  const V z = vzero<V>();
   for (int w = blockIdx.x; w < nact * bpp; w += gridDim.x) {
     const int k = w / bpp;
     const int cidx = (w - k * bpp) * blockDim.x + threadIdx.x;
     if (cidx >= nc) continue;
     const int p = B.act[k];
     const int slot = B.slot ? B.slot[p] : p;
-    const int J = cidx / C.nr, I = cidx - J * C.nr;
+    const int J = cidx / C.nr, I = cidx - J * C.nr, i0 = 2 * I, j0 = 2 * J;
     const T s2 = s2of<T>(B, slot);
-    const size_t base = size_t(p) * L.nr * L.nt;
+    const size_t base = size_t(p) * nr * nt;
+    const V* ep = e + base;
+    const V* fp = f + base;
+    // e on rows j0 - 1 .. j0 + 2 at columns i0, i0 + 1; W and E neighbours on rows j0, j0 + 1
+    V r[4][2], W[2], E[2], fv[2][2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 - 1 + q;
+      if (j >= 0 && j < nt) ld_pair(r[q][0], r[q][1], ep + size_t(j) * nr + i0);
+      else r[q][0] = r[q][1] = z;
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const size_t row = size_t(j0 + b) * nr;
+      W[b] = i0 > 0 ? ep[row + i0 - 1] : z;
+      E[b] = i0 + 2 < nr ? ep[row + i0 + 2] : z;
+      ld_pair(fv[b][0], fv[b][1], fp + row + i0);
+    }
     T ax = 0, ay = 0;
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
-        const int i = 2 * I + a, j = 2 * J + b;
-        const V r = defect<T>(L, rt, tt, s2, e + base, f + base, i, j);
+        const int i = i0 + a, j = j0 + b;
+        const V c = r[b + 1][a];
+        const V Ev = a ? E[b] : r[b + 1][1];
+        const V Wv = a ? r[b + 1][0] : W[b];
+        const V N = r[b + 2][a], S = r[b][a];
+        const T aE = RTAB(rt, RT_AE, i + 1), aW = RTAB(rt, RT_AW, i + 1), P = RTAB(rt, RT_P, i + 1);
+        const T aN = P * TTAB(tt, TT_AN, j + 1), aS = P * TTAB(tt, TT_AS, j + 1);
+        const T d = fmac(-(s2 * RTAB(rt, RT_Q, i + 1)), TTAB(tt, TT_T, j + 1),
+                         fmac(P, TTAB(tt, TT_DT, j + 1), RTAB(rt, RT_DR, i + 1)));
+        const T rx = fv[b][a].x - fmac(d, c.x, fmac(aS, S.x, fmac(aN, N.x, fmac(aW, Wv.x, aE * Ev.x))));
+        const T ry = fv[b][a].y - fmac(d, c.y, fmac(aS, S.y, fmac(aN, N.y, fmac(aW, Wv.y, aE * Ev.y))));
         const T wgt = RTAB(rt, RT_RW, i + 1) * TTAB(tt, TT_RW, j + 1);
-        ax += wgt * r.x;
-        ay += wgt * r.y;
+        ax = fmac(wgt, rx, ax);
+        ay = fmac(wgt, ry, ay);
       }
     fc[size_t(p) * nc + cidx] = vmk<V, T>(ax, ay);
   }
