@@ -618,16 +618,18 @@ def launches_per_solve(s, st):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of full-batch
 # launches on workload 3 (all 129 modes), from the ncu captures of the
 # profiling case (python -m paper_2606_17636_gb300.profile_case
-# --smooth-first): one k_vsmem launch, one finest-level smoothing cycle
-# (k_rpass2 + k_tpass2) and the first stencil launch of k_residual.  They
-# hold for the kernels as captured; a changed kernel needs a new capture.
-VSMEM_TRAFFIC_BYTES = None
-SMOOTH_CYCLE_TRAFFIC_BYTES = 67735552 + 7611136 + 67792896 + 5309440
-RESIDUAL_TRAFFIC_BYTES = 136468480 + 16737024
+# --schedule 2,1,2,4,16,2,2 --smooth-first): one k_vsmem launch, one
+# finest-level smoothing cycle (k_rpass2 + k_tpass2) and the first stencil
+# launch of k_residual.  They hold for the kernels as captured; a changed
+# kernel needs a new capture.
+VSMEM_TRAFFIC_BYTES = 13804288 + 1536
+SMOOTH_CYCLE_TRAFFIC_BYTES = 67736064 + 8047872 + 67791616 + 6110720
+RESIDUAL_TRAFFIC_BYTES = 136426752 + 16644608
 # ncu sm__inst_executed_pipe_fp64 (percent of peak, sustained active) of the
-# kernels bound by the FP64 pipe, at 256 x 128 x 128 (the same kernels with
-# 65 mode planes)
-FP64_PIPE_PCT = {"k_residual": 76.8, "k_fft_fwd": 83.3, "k_fft_inv": 82.3, "k_boundary": 87.1}
+# kernels bound by the FP64 pipe: k_residual and k_fft_fwd from the same
+# capture at 256 x 128 x 256, k_fft_inv and k_boundary at 256 x 128 x 128
+# (the same kernels with 65 mode planes)
+FP64_PIPE_PCT = {"k_residual": 80.1, "k_fft_fwd": 83.8, "k_fft_inv": 82.3, "k_boundary": 87.1}
 
 
 def vcycle_flops_per_cell(sched):
