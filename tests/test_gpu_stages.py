@@ -3,7 +3,8 @@ C ABI stage entry points)."""
 import numpy as np
 import pytest
 
-from gpu_helpers import SMALL, clumps, oracle_plane, to_gpu, to_oracle
+from gpu_helpers import SMALL, clumps, oracle_plane, rel_l2, to_gpu, to_oracle
+from paper_2606_17636_gb300 import workloads
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -250,12 +251,11 @@ def test_fused_vcycle_matches_oracle_vcycle(ps, key, precision, tol):
 # form), 32 x 32 under 64 x 64 (cylinder with the axis), and 64 x 32 with an
 # off-centre polar range (the general separable form)
 LARGE = {
-    "sph_log_128x64": dict(geometry=0, n_r=128, n_tz=64, n_phi=8, spacing=1, r_in=0.05, r_out=20.0,
-                           t_min=None, t_max=None),
-    "cyl_axis_128x128": dict(geometry=1, n_r=128, n_tz=128, n_phi=8, spacing=0, r_in=0.0, r_out=1.0,
-                             t_min=-0.5, t_max=0.5),
-    "sph_band_128x64": dict(geometry=0, n_r=128, n_tz=64, n_phi=8, spacing=0, r_in=1.0, r_out=2.0,
-                            t_min=0.3 * np.pi, t_max=0.65 * np.pi),
+    "sph_log_128x64": workloads.spec(workloads.SPHERICAL, 128, 64, 8, workloads.LOG, 0.05, 20.0),
+    "cyl_axis_128x128": workloads.spec(workloads.CYLINDRICAL, 128, 128, 8, workloads.UNIFORM, 0.0, 1.0,
+                                       -0.5, 0.5),
+    "sph_band_128x64": workloads.spec(workloads.SPHERICAL, 128, 64, 8, workloads.UNIFORM, 1.0, 2.0,
+                                      0.3 * np.pi, 0.65 * np.pi),
 }
 
 
@@ -268,13 +268,10 @@ def test_fused_vcycle_with_the_large_coarsest_level(ps, key, precision, tol):
     with FP32 polar transforms around FP64 radial sweeps: its error stays
     within the FP32 V-cycle's 1e-4."""
     from oracle import mg
-    from oracle.geometry import Plane
     sp = LARGE[key]
     s = ps.Solver.from_spec(sp, precision=precision, use_graph=False, coarsest_size=ps.COARSEST_LARGE)
     plan = ps.plan_inspect(sp, precision=precision, coarsest_size=ps.COARSEST_LARGE)
-    p = Plane.make(sp["geometry"], sp["n_r"], sp["n_tz"], sp["n_phi"], sp["spacing"], sp["r_in"], sp["r_out"],
-                   t_min=sp["t_min"], t_max=sp["t_max"])
-    H = mg.Hierarchy(p, min_cells=32, max_coarse=2048)
+    H = mg.Hierarchy(oracle_plane(sp), min_cells=32, max_coarse=2048)
     assert [(l.plane.n_r, l.plane.n_t) for l in H.levels] == plan["levels"]
     assert s.n_levels == len(plan["levels"]) >= 2
     lev = s.fused_level()
@@ -289,4 +286,25 @@ def test_fused_vcycle_with_the_large_coarsest_level(ps, key, precision, tol):
         ref = u[1:-1, 1:-1].T
         err = np.abs(got[m] - ref).max() / np.abs(ref).max()
         assert err <= tol, (m, err)
+    s.close()
+
+
+@pytest.mark.parametrize("key", ["sph_log_128x64", "cyl_axis_128x128"])
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-11, 1e-9), (1, 1e-9, 1e-7)])
+def test_solve_with_the_large_coarsest_level(ps, key, precision, tol, bound):
+    """Whole solves (captured graph) on the large coarsest-level rule against
+    the oracle's solve, every mode solved directly: the coarsest size changes
+    the V-cycle, not the solution.  FP64 path at tol 1e-11, mixed path at
+    1e-9."""
+    from oracle import dgf, james
+    sp = LARGE[key]
+    s = ps.Solver.from_spec(sp, precision=precision, use_graph=True, coarsest_size=ps.COARSEST_LARGE)
+    assert s.n_levels == len(ps.plan_inspect(sp, precision=precision, coarsest_size=ps.COARSEST_LARGE)["levels"])
+    p = oracle_plane(sp)
+    rho = clumps(sp, 43)
+    ref = james.solve(p, rho, dgf.dgf(p))
+    phi, rc = s.solve(torch.from_numpy(rho).cuda(), tol=tol)
+    assert rc == ps.OK
+    err = rel_l2(p, phi.cpu().numpy(), ref)
+    assert err <= bound, err
     s.close()
