@@ -93,6 +93,32 @@ def test_struct_layouts_match_the_header(tmp_path):
             assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
 
 
+def test_enum_values_match_the_header(tmp_path):
+    """The binding's constants for the descriptor's choices have the
+    header's values."""
+    import shutil
+    import subprocess
+    import paper_2606_17636_gb300 as ps
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    names = {"PSOLVE_COARSEST_AUTO": ps.COARSEST_AUTO, "PSOLVE_COARSEST_SMALL": ps.COARSEST_SMALL,
+             "PSOLVE_COARSEST_LARGE": ps.COARSEST_LARGE, "PSOLVE_DGF_AUTO": ps.DGF_AUTO,
+             "PSOLVE_DGF_AUX": ps.DGF_AUX, "PSOLVE_DGF_EXTENDED": ps.DGF_EXTENDED,
+             "PSOLVE_MIXED": ps.MIXED, "PSOLVE_FP64": ps.FP64}
+    lines = ['#include <stdio.h>', '#include "psolve.h"', "int main(void) {"]
+    lines += ['printf("%s %%d\\n", (int)%s);' % (n, n) for n in names]
+    lines += ["return 0;", "}"]
+    src = tmp_path / "enums.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "enums"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for n, v in names.items():
+        assert int(got[n]) == v, n
+
+
 def test_schedule_entry_points_reject_null_arguments(libpath):
     import paper_2606_17636_gb300 as ps
     L = ps.lib()
