@@ -153,3 +153,31 @@ def test_batch_graph_matches_single_solves_and_times_each_problem(ps):
     assert e.value.code == ps.ERR_ARG
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("nu_pre,nu_post", [(1, 1), (2, 1), (3, 2)])
+def test_update_on_the_last_smoothing_pass(ps, nu_pre, nu_post):
+    """On a grid whose finest level runs the level-wide passes (256 x 128:
+    the fused kernel starts at 128 x 64), the refinement's update rides on
+    the last post-smoothing pass (on grids held wholly by the fused kernel it
+    is a launch of its own).  Every schedule reaches the default schedule's
+    answer, and graph and eager mode give bitwise the same result."""
+    from paper_2606_17636_gb300 import workloads
+    sp = workloads.spec(workloads.SPHERICAL, 256, 128, 8, workloads.LOG, 0.05, 20.0)
+    rho = torch.from_numpy(clumps(sp, 47)).cuda()
+    ref_s = ps.Solver.from_spec(sp, precision=ps.MIXED, use_graph=False)
+    assert ref_s.fused_level() >= 1
+    ref, rc = ref_s.solve(rho, tol=1e-10)
+    assert rc == ps.OK
+    out = []
+    for graph in (True, False):
+        s = ps.Solver.from_spec(sp, precision=ps.MIXED, use_graph=graph)
+        s.set_schedule(nu_pre, nu_post, 2, lines_r=4, cols_t=16, tail_planes=0)
+        phi, rc = s.solve(rho, tol=1e-10)
+        assert rc == ps.OK
+        out.append(phi.clone())
+        s.close()
+    assert torch.equal(out[0], out[1])
+    d = float(torch.linalg.vector_norm(out[0] - ref) / torch.linalg.vector_norm(ref))
+    assert d <= 1e-8, d
+    ref_s.close()
