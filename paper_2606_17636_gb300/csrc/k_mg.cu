@@ -279,10 +279,11 @@ __device__ void retire_block(int* act, int* nact, const Sum4* __restrict__ psum,
                              unsigned long long handle, int* scan, int tail_planes);
 
 // FP64 defect at (i, j) from the per-cell products (one FP64 operation for
-// the mode's diagonal, five fused multiply-adds per component starting from
-// the right-hand side).
+// the mode's diagonal read from its own table dm, five fused multiply-adds per
+// component starting from the right-hand side).
 __device__ __forceinline__ double2 defect_tab(const LevelDev& L, const double* __restrict__ ct,
-                                              int n, double s2, const double2* __restrict__ e,
+                                              const double* __restrict__ dm, int n,
+                                              const double2* __restrict__ e,
                                               const double2* __restrict__ f, int i, int j) {
   const int nr = L.nr, nt = L.nt, idx = j * nr + i;
   const double2 c = e[idx];
@@ -292,7 +293,7 @@ __device__ __forceinline__ double2 defect_tab(const LevelDev& L, const double* _
   const double2 S = (j > 0) ? e[idx - nr] : make_double2(0.0, 0.0);
   const double aE = RTAB(L.rd, RT_AE, i + 1), aW = RTAB(L.rd, RT_AW, i + 1);
   const double aN = ct[idx], aS = ct[n + idx];
-  const double d = fma(-s2, ct[3 * n + idx], ct[2 * n + idx]);
+  const double d = dm[idx];
   const double2 fv = f[idx];
   double rx = fma(-aE, E.x, fv.x), ry = fma(-aE, E.y, fv.y);
   rx = fma(-aW, W.x, rx);
@@ -310,7 +311,8 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
                                                   const double2* __restrict__ u,
                                                   vec2_t<T>* __restrict__ r, Sum4* part,
                                                   Sum4* psum, int* cnt, int bpp, RetireArgs ra,
-                                                  const double* __restrict__ ctab) {
+                                                  const double* __restrict__ ctab,
+                                                  const double* __restrict__ dtab) {
   __shared__ Sum4 sh[8];
   __shared__ float4 shf[8];
   __shared__ int last, glast;
@@ -342,8 +344,8 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
       if (idx < n) {
         const int j = idx / nr, i = idx - j * nr;
         const size_t base = size_t(p) * n;
-        const double s2 = B.s2d[slot];
-        const double2 rv = r_is_f ? f[base + idx] : defect_tab(L, ctab, n, s2, u + base, f + base, i, j);
+        const double2 rv = r_is_f ? f[base + idx]
+                                  : defect_tab(L, ctab, dtab + size_t(slot) * n, n, u + base, f + base, i, j);
         const vec2_t<T> ro = vmk<vec2_t<T>, T>(to_buf<T>(rv.x), to_buf<T>(rv.y));
         r[base + idx] = ro;
         const float dv = L.rf[RT_V * (nr + 2) + i + 1] * L.tf[TT_V * (nt + 2) + j + 1];
@@ -405,10 +407,10 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const dou
 template <typename T>
 void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
                      vec2_t<T>* r, Sum4* part, Sum4* psum, int* cnt, const RetireArgs& ra,
-                     cudaStream_t st, const double* ctab) {
+                     cudaStream_t st, const double* ctab, const double* dtab) {
   const int bpp = residual_blocks(L.nr, L.nt);
   k_residual<T><<<work_grid(long(bpp) * B.max_planes), 256, 0, st>>>(L, B, f, u, r, part, psum,
-                                                                       cnt, bpp, ra, ctab);
+                                                                       cnt, bpp, ra, ctab, dtab);
 }
 
 // ---------------------------------------------------------------------------
@@ -523,7 +525,7 @@ void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t 
                                  cudaStream_t);                                                  \
   template void launch_residual<T>(const LevelDev&, const Batch&, const double2*,               \
                                    const double2*, vec2_t<T>*, Sum4*, Sum4*, int*,        \
-                                   const RetireArgs&, cudaStream_t, const double*);
+                                   const RetireArgs&, cudaStream_t, const double*, const double*);
 INST(float)
 INST(double)
 

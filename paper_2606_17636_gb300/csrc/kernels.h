@@ -225,11 +225,12 @@ struct RetireArgs {
 // counts cycles, sets the status, compacts the active list and sets the
 // continue flag (and the graph conditional).
 // ctab: the level's per-cell FP64 products [4][nt][nr] (P aN, P aS,
-// DR + P DT, Q T), the same for every mode.
+// DR + P DT, Q T), the same for every mode; dtab: the diagonal
+// DR + P DT - s_m^2 Q T per mode slot [slots][nt][nr].
 template <typename T>
 void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
                      vec2_t<T>* r, Sum4* part, Sum4* psum, int* cnt, const RetireArgs& ra,
-                     cudaStream_t st, const double* ctab);
+                     cudaStream_t st, const double* ctab, const double* dtab);
 int residual_blocks(int nr, int nt);
 
 void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t st);

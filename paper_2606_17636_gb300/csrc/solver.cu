@@ -120,6 +120,14 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
       }
     d_ctab = upload(A, ct);
     if (!d_ctab) { err = "out of device memory"; return false; }
+    // the mode's diagonal per slot and cell, D_r + P D_theta - s_m^2 Q T:
+    // the same correctly rounded fused multiply-add the residual would
+    // otherwise repeat on every iteration
+    std::vector<double> dm(s2.size() * n);
+    for (size_t k = 0; k < s2.size(); ++k)
+      for (size_t q = 0; q < n; ++q) dm[k * n + q] = std::fma(-s2[k], ct[3 * n + q], ct[2 * n + q]);
+    d_dtab = upload(A, dm);
+    if (!d_dtab) { err = "out of device memory"; return false; }
   }
   if (!H.coarse_inv.empty()) d_inv = upload(A, H.coarse_inv);
   if (!H.coarse_blk.empty()) d_blk = upload(A, H.coarse_blk);
@@ -404,9 +412,9 @@ void MGSolver::residual(const double2* ff, const double2* u, double tol, cudaStr
   ra.zero_guess = zero_guess;
   ra.tail_planes = tail_planes;
   if (opt.precision)
-    launch_residual<float>(lv[0], batch, ff, u, (float2*)f[0], d_part, d_psum, d_cnt, ra, st, d_ctab);
+    launch_residual<float>(lv[0], batch, ff, u, (float2*)f[0], d_part, d_psum, d_cnt, ra, st, d_ctab, d_dtab);
   else
-    launch_residual<double>(lv[0], batch, ff, u, (double2*)f[0], d_part, d_psum, d_cnt, ra, st, d_ctab);
+    launch_residual<double>(lv[0], batch, ff, u, (double2*)f[0], d_part, d_psum, d_cnt, ra, st, d_ctab, d_dtab);
 }
 
 void MGSolver::residual_to(const double2* ff, const double2* u, void* r, cudaStream_t st) {
@@ -421,9 +429,9 @@ void MGSolver::residual_to(const double2* ff, const double2* u, void* r, cudaStr
   ra.zero_guess = 0;
   ra.tail_planes = 0;
   if (opt.precision)
-    launch_residual<float>(lv[0], batch, ff, u, (float2*)r, d_part, d_psum, d_cnt, ra, st, d_ctab);
+    launch_residual<float>(lv[0], batch, ff, u, (float2*)r, d_part, d_psum, d_cnt, ra, st, d_ctab, d_dtab);
   else
-    launch_residual<double>(lv[0], batch, ff, u, (double2*)r, d_part, d_psum, d_cnt, ra, st, d_ctab);
+    launch_residual<double>(lv[0], batch, ff, u, (double2*)r, d_part, d_psum, d_cnt, ra, st, d_ctab, d_dtab);
 }
 
 // One V-cycle on the error equation L e_0 = f_0 (f_0 = FP64 residual in the
