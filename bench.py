@@ -128,7 +128,7 @@ def peaks():
 
 
 # --------------------------------------------------------------------------
-# CPU oracle baseline (the reference arm of this build)
+# CPU oracle baseline (the reference arm: the oracle timed as it stands)
 # --------------------------------------------------------------------------
 def oracle_desc(spec):
     return (spec["geometry"], spec["n_r"], spec["n_tz"], spec["n_phi"], spec["spacing"],
