@@ -253,27 +253,6 @@ int residual_blocks(int nr, int nt) {
   return (nr * nt + 255) / 256;
 }
 
-__device__ __forceinline__ Sum4 add4(Sum4 a, Sum4 b) {
-  return sum4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-}
-
-__device__ Sum4 block_sum4(Sum4 v, Sum4* sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-    v.z += __shfl_down_sync(0xffffffffu, v.z, o);
-    v.w += __shfl_down_sync(0xffffffffu, v.w, o);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  Sum4 s = sum4(0, 0, 0, 0);
-  if (threadIdx.x == 0)
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) s = add4(s, sh[w]);
-  return s;
-}
-
 __device__ void retire_block(int* act, int* nact, const Sum4* __restrict__ psum, RetireState S,
                              double tol, int max_cycles, int stagnation, int use_cond,
                              unsigned long long handle, int* scan, int tail_planes);
@@ -306,107 +285,174 @@ __device__ __forceinline__ double2 defect_tab(const LevelDev& L, const double* _
 }
 
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const double2* __restrict__ f,
-                                                  const double2* __restrict__ u,
-                                                  vec2_t<T>* __restrict__ r, Sum4* part,
-                                                  Sum4* psum, int* cnt, int bpp, RetireArgs ra,
-                                                  const double* __restrict__ ctab,
-                                                  const double* __restrict__ dtab) {
-  __shared__ Sum4 sh[8];
-  __shared__ float4 shf[8];
-  __shared__ int last, glast;
-  __shared__ int scan[256];
-  // nact is read once: the retiring block rewrites it only after every work
-  // item of this launch has been summed
-  const int nact = *B.nact;
+// The four sums of one work item or block, combined across a warp (lane 0).
+__device__ __forceinline__ SqPart sq_warp_sum4(const SqPart& q) {
+  SqPart t;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const SqAcc a = sq_warp_sum(SqAcc{q.s[c], q.e[c]});
+    t.s[c] = a.s;
+    t.e[c] = a.e;
+  }
+  return t;
+}
+__device__ __forceinline__ SqPart sq_part(SqAcc x, SqAcc y, SqAcc z, SqAcc w) {
+  SqPart q;
+  q.s[0] = x.s; q.s[1] = y.s; q.s[2] = z.s; q.s[3] = w.s;
+  q.e[0] = x.e; q.e[1] = y.e; q.e[2] = z.e; q.e[3] = w.e;
+  return q;
+}
+__device__ __forceinline__ SqPart sq_part_zero() {
+  const SqAcc z = sq_zero();
+  return sq_part(z, z, z, z);
+}
+// Warp 0 combines the per-warp sums the block left in sh[0 .. nw).
+__device__ __forceinline__ SqPart sq_block_tail(const SqPart* sh, int lane, int nw) {
+  return sq_warp_sum4(lane < nw ? sh[lane] : sq_part_zero());
+}
+
+// The residual work items of one launch.  ZERO: u = 0 on the first
+// iteration, so r = f and |r|^2 = |f|^2 (no stencil); CPT: cells per thread
+// and work item.  Both are fixed per launch, so each combination is its own
+// loop and no branch of the other remains in the cell loop.
+template <typename T, bool ZERO, int CPT>
+__device__ __forceinline__ void residual_items(const LevelDev& L, const Batch& B,
+                                               const double2* __restrict__ f,
+                                               const double2* __restrict__ u,
+                                               vec2_t<T>* __restrict__ r, SqPart* part, Sum4* psum,
+                                               int* cnt, int bpp, const RetireArgs& ra,
+                                               const double* __restrict__ ctab,
+                                               const double* __restrict__ dtab, int nact,
+                                               bool want_f, SqPart* sh, int* flag, int* scan) {
   const int nr = L.nr, nt = L.nt, n = nr * nt;
-  const bool want_f = *ra.S.iter == 0;     // |f| is needed on the first iteration only
-  // from a zero initial guess the first defect is f itself (no stencil)
-  const bool r_is_f = want_f && ra.zero_guess;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // Work items of cpt x 256 cells: with many planes active the per-item
-  // reduction, fence and arrival count are paid once per 1024 cells; with few
-  // planes every item is 256 cells, spreading a plane's FP64 work over more
-  // SMs.  bpp (the caller's) is the item count for cpt = 1.
-  const int cpt = nact >= 16 ? 4 : 1;
-  const int ipp = (bpp + cpt - 1) / cpt;   // items per plane
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = int(blockDim.x >> 5);
+  const int ipp = (bpp + CPT - 1) / CPT;   // items per plane
   for (int w = blockIdx.x; w < nact * ipp; w += gridDim.x) {
     const int k = w / ipp, bx = w - k * ipp;
     const int p = B.act[k];
     const int slot = B.slot ? B.slot[p] : p;
-    // the residual is FP64; its norm only drives the convergence test, so the
-    // volume-weighted squares are accumulated in FP32 within the block
-    float4 accf = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-    for (int c = 0; c < cpt; ++c) {
-      const int idx = (bx * cpt + c) * blockDim.x + threadIdx.x;
+    const size_t base = size_t(p) * n;
+    // the residual is FP64; its norm only drives the convergence test, so
+    // the volume-weighted squares of its FP32 rounding are summed in FP32
+    // (SqAcc: exact power-of-two scaling, no under- or overflow)
+    SqAcc ax = sq_zero(), ay = sq_zero(), az = sq_zero(), aw = sq_zero();
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int idx = (bx * CPT + c) * blockDim.x + threadIdx.x;
       if (idx < n) {
         const int j = idx / nr, i = idx - j * nr;
-        const size_t base = size_t(p) * n;
-        const double2 rv = r_is_f ? f[base + idx]
-                                  : defect_tab(L, ctab, dtab + size_t(slot) * n, n, u + base, f + base, i, j);
+        double2 rv;
+        if constexpr (ZERO) rv = f[base + idx];
+        else rv = defect_tab(L, ctab, dtab + size_t(slot) * n, n, u + base, f + base, i, j);
         const vec2_t<T> ro = vmk<vec2_t<T>, T>(to_buf<T>(rv.x), to_buf<T>(rv.y));
         r[base + idx] = ro;
         const float dv = L.rf[RT_V * (nr + 2) + i + 1] * L.tf[TT_V * (nt + 2) + j + 1];
-        const float rx = float(ro.x), ry = float(ro.y);
-        accf.x += dv * rx * rx;
-        accf.y += dv * ry * ry;
-        if (want_f) {
+        sq_add(ax, ro.x, dv);   // the residual as stored: FP32 values, or FP64 ones
+        sq_add(ay, ro.y, dv);
+        if (!ZERO && want_f) {
           const double2 fv = f[base + idx];
-          const float fx = f64_to_f32(fv.x), fy = f64_to_f32(fv.y);
-          accf.z += dv * fx * fx;
-          accf.w += dv * fy * fy;
+          sq_add(az, fv.x, dv);
+          sq_add(aw, fv.y, dv);
         }
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      accf.x += __shfl_down_sync(0xffffffffu, accf.x, o);
-      accf.y += __shfl_down_sync(0xffffffffu, accf.y, o);
-      accf.z += __shfl_down_sync(0xffffffffu, accf.z, o);
-      accf.w += __shfl_down_sync(0xffffffffu, accf.w, o);
+    ax = sq_warp_sum(ax);
+    ay = sq_warp_sum(ay);
+    if (ZERO) {   // r = f: the same sums
+      az = ax;
+      aw = ay;
+    } else if (want_f) {
+      az = sq_warp_sum(az);
+      aw = sq_warp_sum(aw);
     }
-    if (lane == 0) shf[warp] = accf;
+    if (lane == 0) sh[warp] = sq_part(ax, ay, az, aw);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      Sum4 acc = sum4(0, 0, 0, 0);
-      for (int q = 0; q < int(blockDim.x >> 5); ++q)
-        acc = add4(acc, sum4(shf[q].x, shf[q].y, shf[q].z, shf[q].w));
-      part[size_t(p) * bpp + bx] = acc;
-      __threadfence();
-      last = (atomicAdd(&cnt[p], 1) == ipp - 1);
-    }
-    __syncthreads();
-    if (last) {
-      __threadfence();
-      Sum4 t = sum4(0, 0, 0, 0);
-      for (int b = threadIdx.x; b < ipp; b += blockDim.x) {
-        const double2* q2 = reinterpret_cast<const double2*>(&part[size_t(p) * bpp + b]);
-        const double2 qa = __ldcg(q2), qb = __ldcg(q2 + 1);
-        t = add4(t, sum4(qa.x, qa.y, qb.x, qb.y));
-      }
-      const Sum4 tot = block_sum4(t, sh);
-      if (threadIdx.x == 0) {
-        psum[p] = tot;
-        cnt[p] = 0;
+    if (warp == 0) {
+      const SqPart t = sq_block_tail(sh, lane, nw);
+      if (lane == 0) {
+        part[size_t(p) * bpp + bx] = t;
         __threadfence();
-        glast = (atomicAdd(ra.gcnt, 1) == nact - 1);
+        flag[0] = (atomicAdd(&cnt[p], 1) == ipp - 1);
+      }
+    }
+    __syncthreads();
+    if (flag[0]) {   // the plane's last item: its sums over the items in item order
+      __threadfence();
+      SqPart t = sq_part_zero();
+      for (int b = threadIdx.x; b < ipp; b += blockDim.x) {
+        const SqPart* q = &part[size_t(p) * bpp + b];
+        const float4 qs = __ldcg(reinterpret_cast<const float4*>(q->s));
+        const int4 qb = __ldcg(reinterpret_cast<const int4*>(q->e));
+        const float vs[4] = {qs.x, qs.y, qs.z, qs.w};
+        const int vb[4] = {qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const SqAcc m = sq_merge(SqAcc{t.s[c], t.e[c]}, SqAcc{vs[c], vb[c]});
+          t.s[c] = m.s;
+          t.e[c] = m.e;
+        }
+      }
+      t = sq_warp_sum4(t);
+      if (lane == 0) sh[warp] = t;   // warp 0 read sh before the barrier above
+      __syncthreads();
+      if (warp == 0) {
+        const SqPart q = sq_block_tail(sh, lane, nw);
+        if (lane == 0) {
+          psum[p] = sum4(sq_value(SqAcc{q.s[0], q.e[0]}), sq_value(SqAcc{q.s[1], q.e[1]}),
+                         sq_value(SqAcc{q.s[2], q.e[2]}), sq_value(SqAcc{q.s[3], q.e[3]}));
+          cnt[p] = 0;
+          __threadfence();
+          flag[1] = (atomicAdd(ra.gcnt, 1) == nact - 1);
+        }
       }
       __syncthreads();
-      if (glast) {   // every plane's sum is in: retire converged planes (App. B)
+      if (flag[1]) {   // every plane's sum is in: retire converged planes (App. B)
         __threadfence();
         retire_block(const_cast<int*>(B.act), const_cast<int*>(B.nact), psum, ra.S, ra.tol,
                      ra.max_cycles, ra.stagnation, ra.use_cond, ra.handle, scan, ra.tail_planes);
         if (threadIdx.x == 0) *ra.gcnt = 0;
       }
     }
-    __syncthreads();   // shf / last / glast are reused by the next work item
+    __syncthreads();   // sh and flag are reused by the next work item
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_residual(LevelDev L, Batch B, const double2* __restrict__ f,
+                                                  const double2* __restrict__ u,
+                                                  vec2_t<T>* __restrict__ r, SqPart* part,
+                                                  Sum4* psum, int* cnt, int bpp, RetireArgs ra,
+                                                  const double* __restrict__ ctab,
+                                                  const double* __restrict__ dtab) {
+  __shared__ SqPart sh[8];
+  __shared__ int flag[2];
+  __shared__ int scan[256];
+  // nact is read once: the retiring block rewrites it only after every work
+  // item of this launch has been summed
+  const int nact = *B.nact;
+  const bool want_f = *ra.S.iter == 0;     // |f| is needed on the first iteration only
+  // from a zero initial guess the first defect is f itself (no stencil)
+  const bool r_is_f = want_f && ra.zero_guess;
+  // Work items of CPT x 256 cells: with many planes active the per-item
+  // reduction, fence and arrival count are paid once per 1024 cells; with few
+  // planes every item is 256 cells, spreading a plane's FP64 work over more
+  // SMs.  bpp (the caller's) is the item count for CPT = 1.
+  if (r_is_f) {
+    if (nact >= 16)
+      residual_items<T, true, 4>(L, B, f, u, r, part, psum, cnt, bpp, ra, ctab, dtab, nact, want_f, sh, flag, scan);
+    else
+      residual_items<T, true, 1>(L, B, f, u, r, part, psum, cnt, bpp, ra, ctab, dtab, nact, want_f, sh, flag, scan);
+  } else {
+    if (nact >= 16)
+      residual_items<T, false, 4>(L, B, f, u, r, part, psum, cnt, bpp, ra, ctab, dtab, nact, want_f, sh, flag, scan);
+    else
+      residual_items<T, false, 1>(L, B, f, u, r, part, psum, cnt, bpp, ra, ctab, dtab, nact, want_f, sh, flag, scan);
   }
 }
 
 template <typename T>
 void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
-                     vec2_t<T>* r, Sum4* part, Sum4* psum, int* cnt, const RetireArgs& ra,
+                     vec2_t<T>* r, SqPart* part, Sum4* psum, int* cnt, const RetireArgs& ra,
                      cudaStream_t st, const double* ctab, const double* dtab) {
   const int bpp = residual_blocks(L.nr, L.nt);
   k_residual<T><<<work_grid(long(bpp) * B.max_planes), 256, 0, st>>>(L, B, f, u, r, part, psum,
@@ -524,7 +570,7 @@ void launch_init_active(int* act, int* nact, int n, RetireState S, cudaStream_t 
   template void launch_update<T>(const LevelDev&, const Batch&, double2*, const vec2_t<T>*,     \
                                  cudaStream_t);                                                  \
   template void launch_residual<T>(const LevelDev&, const Batch&, const double2*,               \
-                                   const double2*, vec2_t<T>*, Sum4*, Sum4*, int*,        \
+                                   const double2*, vec2_t<T>*, SqPart*, Sum4*, int*,      \
                                    const RetireArgs&, cudaStream_t, const double*, const double*);
 INST(float)
 INST(double)

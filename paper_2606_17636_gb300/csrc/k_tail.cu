@@ -58,6 +58,8 @@ enum { TS_ACTIVE = 1, TS_OK = 0, TS_STAGNATED = 2, TS_NOTCONV = -4, TS_NONFINITE
 struct __align__(16) D4 {
   double x, y, z, w;
 };
+static_assert(sizeof(D4) == sizeof(SqPart) && alignof(D4) == alignof(SqPart),
+              "the warp sums reuse the D4 reduction slots");
 
 __device__ __forceinline__ V vz() { return make_float2(0.f, 0.f); }
 
@@ -649,7 +651,8 @@ __global__ void __launch_bounds__(kTailThreads, 1)
     // FP64 residual of the own rows (the defect expression of the
     // level-wide residual kernel), stored as the FP32 right-hand side of
     // level 0; volume-weighted squares accumulated in FP32 per thread
-    float ax = 0.f, ay = 0.f;
+    // (SqAcc, as in the level-wide residual kernel)
+    SqAcc ax = sq_zero(), ay = sq_zero();
     {
       const LevelDev& L0 = sL[0];
       for (int idx = threadIdx.x; idx < s0 * nr0; idx += blockDim.x) {
@@ -679,19 +682,27 @@ __global__ void __launch_bounds__(kTailThreads, 1)
         const V ro = make_float2(f64_to_f32(rx), f64_to_f32(ry));
         rowp(sm, t0.fo, nr0, h, r)[i ^ tsw(nr0, j)] = ro;
         const float dv = L0.rf[RT_V * NR0 + i + 1] * L0.tf[TT_V * NT0 + j + 1];
-        ax += dv * ro.x * ro.x;
-        ay += dv * ro.y * ro.y;
+        sq_add(ax, ro.x, dv);
+        sq_add(ay, ro.y, dv);
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      ax += __shfl_down_sync(0xffffffffu, ax, o);
-      ay += __shfl_down_sync(0xffffffffu, ay, o);
+    ax = sq_warp_sum(ax);
+    ay = sq_warp_sum(ay);
+    SqPart* rq = reinterpret_cast<SqPart*>(red);   // the same 32 bytes per warp
+    if ((threadIdx.x & 31) == 0) {
+      SqPart q;
+      q.s[0] = ax.s; q.s[1] = ay.s; q.s[2] = 0.f; q.s[3] = 0.f;
+      q.e[0] = ax.e; q.e[1] = ay.e; q.e[2] = sq_zero().e; q.e[3] = sq_zero().e;
+      rq[threadIdx.x >> 5] = q;
     }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = D4{ax, ay, 0.0, 0.0};
     __syncthreads();
-    if (threadIdx.x < C) {   // the CTA's partial to every CTA of the cluster
-      D4 tsum{0.0, 0.0, dead ? 1.0 : 0.0, 0.0};
-      for (int w = 0; w < int(blockDim.x >> 5); ++w) { tsum.x += red[w].x; tsum.y += red[w].y; }
+    if (threadIdx.x < C) {   // the CTA's partial (FP64) to every CTA of the cluster
+      SqAcc sx = sq_zero(), sy = sq_zero();
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+        sx = sq_merge(sx, SqAcc{rq[w].s[0], rq[w].e[0]});
+        sy = sq_merge(sy, SqAcc{rq[w].s[1], rq[w].e[1]});
+      }
+      const D4 tsum{sq_value(sx), sq_value(sy), dead ? 1.0 : 0.0, 0.0};
       *cl.map_shared_rank(part + rank, int(threadIdx.x)) = tsum;
     }
     __syncthreads();

@@ -75,6 +75,78 @@ __device__ __forceinline__ double f32_to_f64(float x) {
   return __longlong_as_double(static_cast<long long>(d));
 }
 
+// Volume-weighted sums of squares in FP32 over the whole binary64 range.  A
+// sum is an FP32 value s with an exponent e and stands for s 2^(2e): every
+// value v is entered as v 2^-e, e being the largest exponent met so far
+// (clamped to binary32's normal range for FP32 values, binary64's for FP64
+// values), so the largest scaled value lies in [1, 2) and no square under-
+// or overflows FP32 whatever the scale of the data (the weights are at most
+// 1).  When a larger exponent arrives the sum so far is scaled down to it
+// (a part below 2^-126 of the new scale is dropped, far below FP32's
+// rounding).  Non-finite values give non-finite sums.  Only integer and
+// FP32 instructions: the reduction of the FP64 residual kernel stays off
+// the FP64 pipe.
+struct SqAcc {
+  float s;
+  int e;
+};
+__device__ __forceinline__ float pow2f(int k) {   // 2^k for k in [-126, 127], 0 below
+  return k < -126 ? 0.f : __uint_as_float(unsigned(k + 127) << 23);
+}
+__device__ __forceinline__ SqAcc sq_zero() { return SqAcc{0.f, -1022}; }
+__device__ __forceinline__ void sq_add(SqAcc& a, float v, float w) {
+  const int eb = int((__float_as_uint(v) >> 23) & 0xffu);
+  const int ne = max(a.e, min(max(eb, 1), 253) - 127);
+  a.s *= pow2f(2 * (a.e - ne));
+  a.e = ne;
+  const float x = v * pow2f(-ne);   // exact while the scaled value is normal
+  a.s = __fmaf_rn(w * x, x, a.s);
+}
+__device__ __forceinline__ void sq_add(SqAcc& a, double v, float w) {
+  const long long bits = __double_as_longlong(v);
+  const int eb = int((bits >> 52) & 0x7ff);
+  const int ne = max(a.e, min(max(eb, 1), 2046) - 1023);
+  a.s *= pow2f(2 * (a.e - ne));
+  a.e = ne;
+  // v 2^-ne through the exponent field: inf and NaN kept, zero where the
+  // scaled value (or v itself) is below binary64's normal range
+  const int sb = eb - ne;
+  const double y = eb == 2047 ? v
+                 : (eb == 0 || sb < 1 ? 0.0 : __longlong_as_double(bits - static_cast<long long>(ne) * (1ll << 52)));
+  const float x = f64_to_f32(y);
+  a.s = __fmaf_rn(w * x, x, a.s);
+}
+__device__ __forceinline__ SqAcc sq_merge(SqAcc a, SqAcc c) {
+  const int e = max(a.e, c.e);
+  return SqAcc{__fmaf_rn(a.s, pow2f(2 * (a.e - e)), c.s * pow2f(2 * (c.e - e))), e};
+}
+// The sum over the warp's 32 lanes, complete in lane 0.
+__device__ __forceinline__ SqAcc sq_warp_sum(SqAcc a) {
+  const int e = __reduce_max_sync(0xffffffffu, a.e);
+  float s = a.s * pow2f(2 * (a.e - e));
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  return SqAcc{s, e};
+}
+// s 2^(2e) in FP64 through the exponent field: exact inside binary64's
+// normal range, infinity above it, zero below it.
+__device__ __forceinline__ double sq_value(SqAcc a) {
+  const double d = f32_to_f64(a.s);
+  if (a.s == 0.f || !isfinite(a.s)) return d;
+  const long long bits = __double_as_longlong(d);
+  const int eb = int((bits >> 52) & 0x7ff) + 2 * a.e;
+  if (eb >= 2047) return __longlong_as_double(0x7ff0000000000000ll);
+  if (eb < 1) return 0.0;
+  return __longlong_as_double(bits + static_cast<long long>(2 * a.e) * (1ll << 52));
+}
+#endif
+
+// One work item's four sums of squares as SqAcc pairs (s[c], e[c]).
+struct __align__(16) SqPart {
+  float s[4];
+  int e[4];
+};
+
+#ifdef __CUDACC__
 // An FP64 value in the buffer precision T, and back.
 template <typename T>
 __device__ __forceinline__ T to_buf(double x) {
@@ -219,8 +291,9 @@ struct RetireArgs {
 };
 
 // r = f - L u (FP64), stored as T2, and the volume-weighted norms per plane
-// (deterministic: each block writes its partial to part[p * nblk + b]; the
-// last block of a plane adds them in block order into psum[p]).  The last
+// (deterministic: each work item writes its FP32 partial sums (SqAcc) to
+// part[p * nblk + b]; the last item of a plane to finish combines them in a
+// fixed order and stores them as FP64 in psum[p]).  The last
 // plane to finish then applies the App. B criterion to every active plane,
 // counts cycles, sets the status, compacts the active list and sets the
 // continue flag (and the graph conditional).
@@ -229,7 +302,7 @@ struct RetireArgs {
 // DR + P DT - s_m^2 Q T per mode slot [slots][nt][nr].
 template <typename T>
 void launch_residual(const LevelDev& L, const Batch& B, const double2* f, const double2* u,
-                     vec2_t<T>* r, Sum4* part, Sum4* psum, int* cnt, const RetireArgs& ra,
+                     vec2_t<T>* r, SqPart* part, Sum4* psum, int* cnt, const RetireArgs& ra,
                      cudaStream_t st, const double* ctab, const double* dtab);
 int residual_blocks(int nr, int nt);
 

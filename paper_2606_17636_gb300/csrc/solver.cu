@@ -62,6 +62,26 @@ static std::vector<float> to_f(const std::vector<double>& v) {
   return std::vector<float>(v.begin(), v.end());
 }
 
+// The FP32 copy of a level table with its volume row (len entries from
+// row * len) scaled by a power of two that brings the largest entry into
+// [1/2, 1).  The row only weights the squares of the convergence norms
+// (App. B), whose test compares ratios of two such sums, so the scaling
+// leaves every decision unchanged, and it keeps the weights (and the product
+// of the radial and polar ones) inside FP32's range for grids in any length
+// unit.
+static std::vector<float> to_f_volume(const std::vector<double>& v, int row, int len) {
+  std::vector<float> out = to_f(v);
+  double mx = 0.0;
+  for (int i = 0; i < len; ++i) mx = std::max(mx, std::fabs(v[size_t(row) * len + i]));
+  if (mx > 0.0 && std::isfinite(mx)) {
+    int e = 0;
+    std::frexp(mx, &e);
+    for (int i = 0; i < len; ++i)
+      out[size_t(row) * len + i] = float(std::ldexp(v[size_t(row) * len + i], -e));
+  }
+  return out;
+}
+
 bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vector<int>& modes,
                     const std::vector<int>& plane_slot, int mp, const MGOptions& o,
                     std::string& err) {
@@ -89,8 +109,8 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
     d.nt = h.g.t.n;
     d.rd = upload_tab(A, h.rtab);
     d.td = upload_tab(A, h.ttab);
-    d.rf = upload_tab(A, to_f(h.rtab));
-    d.tf = upload_tab(A, to_f(h.ttab));
+    d.rf = upload_tab(A, to_f_volume(h.rtab, RT_V, d.nr + 2));
+    d.tf = upload_tab(A, to_f_volume(h.ttab, TT_V, d.nt + 2));
     d.omr_d = upload(A, h.om_r);
     d.omt_d = upload(A, h.om_t);
     d.omr_f = upload(A, to_f(h.om_r));
@@ -280,7 +300,7 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
   const int nblk = residual_blocks(lv[0].nr, lv[0].nt);
   d_act = static_cast<int*>(A.get(sizeof(int) * mp));
   d_nact = static_cast<int*>(A.get(sizeof(int)));
-  d_part = static_cast<Sum4*>(A.get(sizeof(Sum4) * size_t(mp) * nblk));
+  d_part = static_cast<SqPart*>(A.get(sizeof(SqPart) * size_t(mp) * nblk));
   d_psum = static_cast<Sum4*>(A.get(sizeof(Sum4) * mp));
   d_cnt = static_cast<int*>(A.get(sizeof(int) * mp));
   d_cycles = static_cast<int*>(A.get(sizeof(int) * mp));
@@ -326,8 +346,12 @@ bool MGSolver::init(Arena& A, const PlaneGeo& fine, bool neumann, const std::vec
         const LevelHost& hl = H.lv[l];
         const int nr = lv[l].nr, nt = lv[l].nt;
         float* o = pk.data() + q * tab + off[l];
-        o = std::copy(hl.rtab.begin(), hl.rtab.end(), o);
-        o = std::copy(hl.ttab.begin(), hl.ttab.end(), o);
+        // the FP32 level tables as uploaded (volume rows scaled alike), so
+        // the tail's norms match the level-wide residual kernel's
+        const std::vector<float> rt = to_f_volume(hl.rtab, RT_V, nr + 2);
+        const std::vector<float> tt = to_f_volume(hl.ttab, TT_V, nt + 2);
+        o = std::copy(rt.begin(), rt.end(), o);
+        o = std::copy(tt.begin(), tt.end(), o);
         o = std::copy(hl.om_r.begin() + q * nt, hl.om_r.begin() + (q + 1) * nt, o);
         std::copy(hl.om_t.begin() + q * nr, hl.om_t.begin() + (q + 1) * nr, o);
       }

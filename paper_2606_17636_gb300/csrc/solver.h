@@ -103,7 +103,7 @@ class MGSolver {
   double* d_sep = nullptr;
   double* d_ctab = nullptr;   // level-0 per-cell FP64 products [4][nt][nr]
   double* d_dtab = nullptr;   // level-0 diagonal of each mode slot [slots][nt][nr]
-  Sum4* d_part = nullptr;
+  SqPart* d_part = nullptr;
   Sum4* d_psum = nullptr;
   int* d_cnt = nullptr;
   int* d_gcnt = nullptr;
