@@ -111,7 +111,9 @@ typedef struct {
   int n_modes;              /* M = n_phi/2 + 1                                   */
   int iterations_psi;       /* outer iterations of the Psi solve (max over modes) */
   int iterations_phi;       /* same for the Phi solve                            */
-  double rel_residual_psi;  /* sqrt(sum_m |r^m|^2 / sum_m |f^m|^2), volume-weighted */
+  double rel_residual_psi;  /* sqrt(sum_m |r^m|^2 / sum_m |f^m|^2), volume-weighted
+                               (sums of squares formed in FP32 with power-of-two
+                               exponents: about 1e-6 relative, any data scale) */
   double rel_residual_phi;
   double setup_ms;          /* psolve_create wall time (incl. DGF tables)        */
   int* cycles_psi;          /* per-mode V-cycles, Psi solve (may be NULL)        */
@@ -334,10 +336,23 @@ int psolve_set_schedule(psolve_t h, const psolve_schedule* s);
  * the solve with the handle's current schedule, which then stays installed. */
 int psolve_autotune(psolve_t h, const double* rho, double* phi, double tol,
                     psolve_schedule* out);
+/* Statistics of the handle's last solve (App. B: per-mode cycle counts and
+ * convergence status; the relative residuals of the Psi and Phi solves over
+ * all modes).  Synchronises the handle's stream first.  st is caller-owned;
+ * its array members, when non-NULL, receive M entries each.  Returns
+ * PSOLVE_OK, PSOLVE_ERR_ARG (null argument) or PSOLVE_ERR_CUDA. */
 int psolve_get_stats(psolve_t h, psolve_stats* st);
-/* Number of boundary points nb (the side of the DGF table) and modes M. */
+/* Number of boundary points nb (the side of the DGF table), modes M and
+ * multigrid levels of the handle; each output pointer may be NULL.  Host
+ * only.  Returns PSOLVE_OK or PSOLVE_ERR_ARG (null handle). */
 int psolve_get_sizes(psolve_t h, int* n_modes, int* n_boundary, int* n_levels);
+/* Message of the last failing call on the calling thread (a thread-local
+ * string owned by the library, valid until that thread's next failing
+ * call); "" when no call has failed. */
 const char* psolve_last_error(void);
+/* Frees the handle and every device buffer it owns, after synchronising its
+ * stream.  The caller's stream (psolve_set_stream) and buffers are not
+ * touched.  NULL is ignored. */
 void psolve_destroy(psolve_t h);
 
 /* ---- stage entry points (each runs one step of the solve on all modes) ---- */
