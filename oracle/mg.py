@@ -38,6 +38,12 @@ Readings fixed here (the paper leaves them open):
   real component, relative to that of the right-hand side (the defect of the
   zero initial guess), floored at ``floor``; a plane is done when both
   components meet it.
+* Cycle: the V-cycle of Sec. 3 (gamma = 1).  gamma > 1 is not the paper's:
+  a level whose coarser neighbour is not the coarsest level runs gamma
+  cycles per visit on its coarse equation, each starting from the previous
+  correction (gamma = 2: the textbook W-cycle; the coarsest level, solved
+  exactly, is visited once).  It exists to study where the low modes lose
+  convergence; no kernel runs it.
 """
 import numpy as np
 import scipy.sparse.linalg as spla
@@ -72,7 +78,7 @@ class Level:
 
 class Hierarchy:
     def __init__(self, plane, neumann_inner=False, min_cells=16, nu1=2, nu2=2, n_sor=2,
-                 max_coarse=1024):
+                 max_coarse=1024, gamma=1):
         planes = [plane]
         while True:
             nr, nt = planes[-1].n_r, planes[-1].n_t
@@ -80,7 +86,7 @@ class Hierarchy:
                 break
             planes.append(planes[-1].coarsen())
         self.levels = [Level(p, neumann_inner) for p in planes]
-        self.nu1, self.nu2, self.n_sor = nu1, nu2, n_sor
+        self.nu1, self.nu2, self.n_sor, self.gamma = nu1, nu2, n_sor, gamma
         self._omega = {}
         self._coarse = {}
 
@@ -201,7 +207,8 @@ class Hierarchy:
 
     # -- V-cycle ----------------------------------------------------------------
     def vcycle(self, lev, m, u, f):
-        """One V-cycle on L_m u = f at ``lev``; u with ghosts, modified in place."""
+        """One V-cycle (W-cycle for gamma = 2) on L_m u = f at ``lev``; u with
+        ghosts, modified in place."""
         p = self.levels[lev].plane
         if lev == len(self.levels) - 1:
             lu = self.coarse_lu(m)
@@ -214,7 +221,10 @@ class Hierarchy:
         fc = self.restrict(lev, r)
         C = self.levels[lev + 1].plane
         ec = np.zeros((C.n_r + 2, C.n_t + 2), dtype=u.dtype)
-        self.vcycle(lev + 1, m, ec, fc)
+        # the coarsest level is solved exactly: one visit is enough
+        visits = self.gamma if lev + 2 < len(self.levels) else 1
+        for _ in range(visits):
+            self.vcycle(lev + 1, m, ec, fc)
         u[1:-1, 1:-1] += self.prolong(lev, m, ec[1:-1, 1:-1])
         self.smooth(lev, m, u, f, self.nu2)
         return u

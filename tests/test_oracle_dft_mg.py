@@ -190,3 +190,46 @@ def test_wkb_omega_is_near_the_scanned_optimum(case, N):
     at_pred = np.log(sc["tol"]) / np.log(_sor_radius(A, w_pred))
     assert at_pred <= 1.8 * best
     assert abs(w_pred - grid[iters.argmin()]) <= 0.02
+
+
+def _three_level_log_sphere():
+    p = Plane.make(SPHERICAL, 64, 32, 8, LOG, 0.05, 20.0)
+    f = np.random.default_rng(3).standard_normal((64, 32)) + 0j
+    return p, f
+
+
+def test_repeated_coarse_cycles_reach_the_two_grid_cycle():
+    """With gamma repeats of the coarse cycle per visit, the correction of the
+    middle level converges to the exact solution of its coarse equation, so
+    one cycle with a large gamma equals a two-grid cycle whose coarse
+    equation is solved by a sparse direct solver (checks that the repeats
+    continue from the previous correction on the same restricted defect)."""
+    p, f = _three_level_log_sphere()
+    H = mg.Hierarchy(p, min_cells=8, max_coarse=128, nu1=2, nu2=1, gamma=40)
+    assert [(l.plane.n_r, l.plane.n_t) for l in H.levels] == [(64, 32), (32, 16), (16, 8)]
+    u = np.zeros((66, 34), dtype=complex)
+    H.vcycle(0, 0, u, f)
+    # the two-grid cycle, written out
+    v = np.zeros((66, 34), dtype=complex)
+    H.smooth(0, 0, v, f, 2)
+    fc = H.restrict(0, H.residual(0, 0, v, f))
+    C = H.levels[1].plane
+    lu = spla.splu(operator.matrix(C, 0).tocsc())
+    b = operator.to_vec(fc)
+    ec = lu.solve(np.ascontiguousarray(b.real)) + 1j * lu.solve(np.ascontiguousarray(b.imag))
+    v[1:-1, 1:-1] += H.prolong(0, 0, operator.from_vec(ec, C.n_r, C.n_t))
+    H.smooth(0, 0, v, f, 1)
+    assert np.abs(u - v).max() <= 1e-10 * np.abs(v).max()
+
+
+def test_w_cycle_converges_at_the_two_grid_rate_for_m0():
+    """On a stretched logarithmic grid (r_out / r_in = 400) the m = 0 V-cycle
+    is held back by its inexact coarse correction: the W-cycle (gamma = 2)
+    needs fewer cycles than the V-cycle and no more than the two-grid
+    method (gamma large).  Default gamma = 1 is the paper's V-cycle."""
+    p, f = _three_level_log_sphere()
+    counts = {g: mg.Hierarchy(p, min_cells=8, max_coarse=128, nu1=2, nu2=1, gamma=g).solve(0, f, 1e-8)[1]
+              for g in (1, 2, 40)}
+    assert mg.Hierarchy(p).gamma == 1
+    assert counts[2] < counts[1], counts
+    assert counts[2] <= counts[40], counts
